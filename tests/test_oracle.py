@@ -1,0 +1,148 @@
+"""Pins of the FP64 oracle (no GPU) against what the mathematics fixes:
+dense Cholesky solves, the A-DEF2 invariant Z^T r_k = 0, monotone energy
+error, reductions to textbook CG, finite termination with exact eigenvector
+deflation, one-iteration convergence with the exact preconditioner, and the
+equivalence of A-DEF2 (started by Algorithm 2) with Nicolaides' deflated CG
+(Section 3.2).  A dropped term, a sign flip in lambda - mu, a transposed
+triangular solve or a wrong coarse column would break at least one of them."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+import xfem_inputs as X
+from oracle import adef2 as O
+from xfem_inputs.cracks import PlanarEdgeCrack, WarpedPennyCrack
+
+
+@pytest.fixture(scope="module")
+def cube8():
+    P = X.make("cube8_edge")
+    K, M, C = O.setup(P)
+    return P, K, M, C
+
+
+def small_problems():
+    return [X.build_problem(3, [PlanarEdgeCrack(0.5, 0.45, 0.2)], 1),
+            X.build_problem(4, [PlanarEdgeCrack(0.43, 0.6, 0.15)], 2),
+            X.build_problem(4, [WarpedPennyCrack((0.5, 0.5, 0.55), 0.3, 0.02, 0.1)], 2)]
+
+
+@pytest.mark.parametrize("idx", [0, 1, 2])
+def test_converges_to_dense_cholesky_solution(idx):
+    P = small_problems()[idx]
+    K, M, C = O.setup(P)
+    res = O.adef2_pcg(K, P.f, M, C, tol=1e-14)
+    Kd = K.toarray()
+    u = sla.cho_solve(sla.cho_factor(Kd), P.f)
+    std = np.zeros(P.n, bool)
+    for I in range(P.n_nodes):
+        std[P.dof_ptr[I]:P.dof_ptr[I] + 3] = True
+    assert res.converged
+    assert np.linalg.norm(res.u - u) <= 1e-9 * np.linalg.norm(u)
+    assert np.linalg.norm((res.u - u)[std]) <= 1e-11 * np.linalg.norm(u[std])
+
+
+def test_deflated_residuals_are_orthogonal_to_Z(cube8):
+    P, K, M, C = cube8
+    res = O.adef2_pcg(K, P.f, M, C, tol=1e-10, record=True)
+    zn = sp.linalg.norm(C.Z)
+    assert max(res.ztr) <= 1e-10 * zn * np.linalg.norm(P.f)
+
+
+def test_energy_error_decreases_monotonically(cube8):
+    P, K, M, C = cube8
+    Kd = K.toarray()
+    u_star = sla.cho_solve(sla.cho_factor(Kd), P.f)
+    res = O.adef2_pcg(K, P.f, M, C, tol=1e-9, max_iterates=200)
+    errs = [np.sqrt((u_star - u) @ (Kd @ (u_star - u))) for u in res.iterates]
+    assert len(errs) > 20
+    assert all(b <= a * (1 + 1e-9) for a, b in zip(errs, errs[1:]))
+
+
+def _textbook_cg(A, b, tol, maxit):
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = r @ r
+    xs = []
+    for _ in range(maxit):
+        Ap = A @ p
+        a = rr / (p @ Ap)
+        x = x + a * p
+        r = r - a * Ap
+        xs.append(x.copy())
+        if np.linalg.norm(r) <= tol * np.linalg.norm(b):
+            break
+        rr2 = r @ r
+        p = r + rr2 / rr * p
+        rr = rr2
+    return xs
+
+
+def test_no_deflation_identity_preconditioner_is_textbook_cg():
+    P = X.build_problem(5, [], 1)                # uncracked: plain CG converges
+    K = O.stiffness_csr(P)
+    C0 = O.Coarse(K, sp.csc_matrix((P.n, 0)))
+    res = O.adef2_pcg(K, P.f, O.Identity(), C0, tol=1e-10, max_iterates=5000)
+    ref = _textbook_cg(K, P.f, 1e-10, 5000)
+    assert res.converged
+    assert res.iterations == len(ref)
+    for a, b in zip(res.iterates[1:], ref):
+        assert np.linalg.norm(a - b) <= 1e-8 * np.linalg.norm(b)
+
+
+def test_exact_preconditioner_converges_in_one_iteration(cube8):
+    P, K, _, C = cube8
+    M1 = O.BlockJacobi(K, [0, P.n])              # one block holding all of K
+    res = O.adef2_pcg(K, P.f, M1, C, tol=1e-8)
+    assert res.iterations <= 1
+
+
+def test_eigenvector_deflation_terminates_finitely():
+    P = small_problems()[1]
+    K, _, _ = O.setup(P)
+    w, V = np.linalg.eigh(K.toarray())
+    keep = 3                                    # leave the 3 largest eigenvalues
+    Z = sp.csc_matrix(V[:, :-keep])
+    C = O.Coarse(K, Z)
+    res = O.adef2_pcg(K, P.f, O.Identity(), C, tol=1e-10)
+    assert res.iterations <= keep
+
+
+def test_adef2_matches_nicolaides_deflated_cg(cube8):
+    P, K, M, C = cube8
+    a = O.adef2_pcg(K, P.f, M, C, tol=1e-8, max_iterates=12)
+    _, _, b = O.nicolaides_dcg(K, P.f, M, C, tol=1e-8, max_iterates=12)
+    for ua, ub in zip(a.iterates, b):
+        assert np.linalg.norm(ua - ub) <= 1e-9 * np.linalg.norm(ub)
+
+
+def test_global_and_centred_rigid_coordinates_give_same_iterates():
+    P = X.build_problem(8, [PlanarEdgeCrack(0.5, 0.45, 0.15)], 2)
+    Pg = X.build_problem(8, [PlanarEdgeCrack(0.5, 0.45, 0.15)], 2, centred_modes=False)
+    a = O.solve(P, tol=1e-8)
+    b = O.solve(Pg, tol=1e-8)
+    assert abs(a.iterations - b.iterations) <= 1
+    assert np.linalg.norm(a.u - b.u) <= 1e-7 * np.linalg.norm(b.u)
+
+
+def test_paper_trends_on_cube8(cube8):
+    P, K, M, C = cube8
+    bj_enr = O.adef2_pcg(K, P.f, M, C).iterations
+    K0, M0, C0 = O.setup(P, enriched_modes=False)
+    bj_std = O.adef2_pcg(K0, P.f, M0, C0).iterations
+    Mj = O.BlockJacobi(K, np.arange(P.n + 1))  # point Jacobi: blocks of one dof
+    j_enr = O.adef2_pcg(K, P.f, Mj, C).iterations
+    assert bj_enr <= bj_std                     # enriched deflation never hurts
+    assert bj_enr < j_enr                       # block Jacobi beats point Jacobi
+
+
+def test_indefinite_block_is_rejected():
+    P = X.make("cube8_edge")
+    K = O.stiffness_csr(P).tolil()
+    d = int(P.dof_ptr[5])
+    K[d, d] = -1.0
+    with pytest.raises(O.NotSPD) as ei:
+        O.BlockJacobi(K.tocsr(), P.dof_ptr)
+    assert ei.value.args[0] == 5
