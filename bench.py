@@ -1,0 +1,325 @@
+"""Benchmark: time to ||f - K u|| / ||f|| <= 1e-8 on the 48^3 two-crack cube.
+
+Default arm: the GPU library.  One step = one full solve (all steps of the
+hot path: Algorithm 2 start, A-DEF2 PCG iterations, FP64 refinement for the
+mixed path) with the load vector already resident in HBM; L2 is flushed
+(a 256 MiB write) before every timed step, outside the step's events.
+Reported: mixed (FP32 inner / FP64 refinement) solve time as the value, the
+plain FP64 solve time beside it, iterations, SpMV bandwidth against the
+measured HBM copy bandwidth, the FP64 CPU oracle on a bounded sample, and an
+end-to-end figure through the host-memory entry point.
+
+--impl reference: the CPU oracle as the reference arm (same metric and
+workload, each step a bounded sample of oracle iterations scaled to the
+oracle's own iteration count).
+"""
+import argparse
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import hashlib
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to ‖r‖/‖f‖≤1e-8: mixed vs FP64 DPCG on GB300; SpMV GB/s vs HBM peak"
+WORKLOAD = "cube48_two_cracks"
+TOL = 1e-8
+FALLBACK_HBM = 6800.0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM, "fallback"
+
+
+def profiled_traffic(kernel_file, summary):
+    """Per-launch DRAM bytes of the FP32 SpMV from the committed ncu summary,
+    or None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", summary)
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]{12})", txt)
+    if not m or not h:
+        return None
+    src = open(os.path.join(ROOT, "paper_2111_09294_gb300", "csrc", kernel_file), "rb").read()
+    if hashlib.sha256(src).hexdigest()[:12] != h.group(1):
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, v, device=None):
+    if pg is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(P, iterations_full, sample_iters):
+    """Time the oracle's setup-free solve on a bounded number of iterations and
+    scale to the full iteration count."""
+    from oracle import adef2 as O
+    K, M, C = O.setup(P)
+    t0 = time.perf_counter()
+    r = O.adef2_pcg(K, P.f, M, C, tol=TOL, maxit=sample_iters)
+    dt = time.perf_counter() - t0
+    per_it = dt / max(r.iterations, 1)
+    return per_it * iterations_full * 1e3, per_it, r.iterations, (K, M, C)
+
+
+def run_reference(args):
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return
+    import xfem_inputs as X
+    from oracle import adef2 as O
+    P = X.make(args.workload)
+    K, M, C = O.setup(P)
+    full = O.adef2_pcg(K, P.f, M, C, tol=TOL)
+    its = full.iterations
+    times = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = O.adef2_pcg(K, P.f, M, C, tol=TOL, maxit=args.sample_iters)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt / r.iterations * its * 1e3)
+    value = float(np.mean(times))
+    sample = (f"{args.sample_iters} oracle iterations per step, scaled to the oracle's "
+              f"{its} iterations to 1e-8 (setup excluded)")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": value,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": config_dict(P, C.k),
+           "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0},
+           "oracle_iterations": its}
+    print(json.dumps(out))
+
+
+def config_dict(P, k):
+    return {"workload": f"{WORKLOAD}: 48^3 hexes, penny r=0.2 + edge crack depth 0.25, "
+                        f"warped, r_e=0.05, 8^3 boxes",
+            "n_dofs": int(P.n), "n_nodes": int(P.n_nodes), "enriched_dofs":
+            int(P.n_heaviside_dofs + P.n_tip_dofs), "coarse_k": int(k), "tol": TOL,
+            "l2": "flushed (256 MiB write) before every timed step"}
+
+
+def run_ours(args):
+    import torch
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import xfem_inputs as X
+    from paper_2111_09294_gb300 import Solver
+    P = X.make(args.workload)
+    stream = torch.cuda.current_stream(dev)
+    mixed = Solver.from_problem(P, precision="mixed", time_spmv=True, inner_tol=args.inner_tol)
+    fp64 = Solver.from_problem(P, precision="fp64", time_spmv=True)
+    f = torch.tensor(P.f, device=dev)
+    u = torch.empty_like(f)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(solver, steps, warmup, collect):
+        for _ in range(warmup):
+            solver.solve(f, tol=TOL, out=u)
+        ms, infos = [], []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, info = solver.solve(f, tol=TOL, out=u)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            infos.append(info)
+        return ms, infos
+
+    torch.cuda.synchronize()
+    barrier(pg)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_mixed, inf_mixed = timed(mixed, args.steps, args.warmup, True)
+    torch.cuda.synchronize()
+    barrier(pg)
+    clk = clocks.stop()
+    ms_fp64, inf_fp64 = timed(fp64, args.steps, args.warmup, True)
+    torch.cuda.synchronize()
+    barrier(pg)
+    t_mixed = max_over_ranks(pg, float(np.mean(ms_mixed)), dev)
+    t_fp64 = max_over_ranks(pg, float(np.mean(ms_fp64)), dev)
+    res_true = max(i["rel_res_true"] for i in inf_mixed)
+    assert res_true <= TOL, res_true
+
+    # end to end through the host-memory entry point (pinned buffers)
+    fh = torch.tensor(P.f, dtype=torch.float64).pin_memory()
+    uh = torch.empty(P.n, dtype=torch.float64).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        mixed.solve_host(fh, uh, tol=TOL)
+    e2e = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mixed.solve_host(fh, uh, tol=TOL)
+        e2e.append((time.perf_counter() - t0) * 1e3)
+    t_e2e = max_over_ranks(pg, float(np.mean(e2e)), dev)
+
+    if rank != 0:
+        return
+    info = mixed.info
+    n_sp = sum(i["n_spmv_timed"] for i in inf_mixed)
+    t_sp = sum(i["t_spmv_ms"] for i in inf_mixed)
+    spmv_ms = t_sp / max(n_sp, 1)
+    achieved = info["spmv_bytes_fp32"] / (spmv_ms * 1e-3) / 1e9
+    n64 = sum(i["n_spmv_timed"] for i in inf_fp64)
+    spmv64_ms = sum(i["t_spmv_ms"] for i in inf_fp64) / max(n64, 1)
+    achieved64 = info["spmv_bytes_fp64"] / (spmv64_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    traffic = profiled_traffic("spmv.cu", f"spmv_fp32_{WORKLOAD}.md")
+    its_fp64 = inf_fp64[-1]["iterations"]
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        est_ms, per_it, n_s, _ = oracle_sample(P, its_fp64, args.sample_iters)
+        cpu = {"value": est_ms, "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": f"{n_s} FP64 oracle iterations ({per_it * 1e3:.1f} ms each, 1 thread) "
+                         f"scaled to {its_fp64} iterations to 1e-8, setup excluded"}
+    out = {
+        "metric": METRIC, "value": t_mixed, "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_mixed,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 inner / f64 refinement", "data": "synthetic",
+        "config": config_dict(P, info["k"]),
+        "fp64_ms": t_fp64, "speedup_mixed_vs_fp64": t_fp64 / t_mixed,
+        "iterations_mixed": inf_mixed[-1]["iterations"],
+        "outer_cycles_mixed": inf_mixed[-1]["outer_cycles"], "iterations_fp64": its_fp64,
+        "rel_res_true_mixed": res_true, "rel_res_true_fp64": inf_fp64[-1]["rel_res_true"],
+        "setup_ms": info["t_setup_ms"],
+        "spmv_fp32_gbs": achieved, "spmv_fp64_gbs": achieved64,
+        "roofline": {"bound": "hbm", "kernel": "k_spmv<float> (inner FP32 SpMV)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_kind,
+                     "traffic": traffic, "algorithmic_bytes": info["spmv_bytes_fp32"],
+                     "avg_launch_ms": spmv_ms},
+        "e2e": {"value": t_e2e, "unit": "ms", "h2d_bytes_per_step": 8 * P.n,
+                "d2h_bytes_per_step": 8 * P.n},
+        "gpu_launches": int(sum(i["n_launches"] for i in inf_mixed)),
+        "clocks": clk,
+    }
+    if cpu is not None:
+        out["cpu_baseline"] = cpu
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--inner-tol", type=float, default=1e-5)
+    ap.add_argument("--sample-iters", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

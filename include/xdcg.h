@@ -1,0 +1,167 @@
+/*
+ * xdcg -- adapted deflated conjugate gradients for XFEM/GFEM crack systems
+ * on one GB300 GPU (sm_103a).
+ *
+ * Solves K u = f, K symmetric positive definite (Section 2.4, Eq.
+ * linear_system), by conjugate gradients (Algorithm 1) preconditioned by
+ * the multiplicative A-DEF2 combination (Section 3.2) of
+ *   - subdomain deflation: per box subdomain the six rigid-body modes of
+ *     Eq. dcg_deflation_space, plus, in boxes holding jump-enriched nodes,
+ *     the six enriched modes of Eqs. dcg_deflation_space_enr_std and
+ *     dcg_deflation_space_enr_enr (Section 3.3), and
+ *   - block Jacobi over node blocks that include the enriched dofs
+ *     (Section 3.4, Eqs. block_jacobi, block_jacobi_enr),
+ * started from the initial solution of Algorithm 2 (with u_-1 = 0) and
+ * stopped when ||r_i||_2 <= tol ||f||_2 (relative tolerance, Section 4).
+ *
+ * Conventions shared by every entry point:
+ *   - All functions return an xdcg_status; nothing is thrown across the ABI.
+ *   - "device" pointers are CUDA global-memory addresses on the device that
+ *     is current when xdcg_setup is called; "host" pointers are ordinary
+ *     (pageable or pinned) host memory.
+ *   - A context is bound to the CUDA stream given at set-up; every call on
+ *     it is ordered on that stream.  A context is not thread-safe.
+ *   - dof layout: node I owns the contiguous dofs [dof_ptr[I], dof_ptr[I+1]),
+ *     ordered [3 standard | 3 jump] or [3 standard | 12 branch]; so every
+ *     node block has b_I in {3, 6, 15} dofs.
+ */
+#ifndef XDCG_H
+#define XDCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct xdcg_ctx xdcg_ctx;   /* opaque; owns all of its device memory */
+
+typedef enum {
+    XDCG_OK = 0,
+    XDCG_INVALID_ARG = 1,      /* bad pointer, size, index, pattern or option */
+    XDCG_NOT_SPD_BLOCK = 2,    /* a node block failed its Cholesky factorisation;
+                                  result.bad_index names the node */
+    XDCG_COARSE_NOT_SPD = 3,   /* E = Z^T K Z failed its factorisation;
+                                  result.bad_index names the coarse pivot */
+    XDCG_BREAKDOWN = 4,        /* p^T K p <= 0 or not finite during the iteration */
+    XDCG_NO_CONVERGENCE = 5,   /* max_iter reached; u holds the last iterate */
+    XDCG_CUDA_ERROR = 6,       /* a CUDA runtime call failed */
+    XDCG_OOM = 7               /* device allocation failed */
+} xdcg_status;
+
+enum { XDCG_HOST = 0, XDCG_DEVICE = 1 };       /* memory space of input arrays */
+enum { XDCG_FP64 = 0, XDCG_MIXED = 1 };        /* solve precision */
+
+/* Stiffness matrix K in node-blocked CSR, full symmetric storage, FP64.
+ * Row I lists the nodes J coupled to I (sharing an element), sorted, with
+ * the diagonal J = I present; block (I, J) is b_I x b_J, row-major, at
+ * val[val_ptr[p] .. val_ptr[p+1]).  The pattern and the values must be
+ * symmetric (checked at set-up to 1e-12 relative).  Read-only; copied at
+ * set-up, so the caller may free it when xdcg_setup returns. */
+typedef struct {
+    int32_t n_nodes;
+    const int32_t *dof_ptr;    /* [n_nodes + 1], dof_ptr[0] = 0 */
+    const int32_t *row_ptr;    /* [n_nodes + 1] */
+    const int32_t *col;        /* [row_ptr[n_nodes]] */
+    const int64_t *val_ptr;    /* [row_ptr[n_nodes] + 1] */
+    const double *val;         /* [val_ptr[row_ptr[n_nodes]]] */
+    int32_t mem;               /* XDCG_HOST or XDCG_DEVICE, for all six arrays */
+} xdcg_matrix;
+
+/* Geometric description of the deflation space Z (Section 3.3).  The
+ * library builds Z on the device from it: for node I in box s = sub[I] and
+ * x = coords[I] - centre[s], the rigid block R(x) of Eq. dcg_deflation_space
+ * on I's standard dofs (columns 6 s' .. 6 s' + 5 of box s); if
+ * enriched_modes is set and the jump-enriched nodes (b_I = 6) of box s are
+ * not all on one line, six more columns holding hsign[I] * R(x) on the
+ * standard dofs (Eq. dcg_deflation_space_enr_std), R(x) on the jump dofs
+ * (Eq. dcg_deflation_space_enr_enr) and 0 on branch dofs.  hsign[I] is
+ * H(x_I) = +-1, the side of the box's crack on which node I lies.  The
+ * resulting Z must have full column rank (checked through E). */
+typedef struct {
+    int32_t n_sub;
+    const int32_t *sub_of_node;  /* [n_nodes], values in [0, n_sub) */
+    const double *coords;        /* [3 n_nodes], x y z per node */
+    const int8_t *hsign;         /* [n_nodes], +1 or -1 */
+    const double *centre;        /* [3 n_sub] */
+    int32_t enriched_modes;      /* 0: rigid modes only; 1: add enriched modes */
+    int32_t mem;                 /* XDCG_HOST or XDCG_DEVICE, for all four arrays */
+} xdcg_deflation;
+
+typedef struct {
+    double tol;              /* relative residual target, default 1e-8 */
+    int32_t max_iter;        /* total CG iterations (inner ones for MIXED), default 10000 */
+    int32_t precision;       /* XDCG_FP64 (default) or XDCG_MIXED */
+    double inner_tol;        /* MIXED: inner FP32 solve stops at inner_tol * ||r||, default 1e-5 */
+    int32_t max_outer;       /* MIXED: refinement cycles, default 30 */
+    int32_t time_spmv;       /* 1: bracket every SpMV launch by CUDA events */
+} xdcg_options;
+
+typedef struct {
+    int32_t iterations;          /* loop bodies run (products K p), summed over cycles */
+    int32_t outer_cycles;        /* MIXED: refinement cycles; FP64: 1 */
+    double rel_res_recursive;    /* last recursive ||r|| / ||f|| */
+    double rel_res_true;         /* ||f - K u|| / ||f|| in FP64 after the solve */
+    double t_solve_ms;           /* CUDA-event time of the solve on the context stream */
+    int32_t bad_index;           /* failing node or coarse pivot, else -1 */
+    int32_t n_spmv_timed;        /* SpMV launches timed (time_spmv) */
+    double t_spmv_ms;            /* their summed CUDA-event time */
+    int64_t n_launches;          /* kernels launched by this call */
+} xdcg_result;
+
+typedef struct {
+    int64_t n;                   /* dofs */
+    int32_t n_nodes;
+    int32_t k;                   /* coarse dimension */
+    int64_t nnz;                 /* scalar nonzeros of K */
+    int64_t nnzb3;               /* 3x3 blocks of the chunked SpMV layout */
+    int64_t spmv_bytes_fp64;     /* algorithmic bytes of one FP64 SpMV */
+    int64_t spmv_bytes_fp32;     /* algorithmic bytes of one FP32 SpMV */
+    int64_t iter_bytes_fp64;     /* algorithmic bytes of one FP64 iteration */
+    int64_t iter_bytes_fp32;     /* algorithmic bytes of one FP32 inner iteration */
+    double t_setup_ms;           /* wall time of xdcg_setup */
+} xdcg_info_t;
+
+/* Fill *opt with the defaults listed above. */
+xdcg_status xdcg_default_options(xdcg_options *opt);
+
+/* Validate K and the deflation description, copy them to the device, lay K
+ * out for the SpMV (FP64 and, for MIXED, FP32 copies), factor the node
+ * blocks (FP64 Cholesky), build Z, W = K Z and E = Z^T K Z, and invert E in
+ * FP64.  stream: a cudaStream_t (NULL = legacy default stream).  blocks must
+ * be NULL (one block per node).  On error *out is NULL. */
+xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflation *Z,
+                       const void *blocks, const xdcg_options *opt, void *stream);
+
+/* Solve K u = f with the options given at set-up, tol overriding opt.tol
+ * when > 0.  f, u: caller-owned device arrays of n doubles (may not alias).
+ * res may be NULL.  On NO_CONVERGENCE u holds the last iterate. */
+xdcg_status xdcg_solve(xdcg_ctx *ctx, const double *f, double *u, double tol, xdcg_result *res);
+
+/* As xdcg_solve with host arrays: copies f to the device, solves, copies u
+ * back, all on the context stream; returns after u is on the host. */
+xdcg_status xdcg_solve_host(xdcg_ctx *ctx, const double *f_host, double *u_host, double tol,
+                            xdcg_result *res);
+
+xdcg_status xdcg_get_info(const xdcg_ctx *ctx, xdcg_info_t *info);
+
+/* y = K x in the given precision (XDCG_FP64: double arrays; XDCG_MIXED:
+ * float arrays, FP32 values and accumulation).  x, y: device, length n.
+ * If xty is not NULL it receives x^T y (FP64 reduction) on the host. */
+xdcg_status xdcg_spmv(xdcg_ctx *ctx, int32_t precision, const void *x, void *y, double *xty);
+
+/* z = A-DEF2 preconditioner applied to r (Algorithm 3, one merged coarse
+ * solve), FP64.  r, z: device, length n. */
+xdcg_status xdcg_precond(xdcg_ctx *ctx, const double *r, double *z);
+
+/* Copy the coarse matrix E (k x k, row-major, FP64) to host memory E_host. */
+xdcg_status xdcg_coarse_matrix(xdcg_ctx *ctx, double *E_host);
+
+xdcg_status xdcg_destroy(xdcg_ctx *ctx);
+
+const char *xdcg_status_string(xdcg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XDCG_H */

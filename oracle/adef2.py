@@ -42,17 +42,24 @@ class Breakdown(Exception):
 
 def stiffness_csr(P):
     """K as a scipy CSR matrix from the node-blocked storage of Problem P."""
+    dof = np.asarray(P.dof_ptr, dtype=np.int64)
+    rowp = np.asarray(P.row_ptr, dtype=np.int64)
+    col = np.asarray(P.col, dtype=np.int64)
+    vptr = np.asarray(P.val_ptr, dtype=np.int64)
+    bsz = np.diff(dof)
+    I = np.repeat(np.arange(P.n_nodes), np.diff(rowp))
+    bI, bJ = bsz[I], bsz[col]
     rows, cols, vals = [], [], []
-    for I in range(P.n_nodes):
-        r0, r1 = int(P.dof_ptr[I]), int(P.dof_ptr[I + 1])
-        for p in range(P.row_ptr[I], P.row_ptr[I + 1]):
-            J = int(P.col[p])
-            c0, c1 = int(P.dof_ptr[J]), int(P.dof_ptr[J + 1])
-            blk = P.val[P.val_ptr[p]:P.val_ptr[p + 1]].reshape(r1 - r0, c1 - c0)
-            rr, cc = np.meshgrid(np.arange(r0, r1), np.arange(c0, c1), indexing="ij")
-            rows.append(rr.ravel())
-            cols.append(cc.ravel())
-            vals.append(blk.ravel())
+    for ri in np.unique(bI):
+        for cj in np.unique(bJ):
+            sel = np.nonzero((bI == ri) & (bJ == cj))[0]
+            if sel.size == 0:
+                continue
+            a = np.arange(ri)[:, None].repeat(cj, 1).ravel()     # row within block
+            b = np.arange(cj)[None, :].repeat(ri, 0).ravel()     # column within block
+            rows.append((dof[I[sel]][:, None] + a[None, :]).ravel())
+            cols.append((dof[col[sel]][:, None] + b[None, :]).ravel())
+            vals.append(P.val[(vptr[sel][:, None] + np.arange(ri * cj)[None, :]).ravel()])
     return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                          shape=(P.n, P.n))
 
@@ -99,27 +106,31 @@ def deflation_basis(P, enriched=True):
     m_s = np.where(has_jump, 12, 6)
     col0 = np.zeros(P.n_sub + 1, dtype=np.int64)
     col0[1:] = np.cumsum(m_s)
+    dof = np.asarray(P.dof_ptr, dtype=np.int64)
+    X = np.asarray(P.coords) - np.asarray(P.centres)[sub]
+    zero, one = np.zeros(P.n_nodes), np.ones(P.n_nodes)
+    # rigid block of Eq. dcg_deflation_space, entry [a][b] for every node
+    R = np.array([[one, zero, zero, zero, X[:, 2], -X[:, 1]],
+                  [zero, one, zero, -X[:, 2], zero, X[:, 0]],
+                  [zero, zero, one, X[:, 1], -X[:, 0], zero]])      # (3, 6, N)
+    c0 = col0[sub]
+    H = np.asarray(P.hsign, dtype=np.float64)
+    enr = has_jump[sub]
+    jump = enr & (kind == 1)
     rows, cols, vals = [], [], []
-    for I in range(P.n_nodes):
-        s = int(sub[I])
-        d0 = int(P.dof_ptr[I])
-        R = rigid_block(P.coords[I] - P.centres[s])
-        for a in range(3):
-            for b in range(6):
-                if R[a, b] != 0.0:
-                    rows.append(d0 + a); cols.append(col0[s] + b); vals.append(R[a, b])
-        if has_jump[s]:
-            H = float(P.hsign[I])
-            for a in range(3):          # Eq. dcg_deflation_space_enr_std on standard dofs
-                for b in range(6):
-                    if R[a, b] != 0.0:
-                        rows.append(d0 + a); cols.append(col0[s] + 6 + b); vals.append(H * R[a, b])
-            if kind[I] == 1:            # Eq. dcg_deflation_space_enr_enr on jump dofs
-                for a in range(3):
-                    for b in range(6):
-                        if R[a, b] != 0.0:
-                            rows.append(d0 + 3 + a); cols.append(col0[s] + 6 + b)
-                            vals.append(R[a, b])
+    for a in range(3):
+        for b in range(6):
+            v = R[a, b]
+            rows.append(dof[:-1] + a); cols.append(c0 + b); vals.append(v)
+            # Eq. dcg_deflation_space_enr_std on standard dofs of enriched boxes
+            rows.append((dof[:-1] + a)[enr]); cols.append((c0 + 6 + b)[enr])
+            vals.append((H * v)[enr])
+            # Eq. dcg_deflation_space_enr_enr on the jump dofs
+            rows.append((dof[:-1] + 3 + a)[jump]); cols.append((c0 + 6 + b)[jump])
+            vals.append(v[jump])
+    rows, cols, vals = np.concatenate(rows), np.concatenate(cols), np.concatenate(vals)
+    nz = vals != 0.0
+    rows, cols, vals = rows[nz], cols[nz], vals[nz]
     Z = sp.csc_matrix((np.array(vals), (np.array(rows), np.array(cols))),
                       shape=(P.n, int(col0[-1])))
     return Z, col0

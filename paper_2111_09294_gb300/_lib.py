@@ -1,0 +1,105 @@
+"""ctypes declarations of the xdcg C ABI (include/xdcg.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA
+library.  Importing the library fails loudly when it has not been built.
+"""
+import ctypes
+import os
+
+from ctypes import POINTER, c_char_p, c_double, c_int, c_int32, c_int64, c_void_p
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libxdcg.so")
+
+XDCG_HOST, XDCG_DEVICE = 0, 1
+XDCG_FP64, XDCG_MIXED = 0, 1
+
+STATUS = {0: "XDCG_OK", 1: "XDCG_INVALID_ARG", 2: "XDCG_NOT_SPD_BLOCK",
+          3: "XDCG_COARSE_NOT_SPD", 4: "XDCG_BREAKDOWN", 5: "XDCG_NO_CONVERGENCE",
+          6: "XDCG_CUDA_ERROR", 7: "XDCG_OOM"}
+
+# every function the header declares
+EXPORTS = ["xdcg_default_options", "xdcg_setup", "xdcg_solve", "xdcg_solve_host",
+           "xdcg_get_info", "xdcg_spmv", "xdcg_precond", "xdcg_coarse_matrix",
+           "xdcg_destroy", "xdcg_status_string"]
+
+
+class Matrix(ctypes.Structure):
+    _fields_ = [("n_nodes", c_int32), ("dof_ptr", c_void_p), ("row_ptr", c_void_p),
+                ("col", c_void_p), ("val_ptr", c_void_p), ("val", c_void_p), ("mem", c_int32)]
+
+
+class Deflation(ctypes.Structure):
+    _fields_ = [("n_sub", c_int32), ("sub_of_node", c_void_p), ("coords", c_void_p),
+                ("hsign", c_void_p), ("centre", c_void_p), ("enriched_modes", c_int32),
+                ("mem", c_int32)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("tol", c_double), ("max_iter", c_int32), ("precision", c_int32),
+                ("inner_tol", c_double), ("max_outer", c_int32), ("time_spmv", c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("iterations", c_int32), ("outer_cycles", c_int32),
+                ("rel_res_recursive", c_double), ("rel_res_true", c_double),
+                ("t_solve_ms", c_double), ("bad_index", c_int32), ("n_spmv_timed", c_int32),
+                ("t_spmv_ms", c_double), ("n_launches", c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", c_int64), ("n_nodes", c_int32), ("k", c_int32), ("nnz", c_int64),
+                ("nnzb3", c_int64), ("spmv_bytes_fp64", c_int64), ("spmv_bytes_fp32", c_int64),
+                ("iter_bytes_fp64", c_int64), ("iter_bytes_fp32", c_int64),
+                ("t_setup_ms", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load():
+    """Load libxdcg.so (built by paper_2111_09294_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    lib.xdcg_default_options.argtypes = [POINTER(Options)]
+    lib.xdcg_setup.argtypes = [POINTER(c_void_p), POINTER(Matrix), POINTER(Deflation), c_void_p,
+                               POINTER(Options), c_void_p]
+    lib.xdcg_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_double, POINTER(Result)]
+    lib.xdcg_solve_host.argtypes = [c_void_p, c_void_p, c_void_p, c_double, POINTER(Result)]
+    lib.xdcg_get_info.argtypes = [c_void_p, POINTER(Info)]
+    lib.xdcg_spmv.argtypes = [c_void_p, c_int32, c_void_p, c_void_p, POINTER(c_double)]
+    lib.xdcg_precond.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.xdcg_coarse_matrix.argtypes = [c_void_p, c_void_p]
+    lib.xdcg_destroy.argtypes = [c_void_p]
+    lib.xdcg_status_string.argtypes = [c_int]
+    lib.xdcg_status_string.restype = c_char_p
+    for name in EXPORTS:
+        if name != "xdcg_status_string":
+            getattr(lib, name).restype = c_int
+    _lib = lib
+    return lib
+
+
+class XdcgError(RuntimeError):
+    def __init__(self, status, what, bad_index=-1):
+        self.status = status
+        self.bad_index = bad_index
+        msg = load().xdcg_status_string(status).decode()
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({msg})"
+                         + (f", index {bad_index}" if bad_index >= 0 else ""))
+
+
+def check(status, what, bad_index=-1):
+    if status != 0:
+        raise XdcgError(status, what, bad_index)

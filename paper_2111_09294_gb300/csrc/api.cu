@@ -1,0 +1,953 @@
+// Host side of the xdcg C ABI: input validation, layout planning (integer
+// structure only; every floating-point operation runs in a kernel), set-up
+// kernels, and the solve drivers for the FP64 and the FP32-inner / FP64-
+// refinement paths.
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace xdcg;
+
+namespace {
+
+constexpr int kBatch = 8;              // iterations enqueued between convergence polls
+constexpr int kMaxGrid = 1 << 16;      // partial-sum slots per reduction value
+
+struct Level64 {
+    SpmvDev<double> A;
+    NodeDev<double> N;
+    BoxDev<double> B;
+};
+struct Level32 {
+    SpmvDev<float> A;
+    NodeDev<float> N;
+    BoxDev<float> B;
+};
+
+}  // namespace
+
+struct xdcg_ctx {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    xdcg_options opt{};
+    xdcg_info_t info{};
+    bool mixed = false;
+
+    int nNodes = 0, nBox = 0, k = 0;
+    long long n = 0;
+    std::vector<void *> allocs;
+
+    Level64 L64{};
+    Level32 L32{};
+    double *Einv = nullptr;
+    double *E = nullptr;                      // E = Z^T K Z as assembled (diagnostics)
+    std::vector<void *> temps;                // set-up temporaries
+
+    // FP64 work vectors
+    double *u64 = nullptr, *r64 = nullptr, *p64 = nullptr, *q64 = nullptr, *y64 = nullptr;
+    double *f64 = nullptr, *uh64 = nullptr;   // host-path staging
+    // FP32 work vectors (inner solve)
+    float *f32 = nullptr, *u32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr,
+          *y32 = nullptr;
+    double *g = nullptr, *zr = nullptr, *nu = nullptr;
+    double *partials = nullptr;
+    Scalars *sc = nullptr, *sc32 = nullptr, *aux = nullptr;
+    Scalars *h_sc = nullptr;   // pinned
+    int *h_done = nullptr;     // pinned, 2 slots
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, evb[2] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> evS, evE;
+    long long launches = 0;
+};
+
+namespace {
+
+#define CK(call)                                      \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return XDCG_CUDA_ERROR; \
+    } while (0)
+
+template <typename T>
+T *dalloc(xdcg_ctx *c, size_t count) {
+    void *p = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) return nullptr;
+    c->allocs.push_back(p);
+    return (T *)p;
+}
+
+template <typename T>
+T *dalloc_tmp(xdcg_ctx *c, size_t count) {
+    void *p = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) return nullptr;
+    c->temps.push_back(p);
+    return (T *)p;
+}
+
+template <typename T>
+T *upload_tmp(xdcg_ctx *c, const std::vector<T> &v) {
+    T *d = dalloc_tmp<T>(c, v.size());
+    if (!d) return nullptr;
+    if (!v.empty() && cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice,
+                                      c->st) != cudaSuccess)
+        return nullptr;
+    return d;
+}
+
+template <typename T>
+T *upload(xdcg_ctx *c, const std::vector<T> &v) {
+    T *d = dalloc<T>(c, v.size());
+    if (!d) return nullptr;
+    if (!v.empty() && cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice,
+                                      c->st) != cudaSuccess)
+        return nullptr;
+    return d;
+}
+
+template <typename T>
+bool fetch(std::vector<T> &dst, const T *src, size_t count, int mem) {
+    dst.resize(count);
+    if (count == 0) return true;
+    if (!src) return false;
+    if (mem == XDCG_DEVICE)
+        return cudaMemcpy(dst.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost) == cudaSuccess;
+    std::memcpy(dst.data(), src, count * sizeof(T));
+    return true;
+}
+
+// Every point of x (p x 3) on one line?  (true for fewer than 3 points)
+bool points_collinear(const std::vector<double> &x) {
+    const size_t p = x.size() / 3;
+    if (p < 3) return true;
+    const double *a = &x[0];
+    size_t far = 0;
+    double best = -1.0;
+    for (size_t i = 0; i < p; ++i) {
+        double d = 0;
+        for (int e = 0; e < 3; ++e) d += (x[3 * i + e] - a[e]) * (x[3 * i + e] - a[e]);
+        if (d > best) { best = d; far = i; }
+    }
+    double ab[3];
+    for (int e = 0; e < 3; ++e) ab[e] = x[3 * far + e] - a[e];
+    const double ab2 = ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2];
+    for (size_t i = 0; i < p; ++i) {
+        double v[3];
+        for (int e = 0; e < 3; ++e) v[e] = x[3 * i + e] - a[e];
+        const double c0 = v[1] * ab[2] - v[2] * ab[1];
+        const double c1 = v[2] * ab[0] - v[0] * ab[2];
+        const double c2 = v[0] * ab[1] - v[1] * ab[0];
+        if (c0 * c0 + c1 * c1 + c2 * c2 > 1e-12 * ab2 * ab2) return false;
+    }
+    return true;
+}
+
+__global__ void k_init_scalars(Scalars *sc, double tol2, const double *ffsrc, int max_it) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        Scalars z{};
+        z.tol2ff = ffsrc ? tol2 * (*ffsrc) : tol2;
+        z.max_it = max_it;
+        *sc = z;
+    }
+}
+
+void init_scalars(xdcg_ctx *c, Scalars *sc, double tol2, const double *ffsrc, int max_it) {
+    k_init_scalars<<<1, 32, 0, c->st>>>(sc, tol2, ffsrc, max_it);
+    c->launches++;
+}
+
+xdcg_status map_done(int done) {
+    switch (done) {
+        case kConverged: return XDCG_OK;
+        case kBreakdown: return XDCG_BREAKDOWN;
+        case kMaxIter: return XDCG_NO_CONVERGENCE;
+        default: return XDCG_NO_CONVERGENCE;
+    }
+}
+
+// ---- one preconditioned CG run (Algorithms 1-3) ----------------------------
+
+template <typename T, typename LV>
+xdcg_status run_pcg(xdcg_ctx *c, LV &L, const T *f, T *u, T *r, T *p, T *q, T *y, Scalars *sc,
+                    int max_it, bool time_spmv, int *its_out, int *done_out, double *t_spmv,
+                    int *n_spmv) {
+    cudaStream_t st = c->st;
+    // Algorithm 2 with u_-1 = 0: u_0 = Z E^-1 Z^T f
+    launch_restrict<T>(L.N, L.B, f, nullptr, 0, c->g, nullptr, st, sc);
+    launch_coarse(c->Einv, c->k, c->g, nullptr, c->nu, 0, c->partials, sc, st);
+    launch_prolong<T>(L.N, c->nu, nullptr, u, 1, sc, st);
+    // r_0 = f - K u_0, z_0 by Algorithm 3, p_0 = z_0
+    launch_spmv<T>(L.A, u, r, f, 1, c->partials, sc, kFinRR, 0, st);
+    launch_update<T>(L.N, u, r, nullptr, nullptr, y, 1, c->partials, sc, st);
+    launch_restrict<T>(L.N, L.B, r, y, 1, c->g, c->zr, st, sc);
+    launch_coarse(c->Einv, c->k, c->g, c->zr, c->nu, 1, c->partials, sc, st);
+    launch_prolong<T>(L.N, c->nu, y, p, 2, sc, st);
+    c->launches += 8;
+
+    int launched = 0;
+    const int max_batches = max_it / kBatch + 2;
+    for (int b = 0; b < max_batches; ++b) {
+        for (int i = 0; i < kBatch; ++i) {
+            if (time_spmv) {
+                if ((int)c->evS.size() <= launched) {
+                    cudaEvent_t e0, e1;
+                    CK(cudaEventCreate(&e0));
+                    CK(cudaEventCreate(&e1));
+                    c->evS.push_back(e0);
+                    c->evE.push_back(e1);
+                }
+                CK(cudaEventRecord(c->evS[launched], st));
+            }
+            launch_spmv<T>(L.A, p, q, nullptr, 0, c->partials, sc, kFinAlpha, 0, st);
+            if (time_spmv) CK(cudaEventRecord(c->evE[launched], st));
+            launch_update<T>(L.N, u, r, p, q, y, 0, c->partials, sc, st);
+            launch_restrict<T>(L.N, L.B, r, y, 1, c->g, c->zr, st, sc);
+            launch_coarse(c->Einv, c->k, c->g, c->zr, c->nu, 2, c->partials, sc, st);
+            launch_prolong<T>(L.N, c->nu, y, p, 0, sc, st);
+            c->launches += 5;
+            ++launched;
+        }
+        CK(cudaMemcpyAsync(&c->h_done[b & 1], &sc->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaEventRecord(c->evb[b & 1], st));
+        if (b >= 1) {
+            CK(cudaEventSynchronize(c->evb[(b - 1) & 1]));
+            if (c->h_done[(b - 1) & 1] != kRunning) break;
+        }
+    }
+    CK(cudaMemcpyAsync(c->h_sc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    *its_out = c->h_sc->its;
+    *done_out = c->h_sc->done;
+    if (time_spmv) {
+        const int nt = std::min(launched, c->h_sc->its);
+        for (int i = 0; i < nt; ++i) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, c->evS[i], c->evE[i]));
+            *t_spmv += ms;
+        }
+        *n_spmv += nt;
+    }
+    return XDCG_OK;
+}
+
+xdcg_status read_aux(xdcg_ctx *c, double *vals, int count) {
+    CK(cudaMemcpyAsync(c->h_sc, c->aux, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    for (int i = 0; i < count; ++i) vals[i] = c->h_sc->scratch[i];
+    return XDCG_OK;
+}
+
+xdcg_status solve_fp64(xdcg_ctx *c, const double *f, double *u, double tol, xdcg_result *res) {
+    cudaStream_t st = c->st;
+    init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
+    launch_dot<double>(f, f, c->n, c->partials, c->aux, kFinStore, 0, st);
+    init_scalars(c, c->sc, tol * tol, &c->aux->scratch[0], c->opt.max_iter);
+    c->launches += 1;
+    int its = 0, done = 0;
+    xdcg_status s = run_pcg<double>(c, c->L64, f, u, c->r64, c->p64, c->q64, c->y64, c->sc,
+                                    c->opt.max_iter, c->opt.time_spmv != 0, &its, &done,
+                                    &res->t_spmv_ms, &res->n_spmv_timed);
+    if (s != XDCG_OK) return s;
+    const double rr = c->h_sc->rr;
+    // true residual f - K u in FP64
+    launch_spmv<double>(c->L64.A, u, c->r64, f, 1, c->partials, c->aux, kFinStore, 1, st);
+    c->launches += 1;
+    double v[2];
+    if ((s = read_aux(c, v, 2)) != XDCG_OK) return s;
+    const double ff = v[0];
+    res->iterations = its;
+    res->outer_cycles = 1;
+    res->rel_res_recursive = ff > 0 ? std::sqrt(rr / ff) : 0.0;
+    res->rel_res_true = ff > 0 ? std::sqrt(v[1] / ff) : 0.0;
+    return map_done(done);
+}
+
+xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, xdcg_result *res) {
+    cudaStream_t st = c->st;
+    init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
+    launch_dot<double>(f, f, c->n, c->partials, c->aux, kFinStore, 0, st);
+    c->launches += 1;
+    double v[2];
+    xdcg_status s;
+    if ((s = read_aux(c, v, 1)) != XDCG_OK) return s;
+    const double ff = v[0];
+    CK(cudaMemsetAsync(u, 0, c->n * sizeof(double), st));
+    CK(cudaMemcpyAsync(c->r64, f, c->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    double rn2 = ff;
+    int total = 0, cycles = 0;
+    xdcg_status status = XDCG_NO_CONVERGENCE;
+    double last_inner_rel = 1.0;
+    while (true) {
+        if (ff == 0.0 || rn2 <= tol * tol * ff) { status = XDCG_OK; break; }
+        if (cycles >= c->opt.max_outer || total >= c->opt.max_iter) break;
+        const double rn = std::sqrt(rn2);
+        launch_scale_to_f32(c->r64, c->f32, c->n, 1.0 / rn, st);
+        init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
+        launch_dot<float>(c->f32, c->f32, c->n, c->partials, c->aux, kFinStore, 0, st);
+        const double eta = c->opt.inner_tol;
+        init_scalars(c, c->sc32, eta * eta, &c->aux->scratch[0], c->opt.max_iter - total);
+        c->launches += 2;
+        int its = 0, done = 0;
+        s = run_pcg<float>(c, c->L32, c->f32, c->u32, c->r32, c->p32, c->q32, c->y32, c->sc32,
+                           c->opt.max_iter - total, c->opt.time_spmv != 0, &its, &done,
+                           &res->t_spmv_ms, &res->n_spmv_timed);
+        if (s != XDCG_OK) return s;
+        total += its;
+        cycles++;
+        last_inner_rel = std::sqrt(c->h_sc->rr);
+        launch_accumulate_f64(u, c->u32, c->n, rn, st);
+        init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
+        launch_spmv<double>(c->L64.A, u, c->r64, f, 1, c->partials, c->aux, kFinStore, 0, st);
+        c->launches += 3;
+        if ((s = read_aux(c, v, 1)) != XDCG_OK) return s;
+        const double prev = rn2;
+        rn2 = v[0];
+        if (!std::isfinite(rn2)) { status = XDCG_BREAKDOWN; break; }
+        if (done == kBreakdown && rn2 >= prev) { status = XDCG_BREAKDOWN; break; }
+    }
+    res->iterations = total;
+    res->outer_cycles = cycles;
+    res->rel_res_recursive = last_inner_rel;
+    res->rel_res_true = ff > 0 ? std::sqrt(rn2 / ff) : 0.0;
+    return status;
+}
+
+xdcg_status do_solve(xdcg_ctx *c, const double *f, double *u, double tol, xdcg_result *out) {
+    xdcg_result res{};
+    res.bad_index = -1;
+    if (tol <= 0) tol = c->opt.tol;
+    const long long l0 = c->launches;
+    CK(cudaEventRecord(c->ev0, c->st));
+    xdcg_status s = (c->opt.precision == XDCG_MIXED) ? solve_mixed(c, f, u, tol, &res)
+                                                    : solve_fp64(c, f, u, tol, &res);
+    if (s == XDCG_CUDA_ERROR) return s;
+    CK(cudaEventRecord(c->ev1, c->st));
+    CK(cudaEventSynchronize(c->ev1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    res.t_solve_ms = ms;
+    res.n_launches = c->launches - l0;
+    if (out) *out = res;
+    return s;
+}
+
+void free_ctx(xdcg_ctx *c) {
+    if (!c) return;
+    for (void *p : c->allocs) cudaFree(p);
+    for (void *p : c->temps) cudaFree(p);
+    if (c->h_sc) cudaFreeHost(c->h_sc);
+    if (c->h_done) cudaFreeHost(c->h_done);
+    for (auto e : c->evS) cudaEventDestroy(e);
+    for (auto e : c->evE) cudaEventDestroy(e);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    for (auto e : c->evb)
+        if (e) cudaEventDestroy(e);
+    delete c;
+}
+
+// ---- set-up -----------------------------------------------------------------
+
+xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *Zd, int *bad) {
+    const int N = K->n_nodes;
+    if (N <= 0 || !K->dof_ptr || !K->row_ptr) return XDCG_INVALID_ARG;
+    if ((K->mem != XDCG_HOST && K->mem != XDCG_DEVICE) ||
+        (Zd->mem != XDCG_HOST && Zd->mem != XDCG_DEVICE))
+        return XDCG_INVALID_ARG;
+    std::vector<int> dof, rowp, col;
+    std::vector<long long> vptr;
+    std::vector<double> val;
+    if (!fetch(dof, K->dof_ptr, N + 1, K->mem) || !fetch(rowp, K->row_ptr, N + 1, K->mem))
+        return XDCG_INVALID_ARG;
+    if (dof[0] != 0 || rowp[0] != 0) return XDCG_INVALID_ARG;
+    for (int I = 0; I < N; ++I) {
+        const int b = dof[I + 1] - dof[I];
+        if (b != 3 && b != 6 && b != 15) return XDCG_INVALID_ARG;
+        if (rowp[I + 1] < rowp[I]) return XDCG_INVALID_ARG;
+    }
+    const long long nnzb = rowp[N];
+    if (!fetch(col, K->col, nnzb, K->mem)) return XDCG_INVALID_ARG;
+    std::vector<int64_t> vp64;
+    if (!fetch(vp64, K->val_ptr, nnzb + 1, K->mem)) return XDCG_INVALID_ARG;
+    vptr.assign(vp64.begin(), vp64.end());
+    if (vptr[0] != 0) return XDCG_INVALID_ARG;
+    for (int I = 0; I < N; ++I) {
+        bool diag = false;
+        for (long long p = rowp[I]; p < rowp[I + 1]; ++p) {
+            const int J = col[p];
+            if (J < 0 || J >= N) return XDCG_INVALID_ARG;
+            if (p > rowp[I] && col[p - 1] >= J) return XDCG_INVALID_ARG;
+            if (J == I) diag = true;
+            if (vptr[p + 1] - vptr[p] != (long long)(dof[I + 1] - dof[I]) * (dof[J + 1] - dof[J]))
+                return XDCG_INVALID_ARG;
+        }
+        if (!diag) return XDCG_INVALID_ARG;
+    }
+    if (!fetch(val, K->val, vptr[nnzb], K->mem)) return XDCG_INVALID_ARG;
+    double vmax = 0.0;
+    for (double v : val) {
+        if (!std::isfinite(v)) return XDCG_INVALID_ARG;
+        vmax = std::max(vmax, std::fabs(v));
+    }
+    // symmetry of pattern and values
+    for (int I = 0; I < N; ++I) {
+        const int bI = dof[I + 1] - dof[I];
+        for (long long p = rowp[I]; p < rowp[I + 1]; ++p) {
+            const int J = col[p];
+            if (J < I) continue;
+            const int bJ = dof[J + 1] - dof[J];
+            const int *beg = &col[rowp[J]], *end = &col[0] + rowp[J + 1];
+            const int *it = std::lower_bound(beg, end, I);
+            if (it == end || *it != I) return XDCG_INVALID_ARG;
+            const long long q = rowp[J] + (it - beg);
+            for (int a = 0; a < bI; ++a)
+                for (int b2 = 0; b2 < bJ; ++b2)
+                    if (std::fabs(val[vptr[p] + a * bJ + b2] - val[vptr[q] + b2 * bI + a]) >
+                        1e-12 * vmax)
+                        return XDCG_INVALID_ARG;
+        }
+    }
+    // deflation description
+    const int S = Zd->n_sub;
+    if (S <= 0) return XDCG_INVALID_ARG;
+    std::vector<int> sub;
+    std::vector<double> coords, centre;
+    std::vector<int8_t> hs;
+    if (!fetch(sub, Zd->sub_of_node, N, Zd->mem) || !fetch(coords, Zd->coords, 3 * (size_t)N, Zd->mem) ||
+        !fetch(hs, Zd->hsign, N, Zd->mem) || !fetch(centre, Zd->centre, 3 * (size_t)S, Zd->mem))
+        return XDCG_INVALID_ARG;
+    for (int I = 0; I < N; ++I) {
+        if (sub[I] < 0 || sub[I] >= S) return XDCG_INVALID_ARG;
+        if (hs[I] != 1 && hs[I] != -1) return XDCG_INVALID_ARG;
+        for (int e = 0; e < 3; ++e)
+            if (!std::isfinite(coords[3 * I + e])) return XDCG_INVALID_ARG;
+    }
+
+    c->nNodes = N;
+    c->n = dof[N];
+    c->nBox = S;
+    const long long n = c->n;
+
+    // ---- chunk rows: S (pure standard) and X (the rest)
+    std::vector<int> kindb(N);
+    for (int I = 0; I < N; ++I) kindb[I] = dof[I + 1] - dof[I];
+    std::vector<int> sRows, xRows;
+    std::vector<int> rowNode, rowPart;   // per chunk row: node and chunk within node
+    const long long nChunks = n / 3;
+    rowNode.resize(nChunks);
+    rowPart.resize(nChunks);
+    for (int I = 0; I < N; ++I)
+        for (int ci = 0; ci < kindb[I] / 3; ++ci) {
+            rowNode[dof[I] / 3 + ci] = I;
+            rowPart[dof[I] / 3 + ci] = ci;
+        }
+    std::vector<char> pure(N, 0);
+    for (int I = 0; I < N; ++I) {
+        bool ok = kindb[I] == 3;
+        for (long long p = rowp[I]; ok && p < rowp[I + 1]; ++p) ok = kindb[col[p]] == 3;
+        pure[I] = ok;
+    }
+    std::vector<int> rowLen(nChunks, 0);
+    for (long long r = 0; r < nChunks; ++r) {
+        const int I = rowNode[r];
+        int len = 0;
+        for (long long p = rowp[I]; p < rowp[I + 1]; ++p) len += kindb[col[p]] / 3;
+        rowLen[r] = len;
+        if (pure[I] && rowPart[r] == 0)
+            sRows.push_back((int)r);
+        else
+            xRows.push_back((int)r);
+    }
+    // blocks of chunk row r in column order: (col chunk, pointer to 3x3 source)
+    auto for_blocks = [&](long long r, auto &&fn) {
+        const int I = rowNode[r], ci = rowPart[r];
+        const int bI = kindb[I];
+        int t = 0;
+        for (long long p = rowp[I]; p < rowp[I + 1]; ++p) {
+            const int J = col[p];
+            const int bJ = kindb[J];
+            for (int cj = 0; cj < bJ / 3; ++cj, ++t) {
+                double blk[9];
+                for (int a = 0; a < 3; ++a)
+                    for (int b2 = 0; b2 < 3; ++b2)
+                        blk[a * 3 + b2] = val[vptr[p] + (3 * ci + a) * bJ + 3 * cj + b2];
+                fn(t, dof[J] / 3 + cj, blk);
+            }
+        }
+        (void)bI;
+    };
+    const int nS = (int)sRows.size(), nSlices = (nS + 31) / 32;
+    std::vector<int> lenS(nS);
+    std::vector<long long> slicePtr(nSlices + 1, 0);
+    for (int s = 0; s < nSlices; ++s) {
+        int mx = 0;
+        for (int l = 0; l < 32 && s * 32 + l < nS; ++l) mx = std::max(mx, rowLen[sRows[s * 32 + l]]);
+        slicePtr[s + 1] = slicePtr[s] + 32LL * mx;
+    }
+    std::vector<int> colS(slicePtr[nSlices]);
+    std::vector<double> valS(9 * (size_t)slicePtr[nSlices], 0.0);
+    for (int s = 0; s < nSlices; ++s)
+        for (int l = 0; l < 32 && s * 32 + l < nS; ++l) {
+            const int r = sRows[s * 32 + l];
+            lenS[s * 32 + l] = rowLen[r];
+            const long long base = slicePtr[s];
+            const long long slots = (slicePtr[s + 1] - base) / 32;
+            for (long long j = 0; j < slots; ++j) colS[base + j * 32 + l] = r;
+            for_blocks(r, [&](int t, int cc, const double *blk) {
+                colS[base + (long long)t * 32 + l] = cc;
+                for (int e = 0; e < 9; ++e) valS[9 * base + ((long long)t * 9 + e) * 32 + l] = blk[e];
+            });
+        }
+    const int nX = (int)xRows.size();
+    std::vector<int> lenX(nX);
+    std::vector<long long> ptrX(nX + 1, 0);
+    for (int i = 0; i < nX; ++i) {
+        lenX[i] = rowLen[xRows[i]];
+        ptrX[i + 1] = ptrX[i] + 32LL * ((lenX[i] + 31) / 32);
+    }
+    std::vector<int> colX(std::max<long long>(ptrX[nX], 1), 0);
+    std::vector<double> valX(9 * (size_t)std::max<long long>(ptrX[nX], 1), 0.0);
+    for (int i = 0; i < nX; ++i) {
+        const int r = xRows[i];
+        const long long base = ptrX[i];
+        for (long long t = 0; t < ptrX[i + 1] - base; ++t) colX[base + t] = r;
+        for_blocks(r, [&](int t, int cc, const double *blk) {
+            colX[base + t] = cc;
+            for (int e = 0; e < 9; ++e)
+                valX[9 * base + 288LL * (t >> 5) + 32 * e + (t & 31)] = blk[e];
+        });
+    }
+    long long nnzb3 = 0;
+    for (long long r = 0; r < nChunks; ++r) nnzb3 += rowLen[r];
+
+    // ---- node lists and diagonal blocks
+    std::vector<int> lists[3];
+    for (int I = 0; I < N; ++I) lists[kindb[I] == 3 ? 0 : (kindb[I] == 6 ? 1 : 2)].push_back(I);
+    const int Bsz[3] = {3, 6, 15};
+    std::vector<double> Dsoa[3];
+    for (int t = 0; t < 3; ++t) {
+        const int B = Bsz[t], cnt = (int)lists[t].size();
+        Dsoa[t].assign((size_t)B * B * std::max(cnt, 1), 0.0);
+        for (int i = 0; i < cnt; ++i) {
+            const int I = lists[t][i];
+            long long pd = -1;
+            for (long long p = rowp[I]; p < rowp[I + 1]; ++p)
+                if (col[p] == I) pd = p;
+            for (int e = 0; e < B * B; ++e) Dsoa[t][(size_t)e * cnt + i] = val[vptr[pd] + e];
+        }
+    }
+
+    // ---- boxes: own nodes, enriched-mode decision, coarse columns, W entries
+    std::vector<int> ownPtr(S + 1, 0), ownNodes(N);
+    for (int I = 0; I < N; ++I) ownPtr[sub[I] + 1]++;
+    for (int s = 0; s < S; ++s) ownPtr[s + 1] += ownPtr[s];
+    {
+        std::vector<int> fill(ownPtr.begin(), ownPtr.end() - 1);
+        for (int I = 0; I < N; ++I) ownNodes[fill[sub[I]]++] = I;
+    }
+    std::vector<int> menr(S, 0), col0(S + 1, 0);
+    for (int s = 0; s < S; ++s) {
+        if (Zd->enriched_modes) {
+            std::vector<double> pts;
+            for (int t = ownPtr[s]; t < ownPtr[s + 1]; ++t) {
+                const int I = ownNodes[t];
+                if (kindb[I] == 6)
+                    for (int e = 0; e < 3; ++e) pts.push_back(coords[3 * I + e]);
+            }
+            menr[s] = pts.empty() ? 0 : (points_collinear(pts) ? 0 : 1);
+        }
+        col0[s + 1] = col0[s] + (menr[s] ? 12 : 6);
+    }
+    c->k = col0[S];
+    const int k = c->k;
+    // W entries: (box s, node I) for every node I coupled to a node of s;
+    // ordered by box, then owner box of I, then I (segments of E)
+    std::vector<std::vector<int>> extOf(S);
+    {
+        std::vector<int> mark(S, -1);
+        for (int I = 0; I < N; ++I)
+            for (long long p = rowp[I]; p < rowp[I + 1]; ++p) {
+                const int s = sub[col[p]];
+                if (mark[s] != I) { mark[s] = I; extOf[s].push_back(I); }
+            }
+    }
+    std::vector<int> extPtr(S + 1, 0), extNode, extBox;
+    std::vector<long long> wOff(1, 0);
+    std::vector<int> segBox, segOwner, segBegin, segEnd;
+    for (int s = 0; s < S; ++s) {
+        auto &v = extOf[s];
+        std::stable_sort(v.begin(), v.end(), [&](int a, int b) {
+            return sub[a] != sub[b] ? sub[a] < sub[b] : a < b;
+        });
+        const int M = menr[s] ? 12 : 6;
+        for (size_t i = 0; i < v.size(); ++i) {
+            const int e = (int)extNode.size();
+            if (i == 0 || sub[v[i]] != sub[v[i - 1]]) {
+                segBox.push_back(s);
+                segOwner.push_back(sub[v[i]]);
+                segBegin.push_back(e);
+                segEnd.push_back(e);
+            }
+            segEnd.back() = e + 1;
+            extNode.push_back(v[i]);
+            extBox.push_back(s);
+            wOff.push_back(wOff.back() + (long long)kindb[v[i]] * M);
+        }
+        extPtr[s + 1] = (int)extNode.size();
+    }
+    const int nExt = (int)extNode.size();
+    const long long nW = wOff.back();
+    wOff.pop_back();
+
+    // ---- upload and set-up kernels
+    cudaStream_t st = c->st;
+    c->mixed = c->opt.precision == XDCG_MIXED;
+    const bool mixed = c->mixed;
+    int *d_dof = upload(c, dof);
+    int *d_sub = upload(c, sub);
+    std::vector<signed char> hsc(hs.begin(), hs.end());
+    signed char *d_hs = upload(c, hsc);
+    int *d_col0 = upload(c, col0);
+    int *d_menr = upload(c, menr);
+    double *d_x64 = dalloc<double>(c, 3 * (size_t)N);
+    float *d_x32 = mixed ? dalloc<float>(c, 3 * (size_t)N) : nullptr;
+    if (!d_dof || !d_sub || !d_hs || !d_col0 || !d_menr || !d_x64 || (mixed && !d_x32))
+        return XDCG_OOM;
+    {
+        double *d_coords = upload_tmp(c, coords), *d_centre = upload_tmp(c, centre);
+        if (!d_coords || !d_centre) return XDCG_OOM;
+        launch_xrel(N, d_coords, d_centre, d_sub, d_x64, d_x32, st);
+    }
+    // SpMV layouts
+    auto &A = c->L64.A;
+    A.nS = nS;
+    A.nSlices = nSlices;
+    A.rowS = upload(c, sRows);
+    A.lenS = upload(c, lenS);
+    A.slicePtr = upload(c, slicePtr);
+    A.colS = upload(c, colS);
+    double *d_valS = upload(c, valS);
+    A.valS = d_valS;
+    A.nX = nX;
+    A.rowX = upload(c, xRows);
+    A.lenX = upload(c, lenX);
+    A.ptrX = upload(c, ptrX);
+    A.colX = upload(c, colX);
+    double *d_valX = upload(c, valX);
+    A.valX = d_valX;
+    if (!A.rowS || !A.lenS || !A.slicePtr || !A.colS || !A.valS || !A.rowX || !A.lenX ||
+        !A.ptrX || !A.colX || !A.valX)
+        return XDCG_OOM;
+    if (mixed) {
+        auto &A2 = c->L32.A;
+        A2.nS = nS; A2.nSlices = nSlices; A2.rowS = A.rowS; A2.lenS = A.lenS;
+        A2.slicePtr = A.slicePtr; A2.colS = A.colS;
+        A2.nX = nX; A2.rowX = A.rowX; A2.lenX = A.lenX; A2.ptrX = A.ptrX; A2.colX = A.colX;
+        float *v32S = dalloc<float>(c, valS.size()), *v32X = dalloc<float>(c, valX.size());
+        if (!v32S || !v32X) return XDCG_OOM;
+        launch_cast_f32(d_valS, v32S, (long long)valS.size(), st);
+        launch_cast_f32(d_valX, v32X, (long long)valX.size(), st);
+        A2.valS = v32S;
+        A2.valX = v32X;
+    }
+    // node data and block factors
+    int *d_bad = dalloc<int>(c, 2);
+    if (!d_bad) return XDCG_OOM;
+    {
+        std::vector<int> init = {INT_MAX, INT_MAX};
+        CK(cudaMemcpyAsync(d_bad, init.data(), 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    auto &N64 = c->L64.N;
+    N64.nNodes = N;
+    N64.nStd = (int)lists[0].size();
+    N64.nH = (int)lists[1].size();
+    N64.nT = (int)lists[2].size();
+    N64.dofStart = d_dof;
+    N64.sub = d_sub;
+    N64.xrel = d_x64;
+    N64.hsign = d_hs;
+    N64.col0 = d_col0;
+    N64.menr = d_menr;
+    const int *dl[3];
+    double *L64[3];
+    float *L32[3] = {nullptr, nullptr, nullptr};
+    for (int t = 0; t < 3; ++t) {
+        const int B = Bsz[t], cnt = (int)lists[t].size();
+        dl[t] = upload(c, lists[t]);
+        L64[t] = dalloc<double>(c, (size_t)B * (B + 1) / 2 * std::max(cnt, 1));
+        if (mixed) L32[t] = dalloc<float>(c, (size_t)B * (B + 1) / 2 * std::max(cnt, 1));
+        double *d_D = upload_tmp(c, Dsoa[t]);
+        if (!dl[t] || !L64[t] || !d_D || (mixed && !L32[t])) return XDCG_OOM;
+        launch_block_cholesky(B, cnt, dl[t], d_D, L64[t], L32[t], d_bad, st);
+    }
+    N64.stdNodes = dl[0]; N64.hNodes = dl[1]; N64.tNodes = dl[2];
+    N64.Lstd = L64[0]; N64.Lh = L64[1]; N64.Lt = L64[2];
+    if (mixed) {
+        auto &N32 = c->L32.N;
+        N32.nNodes = N; N32.nStd = N64.nStd; N32.nH = N64.nH; N32.nT = N64.nT;
+        N32.stdNodes = dl[0]; N32.hNodes = dl[1]; N32.tNodes = dl[2];
+        N32.dofStart = d_dof; N32.sub = d_sub; N32.xrel = d_x32; N32.hsign = d_hs;
+        N32.col0 = d_col0; N32.menr = d_menr;
+        N32.Lstd = L32[0]; N32.Lh = L32[1]; N32.Lt = L32[2];
+    }
+    // W = K Z and E = Z^T W
+    KinDev kin;
+    kin.nNodes = N;
+    kin.dofStart = d_dof;
+    kin.rowPtr = upload_tmp(c, rowp);
+    kin.col = upload_tmp(c, col);
+    kin.valPtr = upload_tmp(c, vptr);
+    kin.val = upload_tmp(c, val);
+    if (!kin.rowPtr || !kin.col || !kin.valPtr || !kin.val) return XDCG_OOM;
+    int *d_extBox = upload_tmp(c, extBox), *d_extNode = upload(c, extNode);
+    int *d_extPtr = upload(c, extPtr), *d_ownPtr = upload(c, ownPtr), *d_own = upload(c, ownNodes);
+    long long *d_wOff = upload(c, wOff);
+    double *d_W = dalloc<double>(c, nW);
+    if (!d_extBox || !d_extNode || !d_extPtr || !d_ownPtr || !d_own || !d_wOff || !d_W)
+        return XDCG_OOM;
+    launch_build_W(kin, nExt, d_extBox, d_extNode, d_wOff, d_sub, d_x64, d_hs, d_menr, d_W, st);
+    auto &B64 = c->L64.B;
+    B64.nBox = S;
+    B64.ownPtr = d_ownPtr;
+    B64.ownNodes = d_own;
+    B64.extPtr = d_extPtr;
+    B64.extNode = d_extNode;
+    B64.wOff = d_wOff;
+    B64.W = d_W;
+    if (mixed) {
+        float *W32 = dalloc<float>(c, nW);
+        if (!W32) return XDCG_OOM;
+        launch_cast_f32(d_W, W32, nW, st);
+        auto &B32 = c->L32.B;
+        B32.nBox = S; B32.ownPtr = d_ownPtr; B32.ownNodes = d_own; B32.extPtr = d_extPtr;
+        B32.extNode = d_extNode; B32.wOff = d_wOff; B32.W = W32;
+    }
+    c->Einv = dalloc<double>(c, (size_t)k * k);
+    c->E = dalloc<double>(c, (size_t)k * k);
+    double *colbuf = dalloc_tmp<double>(c, k);
+    int *sb = upload_tmp(c, segBox), *so = upload_tmp(c, segOwner),
+        *sbg = upload_tmp(c, segBegin), *se = upload_tmp(c, segEnd);
+    if (!c->Einv || !c->E || !colbuf || !sb || !so || !sbg || !se) return XDCG_OOM;
+    CK(cudaMemsetAsync(c->Einv, 0, (size_t)k * k * sizeof(double), st));
+    launch_build_E((int)segBox.size(), sb, so, sbg, se, d_extNode, d_wOff, d_W, d_dof, d_x64,
+                   d_hs, d_col0, d_menr, k, c->Einv, st);
+    launch_symmetrize(c->Einv, k, st);
+    CK(cudaMemcpyAsync(c->E, c->Einv, (size_t)k * k * sizeof(double), cudaMemcpyDeviceToDevice,
+                       st));
+    // pivot threshold relative to the largest diagonal entry of E
+    {
+        std::vector<double> diag(k);
+        CK(cudaMemcpy2DAsync(diag.data(), sizeof(double), c->Einv, (k + 1) * sizeof(double),
+                             sizeof(double), k, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        double dm = 0;
+        for (double d : diag) dm = std::max(dm, d);
+        launch_sweep_inverse(c->Einv, k, colbuf, d_bad + 1, 1e-14 * dm, st);
+    }
+    int hbad[2];
+    CK(cudaMemcpyAsync(hbad, d_bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    for (void *p : c->temps) cudaFree(p);
+    c->temps.clear();
+    if (hbad[0] != INT_MAX) { *bad = hbad[0]; return XDCG_NOT_SPD_BLOCK; }
+    if (hbad[1] != INT_MAX) { *bad = hbad[1]; return XDCG_COARSE_NOT_SPD; }
+
+    // ---- work vectors and scalar blocks
+    c->u64 = dalloc<double>(c, n); c->r64 = dalloc<double>(c, n); c->p64 = dalloc<double>(c, n);
+    c->q64 = dalloc<double>(c, n); c->y64 = dalloc<double>(c, n);
+    c->f64 = dalloc<double>(c, n); c->uh64 = dalloc<double>(c, n);
+    if (mixed) {
+        c->f32 = dalloc<float>(c, n); c->u32 = dalloc<float>(c, n); c->r32 = dalloc<float>(c, n);
+        c->p32 = dalloc<float>(c, n); c->q32 = dalloc<float>(c, n); c->y32 = dalloc<float>(c, n);
+        if (!c->f32 || !c->u32 || !c->r32 || !c->p32 || !c->q32 || !c->y32) return XDCG_OOM;
+    }
+    c->g = dalloc<double>(c, k); c->zr = dalloc<double>(c, k); c->nu = dalloc<double>(c, k);
+    c->partials = dalloc<double>(c, 4 * (size_t)kMaxGrid);
+    c->sc = dalloc<Scalars>(c, 1); c->sc32 = dalloc<Scalars>(c, 1); c->aux = dalloc<Scalars>(c, 1);
+    if (!c->u64 || !c->r64 || !c->p64 || !c->q64 || !c->y64 || !c->f64 || !c->uh64 || !c->g ||
+        !c->zr || !c->nu || !c->partials || !c->sc || !c->sc32 || !c->aux)
+        return XDCG_OOM;
+    CK(cudaMemsetAsync(c->sc, 0, sizeof(Scalars), st));
+    CK(cudaMemsetAsync(c->sc32, 0, sizeof(Scalars), st));
+    CK(cudaMemsetAsync(c->aux, 0, sizeof(Scalars), st));
+    if (cudaMallocHost(&c->h_sc, sizeof(Scalars)) != cudaSuccess) return XDCG_OOM;
+    if (cudaMallocHost(&c->h_done, 2 * sizeof(int)) != cudaSuccess) return XDCG_OOM;
+    CK(cudaEventCreate(&c->ev0));
+    CK(cudaEventCreate(&c->ev1));
+    CK(cudaEventCreateWithFlags(&c->evb[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->evb[1], cudaEventDisableTiming));
+    CK(cudaStreamSynchronize(st));
+    if (spmv_grid(nSlices, nX) > kMaxGrid) return XDCG_INVALID_ARG;
+
+    // ---- algorithmic byte counts (see the roofline notes of the design)
+    long long nStdN = (long long)lists[0].size(), nHN = (long long)lists[1].size(),
+              nTN = (long long)lists[2].size();
+    auto spmv_bytes = [&](int s) {
+        return 9LL * nnzb3 * s + 4LL * nnzb3 + 8LL * nS + 8LL * nSlices + 16LL * nX + 2LL * n * s;
+    };
+    const long long fac = 6 * nStdN + 21 * nHN + 120 * nTN;
+    auto iter_bytes = [&](int s) {
+        return spmv_bytes(s)
+               + 7LL * n * s + fac * s + 4LL * N                 // update
+               + 2LL * n * s + nW * s + 12LL * nExt + 16LL * k    // restrict
+               + 8LL * k * k + 24LL * k                           // coarse
+               + 3LL * n * s + (3LL * s + 9) * N;                 // prolong
+    };
+    c->info.n = n;
+    c->info.n_nodes = N;
+    c->info.k = k;
+    c->info.nnz = 9 * nnzb3;
+    c->info.nnzb3 = nnzb3;
+    c->info.spmv_bytes_fp64 = spmv_bytes(8);
+    c->info.spmv_bytes_fp32 = spmv_bytes(4);
+    c->info.iter_bytes_fp64 = iter_bytes(8);
+    c->info.iter_bytes_fp32 = iter_bytes(4);
+    return XDCG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+xdcg_status xdcg_default_options(xdcg_options *opt) {
+    if (!opt) return XDCG_INVALID_ARG;
+    opt->tol = 1e-8;
+    opt->max_iter = 10000;
+    opt->precision = XDCG_FP64;
+    opt->inner_tol = 1e-5;
+    opt->max_outer = 30;
+    opt->time_spmv = 0;
+    return XDCG_OK;
+}
+
+xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflation *Z,
+                       const void *blocks, const xdcg_options *opt, void *stream) {
+    if (!out) return XDCG_INVALID_ARG;
+    *out = nullptr;
+    if (!K || !Z || blocks) return XDCG_INVALID_ARG;
+    xdcg_ctx *c = new (std::nothrow) xdcg_ctx();
+    if (!c) return XDCG_OOM;
+    if (opt)
+        c->opt = *opt;
+    else
+        xdcg_default_options(&c->opt);
+    if (!(c->opt.tol > 0) || c->opt.max_iter < 0 || c->opt.max_outer < 1 ||
+        (c->opt.precision != XDCG_FP64 && c->opt.precision != XDCG_MIXED) ||
+        !(c->opt.inner_tol > 0 && c->opt.inner_tol < 1)) {
+        delete c;
+        return XDCG_INVALID_ARG;
+    }
+    c->st = (cudaStream_t)stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return XDCG_CUDA_ERROR; }
+    const auto t0 = std::chrono::steady_clock::now();
+    int bad = -1;
+    xdcg_status s = setup_impl(c, K, Z, &bad);
+    if (s != XDCG_OK) {
+        cudaStreamSynchronize(c->st);
+        free_ctx(c);
+        return s;
+    }
+    c->info.t_setup_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = c;
+    return XDCG_OK;
+}
+
+xdcg_status xdcg_solve(xdcg_ctx *c, const double *f, double *u, double tol, xdcg_result *res) {
+    if (!c || !f || !u || f == u) return XDCG_INVALID_ARG;
+    return do_solve(c, f, u, tol, res);
+}
+
+xdcg_status xdcg_solve_host(xdcg_ctx *c, const double *f_host, double *u_host, double tol,
+                            xdcg_result *res) {
+    if (!c || !f_host || !u_host) return XDCG_INVALID_ARG;
+    CK(cudaMemcpyAsync(c->f64, f_host, c->n * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    xdcg_status s = do_solve(c, c->f64, c->uh64, tol, res);
+    if (s == XDCG_CUDA_ERROR) return s;
+    CK(cudaMemcpyAsync(u_host, c->uh64, c->n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return s;
+}
+
+xdcg_status xdcg_get_info(const xdcg_ctx *c, xdcg_info_t *info) {
+    if (!c || !info) return XDCG_INVALID_ARG;
+    *info = c->info;
+    return XDCG_OK;
+}
+
+xdcg_status xdcg_spmv(xdcg_ctx *c, int32_t precision, const void *x, void *y, double *xty) {
+    if (!c || !x || !y || x == y) return XDCG_INVALID_ARG;
+    if (precision == XDCG_MIXED && !c->mixed) return XDCG_INVALID_ARG;
+    init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
+    if (precision == XDCG_FP64)
+        launch_spmv<double>(c->L64.A, (const double *)x, (double *)y, nullptr, 0, c->partials,
+                            c->aux, kFinStore, 2, c->st);
+    else if (precision == XDCG_MIXED)
+        launch_spmv<float>(c->L32.A, (const float *)x, (float *)y, nullptr, 0, c->partials, c->aux,
+                           kFinStore, 2, c->st);
+    else
+        return XDCG_INVALID_ARG;
+    c->launches++;
+    CK(cudaGetLastError());
+    double v[3];
+    xdcg_status s = read_aux(c, v, 3);
+    if (s != XDCG_OK) return s;
+    if (xty) *xty = v[2];
+    return XDCG_OK;
+}
+
+xdcg_status xdcg_precond(xdcg_ctx *c, const double *r, double *z) {
+    if (!c || !r || !z || r == z) return XDCG_INVALID_ARG;
+    cudaStream_t st = c->st;
+    init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
+    CK(cudaMemcpyAsync(c->r64, r, c->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    launch_update<double>(c->L64.N, nullptr, c->r64, nullptr, nullptr, c->y64, 1, c->partials,
+                          c->aux, st);
+    launch_restrict<double>(c->L64.N, c->L64.B, c->r64, c->y64, 1, c->g, c->zr, st, c->aux);
+    launch_coarse(c->Einv, c->k, c->g, c->zr, c->nu, 0, c->partials, c->aux, st);
+    launch_prolong<double>(c->L64.N, c->nu, c->y64, z, 2, c->aux, st);
+    c->launches += 4;
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    return XDCG_OK;
+}
+
+xdcg_status xdcg_coarse_matrix(xdcg_ctx *c, double *E_host) {
+    if (!c || !E_host) return XDCG_INVALID_ARG;
+    CK(cudaMemcpyAsync(E_host, c->E, (size_t)c->k * c->k * sizeof(double),
+                       cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return XDCG_OK;
+}
+
+xdcg_status xdcg_destroy(xdcg_ctx *c) {
+    if (!c) return XDCG_INVALID_ARG;
+    cudaStreamSynchronize(c->st);
+    free_ctx(c);
+    return XDCG_OK;
+}
+
+const char *xdcg_status_string(xdcg_status s) {
+    switch (s) {
+        case XDCG_OK: return "ok";
+        case XDCG_INVALID_ARG: return "invalid argument";
+        case XDCG_NOT_SPD_BLOCK: return "node block not SPD";
+        case XDCG_COARSE_NOT_SPD: return "coarse matrix E not SPD";
+        case XDCG_BREAKDOWN: return "CG breakdown (p^T K p <= 0 or not finite)";
+        case XDCG_NO_CONVERGENCE: return "no convergence within max_iter";
+        case XDCG_CUDA_ERROR: return "CUDA error";
+        case XDCG_OOM: return "out of device memory";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,215 @@
+// Coarse level of the deflation (Section 3.2): W = K Z and E = Z^T K Z at
+// set-up, the FP64 inverse of E, and the per-iteration coarse solve
+// nu = E^-1 g that replaces the two solves of Algorithm 3 (their difference
+// lambda - mu = E^-1 (Z^T r - Z^T K y)) and the two of Algorithm 2.
+#include "reduce.cuh"
+
+namespace xdcg {
+
+// Row j of the deflation block of a node (b dofs, M = 6 or 12 columns):
+// standard dof a -> R row a (and H * R row a in the enriched columns), jump
+// dof a -> R row a in the enriched columns, branch dofs -> 0.
+__device__ __forceinline__ void z_row(int j, int b, int menr, double X, double Y, double Z,
+                                      double H, double (&o)[12]) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) o[c] = 0.0;
+    double r[6] = {0, 0, 0, 0, 0, 0};
+    const int a = (j < 3) ? j : j - 3;
+    if (j < 3 || (b == 6 && menr)) {
+        if (a == 0) { r[0] = 1.0; r[4] = Z; r[5] = -Y; }
+        if (a == 1) { r[1] = 1.0; r[3] = -Z; r[5] = X; }
+        if (a == 2) { r[2] = 1.0; r[3] = Y; r[4] = -X; }
+    } else {
+        return;
+    }
+    if (j < 3) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) o[c] = r[c];
+        if (menr) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) o[6 + c] = H * r[c];
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) o[6 + c] = r[c];
+    }
+}
+
+// W block of entry e (node I coupled to box s): W_Is = sum_{J in s} K_IJ Z_J.
+__global__ void k_build_W(KinDev K, int nExt, const int *extBox, const int *extNode,
+                          const long long *wOff, const int *sub, const double *xrel,
+                          const signed char *hsign, const int *menr, double *W) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nExt) return;
+    const int s = extBox[e], I = extNode[e];
+    const int M = menr[s] ? 12 : 6;
+    const int bI = K.dofStart[I + 1] - K.dofStart[I];
+    double acc[15 * 12];
+    for (int i = 0; i < bI * M; ++i) acc[i] = 0.0;
+    for (int p = K.rowPtr[I]; p < K.rowPtr[I + 1]; ++p) {
+        const int J = K.col[p];
+        if (sub[J] != s) continue;
+        const int bJ = K.dofStart[J + 1] - K.dofStart[J];
+        const double *Kb = K.val + K.valPtr[p];
+        const double X = xrel[3 * J], Y = xrel[3 * J + 1], Z = xrel[3 * J + 2];
+        const double H = (double)hsign[J];
+        for (int j = 0; j < bJ; ++j) {
+            double zr[12];
+            z_row(j, bJ, menr[s], X, Y, Z, H, zr);
+            for (int i = 0; i < bI; ++i) {
+                const double kij = Kb[i * bJ + j];
+                if (kij == 0.0) continue;
+                for (int c = 0; c < M; ++c) acc[i * M + c] += kij * zr[c];
+            }
+        }
+    }
+    double *Wb = W + wOff[e];
+    for (int i = 0; i < bI * M; ++i) Wb[i] = acc[i];
+}
+
+void launch_build_W(const KinDev &K, int nExt, const int *extBox, const int *extNode,
+                    const long long *wOff, const int *sub, const double *xrel,
+                    const signed char *hsign, const int *menr, double *W, cudaStream_t st) {
+    if (nExt == 0) return;
+    k_build_W<<<(nExt + 127) / 128, 128, 0, st>>>(K, nExt, extBox, extNode, wOff, sub, xrel,
+                                                   hsign, menr, W);
+}
+
+// E block (owner box t rows, box s columns) from one segment of box s's
+// W entries whose nodes belong to t: sum_I Z_It^T W_Is, summed in entry order.
+__global__ void k_build_E(const int *segBox, const int *segOwner, const int *segBegin,
+                          const int *segEnd, const int *extNode, const long long *wOff,
+                          const double *W, const int *dofStart, const double *xrel,
+                          const signed char *hsign, const int *col0, const int *menr, int k,
+                          double *E) {
+    const int g = blockIdx.x;
+    const int s = segBox[g], t = segOwner[g];
+    const int Ms = menr[s] ? 12 : 6, Mt = menr[t] ? 12 : 6;
+    const int a = threadIdx.x / 12, b = threadIdx.x % 12;
+    if (a >= Mt || b >= Ms) return;
+    double sum = 0.0;
+    for (int e = segBegin[g]; e < segEnd[g]; ++e) {
+        const int I = extNode[e];
+        const int bI = dofStart[I + 1] - dofStart[I];
+        const double *Wb = W + wOff[e];
+        const double X = xrel[3 * I], Y = xrel[3 * I + 1], Z = xrel[3 * I + 2];
+        const double H = (double)hsign[I];
+        for (int i = 0; i < bI; ++i) {
+            double zr[12];
+            z_row(i, bI, menr[t], X, Y, Z, H, zr);
+            sum += zr[a] * Wb[i * Ms + b];
+        }
+    }
+    E[(size_t)(col0[t] + a) * k + col0[s] + b] = sum;
+}
+
+void launch_build_E(int nSeg, const int *segBox, const int *segOwner, const int *segBegin,
+                    const int *segEnd, const int *extNode, const long long *wOff,
+                    const double *W, const int *dofStart, const double *xrel,
+                    const signed char *hsign, const int *col0, const int *menr, int k,
+                    double *E, cudaStream_t st) {
+    if (nSeg == 0) return;
+    k_build_E<<<nSeg, 144, 0, st>>>(segBox, segOwner, segBegin, segEnd, extNode, wOff, W,
+                                     dofStart, xrel, hsign, col0, menr, k, E);
+}
+
+__global__ void k_symmetrize(double *E, int k) {
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)k * k) return;
+    const int i = (int)(idx / k), j = (int)(idx % k);
+    if (j <= i) return;
+    const double v = 0.5 * (E[(size_t)i * k + j] + E[(size_t)j * k + i]);
+    E[(size_t)i * k + j] = v;
+    E[(size_t)j * k + i] = v;
+}
+
+void launch_symmetrize(double *E, int k, cudaStream_t st) {
+    const long long n = (long long)k * k;
+    k_symmetrize<<<(int)((n + 255) / 256), 256, 0, st>>>(E, k);
+}
+
+// In-place inversion of an SPD matrix by successive symmetric sweeps: after
+// sweeping every pivot the array holds -E^-1.  A pivot that is not larger
+// than thr (or not finite) marks the matrix as not SPD.
+__global__ void k_sweep_col(const double *A, int k, int j, double *c, int *bad, double thr) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k) return;
+    const double v = A[(size_t)i * k + j];
+    c[i] = v;
+    if (i == j && (!(v > thr) || !isfinite(v))) atomicMin(bad, j);
+}
+
+__global__ void k_sweep_update(double *A, int k, int j, const double *__restrict__ c) {
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)k * k) return;
+    const int i = (int)(idx / k), l = (int)(idx % k);
+    const double inv = 1.0 / c[j];
+    if (i == j && l == j)
+        A[idx] = -inv;
+    else if (i == j)
+        A[idx] = c[l] * inv;
+    else if (l == j)
+        A[idx] = c[i] * inv;
+    else
+        A[idx] -= (c[i] * c[l]) * inv;
+}
+
+__global__ void k_negate(double *A, long long n) {
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx < n) A[idx] = -A[idx];
+}
+
+void launch_sweep_inverse(double *A, int k, double *colbuf, int *bad, double thr,
+                          cudaStream_t st) {
+    const long long n = (long long)k * k;
+    const int gridN = (int)((n + 255) / 256), gridK = (k + 255) / 256;
+    for (int j = 0; j < k; ++j) {
+        k_sweep_col<<<gridK, 256, 0, st>>>(A, k, j, colbuf, bad, thr);
+        k_sweep_update<<<gridN, 256, 0, st>>>(A, k, j, colbuf);
+    }
+    k_negate<<<gridN, 256, 0, st>>>(A, n);
+}
+
+// ---- per-iteration coarse solve -------------------------------------------
+
+// nu = E^-1 g, one warp per row.  mode 0: nothing else (Algorithm 2);
+// mode 1: rho = r^T y + nu^T (Z^T r), beta = 0 (start); mode 2: the same
+// rho_new, beta = rho_new / rho, rho = rho_new (iteration).
+__global__ void __launch_bounds__(kThreads)
+k_coarse(const double *__restrict__ Einv, int k, const double *__restrict__ g,
+         const double *__restrict__ zr, double *nu, int mode, double *partials, Scalars *sc) {
+    if (sc->done != kRunning) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kWarps + warp;
+    double part[1] = {0.0};
+    if (i < k) {
+        const double *row = Einv + (size_t)i * k;
+        double s = 0.0;
+        for (int j = lane; j < k; j += 32) s = fma(row[j], __ldg(g + j), s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            nu[i] = s;
+            if (mode != 0) part[0] = s * zr[i];
+        }
+    }
+    double tot[1];
+    if (grid_sum<1>(part, partials, &sc->ticket[3], tot) && threadIdx.x == 0) {
+        if (mode == 1) {
+            sc->rho = sc->ry + tot[0];
+            sc->beta = 0.0;
+        } else if (mode == 2) {
+            const double rho_new = sc->ry + tot[0];
+            sc->beta = rho_new / sc->rho;
+            sc->rho = rho_new;
+        }
+    }
+}
+
+void launch_coarse(const double *Einv, int k, const double *g, const double *zr, double *nu,
+                   int mode, double *partials, Scalars *sc, cudaStream_t st) {
+    const int grid = (k + kWarps - 1) / kWarps;
+    k_coarse<<<grid > 0 ? grid : 1, kThreads, 0, st>>>(Einv, k, g, zr, nu, mode, partials, sc);
+}
+
+}  // namespace xdcg

@@ -1,0 +1,149 @@
+// Internal declarations of the xdcg library: device layouts, the per-solve
+// scalar block, and the kernel launchers shared by the translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "xdcg.h"
+
+namespace xdcg {
+
+constexpr int kThreads = 256;      // threads per block of the streaming kernels
+constexpr int kWarps = kThreads / 32;
+
+// done flags written by the kernels
+enum : int { kRunning = 0, kConverged = 1, kBreakdown = 2, kMaxIter = 3 };
+
+// what the last block of a reduction does with the reduced value(s)
+enum Fin : int {
+    kFinAlpha = 0,   // value = p^T q: alpha = rho / pq, its += 1, breakdown test
+    kFinRR = 1,      // value = ||r||^2: store rr, converged test against tol2ff
+    kFinStore = 2,   // value stored into scratch[slot]
+};
+
+// Scalars of one CG run, in device memory.  Written only by the last block
+// of a reduction kernel (single writer), read by all later kernels.
+struct Scalars {
+    double rho;       // r^T z
+    double pq;        // p^T K p
+    double alpha, beta;
+    double rr;        // ||r||^2
+    double ry;        // r^T y, y = M^-1 r
+    double tol2ff;    // tol^2 ||f||^2
+    double scratch[4];
+    int its;          // loop bodies run
+    int done;         // kRunning / kConverged / kBreakdown / kMaxIter
+    int max_it;
+    int pad;
+    unsigned int ticket[4];   // last-block tickets, reset by the last block
+};
+
+// Chunked 3x3 BSR over the chunk rows (3 consecutive dofs).  Rows whose
+// blocks all couple standard dofs of standard nodes ("S" rows) use a
+// sliced-ELL layout, one thread per row, 32 rows per slice, slot-major with
+// the 9 values of a slot stored as 9 separate 32-wide runs.  The remaining
+// rows ("X": enriched chunks and standard chunks next to enriched nodes)
+// use one warp per row, lanes over the row's blocks, blocks in groups of 32
+// laid out the same way.
+template <typename T>
+struct SpmvDev {
+    int nS, nSlices;
+    const int *rowS;          // [nS] chunk row
+    const int *lenS;          // [nS] blocks in the row
+    const long long *slicePtr;// [nSlices] first slot of the slice
+    const int *colS;          // [slots] chunk column
+    const T *valS;            // [9 slots]
+    int nX;
+    const int *rowX;          // [nX]
+    const int *lenX;          // [nX]
+    const long long *ptrX;    // [nX] first slot (multiple of 32)
+    const int *colX;
+    const T *valX;
+};
+
+// Node-level data: node lists per block size, packed Cholesky factors of
+// the node blocks (lower triangle row by row, the diagonal stored as its
+// reciprocal), stored structure-of-arrays: entry e of node t of a list at
+// L[e * count + t].
+template <typename T>
+struct NodeDev {
+    int nNodes;
+    int nStd, nH, nT;
+    const int *stdNodes, *hNodes, *tNodes;
+    const int *dofStart;      // [nNodes + 1]
+    const T *Lstd, *Lh, *Lt;  // 6 / 21 / 120 entries per node
+    const int *sub;           // [nNodes] box of each node
+    const T *xrel;            // [3 nNodes] coordinates relative to the box centre
+    const signed char *hsign; // [nNodes]
+    const int *col0;          // [nBox] first coarse column of each box
+    const int *menr;          // [nBox] 1 if the box carries enriched modes
+};
+
+// Box-level data for the restriction g = Z^T a - W^T b.
+template <typename T>
+struct BoxDev {
+    int nBox;
+    const int *ownPtr, *ownNodes;   // nodes of each box
+    const int *extPtr, *extNode;    // nodes coupled to each box (W rows)
+    const long long *wOff;          // offset of each W block (b_I x m_s, row-major)
+    const T *W;
+};
+
+// ---- launchers (defined in the .cu files) --------------------------------
+
+template <typename T>
+void launch_spmv(const SpmvDev<T> &A, const T *x, T *y, const T *b, int residual_mode,
+                 double *partials, Scalars *sc, int fin, int slot, cudaStream_t st);
+int spmv_grid(int nSlices, int nX);
+
+template <typename T>
+void launch_update(const NodeDev<T> &N, T *u, T *r, const T *p, const T *q, T *y, int mode,
+                   double *partials, Scalars *sc, cudaStream_t st);
+
+template <typename T>
+void launch_restrict(const NodeDev<T> &N, const BoxDev<T> &B, const T *a, const T *b, int withW,
+                     double *g, double *zr, cudaStream_t st, const Scalars *sc);
+
+void launch_coarse(const double *Einv, int k, const double *g, const double *zr, double *nu,
+                   int mode, double *partials, Scalars *sc, cudaStream_t st);
+
+template <typename T>
+void launch_prolong(const NodeDev<T> &N, const double *nu, const T *y, T *p, int mode,
+                    Scalars *sc, cudaStream_t st);
+
+template <typename T>
+void launch_dot(const T *a, const T *b, long long n, double *partials, Scalars *sc, int fin,
+                int slot, cudaStream_t st);
+
+// mixed precision helpers
+void launch_scale_to_f32(const double *r64, float *r32, long long n, double s, cudaStream_t st);
+void launch_accumulate_f64(double *u64, const float *d32, long long n, double s, cudaStream_t st);
+
+// ---- set-up kernels -------------------------------------------------------
+
+struct KinDev {   // node-blocked input matrix on the device (FP64)
+    int nNodes;
+    const int *dofStart, *rowPtr, *col;
+    const long long *valPtr;
+    const double *val;
+};
+
+int launch_block_cholesky(int B, int count, const int *nodes, const double *Dsoa, double *L64,
+                          float *L32, int *bad, cudaStream_t st);
+void launch_xrel(int nNodes, const double *coords, const double *centre, const int *sub,
+                 double *x64, float *x32, cudaStream_t st);
+void launch_build_W(const KinDev &K, int nExt, const int *extBox, const int *extNode,
+                    const long long *wOff, const int *sub, const double *xrel,
+                    const signed char *hsign, const int *menr, double *W, cudaStream_t st);
+void launch_build_E(int nSeg, const int *segBox, const int *segOwner, const int *segBegin,
+                    const int *segEnd, const int *extNode, const long long *wOff,
+                    const double *W, const int *dofStart, const double *xrel,
+                    const signed char *hsign, const int *col0, const int *menr, int k,
+                    double *E, cudaStream_t st);
+void launch_symmetrize(double *E, int k, cudaStream_t st);
+void launch_sweep_inverse(double *A, int k, double *colbuf, int *bad, double thr,
+                          cudaStream_t st);
+void launch_cast_f32(const double *a, float *b, long long n, cudaStream_t st);
+
+}  // namespace xdcg

@@ -1,0 +1,89 @@
+// Deterministic warp / block / grid reductions.  Every block stores its
+// partial sums; the last block to finish (ticket counter) adds them in a
+// fixed order, so results do not depend on block scheduling.
+#pragma once
+
+#include "internal.h"
+
+namespace xdcg {
+
+template <int NV>
+__device__ __forceinline__ void warp_sum(double (&v)[NV]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    }
+}
+
+// Sum over the block; the result is valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+    __shared__ double sm[NV][32];
+    warp_sum<NV>(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) sm[i][w] = v[i];
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] = (l < nw) ? sm[i][l] : 0.0;
+        warp_sum<NV>(v);
+    }
+}
+
+// Grid-wide sum.  Returns true in exactly one block (the last to finish),
+// where thread 0 then holds the totals in tot.  partials: NV * gridDim.x doubles.
+template <int NV>
+__device__ __forceinline__ bool grid_sum(double (&v)[NV], double *partials, unsigned int *ticket,
+                                         double (&tot)[NV]) {
+    __shared__ bool last;
+    block_sum<NV>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) partials[(size_t)i * gridDim.x + blockIdx.x] = v[i];
+        __threadfence();
+        unsigned int t = atomicAdd(ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double s[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) s[i] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) s[i] += __ldcg(partials + (size_t)i * gridDim.x + b);
+    }
+    block_sum<NV>(s);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) tot[i] = s[i];
+        *ticket = 0u;
+    }
+    return true;
+}
+
+// Shared last-block actions on the scalar block.
+__device__ __forceinline__ void finalize(Scalars *sc, int fin, int slot, double val) {
+    if (fin == kFinAlpha) {
+        sc->pq = val;
+        sc->its += 1;
+        if (!(val > 0.0) || !isfinite(val)) {
+            sc->done = kBreakdown;
+        } else {
+            sc->alpha = sc->rho / val;
+        }
+    } else if (fin == kFinRR) {
+        sc->rr = val;
+        if (val <= sc->tol2ff) sc->done = kConverged;
+    } else {
+        sc->scratch[slot] = val;
+    }
+}
+
+}  // namespace xdcg

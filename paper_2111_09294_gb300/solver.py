@@ -1,0 +1,132 @@
+"""Python front end of the xdcg library: Solver(K, Z).solve(f, tol) -> u, info.
+
+Device memory and streams come from PyTorch; all arithmetic runs in the CUDA
+library behind the C ABI (include/xdcg.h).
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(np.asarray(a), dtype=dtype)
+
+
+class Solver:
+    """Adapted deflated CG (A-DEF2 + node-block Jacobi) for one stiffness matrix.
+
+    K: node-blocked CSR arrays (dof_ptr, row_ptr, col, val_ptr, val) in host memory;
+    Z: box subdomains (sub_of_node, coords, hsign, centres).
+    precision: "fp64" or "mixed" (FP32 inner PCG inside FP64 iterative refinement).
+    """
+
+    def __init__(self, dof_ptr, row_ptr, col, val_ptr, val, sub_of_node, coords, hsign, centres,
+                 precision="fp64", tol=1e-8, max_iter=10000, inner_tol=1e-5, max_outer=30,
+                 time_spmv=False, enriched_modes=True, stream=None):
+        lib = L.load()
+        self._lib = lib
+        self.ctx = ctypes.c_void_p()
+        keep = [_host(dof_ptr, np.int32), _host(row_ptr, np.int32), _host(col, np.int32),
+                _host(val_ptr, np.int64), _host(val, np.float64), _host(sub_of_node, np.int32),
+                _host(coords, np.float64).reshape(-1), _host(hsign, np.int8),
+                _host(centres, np.float64).reshape(-1)]
+        n_nodes = keep[0].size - 1
+        n_sub = keep[8].size // 3
+        m = L.Matrix(n_nodes, keep[0].ctypes.data, keep[1].ctypes.data, keep[2].ctypes.data,
+                     keep[3].ctypes.data, keep[4].ctypes.data, L.XDCG_HOST)
+        z = L.Deflation(n_sub, keep[5].ctypes.data, keep[6].ctypes.data, keep[7].ctypes.data,
+                        keep[8].ctypes.data, int(bool(enriched_modes)), L.XDCG_HOST)
+        opt = L.Options()
+        lib.xdcg_default_options(ctypes.byref(opt))
+        opt.tol = tol
+        opt.max_iter = max_iter
+        opt.precision = L.XDCG_MIXED if precision == "mixed" else L.XDCG_FP64
+        opt.inner_tol = inner_tol
+        opt.max_outer = max_outer
+        opt.time_spmv = int(bool(time_spmv))
+        self.precision = precision
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        st = L.check(lib.xdcg_setup(ctypes.byref(self.ctx), ctypes.byref(m), ctypes.byref(z),
+                                    None, ctypes.byref(opt), ctypes.c_void_p(stream.cuda_stream)),
+                     "xdcg_setup")
+        info = L.Info()
+        L.check(lib.xdcg_get_info(self.ctx, ctypes.byref(info)), "xdcg_get_info")
+        self.info = info.as_dict()
+        self.n = int(info.n)
+        self.k = int(info.k)
+
+    @classmethod
+    def from_problem(cls, P, **kw):
+        return cls(P.dof_ptr, P.row_ptr, P.col, P.val_ptr, P.val, P.sub_of_node, P.coords,
+                   P.hsign, P.centres, **kw)
+
+    def _dev(self, t, dtype):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype
+                and t.is_contiguous() and t.numel() == self.n):
+            raise ValueError(f"expected a contiguous CUDA {dtype} tensor of {self.n} entries")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def solve(self, f, tol=0.0, out=None, raise_on_error=True):
+        """u with K u = f; f: CUDA float64 tensor.  Returns (u, info dict)."""
+        u = out if out is not None else torch.empty_like(f)
+        res = L.Result()
+        s = self._lib.xdcg_solve(self.ctx, self._dev(f, torch.float64),
+                                 self._dev(u, torch.float64), float(tol), ctypes.byref(res))
+        info = res.as_dict()
+        info["status"] = L.STATUS.get(s, s)
+        if raise_on_error:
+            L.check(s, "xdcg_solve", res.bad_index)
+        return u, info
+
+    def solve_host(self, f_host, u_host, tol=0.0):
+        """Host-memory solve (copies inside the call); f_host, u_host: float64 arrays
+        or pinned CPU tensors of n entries."""
+        def ptr(a):
+            if isinstance(a, torch.Tensor):
+                assert a.dtype == torch.float64 and not a.is_cuda and a.numel() == self.n
+                return ctypes.c_void_p(a.data_ptr())
+            assert a.dtype == np.float64 and a.size == self.n and a.flags.c_contiguous
+            return ctypes.c_void_p(a.ctypes.data)
+        res = L.Result()
+        L.check(self._lib.xdcg_solve_host(self.ctx, ptr(f_host), ptr(u_host), float(tol),
+                                          ctypes.byref(res)), "xdcg_solve_host", res.bad_index)
+        return res.as_dict()
+
+    def spmv(self, x, precision="fp64"):
+        """y = K x; returns (y, x^T y)."""
+        dt = torch.float64 if precision == "fp64" else torch.float32
+        y = torch.empty_like(x)
+        xty = ctypes.c_double()
+        L.check(self._lib.xdcg_spmv(self.ctx, L.XDCG_FP64 if precision == "fp64" else L.XDCG_MIXED,
+                                    self._dev(x, dt), self._dev(y, dt), ctypes.byref(xty)),
+                "xdcg_spmv")
+        return y, xty.value
+
+    def precond(self, r):
+        """z = A-DEF2 preconditioner applied to r (FP64)."""
+        z = torch.empty_like(r)
+        L.check(self._lib.xdcg_precond(self.ctx, self._dev(r, torch.float64),
+                                       self._dev(z, torch.float64)), "xdcg_precond")
+        return z
+
+    def coarse_matrix(self):
+        E = np.empty((self.k, self.k))
+        L.check(self._lib.xdcg_coarse_matrix(self.ctx, ctypes.c_void_p(E.ctypes.data)),
+                "xdcg_coarse_matrix")
+        return E
+
+    def close(self):
+        if self.ctx:
+            self._lib.xdcg_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
