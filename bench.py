@@ -304,6 +304,27 @@ def run_ours(args):
     print(json.dumps(out))
 
 
+def run_profile(args):
+    """One solve bracketed by cudaProfilerStart/Stop (for ncu --profile-from-start off)."""
+    import torch
+    import xfem_inputs as X
+    from paper_2111_09294_gb300 import Solver
+    P = X.make(args.workload)
+    s = Solver.from_problem(P, precision=args.profile, inner_tol=args.inner_tol)
+    f = torch.tensor(P.f, device="cuda")
+    u = torch.empty_like(f)
+    for _ in range(max(args.warmup, 1)):
+        s.solve(f, tol=TOL, out=u)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    _, info = s.solve(f, tol=TOL, out=u)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"profile": args.profile, "iterations": info["iterations"],
+                      "outer_cycles": info["outer_cycles"], "launches": info["n_launches"],
+                      "t_solve_ms": info["t_solve_ms"], "info": s.info}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -314,8 +335,13 @@ def main():
     ap.add_argument("--inner-tol", type=float, default=1e-5)
     ap.add_argument("--sample-iters", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", choices=["mixed", "fp64"], default=None,
+                    help="profiler capture: one solve of the given path between "
+                         "cudaProfilerStart/Stop after warm-up, nothing else timed")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -40,9 +40,9 @@ typedef enum {
     XDCG_OK = 0,
     XDCG_INVALID_ARG = 1,      /* bad pointer, size, index, pattern or option */
     XDCG_NOT_SPD_BLOCK = 2,    /* a node block failed its Cholesky factorisation;
-                                  result.bad_index names the node */
+                                  xdcg_setup's bad_index names the node */
     XDCG_COARSE_NOT_SPD = 3,   /* E = Z^T K Z failed its factorisation;
-                                  result.bad_index names the coarse pivot */
+                                  xdcg_setup's bad_index names the coarse pivot */
     XDCG_BREAKDOWN = 4,        /* p^T K p <= 0 or not finite during the iteration */
     XDCG_NO_CONVERGENCE = 5,   /* max_iter reached; u holds the last iterate */
     XDCG_CUDA_ERROR = 6,       /* a CUDA runtime call failed */
@@ -129,9 +129,12 @@ xdcg_status xdcg_default_options(xdcg_options *opt);
  * out for the SpMV (FP64 and, for MIXED, FP32 copies), factor the node
  * blocks (FP64 Cholesky), build Z, W = K Z and E = Z^T K Z, and invert E in
  * FP64.  stream: a cudaStream_t (NULL = legacy default stream).  blocks must
- * be NULL (one block per node).  On error *out is NULL. */
+ * be NULL (one block per node).  On error *out is NULL and, if bad_index is
+ * not NULL, *bad_index names the failing node (XDCG_NOT_SPD_BLOCK) or coarse
+ * pivot (XDCG_COARSE_NOT_SPD), else -1. */
 xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflation *Z,
-                       const void *blocks, const xdcg_options *opt, void *stream);
+                       const void *blocks, const xdcg_options *opt, void *stream,
+                       int32_t *bad_index);
 
 /* Solve K u = f with the options given at set-up, tol overriding opt.tol
  * when > 0.  f, u: caller-owned device arrays of n doubles (may not alias).
@@ -145,9 +148,12 @@ xdcg_status xdcg_solve_host(xdcg_ctx *ctx, const double *f_host, double *u_host,
 
 xdcg_status xdcg_get_info(const xdcg_ctx *ctx, xdcg_info_t *info);
 
-/* y = K x in the given precision (XDCG_FP64: double arrays; XDCG_MIXED:
- * float arrays, FP32 values and accumulation).  x, y: device, length n.
- * If xty is not NULL it receives x^T y (FP64 reduction) on the host. */
+/* The operator of one solve path applied to x.  XDCG_FP64: y = K x with
+ * double arrays.  XDCG_MIXED: y = K~ x with float arrays, where
+ * K~ = L^-1 K L^-T is the block-scaled matrix of the FP32 inner solve (L the
+ * FP64 Cholesky factors of the node blocks), stored and accumulated in FP32.
+ * x, y: device, length n.  If xty is not NULL it receives x^T y (FP64
+ * reduction) on the host. */
 xdcg_status xdcg_spmv(xdcg_ctx *ctx, int32_t precision, const void *x, void *y, double *xty);
 
 /* z = A-DEF2 preconditioner applied to r (Algorithm 3, one merged coarse

@@ -74,7 +74,7 @@ def load():
     lib = ctypes.CDLL(LIB_PATH)
     lib.xdcg_default_options.argtypes = [POINTER(Options)]
     lib.xdcg_setup.argtypes = [POINTER(c_void_p), POINTER(Matrix), POINTER(Deflation), c_void_p,
-                               POINTER(Options), c_void_p]
+                               POINTER(Options), c_void_p, POINTER(c_int32)]
     lib.xdcg_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_double, POINTER(Result)]
     lib.xdcg_solve_host.argtypes = [c_void_p, c_void_p, c_void_p, c_double, POINTER(Result)]
     lib.xdcg_get_info.argtypes = [c_void_p, POINTER(Info)]

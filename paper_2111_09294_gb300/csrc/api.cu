@@ -24,10 +24,10 @@ struct Level64 {
     NodeDev<double> N;
     BoxDev<double> B;
 };
-struct Level32 {
+struct Level32 {          // block-scaled system K~ = L^-1 K L^-T in FP32
     SpmvDev<float> A;
-    NodeDev<float> N;
-    BoxDev<float> B;
+    ScaledDev D;
+    FacDev F;
 };
 
 }  // namespace
@@ -173,21 +173,60 @@ xdcg_status map_done(int done) {
 
 // ---- one preconditioned CG run (Algorithms 1-3) ----------------------------
 
-template <typename T, typename LV>
-xdcg_status run_pcg(xdcg_ctx *c, LV &L, const T *f, T *u, T *r, T *p, T *q, T *y, Scalars *sc,
-                    int max_it, bool time_spmv, int *its_out, int *done_out, double *t_spmv,
-                    int *n_spmv) {
+// Unscaled path: block-Jacobi applied by the node-block factors, Z from
+// coordinates.  Used in FP64.
+struct PlainPath {
+    xdcg_ctx *c;
+    Level64 &L;
+    void spmv(const double *x, double *y, const double *b, int res, int fin, Scalars *sc) {
+        launch_spmv<double>(L.A, x, y, b, res, c->partials, sc, fin, 0, c->st);
+    }
+    void update(double *u, double *r, const double *p, const double *q, double *y, int mode,
+                Scalars *sc) {
+        launch_update<double>(L.N, u, r, p, q, y, mode, c->partials, sc, c->st);
+    }
+    void restrict_(const double *a, const double *b, int withW, double *zr, Scalars *sc) {
+        launch_restrict<double>(L.N, L.B, a, b, withW, c->g, zr, c->st, sc);
+    }
+    void prolong(const double *y, double *p, int mode, Scalars *sc) {
+        launch_prolong<double>(L.N, c->nu, y, p, mode, sc, c->st);
+    }
+};
+
+// Block-scaled FP32 path: identity preconditioner (y = r), explicit Z~, W~.
+struct ScaledPath {
+    xdcg_ctx *c;
+    Level32 &L;
+    void spmv(const float *x, float *y, const float *b, int res, int fin, Scalars *sc) {
+        launch_spmv<float>(L.A, x, y, b, res, c->partials, sc, fin, 0, c->st);
+    }
+    void update(float *u, float *r, const float *p, const float *q, float *, int mode,
+                Scalars *sc) {
+        launch_update_id(u, r, p, q, c->n, mode, c->partials, sc, c->st);
+    }
+    void restrict_(const float *a, const float *b, int withW, double *zr, Scalars *sc) {
+        launch_restrict_z(L.D, a, b, withW, c->g, zr, sc, c->st);
+    }
+    void prolong(const float *y, float *p, int mode, Scalars *sc) {
+        launch_prolong_z(L.D, c->nu, y, p, mode, sc, c->st);
+    }
+};
+
+template <typename T, typename Path>
+xdcg_status run_pcg(xdcg_ctx *c, Path path, const T *f, T *u, T *r, T *p, T *q, T *y,
+                    Scalars *sc, int max_it, bool time_spmv, int *its_out, int *done_out,
+                    double *t_spmv, int *n_spmv) {
     cudaStream_t st = c->st;
     // Algorithm 2 with u_-1 = 0: u_0 = Z E^-1 Z^T f
-    launch_restrict<T>(L.N, L.B, f, nullptr, 0, c->g, nullptr, st, sc);
+    path.restrict_(f, nullptr, 0, nullptr, sc);
     launch_coarse(c->Einv, c->k, c->g, nullptr, c->nu, 0, c->partials, sc, st);
-    launch_prolong<T>(L.N, c->nu, nullptr, u, 1, sc, st);
+    path.prolong(nullptr, u, 1, sc);
     // r_0 = f - K u_0, z_0 by Algorithm 3, p_0 = z_0
-    launch_spmv<T>(L.A, u, r, f, 1, c->partials, sc, kFinRR, 0, st);
-    launch_update<T>(L.N, u, r, nullptr, nullptr, y, 1, c->partials, sc, st);
-    launch_restrict<T>(L.N, L.B, r, y, 1, c->g, c->zr, st, sc);
+    path.spmv(u, r, f, 1, kFinRR, sc);
+    path.update(u, r, nullptr, nullptr, y, 1, sc);
+    path.restrict_(r, y, 1, c->zr, sc);
     launch_coarse(c->Einv, c->k, c->g, c->zr, c->nu, 1, c->partials, sc, st);
-    launch_prolong<T>(L.N, c->nu, y, p, 2, sc, st);
+    path.prolong(y, p, 2, sc);
     c->launches += 8;
 
     int launched = 0;
@@ -204,12 +243,12 @@ xdcg_status run_pcg(xdcg_ctx *c, LV &L, const T *f, T *u, T *r, T *p, T *q, T *y
                 }
                 CK(cudaEventRecord(c->evS[launched], st));
             }
-            launch_spmv<T>(L.A, p, q, nullptr, 0, c->partials, sc, kFinAlpha, 0, st);
+            path.spmv(p, q, nullptr, 0, kFinAlpha, sc);
             if (time_spmv) CK(cudaEventRecord(c->evE[launched], st));
-            launch_update<T>(L.N, u, r, p, q, y, 0, c->partials, sc, st);
-            launch_restrict<T>(L.N, L.B, r, y, 1, c->g, c->zr, st, sc);
+            path.update(u, r, p, q, y, 0, sc);
+            path.restrict_(r, y, 1, c->zr, sc);
             launch_coarse(c->Einv, c->k, c->g, c->zr, c->nu, 2, c->partials, sc, st);
-            launch_prolong<T>(L.N, c->nu, y, p, 0, sc, st);
+            path.prolong(y, p, 0, sc);
             c->launches += 5;
             ++launched;
         }
@@ -251,9 +290,9 @@ xdcg_status solve_fp64(xdcg_ctx *c, const double *f, double *u, double tol, xdcg
     init_scalars(c, c->sc, tol * tol, &c->aux->scratch[0], c->opt.max_iter);
     c->launches += 1;
     int its = 0, done = 0;
-    xdcg_status s = run_pcg<double>(c, c->L64, f, u, c->r64, c->p64, c->q64, c->y64, c->sc,
-                                    c->opt.max_iter, c->opt.time_spmv != 0, &its, &done,
-                                    &res->t_spmv_ms, &res->n_spmv_timed);
+    xdcg_status s = run_pcg<double>(c, PlainPath{c, c->L64}, f, u, c->r64, c->p64, c->q64,
+                                    c->y64, c->sc, c->opt.max_iter, c->opt.time_spmv != 0, &its,
+                                    &done, &res->t_spmv_ms, &res->n_spmv_timed);
     if (s != XDCG_OK) return s;
     const double rr = c->h_sc->rr;
     // true residual f - K u in FP64
@@ -288,21 +327,22 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, xdc
         if (ff == 0.0 || rn2 <= tol * tol * ff) { status = XDCG_OK; break; }
         if (cycles >= c->opt.max_outer || total >= c->opt.max_iter) break;
         const double rn = std::sqrt(rn2);
-        launch_scale_to_f32(c->r64, c->f32, c->n, 1.0 / rn, st);
+        // scaled inner right-hand side f~ = L^-1 r / ||r||
+        launch_fwd_scale(c->nNodes, c->L32.D.dofStart, c->L32.F, c->r64, 1.0 / rn, c->f32, st);
         init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
         launch_dot<float>(c->f32, c->f32, c->n, c->partials, c->aux, kFinStore, 0, st);
         const double eta = c->opt.inner_tol;
         init_scalars(c, c->sc32, eta * eta, &c->aux->scratch[0], c->opt.max_iter - total);
-        c->launches += 2;
+        c->launches += 3;
         int its = 0, done = 0;
-        s = run_pcg<float>(c, c->L32, c->f32, c->u32, c->r32, c->p32, c->q32, c->y32, c->sc32,
-                           c->opt.max_iter - total, c->opt.time_spmv != 0, &its, &done,
-                           &res->t_spmv_ms, &res->n_spmv_timed);
+        s = run_pcg<float>(c, ScaledPath{c, c->L32}, c->f32, c->u32, c->r32, c->p32, c->q32,
+                           c->r32, c->sc32, c->opt.max_iter - total, c->opt.time_spmv != 0, &its,
+                           &done, &res->t_spmv_ms, &res->n_spmv_timed);
         if (s != XDCG_OK) return s;
         total += its;
         cycles++;
         last_inner_rel = std::sqrt(c->h_sc->rr);
-        launch_accumulate_f64(u, c->u32, c->n, rn, st);
+        launch_bwd_accum(c->nNodes, c->L32.D.dofStart, c->L32.F, c->u32, rn, u, st);
         init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
         launch_spmv<double>(c->L64.A, u, c->r64, f, 1, c->partials, c->aux, kFinStore, 0, st);
         c->launches += 3;
@@ -474,10 +514,10 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
             const int J = col[p];
             const int bJ = kindb[J];
             for (int cj = 0; cj < bJ / 3; ++cj, ++t) {
-                double blk[9];
+                int blk[9];   // positions of the 3x3 block's entries in val
                 for (int a = 0; a < 3; ++a)
                     for (int b2 = 0; b2 < 3; ++b2)
-                        blk[a * 3 + b2] = val[vptr[p] + (3 * ci + a) * bJ + 3 * cj + b2];
+                        blk[a * 3 + b2] = (int)(vptr[p] + (3 * ci + a) * bJ + 3 * cj + b2);
                 fn(t, dof[J] / 3 + cj, blk);
             }
         }
@@ -492,7 +532,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         slicePtr[s + 1] = slicePtr[s] + 32LL * mx;
     }
     std::vector<int> colS(slicePtr[nSlices]);
-    std::vector<double> valS(9 * (size_t)slicePtr[nSlices], 0.0);
+    std::vector<int> srcS(9 * (size_t)slicePtr[nSlices], -1);
     for (int s = 0; s < nSlices; ++s)
         for (int l = 0; l < 32 && s * 32 + l < nS; ++l) {
             const int r = sRows[s * 32 + l];
@@ -500,9 +540,9 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
             const long long base = slicePtr[s];
             const long long slots = (slicePtr[s + 1] - base) / 32;
             for (long long j = 0; j < slots; ++j) colS[base + j * 32 + l] = r;
-            for_blocks(r, [&](int t, int cc, const double *blk) {
+            for_blocks(r, [&](int t, int cc, const int *blk) {
                 colS[base + (long long)t * 32 + l] = cc;
-                for (int e = 0; e < 9; ++e) valS[9 * base + ((long long)t * 9 + e) * 32 + l] = blk[e];
+                for (int e = 0; e < 9; ++e) srcS[9 * base + ((long long)t * 9 + e) * 32 + l] = blk[e];
             });
         }
     const int nX = (int)xRows.size();
@@ -513,15 +553,15 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         ptrX[i + 1] = ptrX[i] + 32LL * ((lenX[i] + 31) / 32);
     }
     std::vector<int> colX(std::max<long long>(ptrX[nX], 1), 0);
-    std::vector<double> valX(9 * (size_t)std::max<long long>(ptrX[nX], 1), 0.0);
+    std::vector<int> srcX(9 * (size_t)std::max<long long>(ptrX[nX], 1), -1);
     for (int i = 0; i < nX; ++i) {
         const int r = xRows[i];
         const long long base = ptrX[i];
         for (long long t = 0; t < ptrX[i + 1] - base; ++t) colX[base + t] = r;
-        for_blocks(r, [&](int t, int cc, const double *blk) {
+        for_blocks(r, [&](int t, int cc, const int *blk) {
             colX[base + t] = cc;
             for (int e = 0; e < 9; ++e)
-                valX[9 * base + 288LL * (t >> 5) + 32 * e + (t & 31)] = blk[e];
+                srcX[9 * base + 288LL * (t >> 5) + 32 * e + (t & 31)] = blk[e];
         });
     }
     long long nnzb3 = 0;
@@ -617,15 +657,24 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     int *d_col0 = upload(c, col0);
     int *d_menr = upload(c, menr);
     double *d_x64 = dalloc<double>(c, 3 * (size_t)N);
-    float *d_x32 = mixed ? dalloc<float>(c, 3 * (size_t)N) : nullptr;
-    if (!d_dof || !d_sub || !d_hs || !d_col0 || !d_menr || !d_x64 || (mixed && !d_x32))
-        return XDCG_OOM;
+    if (!d_dof || !d_sub || !d_hs || !d_col0 || !d_menr || !d_x64) return XDCG_OOM;
     {
         double *d_coords = upload_tmp(c, coords), *d_centre = upload_tmp(c, centre);
         if (!d_coords || !d_centre) return XDCG_OOM;
-        launch_xrel(N, d_coords, d_centre, d_sub, d_x64, d_x32, st);
+        launch_xrel(N, d_coords, d_centre, d_sub, d_x64, nullptr, st);
     }
-    // SpMV layouts
+    KinDev kin;   // the input matrix on the device, for the set-up kernels
+    kin.nNodes = N;
+    kin.dofStart = d_dof;
+    kin.rowPtr = upload_tmp(c, rowp);
+    kin.col = upload_tmp(c, col);
+    kin.valPtr = upload_tmp(c, vptr);
+    double *d_val = upload_tmp(c, val);
+    kin.val = d_val;
+    if (!kin.rowPtr || !kin.col || !kin.valPtr || !kin.val) return XDCG_OOM;
+    // SpMV layouts: values gathered on the device through the index maps
+    int *d_srcS = upload_tmp(c, srcS), *d_srcX = upload_tmp(c, srcX);
+    if (!d_srcS || !d_srcX) return XDCG_OOM;
     auto &A = c->L64.A;
     A.nS = nS;
     A.nSlices = nSlices;
@@ -633,31 +682,22 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     A.lenS = upload(c, lenS);
     A.slicePtr = upload(c, slicePtr);
     A.colS = upload(c, colS);
-    double *d_valS = upload(c, valS);
+    double *d_valS = dalloc<double>(c, srcS.size());
     A.valS = d_valS;
     A.nX = nX;
     A.rowX = upload(c, xRows);
     A.lenX = upload(c, lenX);
     A.ptrX = upload(c, ptrX);
     A.colX = upload(c, colX);
-    double *d_valX = upload(c, valX);
+    double *d_valX = dalloc<double>(c, srcX.size());
     A.valX = d_valX;
     if (!A.rowS || !A.lenS || !A.slicePtr || !A.colS || !A.valS || !A.rowX || !A.lenX ||
         !A.ptrX || !A.colX || !A.valX)
         return XDCG_OOM;
-    if (mixed) {
-        auto &A2 = c->L32.A;
-        A2.nS = nS; A2.nSlices = nSlices; A2.rowS = A.rowS; A2.lenS = A.lenS;
-        A2.slicePtr = A.slicePtr; A2.colS = A.colS;
-        A2.nX = nX; A2.rowX = A.rowX; A2.lenX = A.lenX; A2.ptrX = A.ptrX; A2.colX = A.colX;
-        float *v32S = dalloc<float>(c, valS.size()), *v32X = dalloc<float>(c, valX.size());
-        if (!v32S || !v32X) return XDCG_OOM;
-        launch_cast_f32(d_valS, v32S, (long long)valS.size(), st);
-        launch_cast_f32(d_valX, v32X, (long long)valX.size(), st);
-        A2.valS = v32S;
-        A2.valX = v32X;
-    }
-    // node data and block factors
+    launch_gather(d_srcS, (long long)srcS.size(), d_val, d_valS, nullptr, st);
+    launch_gather(d_srcX, (long long)srcX.size(), d_val, d_valX, nullptr, st);
+
+    // node data and block factors (FP64)
     int *d_bad = dalloc<int>(c, 2);
     if (!d_bad) return XDCG_OOM;
     {
@@ -678,35 +718,18 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     N64.menr = d_menr;
     const int *dl[3];
     double *L64[3];
-    float *L32[3] = {nullptr, nullptr, nullptr};
     for (int t = 0; t < 3; ++t) {
         const int B = Bsz[t], cnt = (int)lists[t].size();
         dl[t] = upload(c, lists[t]);
         L64[t] = dalloc<double>(c, (size_t)B * (B + 1) / 2 * std::max(cnt, 1));
-        if (mixed) L32[t] = dalloc<float>(c, (size_t)B * (B + 1) / 2 * std::max(cnt, 1));
         double *d_D = upload_tmp(c, Dsoa[t]);
-        if (!dl[t] || !L64[t] || !d_D || (mixed && !L32[t])) return XDCG_OOM;
-        launch_block_cholesky(B, cnt, dl[t], d_D, L64[t], L32[t], d_bad, st);
+        if (!dl[t] || !L64[t] || !d_D) return XDCG_OOM;
+        launch_block_cholesky(B, cnt, dl[t], d_D, L64[t], nullptr, d_bad, st);
     }
     N64.stdNodes = dl[0]; N64.hNodes = dl[1]; N64.tNodes = dl[2];
     N64.Lstd = L64[0]; N64.Lh = L64[1]; N64.Lt = L64[2];
-    if (mixed) {
-        auto &N32 = c->L32.N;
-        N32.nNodes = N; N32.nStd = N64.nStd; N32.nH = N64.nH; N32.nT = N64.nT;
-        N32.stdNodes = dl[0]; N32.hNodes = dl[1]; N32.tNodes = dl[2];
-        N32.dofStart = d_dof; N32.sub = d_sub; N32.xrel = d_x32; N32.hsign = d_hs;
-        N32.col0 = d_col0; N32.menr = d_menr;
-        N32.Lstd = L32[0]; N32.Lh = L32[1]; N32.Lt = L32[2];
-    }
+
     // W = K Z and E = Z^T W
-    KinDev kin;
-    kin.nNodes = N;
-    kin.dofStart = d_dof;
-    kin.rowPtr = upload_tmp(c, rowp);
-    kin.col = upload_tmp(c, col);
-    kin.valPtr = upload_tmp(c, vptr);
-    kin.val = upload_tmp(c, val);
-    if (!kin.rowPtr || !kin.col || !kin.valPtr || !kin.val) return XDCG_OOM;
     int *d_extBox = upload_tmp(c, extBox), *d_extNode = upload(c, extNode);
     int *d_extPtr = upload(c, extPtr), *d_ownPtr = upload(c, ownPtr), *d_own = upload(c, ownNodes);
     long long *d_wOff = upload(c, wOff);
@@ -722,14 +745,6 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     B64.extNode = d_extNode;
     B64.wOff = d_wOff;
     B64.W = d_W;
-    if (mixed) {
-        float *W32 = dalloc<float>(c, nW);
-        if (!W32) return XDCG_OOM;
-        launch_cast_f32(d_W, W32, nW, st);
-        auto &B32 = c->L32.B;
-        B32.nBox = S; B32.ownPtr = d_ownPtr; B32.ownNodes = d_own; B32.extPtr = d_extPtr;
-        B32.extNode = d_extNode; B32.wOff = d_wOff; B32.W = W32;
-    }
     c->Einv = dalloc<double>(c, (size_t)k * k);
     c->E = dalloc<double>(c, (size_t)k * k);
     double *colbuf = dalloc_tmp<double>(c, k);
@@ -751,6 +766,53 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         double dm = 0;
         for (double d : diag) dm = std::max(dm, d);
         launch_sweep_inverse(c->Einv, k, colbuf, d_bad + 1, 1e-14 * dm, st);
+    }
+
+    // block-scaled FP32 level of the mixed path: K~ = L^-1 K L^-T, Z~ = L^T Z, W~ = L^-1 W
+    if (mixed) {
+        std::vector<int> nodeList(N), nodeIdx(N);
+        for (int t = 0; t < 3; ++t)
+            for (size_t i = 0; i < lists[t].size(); ++i) {
+                nodeList[lists[t][i]] = t;
+                nodeIdx[lists[t][i]] = (int)i;
+            }
+        FacDev F;
+        for (int t = 0; t < 3; ++t) {
+            F.L[t] = L64[t];
+            F.cnt[t] = (int)lists[t].size();
+        }
+        F.nodeList = upload(c, nodeList);
+        F.nodeIdx = upload(c, nodeIdx);
+        std::vector<int> blockRow(nnzb);
+        for (int I = 0; I < N; ++I)
+            for (long long p = rowp[I]; p < rowp[I + 1]; ++p) blockRow[p] = I;
+        int *d_brow = upload_tmp(c, blockRow);
+        double *d_Kt = dalloc_tmp<double>(c, val.size());
+        std::vector<long long> zOff(N + 1, 0);
+        for (int I = 0; I < N; ++I) zOff[I + 1] = zOff[I] + (long long)kindb[I] * (menr[sub[I]] ? 12 : 6);
+        long long *d_zOff = upload(c, zOff);
+        float *d_Zt = dalloc<float>(c, zOff[N]);
+        float *d_Wt = dalloc<float>(c, nW);
+        float *v32S = dalloc<float>(c, srcS.size()), *v32X = dalloc<float>(c, srcX.size());
+        if (!F.nodeList || !F.nodeIdx || !d_brow || !d_Kt || !d_zOff || !d_Zt || !d_Wt || !v32S ||
+            !v32X)
+            return XDCG_OOM;
+        c->L32.F = F;
+        CK(cudaMemcpyAsync(d_Kt, d_val, val.size() * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        launch_scale_blocks(kin, d_brow, nnzb, F, d_Kt, st);
+        launch_gather(d_srcS, (long long)srcS.size(), d_Kt, nullptr, v32S, st);
+        launch_gather(d_srcX, (long long)srcX.size(), d_Kt, nullptr, v32X, st);
+        auto &A2 = c->L32.A;
+        A2.nS = nS; A2.nSlices = nSlices; A2.rowS = A.rowS; A2.lenS = A.lenS;
+        A2.slicePtr = A.slicePtr; A2.colS = A.colS; A2.valS = v32S;
+        A2.nX = nX; A2.rowX = A.rowX; A2.lenX = A.lenX; A2.ptrX = A.ptrX; A2.colX = A.colX;
+        A2.valX = v32X;
+        launch_build_Zt(N, d_dof, d_sub, d_x64, d_hs, d_menr, F, d_zOff, d_Zt, st);
+        launch_scale_W(nExt, d_extBox, d_extNode, d_wOff, d_menr, d_dof, F, d_W, d_Wt, st);
+        auto &D = c->L32.D;
+        D.nNodes = N; D.nBox = S; D.dofStart = d_dof; D.sub = d_sub; D.col0 = d_col0;
+        D.menr = d_menr; D.zOff = d_zOff; D.Zt = d_Zt; D.ownPtr = d_ownPtr; D.ownNodes = d_own;
+        D.extPtr = d_extPtr; D.extNode = d_extNode; D.wOff = d_wOff; D.Wt = d_Wt;
     }
     int hbad[2];
     CK(cudaMemcpyAsync(hbad, d_bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -795,13 +857,19 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         return 9LL * nnzb3 * s + 4LL * nnzb3 + 8LL * nS + 8LL * nSlices + 16LL * nX + 2LL * n * s;
     };
     const long long fac = 6 * nStdN + 21 * nHN + 120 * nTN;
-    auto iter_bytes = [&](int s) {
-        return spmv_bytes(s)
-               + 7LL * n * s + fac * s + 4LL * N                 // update
-               + 2LL * n * s + nW * s + 12LL * nExt + 16LL * k    // restrict
-               + 8LL * k * k + 24LL * k                           // coarse
-               + 3LL * n * s + (3LL * s + 9) * N;                 // prolong
-    };
+    long long nZt = 0;
+    for (int I = 0; I < N; ++I) nZt += (long long)kindb[I] * (menr[sub[I]] ? 12 : 6);
+    // FP64 path: SpMV; update (u, p, r, q read, u, r, y written, factors);
+    // restriction (r, y, W, box lists); coarse GEMV (E^-1 and k-vectors);
+    // prolongation (y, p read, p written, node geometry)
+    const long long iter64 = spmv_bytes(8) + 7LL * n * 8 + fac * 8 + 4LL * N
+                             + 2LL * n * 8 + nW * 8 + 12LL * nExt + 16LL * k
+                             + 8LL * k * k + 24LL * k + 3LL * n * 8 + 33LL * N;
+    // FP32 scaled path: identity preconditioner (no y), explicit Z~ read by
+    // the restriction and the prolongation
+    const long long iter32 = spmv_bytes(4) + 6LL * n * 4
+                             + n * 4 + nZt * 4 + nW * 4 + 12LL * nExt + 16LL * k
+                             + 8LL * k * k + 24LL * k + 3LL * n * 4 + nZt * 4 + 20LL * N;
     c->info.n = n;
     c->info.n_nodes = N;
     c->info.k = k;
@@ -809,8 +877,8 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     c->info.nnzb3 = nnzb3;
     c->info.spmv_bytes_fp64 = spmv_bytes(8);
     c->info.spmv_bytes_fp32 = spmv_bytes(4);
-    c->info.iter_bytes_fp64 = iter_bytes(8);
-    c->info.iter_bytes_fp32 = iter_bytes(4);
+    c->info.iter_bytes_fp64 = iter64;
+    c->info.iter_bytes_fp32 = iter32;
     return XDCG_OK;
 }
 
@@ -830,7 +898,9 @@ xdcg_status xdcg_default_options(xdcg_options *opt) {
 }
 
 xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflation *Z,
-                       const void *blocks, const xdcg_options *opt, void *stream) {
+                       const void *blocks, const xdcg_options *opt, void *stream,
+                       int32_t *bad_index) {
+    if (bad_index) *bad_index = -1;
     if (!out) return XDCG_INVALID_ARG;
     *out = nullptr;
     if (!K || !Z || blocks) return XDCG_INVALID_ARG;
@@ -851,6 +921,7 @@ xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflatio
     const auto t0 = std::chrono::steady_clock::now();
     int bad = -1;
     xdcg_status s = setup_impl(c, K, Z, &bad);
+    if (bad_index) *bad_index = bad;
     if (s != XDCG_OK) {
         cudaStreamSynchronize(c->st);
         free_ctx(c);

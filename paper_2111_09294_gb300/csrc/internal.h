@@ -120,6 +120,44 @@ void launch_dot(const T *a, const T *b, long long n, double *partials, Scalars *
 void launch_scale_to_f32(const double *r64, float *r32, long long n, double s, cudaStream_t st);
 void launch_accumulate_f64(double *u64, const float *d32, long long n, double s, cudaStream_t st);
 
+// ---- block-scaled FP32 path (mixed precision) -------------------------------
+
+// FP64 node-block Cholesky factors of all nodes: node I's factor is list
+// nodeList[I] (0: 3x3, 1: 6x6, 2: 15x15), position nodeIdx[I] in that list.
+struct FacDev {
+    const double *L[3];
+    int cnt[3];
+    const int *nodeList, *nodeIdx;
+};
+
+// Explicit scaled deflation basis Z~ = L^T Z (per node b_I x M_s, row-major
+// at zOff[I]) and scaled W~ = L^-1 W, both FP32, plus box lists.
+struct ScaledDev {
+    int nNodes, nBox;
+    const int *dofStart, *sub, *col0, *menr;
+    const long long *zOff;
+    const float *Zt;
+    const int *ownPtr, *ownNodes, *extPtr, *extNode;
+    const long long *wOff;
+    const float *Wt;
+};
+
+void launch_gather(const int *src, long long n, const double *v, double *out64, float *out32,
+                   cudaStream_t st);
+void launch_build_Zt(int nNodes, const int *dofStart, const int *sub, const double *xrel,
+                     const signed char *hsign, const int *menr, const FacDev &F,
+                     const long long *zOff, float *Zt, cudaStream_t st);
+void launch_fwd_scale(int nNodes, const int *dofStart, const FacDev &F, const double *r, double s,
+                      float *out, cudaStream_t st);
+void launch_bwd_accum(int nNodes, const int *dofStart, const FacDev &F, const float *ut,
+                      double scale, double *u, cudaStream_t st);
+void launch_update_id(float *u, float *r, const float *p, const float *q, long long n, int mode,
+                      double *partials, Scalars *sc, cudaStream_t st);
+void launch_restrict_z(const ScaledDev &D, const float *a, const float *b, int withW, double *g,
+                       double *zr, const Scalars *sc, cudaStream_t st);
+void launch_prolong_z(const ScaledDev &D, const double *nu, const float *y, float *p, int mode,
+                      Scalars *sc, cudaStream_t st);
+
 // ---- set-up kernels -------------------------------------------------------
 
 struct KinDev {   // node-blocked input matrix on the device (FP64)
@@ -145,5 +183,10 @@ void launch_symmetrize(double *E, int k, cudaStream_t st);
 void launch_sweep_inverse(double *A, int k, double *colbuf, int *bad, double thr,
                           cudaStream_t st);
 void launch_cast_f32(const double *a, float *b, long long n, cudaStream_t st);
+void launch_scale_blocks(const KinDev &K, const int *blockRow, long long nnzb, const FacDev &F,
+                         double *Kt, cudaStream_t st);
+void launch_scale_W(int nExt, const int *extBox, const int *extNode, const long long *wOff,
+                    const int *menr, const int *dofStart, const FacDev &F, const double *W,
+                    float *Wt, cudaStream_t st);
 
 }  // namespace xdcg

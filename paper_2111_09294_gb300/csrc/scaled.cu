@@ -1,0 +1,345 @@
+// FP32 inner solve of the mixed-precision path, run on the block-scaled
+// system  K~ = L^-1 K L^-T,  f~ = L^-1 r,  u = L^-T u~,  with L the FP64
+// Cholesky factors of the node blocks (Eqs. block_jacobi, block_jacobi_enr).
+//
+// With M = L L^T the block-Jacobi preconditioner of Algorithm 3 becomes the
+// identity, the deflation basis becomes Z~ = L^T Z, W~ = K~ Z~ = L^-1 W, and
+// E = Z~^T K~ Z~ = Z^T K Z is unchanged; A-DEF2 on the scaled system produces
+// the same iterates as on the original one in exact arithmetic.  In FP32 the
+// scaling matters: the near-dependent enriched directions that give K its
+// ~1e9 condition number are scaled out, so p^T K~ p stays positive where the
+// unscaled FP32 recurrence breaks down.
+#include "reduce.cuh"
+
+namespace xdcg {
+
+__host__ __device__ constexpr int tri2(int i, int j) { return i * (i + 1) / 2 + j; }
+
+// entry (i, j), j <= i, of node I's factor; the diagonal is stored inverted
+__device__ __forceinline__ double Lent(const FacDev &F, int l, int t, int i, int j) {
+    return F.L[l][(size_t)tri2(i, j) * F.cnt[l] + t];
+}
+
+// x := L^-1 x (forward substitution) in place, x[k * stride] for k < b
+template <typename P>
+__device__ __forceinline__ void fwd_solve(const FacDev &F, int l, int t, int b, P x, int stride) {
+    for (int i = 0; i < b; ++i) {
+        double s = x[i * stride];
+        for (int j = 0; j < i; ++j) s -= Lent(F, l, t, i, j) * x[j * stride];
+        x[i * stride] = s * Lent(F, l, t, i, i);
+    }
+}
+
+// x := L^-T x (backward substitution) in place
+template <typename P>
+__device__ __forceinline__ void bwd_solve(const FacDev &F, int l, int t, int b, P x, int stride) {
+    for (int i = b - 1; i >= 0; --i) {
+        double s = x[i * stride];
+        for (int j = i + 1; j < b; ++j) s -= Lent(F, l, t, j, i) * x[j * stride];
+        x[i * stride] = s * Lent(F, l, t, i, i);
+    }
+}
+
+// ---- set-up -----------------------------------------------------------------
+
+__global__ void k_gather_f64(const int *__restrict__ src, long long n, const double *__restrict__ v,
+                             double *out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int s = src[i];
+        out[i] = s >= 0 ? v[s] : 0.0;
+    }
+}
+
+__global__ void k_gather_f32(const int *__restrict__ src, long long n, const double *__restrict__ v,
+                             float *out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int s = src[i];
+        out[i] = s >= 0 ? (float)v[s] : 0.0f;
+    }
+}
+
+static int grid_of(long long n, int th) {
+    long long g = (n + th - 1) / th;
+    return (int)(g < 8 * 152 ? (g > 0 ? g : 1) : 8 * 152);
+}
+
+void launch_gather(const int *src, long long n, const double *v, double *out64, float *out32,
+                   cudaStream_t st) {
+    if (n <= 0) return;
+    if (out64) k_gather_f64<<<grid_of(n, 256), 256, 0, st>>>(src, n, v, out64);
+    if (out32) k_gather_f32<<<grid_of(n, 256), 256, 0, st>>>(src, n, v, out32);
+}
+
+// K~_IJ = L_I^-1 K_IJ L_J^-T for every node-pair block, in place on a copy of K.
+__global__ void k_scale_blocks(KinDev K, const int *__restrict__ blockRow, long long nnzb,
+                               FacDev F, double *Kt) {
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= nnzb) return;
+    const int I = blockRow[p], J = K.col[p];
+    const int bI = K.dofStart[I + 1] - K.dofStart[I], bJ = K.dofStart[J + 1] - K.dofStart[J];
+    double *B = Kt + K.valPtr[p];                       // bI x bJ, row-major
+    const int lI = F.nodeList[I], tI = F.nodeIdx[I], lJ = F.nodeList[J], tJ = F.nodeIdx[J];
+    for (int c = 0; c < bJ; ++c) fwd_solve(F, lI, tI, bI, B + c, bJ);   // columns: L_I^-1 B
+    for (int r = 0; r < bI; ++r) fwd_solve(F, lJ, tJ, bJ, B + r * bJ, 1); // rows: (.) L_J^-T
+}
+
+void launch_scale_blocks(const KinDev &K, const int *blockRow, long long nnzb, const FacDev &F,
+                         double *Kt, cudaStream_t st) {
+    if (nnzb <= 0) return;
+    k_scale_blocks<<<(int)((nnzb + 127) / 128), 128, 0, st>>>(K, blockRow, nnzb, F, Kt);
+}
+
+// deflation row j of a node (same rule as the unscaled path)
+__device__ __forceinline__ void zrow(int j, int b, int menr, double X, double Y, double Z,
+                                     double H, double (&o)[12]) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) o[c] = 0.0;
+    const bool stdd = j < 3, jump = (b == 6 && j >= 3 && menr);
+    if (!stdd && !jump) return;
+    const int a = stdd ? j : j - 3;
+    double r[6] = {0, 0, 0, 0, 0, 0};
+    if (a == 0) { r[0] = 1.0; r[4] = Z; r[5] = -Y; }
+    if (a == 1) { r[1] = 1.0; r[3] = -Z; r[5] = X; }
+    if (a == 2) { r[2] = 1.0; r[3] = Y; r[4] = -X; }
+    if (stdd) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) o[c] = r[c];
+        if (menr) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) o[6 + c] = H * r[c];
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) o[6 + c] = r[c];
+    }
+}
+
+// Z~_I = L_I^T Z_I (b_I x M, row-major at zOff[I]), FP32.
+__global__ void k_build_Zt(int nNodes, const int *dofStart, const int *sub, const double *xrel,
+                           const signed char *hsign, const int *menr, FacDev F,
+                           const long long *zOff, float *Zt) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nNodes) return;
+    const int b = dofStart[I + 1] - dofStart[I];
+    const int s = sub[I], me = menr[s], M = me ? 12 : 6;
+    const double X = xrel[3 * I], Y = xrel[3 * I + 1], Z = xrel[3 * I + 2], H = hsign[I];
+    const int l = F.nodeList[I], t = F.nodeIdx[I];
+    double acc[15 * 12];
+    for (int e = 0; e < b * M; ++e) acc[e] = 0.0;
+    for (int j = 0; j < b; ++j) {
+        double zr[12];
+        zrow(j, b, me, X, Y, Z, H, zr);
+        bool any = false;
+        for (int c = 0; c < M; ++c) any |= zr[c] != 0.0;
+        if (!any) continue;
+        for (int i = 0; i <= j; ++i) {
+            const double lji = (i == j) ? 1.0 / Lent(F, l, t, j, j) : Lent(F, l, t, j, i);
+            for (int c = 0; c < M; ++c) acc[i * M + c] += lji * zr[c];
+        }
+    }
+    float *out = Zt + zOff[I];
+    for (int e = 0; e < b * M; ++e) out[e] = (float)acc[e];
+}
+
+void launch_build_Zt(int nNodes, const int *dofStart, const int *sub, const double *xrel,
+                     const signed char *hsign, const int *menr, const FacDev &F,
+                     const long long *zOff, float *Zt, cudaStream_t st) {
+    k_build_Zt<<<(nNodes + 127) / 128, 128, 0, st>>>(nNodes, dofStart, sub, xrel, hsign, menr, F,
+                                                     zOff, Zt);
+}
+
+// W~ = L^-1 W per W entry (b_I x M), FP32.
+__global__ void k_scale_W(int nExt, const int *extBox, const int *extNode, const long long *wOff,
+                          const int *menr, const int *dofStart, FacDev F, const double *W,
+                          float *Wt) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nExt) return;
+    const int I = extNode[e], M = menr[extBox[e]] ? 12 : 6;
+    const int b = dofStart[I + 1] - dofStart[I];
+    const int l = F.nodeList[I], t = F.nodeIdx[I];
+    const double *Wb = W + wOff[e];
+    for (int c = 0; c < M; ++c) {
+        double x[15];
+        for (int i = 0; i < b; ++i) x[i] = Wb[i * M + c];
+        fwd_solve(F, l, t, b, x, 1);
+        for (int i = 0; i < b; ++i) Wt[wOff[e] + i * M + c] = (float)x[i];
+    }
+}
+
+void launch_scale_W(int nExt, const int *extBox, const int *extNode, const long long *wOff,
+                    const int *menr, const int *dofStart, const FacDev &F, const double *W,
+                    float *Wt, cudaStream_t st) {
+    if (nExt == 0) return;
+    k_scale_W<<<(nExt + 127) / 128, 128, 0, st>>>(nExt, extBox, extNode, wOff, menr, dofStart, F,
+                                                  W, Wt);
+}
+
+// ---- outer-loop transforms (FP64) -----------------------------------------
+
+// out = (float)(s L^-1 r) per node
+__global__ void k_fwd_scale(int nNodes, const int *dofStart, FacDev F, const double *r, double s,
+                            float *out) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nNodes) return;
+    const int d0 = dofStart[I], b = dofStart[I + 1] - d0;
+    double x[15];
+    for (int i = 0; i < b; ++i) x[i] = r[d0 + i];
+    fwd_solve(F, F.nodeList[I], F.nodeIdx[I], b, x, 1);
+    for (int i = 0; i < b; ++i) out[d0 + i] = (float)(s * x[i]);
+}
+
+void launch_fwd_scale(int nNodes, const int *dofStart, const FacDev &F, const double *r, double s,
+                      float *out, cudaStream_t st) {
+    k_fwd_scale<<<(nNodes + 127) / 128, 128, 0, st>>>(nNodes, dofStart, F, r, s, out);
+}
+
+// u += scale L^-T ut per node
+__global__ void k_bwd_accum(int nNodes, const int *dofStart, FacDev F, const float *ut,
+                            double scale, double *u) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nNodes) return;
+    const int d0 = dofStart[I], b = dofStart[I + 1] - d0;
+    double x[15];
+    for (int i = 0; i < b; ++i) x[i] = (double)ut[d0 + i];
+    bwd_solve(F, F.nodeList[I], F.nodeIdx[I], b, x, 1);
+    for (int i = 0; i < b; ++i) u[d0 + i] += scale * x[i];
+}
+
+void launch_bwd_accum(int nNodes, const int *dofStart, const FacDev &F, const float *ut,
+                      double scale, double *u, cudaStream_t st) {
+    k_bwd_accum<<<(nNodes + 127) / 128, 128, 0, st>>>(nNodes, dofStart, F, ut, scale, u);
+}
+
+// ---- inner FP32 iteration kernels ------------------------------------------
+
+// u += alpha p, r -= alpha q, ||r||^2 (the preconditioner is the identity:
+// y = r, so r^T y = ||r||^2).  mode 1: only the norm.
+__global__ void __launch_bounds__(kThreads)
+k_update_id(float *u, float *r, const float *p, const float *q, long long n, int mode,
+            double *partials, Scalars *sc) {
+    if (sc->done != kRunning) return;
+    const float alpha = (float)sc->alpha;
+    double v[1] = {0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float ri = r[i];
+        if (mode == 0) {
+            u[i] = fmaf(alpha, p[i], u[i]);
+            ri = fmaf(-alpha, q[i], ri);
+            r[i] = ri;
+        }
+        v[0] += (double)ri * (double)ri;
+    }
+    double tot[1];
+    if (grid_sum<1>(v, partials, &sc->ticket[2], tot) && threadIdx.x == 0) {
+        sc->rr = tot[0];
+        sc->ry = tot[0];
+        if (tot[0] <= sc->tol2ff)
+            sc->done = kConverged;
+        else if (sc->its >= sc->max_it)
+            sc->done = kMaxIter;
+        else if (!isfinite(tot[0]))
+            sc->done = kBreakdown;
+    }
+}
+
+void launch_update_id(float *u, float *r, const float *p, const float *q, long long n, int mode,
+                      double *partials, Scalars *sc, cudaStream_t st) {
+    k_update_id<<<grid_of(n, kThreads), kThreads, 0, st>>>(u, r, p, q, n, mode, partials, sc);
+}
+
+constexpr int kBoxThreads = 128;
+
+// g = Z~^T a - W~^T b per box (b = a when the preconditioner is the identity)
+template <int M>
+__device__ __forceinline__ void restrict_z_box(const ScaledDev &D, int s, const float *a,
+                                               const float *b, int withW, double *g,
+                                               double *zr) {
+    double acc[2 * M];
+#pragma unroll
+    for (int c = 0; c < 2 * M; ++c) acc[c] = 0.0;
+    const int o1 = D.ownPtr[s + 1];
+    for (int t = D.ownPtr[s] + threadIdx.x; t < o1; t += blockDim.x) {
+        const int I = D.ownNodes[t];
+        const int d0 = D.dofStart[I], bI = D.dofStart[I + 1] - d0;
+        const float *Zb = D.Zt + D.zOff[I];
+        for (int i = 0; i < bI; ++i) {
+            const double av = (double)a[d0 + i];
+#pragma unroll
+            for (int c = 0; c < M; ++c) acc[c] += (double)Zb[i * M + c] * av;
+        }
+    }
+    if (withW) {
+        const int e1 = D.extPtr[s + 1];
+        for (int e = D.extPtr[s] + threadIdx.x; e < e1; e += blockDim.x) {
+            const int I = D.extNode[e];
+            const int d0 = D.dofStart[I], bI = D.dofStart[I + 1] - d0;
+            const float *Wb = D.Wt + D.wOff[e];
+            for (int i = 0; i < bI; ++i) {
+                const double bv = (double)b[d0 + i];
+#pragma unroll
+                for (int c = 0; c < M; ++c) acc[M + c] += (double)Wb[i * M + c] * bv;
+            }
+        }
+    }
+    block_sum<2 * M>(acc);
+    if (threadIdx.x == 0) {
+        const int c0 = D.col0[s];
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            g[c0 + c] = acc[c] - acc[M + c];
+            if (zr) zr[c0 + c] = acc[c];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBoxThreads)
+k_restrict_z(ScaledDev D, const float *a, const float *b, int withW, double *g, double *zr,
+             const Scalars *sc) {
+    if (sc && sc->done != kRunning) return;
+    const int s = blockIdx.x;
+    if (D.menr[s])
+        restrict_z_box<12>(D, s, a, b, withW, g, zr);
+    else
+        restrict_z_box<6>(D, s, a, b, withW, g, zr);
+}
+
+void launch_restrict_z(const ScaledDev &D, const float *a, const float *b, int withW, double *g,
+                       double *zr, const Scalars *sc, cudaStream_t st) {
+    k_restrict_z<<<D.nBox, kBoxThreads, 0, st>>>(D, a, b, withW, g, zr, sc);
+}
+
+// mode 0: p = y + Z~ nu + beta p;  mode 1: p = Z~ nu;  mode 2: p = y + Z~ nu
+__global__ void __launch_bounds__(kThreads)
+k_prolong_z(ScaledDev D, const double *__restrict__ nu, const float *__restrict__ y, float *p,
+            int mode, Scalars *sc) {
+    if (sc->done != kRunning) return;
+    const int I = blockIdx.x * kThreads + threadIdx.x;
+    if (I >= D.nNodes) return;
+    const int d0 = D.dofStart[I], bI = D.dofStart[I + 1] - d0;
+    const int s = D.sub[I], c0 = D.col0[s], M = D.menr[s] ? 12 : 6;
+    const float *Zb = D.Zt + D.zOff[I];
+    float n12[12];
+    for (int c = 0; c < M; ++c) n12[c] = (float)nu[c0 + c];
+    const float beta = (float)sc->beta;
+    for (int i = 0; i < bI; ++i) {
+        float zv = 0.0f;
+        for (int c = 0; c < M; ++c) zv = fmaf(Zb[i * M + c], n12[c], zv);
+        const int d = d0 + i;
+        if (mode == 0)
+            p[d] = y[d] + zv + beta * p[d];
+        else if (mode == 1)
+            p[d] = zv;
+        else
+            p[d] = y[d] + zv;
+    }
+}
+
+void launch_prolong_z(const ScaledDev &D, const double *nu, const float *y, float *p, int mode,
+                      Scalars *sc, cudaStream_t st) {
+    k_prolong_z<<<(D.nNodes + kThreads - 1) / kThreads, kThreads, 0, st>>>(D, nu, y, p, mode, sc);
+}
+
+}  // namespace xdcg

@@ -51,9 +51,11 @@ class Solver:
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
-        st = L.check(lib.xdcg_setup(ctypes.byref(self.ctx), ctypes.byref(m), ctypes.byref(z),
-                                    None, ctypes.byref(opt), ctypes.c_void_p(stream.cuda_stream)),
-                     "xdcg_setup")
+        bad = ctypes.c_int32(-1)
+        st = lib.xdcg_setup(ctypes.byref(self.ctx), ctypes.byref(m), ctypes.byref(z), None,
+                            ctypes.byref(opt), ctypes.c_void_p(stream.cuda_stream),
+                            ctypes.byref(bad))
+        L.check(st, "xdcg_setup", bad.value)
         info = L.Info()
         L.check(lib.xdcg_get_info(self.ctx, ctypes.byref(info)), "xdcg_get_info")
         self.info = info.as_dict()

@@ -53,5 +53,7 @@ def test_setup_rejects_null_arguments(lib):
     import ctypes
     ctx = ctypes.c_void_p()
     # host-side validation returns before any CUDA call
-    assert lib.xdcg_setup(None, None, None, None, None, None) == 1
-    assert lib.xdcg_setup(ctypes.byref(ctx), None, None, None, None, None) == 1
+    bad = ctypes.c_int32(7)
+    assert lib.xdcg_setup(None, None, None, None, None, None, ctypes.byref(bad)) == 1
+    assert bad.value == -1
+    assert lib.xdcg_setup(ctypes.byref(ctx), None, None, None, None, None, None) == 1

@@ -59,11 +59,28 @@ def test_spmv_fp64_and_fp32(name):
     y = y.cpu().numpy()
     assert np.all(np.abs(y - y_ref) <= 1e-12 * bound)
     assert abs(xty - x @ y_ref) <= 1e-12 * (np.abs(x) @ bound)
+    # the FP32 operator is the block-scaled K~ = L^-1 K L^-T (L: node-block factors)
+    Lb, Li = block_factor_matrices(M, K.shape)
+    Kt = (Li @ K @ Li.T).tocsr()
     x32 = x.astype(np.float32)
     y32, _ = s.spmv(torch.tensor(x32, device=dev), "mixed")
-    yr32 = K @ x32.astype(np.float64)
-    assert np.all(np.abs(y32.cpu().numpy() - yr32) <= 2e-5 * (abs(K) @ np.abs(x32)))
+    yr32 = Kt @ x32.astype(np.float64)
+    assert np.all(np.abs(y32.cpu().numpy() - yr32) <= 2e-5 * (abs(Kt) @ np.abs(x32)))
     s.close()
+
+
+def block_factor_matrices(M, shape):
+    """Block-diagonal Cholesky factor L of the oracle's node blocks and its inverse."""
+    r, c, v, vi = [], [], [], []
+    for idx, L in M.groups:
+        Linv = np.linalg.inv(L)
+        for t in range(idx.shape[0]):
+            rr, cc = np.meshgrid(idx[t], idx[t], indexing="ij")
+            r.append(rr.ravel()); c.append(cc.ravel())
+            v.append(L[t].ravel()); vi.append(Linv[t].ravel())
+    r, c = np.concatenate(r), np.concatenate(c)
+    return (sp.csr_matrix((np.concatenate(v), (r, c)), shape=shape),
+            sp.csr_matrix((np.concatenate(vi), (r, c)), shape=shape))
 
 
 @pytest.mark.parametrize("name", CONFIGS)
