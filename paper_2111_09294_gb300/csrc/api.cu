@@ -26,8 +26,9 @@ struct Level64 {
 };
 struct Level32 {          // block-scaled system K~ = L^-1 K L^-T in FP32
     SpmvDev<float> A;
-    ScaledDev D;
+    BoxDev<float> B;
     FacDev F;
+    const int *dofStart;
 };
 
 }  // namespace
@@ -56,6 +57,7 @@ struct xdcg_ctx {
     float *f32 = nullptr, *u32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr,
           *y32 = nullptr;
     double *g = nullptr, *zr = nullptr, *nu = nullptr;
+    float *nu32 = nullptr;
     double *partials = nullptr;
     Scalars *sc = nullptr, *sc32 = nullptr, *aux = nullptr;
     Scalars *h_sc = nullptr;   // pinned
@@ -186,10 +188,13 @@ struct PlainPath {
         launch_update<double>(L.N, u, r, p, q, y, mode, c->partials, sc, c->st);
     }
     void restrict_(const double *a, const double *b, int withW, double *zr, Scalars *sc) {
-        launch_restrict<double>(L.N, L.B, a, b, withW, c->g, zr, c->st, sc);
+        launch_restrict(L.B, a, b, withW, c->g, zr, sc, c->st);
+    }
+    void coarse(const double *zr, int mode, Scalars *sc) {
+        launch_coarse(c->Einv, c->k, c->g, zr, c->nu, nullptr, mode, c->partials, sc, c->st);
     }
     void prolong(const double *y, double *p, int mode, Scalars *sc) {
-        launch_prolong<double>(L.N, c->nu, y, p, mode, sc, c->st);
+        launch_prolong(L.B, c->nu, y, p, mode, sc, c->st);
     }
 };
 
@@ -205,10 +210,13 @@ struct ScaledPath {
         launch_update_id(u, r, p, q, c->n, mode, c->partials, sc, c->st);
     }
     void restrict_(const float *a, const float *b, int withW, double *zr, Scalars *sc) {
-        launch_restrict_z(L.D, a, b, withW, c->g, zr, sc, c->st);
+        launch_restrict_z(L.B, a, b, withW, c->g, zr, sc, c->st);
+    }
+    void coarse(const double *zr, int mode, Scalars *sc) {
+        launch_coarse(c->Einv, c->k, c->g, zr, c->nu, c->nu32, mode, c->partials, sc, c->st);
     }
     void prolong(const float *y, float *p, int mode, Scalars *sc) {
-        launch_prolong_z(L.D, c->nu, y, p, mode, sc, c->st);
+        launch_prolong_z(L.B, c->nu32, y, p, mode, sc, c->st);
     }
 };
 
@@ -219,13 +227,13 @@ xdcg_status run_pcg(xdcg_ctx *c, Path path, const T *f, T *u, T *r, T *p, T *q, 
     cudaStream_t st = c->st;
     // Algorithm 2 with u_-1 = 0: u_0 = Z E^-1 Z^T f
     path.restrict_(f, nullptr, 0, nullptr, sc);
-    launch_coarse(c->Einv, c->k, c->g, nullptr, c->nu, 0, c->partials, sc, st);
+    path.coarse(nullptr, 0, sc);
     path.prolong(nullptr, u, 1, sc);
     // r_0 = f - K u_0, z_0 by Algorithm 3, p_0 = z_0
     path.spmv(u, r, f, 1, kFinRR, sc);
     path.update(u, r, nullptr, nullptr, y, 1, sc);
     path.restrict_(r, y, 1, c->zr, sc);
-    launch_coarse(c->Einv, c->k, c->g, c->zr, c->nu, 1, c->partials, sc, st);
+    path.coarse(c->zr, 1, sc);
     path.prolong(y, p, 2, sc);
     c->launches += 8;
 
@@ -247,7 +255,7 @@ xdcg_status run_pcg(xdcg_ctx *c, Path path, const T *f, T *u, T *r, T *p, T *q, 
             if (time_spmv) CK(cudaEventRecord(c->evE[launched], st));
             path.update(u, r, p, q, y, 0, sc);
             path.restrict_(r, y, 1, c->zr, sc);
-            launch_coarse(c->Einv, c->k, c->g, c->zr, c->nu, 2, c->partials, sc, st);
+            path.coarse(c->zr, 2, sc);
             path.prolong(y, p, 0, sc);
             c->launches += 5;
             ++launched;
@@ -328,7 +336,7 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, xdc
         if (cycles >= c->opt.max_outer || total >= c->opt.max_iter) break;
         const double rn = std::sqrt(rn2);
         // scaled inner right-hand side f~ = L^-1 r / ||r||
-        launch_fwd_scale(c->nNodes, c->L32.D.dofStart, c->L32.F, c->r64, 1.0 / rn, c->f32, st);
+        launch_fwd_scale(c->nNodes, c->L32.dofStart, c->L32.F, c->r64, 1.0 / rn, c->f32, st);
         init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
         launch_dot<float>(c->f32, c->f32, c->n, c->partials, c->aux, kFinStore, 0, st);
         const double eta = c->opt.inner_tol;
@@ -342,7 +350,7 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, xdc
         total += its;
         cycles++;
         last_inner_rel = std::sqrt(c->h_sc->rr);
-        launch_bwd_accum(c->nNodes, c->L32.D.dofStart, c->L32.F, c->u32, rn, u, st);
+        launch_bwd_accum(c->nNodes, c->L32.dofStart, c->L32.F, c->u32, rn, u, st);
         init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
         launch_spmv<double>(c->L64.A, u, c->r64, f, 1, c->partials, c->aux, kFinStore, 0, st);
         c->launches += 3;
@@ -737,12 +745,49 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     if (!d_extBox || !d_extNode || !d_extPtr || !d_ownPtr || !d_own || !d_wOff || !d_W)
         return XDCG_OOM;
     launch_build_W(kin, nExt, d_extBox, d_extNode, d_wOff, d_sub, d_x64, d_hs, d_menr, d_W, st);
+    // node data in box order (slots) and per-entry dof data for the box kernels
+    std::vector<int> ownDof(N), extDof(nExt);
+    std::vector<unsigned char> ownB(N), extB(nExt);
+    std::vector<signed char> ownH(N);
+    std::vector<double> ownCoords(3 * (size_t)N);
+    std::vector<int> ownSub(N);
+    for (int t = 0; t < N; ++t) {
+        const int I = ownNodes[t];
+        ownDof[t] = dof[I];
+        ownB[t] = (unsigned char)kindb[I];
+        ownH[t] = (signed char)hs[I];
+        ownSub[t] = sub[I];
+        for (int e = 0; e < 3; ++e) ownCoords[3 * (size_t)t + e] = coords[3 * (size_t)I + e];
+    }
+    for (int e = 0; e < nExt; ++e) {
+        extDof[e] = dof[extNode[e]];
+        extB[e] = (unsigned char)kindb[extNode[e]];
+    }
+    int *d_ownDof = upload(c, ownDof), *d_extDof = upload(c, extDof);
+    unsigned char *d_ownB = upload(c, ownB), *d_extB = upload(c, extB);
+    signed char *d_ownH = upload(c, ownH);
+    double *d_ownX = dalloc<double>(c, 3 * (size_t)N);
+    {
+        double *d_oc = upload_tmp(c, ownCoords), *d_centre2 = upload_tmp(c, centre);
+        int *d_os = upload_tmp(c, ownSub);
+        if (!d_oc || !d_centre2 || !d_os) return XDCG_OOM;
+        if (d_ownX) launch_xrel(N, d_oc, d_centre2, d_os, d_ownX, nullptr, st);
+    }
+    if (!d_ownDof || !d_extDof || !d_ownB || !d_extB || !d_ownH || !d_ownX) return XDCG_OOM;
     auto &B64 = c->L64.B;
     B64.nBox = S;
+    B64.col0 = d_col0;
+    B64.menr = d_menr;
     B64.ownPtr = d_ownPtr;
-    B64.ownNodes = d_own;
+    B64.ownDof = d_ownDof;
+    B64.ownB = d_ownB;
+    B64.ownH = d_ownH;
+    B64.ownX = d_ownX;
+    B64.ownZ = nullptr;
+    B64.Zt = nullptr;
     B64.extPtr = d_extPtr;
-    B64.extNode = d_extNode;
+    B64.extDof = d_extDof;
+    B64.extB = d_extB;
     B64.wOff = d_wOff;
     B64.W = d_W;
     c->Einv = dalloc<double>(c, (size_t)k * k);
@@ -788,8 +833,9 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
             for (long long p = rowp[I]; p < rowp[I + 1]; ++p) blockRow[p] = I;
         int *d_brow = upload_tmp(c, blockRow);
         double *d_Kt = dalloc_tmp<double>(c, val.size());
-        std::vector<long long> zOff(N + 1, 0);
-        for (int I = 0; I < N; ++I) zOff[I + 1] = zOff[I] + (long long)kindb[I] * (menr[sub[I]] ? 12 : 6);
+        std::vector<long long> zOff(N + 1, 0);   // explicit Z~ blocks in slot order
+        for (int t = 0; t < N; ++t)
+            zOff[t + 1] = zOff[t] + (long long)ownB[t] * (menr[ownSub[t]] ? 12 : 6);
         long long *d_zOff = upload(c, zOff);
         float *d_Zt = dalloc<float>(c, zOff[N]);
         float *d_Wt = dalloc<float>(c, nW);
@@ -807,12 +853,14 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         A2.slicePtr = A.slicePtr; A2.colS = A.colS; A2.valS = v32S;
         A2.nX = nX; A2.rowX = A.rowX; A2.lenX = A.lenX; A2.ptrX = A.ptrX; A2.colX = A.colX;
         A2.valX = v32X;
-        launch_build_Zt(N, d_dof, d_sub, d_x64, d_hs, d_menr, F, d_zOff, d_Zt, st);
+        launch_build_Zt(N, d_own, d_dof, d_sub, d_x64, d_hs, d_menr, F, d_zOff, d_Zt, st);
         launch_scale_W(nExt, d_extBox, d_extNode, d_wOff, d_menr, d_dof, F, d_W, d_Wt, st);
-        auto &D = c->L32.D;
-        D.nNodes = N; D.nBox = S; D.dofStart = d_dof; D.sub = d_sub; D.col0 = d_col0;
-        D.menr = d_menr; D.zOff = d_zOff; D.Zt = d_Zt; D.ownPtr = d_ownPtr; D.ownNodes = d_own;
-        D.extPtr = d_extPtr; D.extNode = d_extNode; D.wOff = d_wOff; D.Wt = d_Wt;
+        auto &B32 = c->L32.B;
+        B32.nBox = S; B32.col0 = d_col0; B32.menr = d_menr; B32.ownPtr = d_ownPtr;
+        B32.ownDof = d_ownDof; B32.ownB = d_ownB; B32.ownH = d_ownH; B32.ownX = nullptr;
+        B32.ownZ = d_zOff; B32.Zt = d_Zt; B32.extPtr = d_extPtr; B32.extDof = d_extDof;
+        B32.extB = d_extB; B32.wOff = d_wOff; B32.W = d_Wt;
+        c->L32.dofStart = d_dof;
     }
     int hbad[2];
     CK(cudaMemcpyAsync(hbad, d_bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -833,10 +881,11 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         if (!c->f32 || !c->u32 || !c->r32 || !c->p32 || !c->q32 || !c->y32) return XDCG_OOM;
     }
     c->g = dalloc<double>(c, k); c->zr = dalloc<double>(c, k); c->nu = dalloc<double>(c, k);
+    c->nu32 = dalloc<float>(c, k);
     c->partials = dalloc<double>(c, 4 * (size_t)kMaxGrid);
     c->sc = dalloc<Scalars>(c, 1); c->sc32 = dalloc<Scalars>(c, 1); c->aux = dalloc<Scalars>(c, 1);
     if (!c->u64 || !c->r64 || !c->p64 || !c->q64 || !c->y64 || !c->f64 || !c->uh64 || !c->g ||
-        !c->zr || !c->nu || !c->partials || !c->sc || !c->sc32 || !c->aux)
+        !c->zr || !c->nu || !c->nu32 || !c->partials || !c->sc || !c->sc32 || !c->aux)
         return XDCG_OOM;
     CK(cudaMemsetAsync(c->sc, 0, sizeof(Scalars), st));
     CK(cudaMemsetAsync(c->sc32, 0, sizeof(Scalars), st));
@@ -983,9 +1032,9 @@ xdcg_status xdcg_precond(xdcg_ctx *c, const double *r, double *z) {
     CK(cudaMemcpyAsync(c->r64, r, c->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     launch_update<double>(c->L64.N, nullptr, c->r64, nullptr, nullptr, c->y64, 1, c->partials,
                           c->aux, st);
-    launch_restrict<double>(c->L64.N, c->L64.B, c->r64, c->y64, 1, c->g, c->zr, st, c->aux);
-    launch_coarse(c->Einv, c->k, c->g, c->zr, c->nu, 0, c->partials, c->aux, st);
-    launch_prolong<double>(c->L64.N, c->nu, c->y64, z, 2, c->aux, st);
+    launch_restrict(c->L64.B, c->r64, c->y64, 1, c->g, c->zr, c->aux, st);
+    launch_coarse(c->Einv, c->k, c->g, c->zr, c->nu, nullptr, 0, c->partials, c->aux, st);
+    launch_prolong(c->L64.B, c->nu, c->y64, z, 2, c->aux, st);
     c->launches += 4;
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());

@@ -1,0 +1,270 @@
+// Box-level kernels of Algorithm 3: the restriction g = Z^T r - W^T y
+// (right-hand sides of both coarse solves, merged) and the prolongation
+// p = y + Z nu (+ beta p), one CTA per box subdomain.
+//
+// Work split: the lanes of a warp form 32 / M groups of M lanes (M = 6 or 12
+// coarse columns of the box); lane (group, column c) accumulates column c
+// over its share of the box's nodes, so every lane keeps two running sums
+// and the only cross-lane step is a short, fixed-order sum in shared memory.
+// Node data are stored in box order (slots), so a box's nodes are contiguous.
+//
+// Z is applied matrix-free from the node position relative to the box
+// centre (Eqs. dcg_deflation_space, dcg_deflation_space_enr_std,
+// dcg_deflation_space_enr_enr) in the FP64 path, and from the explicit
+// scaled basis Z~ = L^T Z in the FP32 block-scaled path.
+#include "reduce.cuh"
+
+namespace xdcg {
+
+constexpr int kBoxThreads = 512;
+
+// column c (0..5) of R(x)^T a, R the rigid block of Eq. dcg_deflation_space
+template <typename A>
+__device__ __forceinline__ A rigid_col(int c, A a0, A a1, A a2, A X, A Y, A Z) {
+    switch (c) {
+        case 0: return a0;
+        case 1: return a1;
+        case 2: return a2;
+        case 3: return -Z * a1 + Y * a2;
+        case 4: return Z * a0 - X * a2;
+        default: return -Y * a0 + X * a1;
+    }
+}
+
+// Sum over rows i of one node block: acc += blk[i * M + c] * v[d0 + i].  The
+// three standard rows are loaded straight-line so that four entries' loads
+// are in flight together; enriched rows (i >= 3) follow in a loop.
+template <typename T, typename A, int M, int U>
+__device__ __forceinline__ void block_col_dot(const T *base, const long long (&off)[U],
+                                              const int (&d0)[U], const int (&bI)[U],
+                                              const T *v, int c, A &acc) {
+    A w[U][3], x[U][3];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            w[u][i] = bI[u] ? (A)base[off[u] + i * M + c] : A(0);
+            x[u][i] = bI[u] ? (A)v[d0[u] + i] : A(0);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) acc = fma(w[u][i], x[u][i], acc);
+        if (bI[u] > 3) {
+            // enriched rows (3 jump or 12 branch dofs): all loads first
+            A we[12], xe[12];
+#pragma unroll
+            for (int i = 0; i < 12; ++i) {
+                const bool ok = 3 + i < bI[u];
+                we[i] = ok ? (A)base[off[u] + (3 + i) * M + c] : A(0);
+                xe[i] = ok ? (A)v[d0[u] + 3 + i] : A(0);
+            }
+#pragma unroll
+            for (int i = 0; i < 12; ++i) acc = fma(we[i], xe[i], acc);
+        }
+    }
+}
+
+template <typename T, typename A, int M, bool EXPL>
+__device__ __forceinline__ void restrict_box(const BoxDev<T> &B, int s, const T *a, const T *b,
+                                             int withW, double *g, double *zr) {
+    constexpr int G = 32 / M;
+    constexpr int kSlots = (kBoxThreads / 32) * G;
+    constexpr int U = 4;
+    __shared__ double red[2][kSlots * M];
+    __shared__ double tot[2][M];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = lane / M, c = lane - grp * M;
+    const bool act = grp < G;
+    const int slot = warp * G + grp;
+    A za = A(0), wb = A(0);
+    if (act) {
+        const int o0 = B.ownPtr[s], o1 = B.ownPtr[s + 1];
+        if (EXPL) {
+            for (int t = o0 + slot; t < o1; t += U * kSlots) {
+                long long off[U];
+                int d0[U], bI[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int tt = t + u * kSlots;
+                    const bool ok = tt < o1;
+                    off[u] = ok ? B.ownZ[tt] : 0;
+                    d0[u] = ok ? B.ownDof[tt] : 0;
+                    bI[u] = ok ? B.ownB[tt] : 0;
+                }
+                block_col_dot<T, A, M, U>(B.Zt, off, d0, bI, a, c, za);
+            }
+        } else {
+            const int c6 = (M == 12 && c >= 6) ? c - 6 : c;
+            for (int t = o0 + slot; t < o1; t += kSlots) {
+                const int d0 = B.ownDof[t];
+                const A X = B.ownX[3 * t], Y = B.ownX[3 * t + 1], Z = B.ownX[3 * t + 2];
+                A v = rigid_col<A>(c6, a[d0], a[d0 + 1], a[d0 + 2], X, Y, Z);
+                if (M == 12 && c >= 6) {
+                    v *= (A)B.ownH[t];
+                    if (B.ownB[t] == 6)
+                        v += rigid_col<A>(c6, a[d0 + 3], a[d0 + 4], a[d0 + 5], X, Y, Z);
+                }
+                za += v;
+            }
+        }
+        if (withW) {
+            const int e1 = B.extPtr[s + 1];
+            for (int e = B.extPtr[s] + slot; e < e1; e += U * kSlots) {
+                long long off[U];
+                int d0[U], bI[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int ee = e + u * kSlots;
+                    const bool ok = ee < e1;
+                    off[u] = ok ? B.wOff[ee] : 0;
+                    d0[u] = ok ? B.extDof[ee] : 0;
+                    bI[u] = ok ? B.extB[ee] : 0;
+                }
+                block_col_dot<T, A, M, U>(B.W, off, d0, bI, b, c, wb);
+            }
+        }
+        red[0][slot * M + c] = (double)za;
+        red[1][slot * M + c] = (double)wb;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * M) {
+        const int which = threadIdx.x / M, cc = threadIdx.x - which * M;
+        double sum = 0.0;
+        for (int q = 0; q < kSlots; ++q) sum += red[which][q * M + cc];
+        tot[which][cc] = sum;
+    }
+    __syncthreads();
+    if (threadIdx.x < M) {
+        const int c0 = B.col0[s];
+        g[c0 + threadIdx.x] = tot[0][threadIdx.x] - tot[1][threadIdx.x];
+        if (zr) zr[c0 + threadIdx.x] = tot[0][threadIdx.x];
+    }
+}
+
+template <typename T, typename A, bool EXPL>
+__global__ void __launch_bounds__(kBoxThreads)
+k_restrict(BoxDev<T> B, const T *a, const T *b, int withW, double *g, double *zr,
+           const Scalars *sc) {
+    if (sc && sc->done != kRunning) return;
+    const int s = blockIdx.x;
+    if (B.menr[s])
+        restrict_box<T, A, 12, EXPL>(B, s, a, b, withW, g, zr);
+    else
+        restrict_box<T, A, 6, EXPL>(B, s, a, b, withW, g, zr);
+}
+
+void launch_restrict(const BoxDev<double> &B, const double *a, const double *b, int withW,
+                     double *g, double *zr, const Scalars *sc, cudaStream_t st) {
+    k_restrict<double, double, false><<<B.nBox, kBoxThreads, 0, st>>>(B, a, b, withW, g, zr, sc);
+}
+
+void launch_restrict_z(const BoxDev<float> &B, const float *a, const float *b, int withW,
+                       double *g, double *zr, const Scalars *sc, cudaStream_t st) {
+    k_restrict<float, float, true><<<B.nBox, kBoxThreads, 0, st>>>(B, a, b, withW, g, zr, sc);
+}
+
+// ---- prolongation ----------------------------------------------------------
+
+// mode 0: p = y + Z nu + beta p;  mode 1: p = Z nu;  mode 2: p = y + Z nu
+template <typename T>
+__device__ __forceinline__ void emit(T *p, const T *y, int d, T zv, int mode, T beta) {
+    if (mode == 0)
+        p[d] = y[d] + zv + beta * p[d];
+    else if (mode == 1)
+        p[d] = zv;
+    else
+        p[d] = y[d] + zv;
+}
+
+template <typename T, int M, bool EXPL>
+__device__ __forceinline__ void prolong_box(const BoxDev<T> &B, int s, const T *nu, const T *y,
+                                            T *p, int mode, T beta) {
+    const int c0 = B.col0[s];
+    T n[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) n[c] = nu[c0 + c];
+    const int o1 = B.ownPtr[s + 1];
+    for (int t = B.ownPtr[s] + threadIdx.x; t < o1; t += blockDim.x) {
+        const int d0 = B.ownDof[t], bI = B.ownB[t];
+        if (EXPL) {
+            const T *Zb = B.Zt + B.ownZ[t];
+            T z[3][M];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+#pragma unroll
+                for (int c = 0; c < M; ++c) z[i][c] = Zb[i * M + c];
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                T zv = T(0);
+#pragma unroll
+                for (int c = 0; c < M; ++c) zv = fma(z[i][c], n[c], zv);
+                emit(p, y, d0 + i, zv, mode, beta);
+            }
+            for (int i0 = 3; i0 < bI; i0 += 3) {
+                // enriched rows three at a time, loads first
+                T ze[3][M];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+#pragma unroll
+                    for (int c = 0; c < M; ++c) ze[i][c] = Zb[(i0 + i) * M + c];
+                }
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    T zv = T(0);
+#pragma unroll
+                    for (int c = 0; c < M; ++c) zv = fma(ze[i][c], n[c], zv);
+                    emit(p, y, d0 + i0 + i, zv, mode, beta);
+                }
+            }
+        } else {
+            const T X = B.ownX[3 * t], Y = B.ownX[3 * t + 1], Z = B.ownX[3 * t + 2];
+            T v[3], ve[3] = {T(0), T(0), T(0)};
+            v[0] = n[0] + Z * n[4] - Y * n[5];
+            v[1] = n[1] - Z * n[3] + X * n[5];
+            v[2] = n[2] + Y * n[3] - X * n[4];
+            if (M == 12) {
+                ve[0] = n[6] + Z * n[10] - Y * n[11];
+                ve[1] = n[7] - Z * n[9] + X * n[11];
+                ve[2] = n[8] + Y * n[9] - X * n[10];
+                const T H = (T)B.ownH[t];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) v[i] += H * ve[i];
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) emit(p, y, d0 + i, v[i], mode, beta);
+            if (bI == 6) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) emit(p, y, d0 + 3 + i, M == 12 ? ve[i] : T(0), mode, beta);
+            } else {
+                for (int i = 3; i < bI; ++i) emit(p, y, d0 + i, T(0), mode, beta);
+            }
+        }
+    }
+}
+
+template <typename T, bool EXPL>
+__global__ void __launch_bounds__(kBoxThreads)
+k_prolong(BoxDev<T> B, const T *nu, const T *y, T *p, int mode, Scalars *sc) {
+    if (sc->done != kRunning) return;
+    const int s = blockIdx.x;
+    const T beta = (T)sc->beta;
+    if (B.menr[s])
+        prolong_box<T, 12, EXPL>(B, s, nu, y, p, mode, beta);
+    else
+        prolong_box<T, 6, EXPL>(B, s, nu, y, p, mode, beta);
+}
+
+void launch_prolong(const BoxDev<double> &B, const double *nu, const double *y, double *p,
+                    int mode, Scalars *sc, cudaStream_t st) {
+    k_prolong<double, false><<<B.nBox, kBoxThreads, 0, st>>>(B, nu, y, p, mode, sc);
+}
+
+void launch_prolong_z(const BoxDev<float> &B, const float *nu32, const float *y, float *p,
+                      int mode, Scalars *sc, cudaStream_t st) {
+    k_prolong<float, true><<<B.nBox, kBoxThreads, 0, st>>>(B, nu32, y, p, mode, sc);
+}
+
+}  // namespace xdcg

@@ -172,29 +172,59 @@ void launch_sweep_inverse(double *A, int k, double *colbuf, int *bad, double thr
 
 // ---- per-iteration coarse solve -------------------------------------------
 
-// nu = E^-1 g, one warp per row.  mode 0: nothing else (Algorithm 2);
-// mode 1: rho = r^T y + nu^T (Z^T r), beta = 0 (start); mode 2: the same
-// rho_new, beta = rho_new / rho, rho = rho_new (iteration).
+// nu = E^-1 g, one warp per row, four independent FMA chains per lane and
+// 16-byte loads when rows are 16-byte aligned (k even).  nu32, if given,
+// receives an FP32 copy for the FP32 prolongation.  mode 0: nothing else
+// (Algorithm 2); mode 1: rho = r^T y + nu^T (Z^T r), beta = 0 (start);
+// mode 2: the same rho_new, beta = rho_new / rho, rho = rho_new (iteration).
 __global__ void __launch_bounds__(kThreads)
 k_coarse(const double *__restrict__ Einv, int k, const double *__restrict__ g,
-         const double *__restrict__ zr, double *nu, int mode, double *partials, Scalars *sc) {
+         const double *__restrict__ zr, double *nu, float *nu32, int mode, double *partials,
+         Scalars *sc) {
     if (sc->done != kRunning) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kWarps + warp;
     double part[1] = {0.0};
     if (i < k) {
         const double *row = Einv + (size_t)i * k;
-        double s = 0.0;
-        for (int j = lane; j < k; j += 32) s = fma(row[j], __ldg(g + j), s);
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        if ((k & 1) == 0) {
+            const double2 *r2 = reinterpret_cast<const double2 *>(row);
+            const double2 *g2 = reinterpret_cast<const double2 *>(g);
+            const int k2 = k >> 1;
+            int j = lane;
+            for (; j + 32 < k2; j += 64) {
+                const double2 a = __ldg(r2 + j), b = __ldg(r2 + j + 32);
+                const double2 x = __ldg(g2 + j), y = __ldg(g2 + j + 32);
+                s0 = fma(a.x, x.x, s0);
+                s1 = fma(a.y, x.y, s1);
+                s2 = fma(b.x, y.x, s2);
+                s3 = fma(b.y, y.y, s3);
+            }
+            for (; j < k2; j += 32) {
+                const double2 a = __ldg(r2 + j), x = __ldg(g2 + j);
+                s0 = fma(a.x, x.x, s0);
+                s1 = fma(a.y, x.y, s1);
+            }
+        } else {
+            int j = lane;
+            for (; j + 32 < k; j += 64) {
+                s0 = fma(__ldg(row + j), __ldg(g + j), s0);
+                s1 = fma(__ldg(row + j + 32), __ldg(g + j + 32), s1);
+            }
+            for (; j < k; j += 32) s0 = fma(__ldg(row + j), __ldg(g + j), s0);
+        }
+        double s = (s0 + s1) + (s2 + s3);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) {
             nu[i] = s;
+            if (nu32) nu32[i] = (float)s;
             if (mode != 0) part[0] = s * zr[i];
         }
     }
     double tot[1];
-    if (grid_sum<1>(part, partials, &sc->ticket[3], tot) && threadIdx.x == 0) {
+    if (grid_sum<double, 1>(part, partials, &sc->ticket[3], tot) && threadIdx.x == 0) {
         if (mode == 1) {
             sc->rho = sc->ry + tot[0];
             sc->beta = 0.0;
@@ -207,9 +237,10 @@ k_coarse(const double *__restrict__ Einv, int k, const double *__restrict__ g,
 }
 
 void launch_coarse(const double *Einv, int k, const double *g, const double *zr, double *nu,
-                   int mode, double *partials, Scalars *sc, cudaStream_t st) {
+                   float *nu32, int mode, double *partials, Scalars *sc, cudaStream_t st) {
     const int grid = (k + kWarps - 1) / kWarps;
-    k_coarse<<<grid > 0 ? grid : 1, kThreads, 0, st>>>(Einv, k, g, zr, nu, mode, partials, sc);
+    k_coarse<<<grid > 0 ? grid : 1, kThreads, 0, st>>>(Einv, k, g, zr, nu, nu32, mode, partials,
+                                                       sc);
 }
 
 }  // namespace xdcg

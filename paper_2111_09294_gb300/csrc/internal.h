@@ -80,13 +80,26 @@ struct NodeDev {
     const int *menr;          // [nBox] 1 if the box carries enriched modes
 };
 
-// Box-level data for the restriction g = Z^T a - W^T b.
+// Box-level data, node data in box order ("slots": the nodes of box s are
+// slots ownPtr[s] .. ownPtr[s+1]-1), and the W entries of each box (nodes
+// coupled to the box, W block b_I x M_s row-major at wOff[e]).  Z is
+// matrix-free (ownX, ownH) in the FP64 path and explicit (Zt at ownZ[t],
+// b_I x M_s row-major) in the block-scaled FP32 path.
 template <typename T>
 struct BoxDev {
     int nBox;
-    const int *ownPtr, *ownNodes;   // nodes of each box
-    const int *extPtr, *extNode;    // nodes coupled to each box (W rows)
-    const long long *wOff;          // offset of each W block (b_I x m_s, row-major)
+    const int *col0, *menr;       // first coarse column / enriched-mode flag per box
+    const int *ownPtr;            // [nBox + 1]
+    const int *ownDof;            // [slots] first dof of the node
+    const unsigned char *ownB;    // [slots] dofs of the node (3, 6, 15)
+    const signed char *ownH;      // [slots] H(x_I)
+    const T *ownX;                // [3 slots] position relative to the box centre
+    const long long *ownZ;        // [slots] offset of the explicit Z~ block
+    const T *Zt;                  // explicit Z~ (scaled path only)
+    const int *extPtr;            // [nBox + 1]
+    const int *extDof;            // [entries] first dof of the entry's node
+    const unsigned char *extB;    // [entries] dofs of the entry's node
+    const long long *wOff;        // [entries]
     const T *W;
 };
 
@@ -101,16 +114,18 @@ template <typename T>
 void launch_update(const NodeDev<T> &N, T *u, T *r, const T *p, const T *q, T *y, int mode,
                    double *partials, Scalars *sc, cudaStream_t st);
 
-template <typename T>
-void launch_restrict(const NodeDev<T> &N, const BoxDev<T> &B, const T *a, const T *b, int withW,
-                     double *g, double *zr, cudaStream_t st, const Scalars *sc);
+void launch_restrict(const BoxDev<double> &B, const double *a, const double *b, int withW,
+                     double *g, double *zr, const Scalars *sc, cudaStream_t st);
+void launch_restrict_z(const BoxDev<float> &B, const float *a, const float *b, int withW,
+                       double *g, double *zr, const Scalars *sc, cudaStream_t st);
+void launch_prolong(const BoxDev<double> &B, const double *nu, const double *y, double *p,
+                    int mode, Scalars *sc, cudaStream_t st);
+void launch_prolong_z(const BoxDev<float> &B, const float *nu32, const float *y, float *p,
+                      int mode, Scalars *sc, cudaStream_t st);
 
+// nu = E^-1 g (FP64; nu32 optional FP32 copy)
 void launch_coarse(const double *Einv, int k, const double *g, const double *zr, double *nu,
-                   int mode, double *partials, Scalars *sc, cudaStream_t st);
-
-template <typename T>
-void launch_prolong(const NodeDev<T> &N, const double *nu, const T *y, T *p, int mode,
-                    Scalars *sc, cudaStream_t st);
+                   float *nu32, int mode, double *partials, Scalars *sc, cudaStream_t st);
 
 template <typename T>
 void launch_dot(const T *a, const T *b, long long n, double *partials, Scalars *sc, int fin,
@@ -130,33 +145,17 @@ struct FacDev {
     const int *nodeList, *nodeIdx;
 };
 
-// Explicit scaled deflation basis Z~ = L^T Z (per node b_I x M_s, row-major
-// at zOff[I]) and scaled W~ = L^-1 W, both FP32, plus box lists.
-struct ScaledDev {
-    int nNodes, nBox;
-    const int *dofStart, *sub, *col0, *menr;
-    const long long *zOff;
-    const float *Zt;
-    const int *ownPtr, *ownNodes, *extPtr, *extNode;
-    const long long *wOff;
-    const float *Wt;
-};
-
 void launch_gather(const int *src, long long n, const double *v, double *out64, float *out32,
                    cudaStream_t st);
-void launch_build_Zt(int nNodes, const int *dofStart, const int *sub, const double *xrel,
-                     const signed char *hsign, const int *menr, const FacDev &F,
-                     const long long *zOff, float *Zt, cudaStream_t st);
+void launch_build_Zt(int nSlots, const int *slotNode, const int *dofStart, const int *sub,
+                     const double *xrel, const signed char *hsign, const int *menr,
+                     const FacDev &F, const long long *zOff, float *Zt, cudaStream_t st);
 void launch_fwd_scale(int nNodes, const int *dofStart, const FacDev &F, const double *r, double s,
                       float *out, cudaStream_t st);
 void launch_bwd_accum(int nNodes, const int *dofStart, const FacDev &F, const float *ut,
                       double scale, double *u, cudaStream_t st);
 void launch_update_id(float *u, float *r, const float *p, const float *q, long long n, int mode,
                       double *partials, Scalars *sc, cudaStream_t st);
-void launch_restrict_z(const ScaledDev &D, const float *a, const float *b, int withW, double *g,
-                       double *zr, const Scalars *sc, cudaStream_t st);
-void launch_prolong_z(const ScaledDev &D, const double *nu, const float *y, float *p, int mode,
-                      Scalars *sc, cudaStream_t st);
 
 // ---- set-up kernels -------------------------------------------------------
 

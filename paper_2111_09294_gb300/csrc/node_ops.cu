@@ -1,39 +1,11 @@
-// Node- and box-level kernels of the A-DEF2 iteration:
-//   update   u += alpha p, r -= alpha q (Algorithm 1), y = M^-1 r with the
-//            node-block Cholesky factors (Algorithm 3, first step; blocks of
-//            Eqs. block_jacobi / block_jacobi_enr), partial ||r||^2, r^T y;
-//   restrict g = Z^T r - W^T y per box (Algorithm 3, right-hand sides of
-//            both coarse solves merged: lambda - mu = E^-1 (Z^T r - W^T y));
-//   prolong  p = y + Z nu + beta p (Algorithm 3 last step fused with the
-//            direction update of Algorithm 1), or u = Z nu (Algorithm 2).
-// Z is never stored: its rows are rebuilt from the node position relative
-// to the box centre (Eqs. dcg_deflation_space, dcg_deflation_space_enr_std,
-// dcg_deflation_space_enr_enr).
+// Node-level kernels of the A-DEF2 iteration: the update u += alpha p,
+// r -= alpha q (Algorithm 1) fused with y = M^-1 r through the node-block
+// Cholesky factors (Algorithm 3, first step; blocks of Eqs. block_jacobi /
+// block_jacobi_enr) and the partial sums ||r||^2, r^T y; and the set-up
+// factorisation of the node blocks.
 #include "reduce.cuh"
 
 namespace xdcg {
-
-// ---- rigid-body block R(x) of the deflation space -------------------------
-
-// R^T a for a 3-vector a: the 6 coarse entries a node's 3 dofs feed.
-template <typename T>
-__device__ __forceinline__ void rigid_t(double a0, double a1, double a2, T X, T Y, T Z,
-                                        double (&o)[6]) {
-    o[0] = a0;
-    o[1] = a1;
-    o[2] = a2;
-    o[3] = -(double)Z * a1 + (double)Y * a2;
-    o[4] = (double)Z * a0 - (double)X * a2;
-    o[5] = -(double)Y * a0 + (double)X * a1;
-}
-
-// R nu for 6 coarse values: the displacement the rigid modes give the node.
-template <typename T>
-__device__ __forceinline__ void rigid(const T (&n)[6], T X, T Y, T Z, T (&v)[3]) {
-    v[0] = n[0] + Z * n[4] - Y * n[5];
-    v[1] = n[1] - Z * n[3] + X * n[5];
-    v[2] = n[2] + Y * n[3] - X * n[4];
-}
 
 // ---- update + block-Jacobi apply ----------------------------------------
 
@@ -148,7 +120,7 @@ k_update(NodeDev<T> N, T *u, T *r, const T *p, const T *q, T *y, int mode, int n
                                alpha, v[0], v[1]);
     }
     double tot[2];
-    if (grid_sum<2>(v, partials, &sc->ticket[2], tot) && threadIdx.x == 0) {
+    if (grid_sum<double, 2>(v, partials, &sc->ticket[2], tot) && threadIdx.x == 0) {
         sc->ry = tot[1];
         sc->rr = tot[0];
         if (tot[0] <= sc->tol2ff)
@@ -176,143 +148,6 @@ template void launch_update<double>(const NodeDev<double> &, double *, double *,
                                     cudaStream_t);
 template void launch_update<float>(const NodeDev<float> &, float *, float *, const float *,
                                    const float *, float *, int, double *, Scalars *, cudaStream_t);
-
-// ---- restriction g = Z^T a - W^T b -----------------------------------------
-
-constexpr int kBoxThreads = 128;
-
-template <typename T, int M>
-__device__ __forceinline__ void restrict_box(const NodeDev<T> &N, const BoxDev<T> &B, int s,
-                                             const T *a, const T *b, int withW, double *g,
-                                             double *zr) {
-    double acc[2 * M];
-#pragma unroll
-    for (int c = 0; c < 2 * M; ++c) acc[c] = 0.0;
-    const int o1 = B.ownPtr[s + 1];
-    for (int t = B.ownPtr[s] + threadIdx.x; t < o1; t += blockDim.x) {
-        const int I = B.ownNodes[t];
-        const long long d0 = N.dofStart[I];
-        const T X = N.xrel[3 * I], Y = N.xrel[3 * I + 1], Z = N.xrel[3 * I + 2];
-        double z[6];
-        rigid_t<T>((double)a[d0], (double)a[d0 + 1], (double)a[d0 + 2], X, Y, Z, z);
-#pragma unroll
-        for (int c = 0; c < 6; ++c) acc[c] += z[c];
-        if (M == 12) {
-            const double H = (double)N.hsign[I];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) acc[6 + c] += H * z[c];
-            if (N.dofStart[I + 1] - d0 == 6) {
-                rigid_t<T>((double)a[d0 + 3], (double)a[d0 + 4], (double)a[d0 + 5], X, Y, Z, z);
-#pragma unroll
-                for (int c = 0; c < 6; ++c) acc[6 + c] += z[c];
-            }
-        }
-    }
-    if (withW) {
-        const int e1 = B.extPtr[s + 1];
-        for (int e = B.extPtr[s] + threadIdx.x; e < e1; e += blockDim.x) {
-            const int I = B.extNode[e];
-            const long long d0 = N.dofStart[I];
-            const int bI = N.dofStart[I + 1] - (int)d0;
-            const T *Wb = B.W + B.wOff[e];
-            for (int i = 0; i < bI; ++i) {
-                const double bv = (double)b[d0 + i];
-#pragma unroll
-                for (int c = 0; c < M; ++c) acc[M + c] += (double)Wb[i * M + c] * bv;
-            }
-        }
-    }
-    block_sum<2 * M>(acc);
-    if (threadIdx.x == 0) {
-        const int c0 = N.col0[s];
-#pragma unroll
-        for (int c = 0; c < M; ++c) {
-            g[c0 + c] = acc[c] - acc[M + c];
-            if (zr) zr[c0 + c] = acc[c];
-        }
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kBoxThreads)
-k_restrict(NodeDev<T> N, BoxDev<T> B, const T *a, const T *b, int withW, double *g, double *zr,
-           const Scalars *sc) {
-    if (sc && sc->done != kRunning) return;
-    const int s = blockIdx.x;
-    if (N.menr[s])
-        restrict_box<T, 12>(N, B, s, a, b, withW, g, zr);
-    else
-        restrict_box<T, 6>(N, B, s, a, b, withW, g, zr);
-}
-
-template <typename T>
-void launch_restrict(const NodeDev<T> &N, const BoxDev<T> &B, const T *a, const T *b, int withW,
-                     double *g, double *zr, cudaStream_t st, const Scalars *sc) {
-    k_restrict<T><<<B.nBox, kBoxThreads, 0, st>>>(N, B, a, b, withW, g, zr, sc);
-}
-template void launch_restrict<double>(const NodeDev<double> &, const BoxDev<double> &,
-                                      const double *, const double *, int, double *, double *,
-                                      cudaStream_t, const Scalars *);
-template void launch_restrict<float>(const NodeDev<float> &, const BoxDev<float> &, const float *,
-                                     const float *, int, double *, double *, cudaStream_t,
-                                     const Scalars *);
-
-// ---- prolongation ----------------------------------------------------------
-
-// mode 0: p = y + Z nu + beta p;  mode 1: p = Z nu;  mode 2: p = y + Z nu
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_prolong(NodeDev<T> N, const double *__restrict__ nu, const T *__restrict__ y, T *p, int mode,
-          Scalars *sc) {
-    if (sc->done != kRunning) return;
-    const int I = blockIdx.x * kThreads + threadIdx.x;
-    if (I >= N.nNodes) return;
-    const long long d0 = N.dofStart[I];
-    const int bI = N.dofStart[I + 1] - (int)d0;
-    const int s = N.sub[I];
-    const int c0 = N.col0[s];
-    const int menr = N.menr[s];
-    const T X = N.xrel[3 * I], Y = N.xrel[3 * I + 1], Z = N.xrel[3 * I + 2];
-    T n6[6], v[3], ve[3] = {T(0), T(0), T(0)};
-#pragma unroll
-    for (int c = 0; c < 6; ++c) n6[c] = (T)nu[c0 + c];
-    rigid<T>(n6, X, Y, Z, v);
-    if (menr) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) n6[c] = (T)nu[c0 + 6 + c];
-        rigid<T>(n6, X, Y, Z, ve);
-        const T H = (T)N.hsign[I];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) v[c] += H * ve[c];
-    }
-    const T beta = (T)sc->beta;
-    for (int i = 0; i < bI; ++i) {
-        T zv;
-        if (i < 3)
-            zv = v[i];
-        else if (bI == 6 && menr)
-            zv = ve[i - 3];
-        else
-            zv = T(0);
-        const long long d = d0 + i;
-        if (mode == 0)
-            p[d] = y[d] + zv + beta * p[d];
-        else if (mode == 1)
-            p[d] = zv;
-        else
-            p[d] = y[d] + zv;
-    }
-}
-
-template <typename T>
-void launch_prolong(const NodeDev<T> &N, const double *nu, const T *y, T *p, int mode,
-                    Scalars *sc, cudaStream_t st) {
-    k_prolong<T><<<cdiv(N.nNodes, kThreads), kThreads, 0, st>>>(N, nu, y, p, mode, sc);
-}
-template void launch_prolong<double>(const NodeDev<double> &, const double *, const double *,
-                                     double *, int, Scalars *, cudaStream_t);
-template void launch_prolong<float>(const NodeDev<float> &, const double *, const float *,
-                                    float *, int, Scalars *, cudaStream_t);
 
 // ---- set-up: node-block Cholesky (FP64) ------------------------------------
 

@@ -1,14 +1,19 @@
 // Deterministic warp / block / grid reductions.  Every block stores its
 // partial sums; the last block to finish (ticket counter) adds them in a
 // fixed order, so results do not depend on block scheduling.
+//
+// The accumulator type A is the kernel's own precision: FP32 kernels keep
+// their per-thread, warp and block sums in FP32 (FP64 arithmetic runs at
+// 1/64 of the FP32 rate on this GPU), and only the per-block partials are
+// combined in FP64 by the last block.
 #pragma once
 
 #include "internal.h"
 
 namespace xdcg {
 
-template <int NV>
-__device__ __forceinline__ void warp_sum(double (&v)[NV]) {
+template <typename A, int NV>
+__device__ __forceinline__ void warp_sum(A (&v)[NV]) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
@@ -17,10 +22,10 @@ __device__ __forceinline__ void warp_sum(double (&v)[NV]) {
 }
 
 // Sum over the block; the result is valid in thread 0.
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV]) {
-    __shared__ double sm[NV][32];
-    warp_sum<NV>(v);
+template <typename A, int NV>
+__device__ __forceinline__ void block_sum(A (&v)[NV]) {
+    __shared__ A sm[NV][32];
+    warp_sum<A, NV>(v);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
     __syncthreads();
     if (l == 0) {
@@ -30,21 +35,22 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
     __syncthreads();
     if (w == 0) {
 #pragma unroll
-        for (int i = 0; i < NV; ++i) v[i] = (l < nw) ? sm[i][l] : 0.0;
-        warp_sum<NV>(v);
+        for (int i = 0; i < NV; ++i) v[i] = (l < nw) ? sm[i][l] : A(0);
+        warp_sum<A, NV>(v);
     }
 }
 
 // Grid-wide sum.  Returns true in exactly one block (the last to finish),
-// where thread 0 then holds the totals in tot.  partials: NV * gridDim.x doubles.
-template <int NV>
-__device__ __forceinline__ bool grid_sum(double (&v)[NV], double *partials, unsigned int *ticket,
+// where thread 0 then holds the FP64 totals in tot.
+// partials: NV * gridDim.x doubles.
+template <typename A, int NV>
+__device__ __forceinline__ bool grid_sum(A (&v)[NV], double *partials, unsigned int *ticket,
                                          double (&tot)[NV]) {
     __shared__ bool last;
-    block_sum<NV>(v);
+    block_sum<A, NV>(v);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int i = 0; i < NV; ++i) partials[(size_t)i * gridDim.x + blockIdx.x] = v[i];
+        for (int i = 0; i < NV; ++i) partials[(size_t)i * gridDim.x + blockIdx.x] = (double)v[i];
         __threadfence();
         unsigned int t = atomicAdd(ticket, 1u);
         last = (t == gridDim.x - 1);
@@ -59,7 +65,7 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NV], double *partials, unsi
 #pragma unroll
         for (int i = 0; i < NV; ++i) s[i] += __ldcg(partials + (size_t)i * gridDim.x + b);
     }
-    block_sum<NV>(s);
+    block_sum<double, NV>(s);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int i = 0; i < NV; ++i) tot[i] = s[i];

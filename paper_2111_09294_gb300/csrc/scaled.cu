@@ -116,12 +116,13 @@ __device__ __forceinline__ void zrow(int j, int b, int menr, double X, double Y,
     }
 }
 
-// Z~_I = L_I^T Z_I (b_I x M, row-major at zOff[I]), FP32.
-__global__ void k_build_Zt(int nNodes, const int *dofStart, const int *sub, const double *xrel,
-                           const signed char *hsign, const int *menr, FacDev F,
-                           const long long *zOff, float *Zt) {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= nNodes) return;
+// Z~_I = L_I^T Z_I (b_I x M, row-major at zOff[t] for slot t holding node I), FP32.
+__global__ void k_build_Zt(int nSlots, const int *slotNode, const int *dofStart, const int *sub,
+                           const double *xrel, const signed char *hsign, const int *menr,
+                           FacDev F, const long long *zOff, float *Zt) {
+    const int ts = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ts >= nSlots) return;
+    const int I = slotNode[ts];
     const int b = dofStart[I + 1] - dofStart[I];
     const int s = sub[I], me = menr[s], M = me ? 12 : 6;
     const double X = xrel[3 * I], Y = xrel[3 * I + 1], Z = xrel[3 * I + 2], H = hsign[I];
@@ -139,15 +140,15 @@ __global__ void k_build_Zt(int nNodes, const int *dofStart, const int *sub, cons
             for (int c = 0; c < M; ++c) acc[i * M + c] += lji * zr[c];
         }
     }
-    float *out = Zt + zOff[I];
+    float *out = Zt + zOff[ts];
     for (int e = 0; e < b * M; ++e) out[e] = (float)acc[e];
 }
 
-void launch_build_Zt(int nNodes, const int *dofStart, const int *sub, const double *xrel,
-                     const signed char *hsign, const int *menr, const FacDev &F,
-                     const long long *zOff, float *Zt, cudaStream_t st) {
-    k_build_Zt<<<(nNodes + 127) / 128, 128, 0, st>>>(nNodes, dofStart, sub, xrel, hsign, menr, F,
-                                                     zOff, Zt);
+void launch_build_Zt(int nSlots, const int *slotNode, const int *dofStart, const int *sub,
+                     const double *xrel, const signed char *hsign, const int *menr,
+                     const FacDev &F, const long long *zOff, float *Zt, cudaStream_t st) {
+    k_build_Zt<<<(nSlots + 127) / 128, 128, 0, st>>>(nSlots, slotNode, dofStart, sub, xrel, hsign,
+                                                     menr, F, zOff, Zt);
 }
 
 // W~ = L^-1 W per W entry (b_I x M), FP32.
@@ -221,7 +222,7 @@ k_update_id(float *u, float *r, const float *p, const float *q, long long n, int
             double *partials, Scalars *sc) {
     if (sc->done != kRunning) return;
     const float alpha = (float)sc->alpha;
-    double v[1] = {0.0};
+    float v[1] = {0.0f};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         float ri = r[i];
@@ -230,10 +231,10 @@ k_update_id(float *u, float *r, const float *p, const float *q, long long n, int
             ri = fmaf(-alpha, q[i], ri);
             r[i] = ri;
         }
-        v[0] += (double)ri * (double)ri;
+        v[0] = fmaf(ri, ri, v[0]);
     }
     double tot[1];
-    if (grid_sum<1>(v, partials, &sc->ticket[2], tot) && threadIdx.x == 0) {
+    if (grid_sum<float, 1>(v, partials, &sc->ticket[2], tot) && threadIdx.x == 0) {
         sc->rr = tot[0];
         sc->ry = tot[0];
         if (tot[0] <= sc->tol2ff)
@@ -248,98 +249,6 @@ k_update_id(float *u, float *r, const float *p, const float *q, long long n, int
 void launch_update_id(float *u, float *r, const float *p, const float *q, long long n, int mode,
                       double *partials, Scalars *sc, cudaStream_t st) {
     k_update_id<<<grid_of(n, kThreads), kThreads, 0, st>>>(u, r, p, q, n, mode, partials, sc);
-}
-
-constexpr int kBoxThreads = 128;
-
-// g = Z~^T a - W~^T b per box (b = a when the preconditioner is the identity)
-template <int M>
-__device__ __forceinline__ void restrict_z_box(const ScaledDev &D, int s, const float *a,
-                                               const float *b, int withW, double *g,
-                                               double *zr) {
-    double acc[2 * M];
-#pragma unroll
-    for (int c = 0; c < 2 * M; ++c) acc[c] = 0.0;
-    const int o1 = D.ownPtr[s + 1];
-    for (int t = D.ownPtr[s] + threadIdx.x; t < o1; t += blockDim.x) {
-        const int I = D.ownNodes[t];
-        const int d0 = D.dofStart[I], bI = D.dofStart[I + 1] - d0;
-        const float *Zb = D.Zt + D.zOff[I];
-        for (int i = 0; i < bI; ++i) {
-            const double av = (double)a[d0 + i];
-#pragma unroll
-            for (int c = 0; c < M; ++c) acc[c] += (double)Zb[i * M + c] * av;
-        }
-    }
-    if (withW) {
-        const int e1 = D.extPtr[s + 1];
-        for (int e = D.extPtr[s] + threadIdx.x; e < e1; e += blockDim.x) {
-            const int I = D.extNode[e];
-            const int d0 = D.dofStart[I], bI = D.dofStart[I + 1] - d0;
-            const float *Wb = D.Wt + D.wOff[e];
-            for (int i = 0; i < bI; ++i) {
-                const double bv = (double)b[d0 + i];
-#pragma unroll
-                for (int c = 0; c < M; ++c) acc[M + c] += (double)Wb[i * M + c] * bv;
-            }
-        }
-    }
-    block_sum<2 * M>(acc);
-    if (threadIdx.x == 0) {
-        const int c0 = D.col0[s];
-#pragma unroll
-        for (int c = 0; c < M; ++c) {
-            g[c0 + c] = acc[c] - acc[M + c];
-            if (zr) zr[c0 + c] = acc[c];
-        }
-    }
-}
-
-__global__ void __launch_bounds__(kBoxThreads)
-k_restrict_z(ScaledDev D, const float *a, const float *b, int withW, double *g, double *zr,
-             const Scalars *sc) {
-    if (sc && sc->done != kRunning) return;
-    const int s = blockIdx.x;
-    if (D.menr[s])
-        restrict_z_box<12>(D, s, a, b, withW, g, zr);
-    else
-        restrict_z_box<6>(D, s, a, b, withW, g, zr);
-}
-
-void launch_restrict_z(const ScaledDev &D, const float *a, const float *b, int withW, double *g,
-                       double *zr, const Scalars *sc, cudaStream_t st) {
-    k_restrict_z<<<D.nBox, kBoxThreads, 0, st>>>(D, a, b, withW, g, zr, sc);
-}
-
-// mode 0: p = y + Z~ nu + beta p;  mode 1: p = Z~ nu;  mode 2: p = y + Z~ nu
-__global__ void __launch_bounds__(kThreads)
-k_prolong_z(ScaledDev D, const double *__restrict__ nu, const float *__restrict__ y, float *p,
-            int mode, Scalars *sc) {
-    if (sc->done != kRunning) return;
-    const int I = blockIdx.x * kThreads + threadIdx.x;
-    if (I >= D.nNodes) return;
-    const int d0 = D.dofStart[I], bI = D.dofStart[I + 1] - d0;
-    const int s = D.sub[I], c0 = D.col0[s], M = D.menr[s] ? 12 : 6;
-    const float *Zb = D.Zt + D.zOff[I];
-    float n12[12];
-    for (int c = 0; c < M; ++c) n12[c] = (float)nu[c0 + c];
-    const float beta = (float)sc->beta;
-    for (int i = 0; i < bI; ++i) {
-        float zv = 0.0f;
-        for (int c = 0; c < M; ++c) zv = fmaf(Zb[i * M + c], n12[c], zv);
-        const int d = d0 + i;
-        if (mode == 0)
-            p[d] = y[d] + zv + beta * p[d];
-        else if (mode == 1)
-            p[d] = zv;
-        else
-            p[d] = y[d] + zv;
-    }
-}
-
-void launch_prolong_z(const ScaledDev &D, const double *nu, const float *y, float *p, int mode,
-                      Scalars *sc, cudaStream_t st) {
-    k_prolong_z<<<(D.nNodes + kThreads - 1) / kThreads, kThreads, 0, st>>>(D, nu, y, p, mode, sc);
 }
 
 }  // namespace xdcg

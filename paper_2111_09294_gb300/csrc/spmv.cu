@@ -19,7 +19,7 @@ k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__rest
        int nbS, double *partials, Scalars *sc, int fin, int slot) {
     if (sc->done != kRunning) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double part[1] = {0.0};
+    T part[1] = {T(0)};
     if ((int)blockIdx.x < nbS) {
         const int slice = blockIdx.x * kWarps + warp;
         const int rl = slice * 32 + lane;
@@ -51,10 +51,10 @@ k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__rest
                 a0 = br[0] - a0;
                 a1 = br[1] - a1;
                 a2 = br[2] - a2;
-                part[0] = (double)a0 * a0 + (double)a1 * a1 + (double)a2 * a2;
+                part[0] = a0 * a0 + a1 * a1 + a2 * a2;
             } else {
                 const T *xr = x + 3 * (long long)row;
-                part[0] = (double)xr[0] * a0 + (double)xr[1] * a1 + (double)xr[2] * a2;
+                part[0] = xr[0] * a0 + xr[1] * a1 + xr[2] * a2;
             }
             yr[0] = a0;
             yr[1] = a1;
@@ -94,10 +94,10 @@ k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__rest
                     a0 = br[0] - a0;
                     a1 = br[1] - a1;
                     a2 = br[2] - a2;
-                    part[0] = (double)a0 * a0 + (double)a1 * a1 + (double)a2 * a2;
+                    part[0] = a0 * a0 + a1 * a1 + a2 * a2;
                 } else {
                     const T *xr = x + 3 * (long long)row;
-                    part[0] = (double)xr[0] * a0 + (double)xr[1] * a1 + (double)xr[2] * a2;
+                    part[0] = xr[0] * a0 + xr[1] * a1 + xr[2] * a2;
                 }
                 yr[0] = a0;
                 yr[1] = a1;
@@ -106,7 +106,7 @@ k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__rest
         }
     }
     double tot[1];
-    if (grid_sum<1>(part, partials, &sc->ticket[0], tot) && threadIdx.x == 0)
+    if (grid_sum<T, 1>(part, partials, &sc->ticket[0], tot) && threadIdx.x == 0)
         finalize(sc, fin, slot, tot[0]);
 }
 
@@ -138,12 +138,12 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_dot(const T *__restrict__ a, const T *__restrict__ b, long long n, double *partials,
       Scalars *sc, int fin, int slot) {
-    double part[1] = {0.0};
+    T part[1] = {T(0)};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
-        part[0] += (double)a[i] * (double)b[i];
+        part[0] = fma(a[i], b[i], part[0]);
     double tot[1];
-    if (grid_sum<1>(part, partials, &sc->ticket[1], tot) && threadIdx.x == 0)
+    if (grid_sum<T, 1>(part, partials, &sc->ticket[1], tot) && threadIdx.x == 0)
         finalize(sc, fin, slot, tot[0]);
 }
 
