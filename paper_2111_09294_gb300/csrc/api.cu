@@ -26,7 +26,7 @@ struct Level64 {
 };
 struct Level32 {          // block-scaled system K~ = L^-1 K L^-T in FP32
     SpmvDev<float> A;
-    BoxDev<float> B;
+    RowBoxDev R;
     FacDev F;
     const int *dofStart;
 };
@@ -198,28 +198,6 @@ struct PlainPath {
     }
 };
 
-// Block-scaled FP32 path: identity preconditioner (y = r), explicit Z~, W~.
-struct ScaledPath {
-    xdcg_ctx *c;
-    Level32 &L;
-    void spmv(const float *x, float *y, const float *b, int res, int fin, Scalars *sc) {
-        launch_spmv<float>(L.A, x, y, b, res, c->partials, sc, fin, 0, c->st);
-    }
-    void update(float *u, float *r, const float *p, const float *q, float *, int mode,
-                Scalars *sc) {
-        launch_update_id(u, r, p, q, c->n, mode, c->partials, sc, c->st);
-    }
-    void restrict_(const float *a, const float *b, int withW, double *zr, Scalars *sc) {
-        launch_restrict_z(L.B, a, b, withW, c->g, zr, sc, c->st);
-    }
-    void coarse(const double *zr, int mode, Scalars *sc) {
-        launch_coarse(c->Einv, c->k, c->g, zr, c->nu, c->nu32, mode, c->partials, sc, c->st);
-    }
-    void prolong(const float *y, float *p, int mode, Scalars *sc) {
-        launch_prolong_z(L.B, c->nu32, y, p, mode, sc, c->st);
-    }
-};
-
 template <typename T, typename Path>
 xdcg_status run_pcg(xdcg_ctx *c, Path path, const T *f, T *u, T *r, T *p, T *q, T *y,
                     Scalars *sc, int max_it, bool time_spmv, int *its_out, int *done_out,
@@ -258,6 +236,77 @@ xdcg_status run_pcg(xdcg_ctx *c, Path path, const T *f, T *u, T *r, T *p, T *q, 
             path.coarse(c->zr, 2, sc);
             path.prolong(y, p, 0, sc);
             c->launches += 5;
+            ++launched;
+        }
+        CK(cudaMemcpyAsync(&c->h_done[b & 1], &sc->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaEventRecord(c->evb[b & 1], st));
+        if (b >= 1) {
+            CK(cudaEventSynchronize(c->evb[(b - 1) & 1]));
+            if (c->h_done[(b - 1) & 1] != kRunning) break;
+        }
+    }
+    CK(cudaMemcpyAsync(c->h_sc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    *its_out = c->h_sc->its;
+    *done_out = c->h_sc->done;
+    if (time_spmv) {
+        const int nt = std::min(launched, c->h_sc->its);
+        for (int i = 0; i < nt; ++i) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, c->evS[i], c->evE[i]));
+            *t_spmv += ms;
+        }
+        *n_spmv += nt;
+    }
+    return XDCG_OK;
+}
+
+// The FP32 inner solve on the block-scaled system: four kernels per
+// iteration (SpMV with p^T q; restriction fused with the u, r update and
+// ||r||^2; coarse solve; prolongation), the residual double-buffered so that
+// the restriction can read the old residual of neighbouring boxes while it
+// writes the new one of its own.
+xdcg_status run_pcg_scaled(xdcg_ctx *c, const float *f, float *u, float *rA, float *rB, float *p,
+                           float *q, Scalars *sc, int max_it, bool time_spmv, int *its_out,
+                           int *done_out, double *t_spmv, int *n_spmv) {
+    cudaStream_t st = c->st;
+    Level32 &L = c->L32;
+    // Algorithm 2 with u_-1 = 0: u_0 = Z~ E^-1 Z~^T f
+    launch_restrict_update(L.R, nullptr, f, nullptr, nullptr, nullptr, 2, c->g, nullptr,
+                           c->partials, sc, st);
+    launch_coarse(c->Einv, c->k, c->g, nullptr, c->nu, c->nu32, 0, c->partials, sc, st);
+    launch_prolong_rows(L.R, c->nu32, nullptr, u, 1, sc, st);
+    // r_0 = f - K~ u_0 (into rA), z_0 by Algorithm 3 (identity block Jacobi), p_0 = z_0
+    launch_spmv<float>(L.A, u, rA, f, 1, c->partials, sc, kFinRR, 0, st);
+    launch_restrict_update(L.R, nullptr, rA, nullptr, nullptr, nullptr, 1, c->g, c->zr,
+                           c->partials, sc, st);
+    launch_coarse(c->Einv, c->k, c->g, c->zr, c->nu, c->nu32, 1, c->partials, sc, st);
+    launch_prolong_rows(L.R, c->nu32, rA, p, 2, sc, st);
+    c->launches += 7;
+
+    int launched = 0;
+    const int max_batches = max_it / kBatch + 2;
+    for (int b = 0; b < max_batches; ++b) {
+        for (int i = 0; i < kBatch; ++i) {
+            float *rc = (launched & 1) ? rB : rA;
+            float *rn = (launched & 1) ? rA : rB;
+            if (time_spmv) {
+                if ((int)c->evS.size() <= launched) {
+                    cudaEvent_t e0, e1;
+                    CK(cudaEventCreate(&e0));
+                    CK(cudaEventCreate(&e1));
+                    c->evS.push_back(e0);
+                    c->evE.push_back(e1);
+                }
+                CK(cudaEventRecord(c->evS[launched], st));
+            }
+            launch_spmv<float>(L.A, p, q, nullptr, 0, c->partials, sc, kFinAlpha, 0, st);
+            if (time_spmv) CK(cudaEventRecord(c->evE[launched], st));
+            launch_restrict_update(L.R, u, rc, rn, p, q, 0, c->g, c->zr, c->partials, sc, st);
+            launch_coarse(c->Einv, c->k, c->g, c->zr, c->nu, c->nu32, 2, c->partials, sc, st);
+            launch_prolong_rows(L.R, c->nu32, rn, p, 0, sc, st);
+            c->launches += 4;
             ++launched;
         }
         CK(cudaMemcpyAsync(&c->h_done[b & 1], &sc->done, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -343,9 +392,9 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, xdc
         init_scalars(c, c->sc32, eta * eta, &c->aux->scratch[0], c->opt.max_iter - total);
         c->launches += 3;
         int its = 0, done = 0;
-        s = run_pcg<float>(c, ScaledPath{c, c->L32}, c->f32, c->u32, c->r32, c->p32, c->q32,
-                           c->r32, c->sc32, c->opt.max_iter - total, c->opt.time_spmv != 0, &its,
-                           &done, &res->t_spmv_ms, &res->n_spmv_timed);
+        s = run_pcg_scaled(c, c->f32, c->u32, c->r32, c->y32, c->p32, c->q32, c->sc32,
+                           c->opt.max_iter - total, c->opt.time_spmv != 0, &its, &done,
+                           &res->t_spmv_ms, &res->n_spmv_timed);
         if (s != XDCG_OK) return s;
         total += its;
         cycles++;
@@ -531,47 +580,71 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         }
         (void)bI;
     };
-    const int nS = (int)sRows.size(), nSlices = (nS + 31) / 32;
-    std::vector<int> lenS(nS);
-    std::vector<long long> slicePtr(nSlices + 1, 0);
-    for (int s = 0; s < nSlices; ++s) {
-        int mx = 0;
-        for (int l = 0; l < 32 && s * 32 + l < nS; ++l) mx = std::max(mx, rowLen[sRows[s * 32 + l]]);
-        slicePtr[s + 1] = slicePtr[s] + 32LL * mx;
-    }
-    std::vector<int> colS(slicePtr[nSlices]);
-    std::vector<int> srcS(9 * (size_t)slicePtr[nSlices], -1);
-    for (int s = 0; s < nSlices; ++s)
-        for (int l = 0; l < 32 && s * 32 + l < nS; ++l) {
-            const int r = sRows[s * 32 + l];
-            lenS[s * 32 + l] = rowLen[r];
-            const long long base = slicePtr[s];
-            const long long slots = (slicePtr[s + 1] - base) / 32;
-            for (long long j = 0; j < slots; ++j) colS[base + j * 32 + l] = r;
-            for_blocks(r, [&](int t, int cc, const int *blk) {
-                colS[base + (long long)t * 32 + l] = cc;
-                for (int e = 0; e < 9; ++e) srcS[9 * base + ((long long)t * 9 + e) * 32 + l] = blk[e];
-            });
+    // sliced-ELL layouts: S rows in natural order, X rows sorted by length
+    // X rows: bucketed by length (so a slice pads little), in natural order
+    // within a bucket (so a slice's rows are spatial neighbours and the x
+    // gathers of one step coalesce)
+    std::stable_sort(xRows.begin(), xRows.end(), [&](int a, int b) {
+        const int ba = rowLen[a] / kXBucket, bb = rowLen[b] / kXBucket;
+        return ba != bb ? ba > bb : a < b;
+    });
+    struct SellHost {
+        std::vector<int> row, len, col, src;
+        std::vector<long long> slicePtr;
+        int nSlices = 0, ilvSteps = 0;
+    };
+    auto build_sell = [&](const std::vector<int> &rows, int tpr, bool interleave, SellHost &H) {
+        const int rpw = 32 / tpr;
+        const int nr = (int)rows.size();
+        H.nSlices = (nr + rpw - 1) / rpw;
+        H.row = rows;
+        H.len.resize(nr);
+        H.slicePtr.assign(H.nSlices + 1, 0);
+        int gmax = 0;
+        for (int sl = 0; sl < H.nSlices; ++sl) {
+            int mx = 0;
+            for (int q = 0; q < rpw && sl * rpw + q < nr; ++q) mx = std::max(mx, rowLen[rows[sl * rpw + q]]);
+            H.slicePtr[sl + 1] = H.slicePtr[sl] + 32LL * ((mx + tpr - 1) / tpr);
+            gmax = std::max(gmax, (mx + tpr - 1) / tpr);
         }
-    const int nX = (int)xRows.size();
-    std::vector<int> lenX(nX);
-    std::vector<long long> ptrX(nX + 1, 0);
-    for (int i = 0; i < nX; ++i) {
-        lenX[i] = rowLen[xRows[i]];
-        ptrX[i + 1] = ptrX[i] + 32LL * ((lenX[i] + 31) / 32);
-    }
-    std::vector<int> colX(std::max<long long>(ptrX[nX], 1), 0);
-    std::vector<int> srcX(9 * (size_t)std::max<long long>(ptrX[nX], 1), -1);
-    for (int i = 0; i < nX; ++i) {
-        const int r = xRows[i];
-        const long long base = ptrX[i];
-        for (long long t = 0; t < ptrX[i + 1] - base; ++t) colX[base + t] = r;
-        for_blocks(r, [&](int t, int cc, const int *blk) {
-            colX[base + t] = cc;
-            for (int e = 0; e < 9; ++e)
-                srcX[9 * base + 288LL * (t >> 5) + 32 * e + (t & 31)] = blk[e];
-        });
-    }
+        H.ilvSteps = interleave ? std::max(gmax, 1) : 0;
+        const long long slots = interleave ? 32LL * H.nSlices * H.ilvSteps
+                                           : std::max<long long>(H.slicePtr[H.nSlices], 1);
+        H.col.assign(std::max<long long>(slots, 1), 0);
+        H.src.assign(9 * (size_t)std::max<long long>(slots, 1), -1);
+        const long long NS = H.nSlices;
+        for (int sl = 0; sl < H.nSlices; ++sl) {
+            const long long base = H.slicePtr[sl];
+            const long long steps = interleave ? H.ilvSteps : (H.slicePtr[sl + 1] - base) / 32;
+            auto cidx = [&](long long st2, int lane) {
+                return interleave ? (st2 * NS + sl) * 32 + lane : base + st2 * 32 + lane;
+            };
+            auto vidx = [&](long long st2, int e, int lane) {
+                return interleave ? ((st2 * 9 + e) * NS + sl) * 32 + lane
+                                  : 9 * base + (st2 * 9 + e) * 32 + lane;
+            };
+            for (int q = 0; q < rpw && sl * rpw + q < nr; ++q) {
+                const int r = rows[sl * rpw + q];
+                H.len[sl * rpw + q] = rowLen[r];
+                for (long long st2 = 0; st2 < steps; ++st2)
+                    for (int h = 0; h < tpr; ++h) H.col[cidx(st2, q + rpw * h)] = r;
+                for_blocks(r, [&](int t, int cc, const int *blk) {
+                    const long long st2 = t / tpr;
+                    const int lane = q + rpw * (t % tpr);
+                    H.col[cidx(st2, lane)] = cc;
+                    for (int e = 0; e < 9; ++e) H.src[vidx(st2, e, lane)] = blk[e];
+                });
+            }
+            // lanes of a partial last slice point at a valid row
+            for (int q = nr - sl * rpw; q < rpw && q > 0; ++q)
+                for (long long st2 = 0; st2 < steps; ++st2)
+                    for (int h = 0; h < tpr; ++h) H.col[cidx(st2, q + rpw * h)] = 0;
+        }
+    };
+    SellHost HS, HX;
+    build_sell(sRows, kTprS, false, HS);
+    build_sell(xRows, kTprX, false, HX);
+    const int nS = (int)sRows.size(), nX = (int)xRows.size();
     long long nnzb3 = 0;
     for (long long r = 0; r < nChunks; ++r) nnzb3 += rowLen[r];
 
@@ -681,29 +754,24 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     kin.val = d_val;
     if (!kin.rowPtr || !kin.col || !kin.valPtr || !kin.val) return XDCG_OOM;
     // SpMV layouts: values gathered on the device through the index maps
-    int *d_srcS = upload_tmp(c, srcS), *d_srcX = upload_tmp(c, srcX);
-    if (!d_srcS || !d_srcX) return XDCG_OOM;
+    auto upload_sell = [&](const SellHost &H, SellDev<double> &D, int **d_src) -> bool {
+        D.nRows = (int)H.row.size();
+        D.nSlices = H.nSlices;
+        D.ilvSteps = H.ilvSteps;
+        D.row = upload(c, H.row);
+        D.len = upload(c, H.len);
+        D.slicePtr = upload(c, H.slicePtr);
+        D.col = upload(c, H.col);
+        double *v = dalloc<double>(c, H.src.size());
+        *d_src = upload_tmp(c, H.src);
+        D.val = v;
+        if (!D.row || !D.len || !D.slicePtr || !D.col || !v || !*d_src) return false;
+        launch_gather(*d_src, (long long)H.src.size(), d_val, v, nullptr, st);
+        return true;
+    };
     auto &A = c->L64.A;
-    A.nS = nS;
-    A.nSlices = nSlices;
-    A.rowS = upload(c, sRows);
-    A.lenS = upload(c, lenS);
-    A.slicePtr = upload(c, slicePtr);
-    A.colS = upload(c, colS);
-    double *d_valS = dalloc<double>(c, srcS.size());
-    A.valS = d_valS;
-    A.nX = nX;
-    A.rowX = upload(c, xRows);
-    A.lenX = upload(c, lenX);
-    A.ptrX = upload(c, ptrX);
-    A.colX = upload(c, colX);
-    double *d_valX = dalloc<double>(c, srcX.size());
-    A.valX = d_valX;
-    if (!A.rowS || !A.lenS || !A.slicePtr || !A.colS || !A.valS || !A.rowX || !A.lenX ||
-        !A.ptrX || !A.colX || !A.valX)
-        return XDCG_OOM;
-    launch_gather(d_srcS, (long long)srcS.size(), d_val, d_valS, nullptr, st);
-    launch_gather(d_srcX, (long long)srcX.size(), d_val, d_valX, nullptr, st);
+    int *d_srcS = nullptr, *d_srcX = nullptr;
+    if (!upload_sell(HS, A.S, &d_srcS) || !upload_sell(HX, A.X, &d_srcX)) return XDCG_OOM;
 
     // node data and block factors (FP64)
     int *d_bad = dalloc<int>(c, 2);
@@ -836,30 +904,106 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         std::vector<long long> zOff(N + 1, 0);   // explicit Z~ blocks in slot order
         for (int t = 0; t < N; ++t)
             zOff[t + 1] = zOff[t] + (long long)ownB[t] * (menr[ownSub[t]] ? 12 : 6);
-        long long *d_zOff = upload(c, zOff);
-        float *d_Zt = dalloc<float>(c, zOff[N]);
-        float *d_Wt = dalloc<float>(c, nW);
-        float *v32S = dalloc<float>(c, srcS.size()), *v32X = dalloc<float>(c, srcX.size());
+        long long *d_zOff = upload_tmp(c, zOff);
+        float *d_Zt = dalloc_tmp<float>(c, zOff[N]);
+        float *d_Wt = dalloc_tmp<float>(c, nW);
+        float *v32S = dalloc<float>(c, HS.src.size()), *v32X = dalloc<float>(c, HX.src.size());
         if (!F.nodeList || !F.nodeIdx || !d_brow || !d_Kt || !d_zOff || !d_Zt || !d_Wt || !v32S ||
             !v32X)
             return XDCG_OOM;
         c->L32.F = F;
         CK(cudaMemcpyAsync(d_Kt, d_val, val.size() * sizeof(double), cudaMemcpyDeviceToDevice, st));
         launch_scale_blocks(kin, d_brow, nnzb, F, d_Kt, st);
-        launch_gather(d_srcS, (long long)srcS.size(), d_Kt, nullptr, v32S, st);
-        launch_gather(d_srcX, (long long)srcX.size(), d_Kt, nullptr, v32X, st);
+        launch_gather(d_srcS, (long long)HS.src.size(), d_Kt, nullptr, v32S, st);
+        launch_gather(d_srcX, (long long)HX.src.size(), d_Kt, nullptr, v32X, st);
         auto &A2 = c->L32.A;
-        A2.nS = nS; A2.nSlices = nSlices; A2.rowS = A.rowS; A2.lenS = A.lenS;
-        A2.slicePtr = A.slicePtr; A2.colS = A.colS; A2.valS = v32S;
-        A2.nX = nX; A2.rowX = A.rowX; A2.lenX = A.lenX; A2.ptrX = A.ptrX; A2.colX = A.colX;
-        A2.valX = v32X;
+        auto copy_struct = [](const SellDev<double> &D, const float *v, SellDev<float> &E) {
+            E.nRows = D.nRows; E.nSlices = D.nSlices; E.ilvSteps = D.ilvSteps; E.row = D.row;
+            E.len = D.len;
+            E.slicePtr = D.slicePtr; E.col = D.col; E.val = v;
+        };
+        copy_struct(A.S, v32S, A2.S);
+        copy_struct(A.X, v32X, A2.X);
         launch_build_Zt(N, d_own, d_dof, d_sub, d_x64, d_hs, d_menr, F, d_zOff, d_Zt, st);
         launch_scale_W(nExt, d_extBox, d_extNode, d_wOff, d_menr, d_dof, F, d_W, d_Wt, st);
-        auto &B32 = c->L32.B;
-        B32.nBox = S; B32.col0 = d_col0; B32.menr = d_menr; B32.ownPtr = d_ownPtr;
-        B32.ownDof = d_ownDof; B32.ownB = d_ownB; B32.ownH = d_ownH; B32.ownX = nullptr;
-        B32.ownZ = d_zOff; B32.Zt = d_Zt; B32.extPtr = d_extPtr; B32.extDof = d_extDof;
-        B32.extB = d_extB; B32.wOff = d_wOff; B32.W = d_Wt;
+        // row-parallel layouts: own rows (Z~) and coupled rows (W~) of each box,
+        // column-major per box
+        std::vector<int> ownRowPtr(S + 1, 0), ownRowStart(N), ownRowDof;
+        std::vector<long long> zBase(S + 1, 0);
+        for (int sb2 = 0; sb2 < S; ++sb2) {
+            for (int t = ownPtr[sb2]; t < ownPtr[sb2 + 1]; ++t) {
+                ownRowStart[t] = (int)ownRowDof.size();
+                for (int i = 0; i < ownB[t]; ++i) ownRowDof.push_back(ownDof[t] + i);
+            }
+            ownRowPtr[sb2 + 1] = (int)ownRowDof.size();
+            zBase[sb2 + 1] = zBase[sb2] + (long long)(menr[sb2] ? 12 : 6) *
+                                              (ownRowPtr[sb2 + 1] - ownRowPtr[sb2]);
+        }
+        std::vector<int> extRowPtr(S + 1, 0), extRowStart(nExt), extRowDof;
+        std::vector<long long> wBase(S + 1, 0);
+        for (int sb2 = 0; sb2 < S; ++sb2) {
+            for (int e = extPtr[sb2]; e < extPtr[sb2 + 1]; ++e) {
+                extRowStart[e] = (int)extRowDof.size();
+                for (int i = 0; i < extB[e]; ++i) extRowDof.push_back(extDof[e] + i);
+            }
+            extRowPtr[sb2 + 1] = (int)extRowDof.size();
+            wBase[sb2 + 1] = wBase[sb2] + (long long)(menr[sb2] ? 12 : 6) *
+                                              (extRowPtr[sb2 + 1] - extRowPtr[sb2]);
+        }
+        RowBoxDev &R = c->L32.R;
+        R.nBox = S;
+        R.col0 = d_col0;
+        R.menr = d_menr;
+        R.ownRowPtr = upload(c, ownRowPtr);
+        R.ownRowDof = upload(c, ownRowDof);
+        R.zBase = upload(c, zBase);
+        R.extRowPtr = upload(c, extRowPtr);
+        R.extRowDof = upload(c, extRowDof);
+        R.wBase = upload(c, wBase);
+        float *Zcm = dalloc<float>(c, zBase[S]), *Wcm = dalloc<float>(c, wBase[S]);
+        int *d_ownSub = upload_tmp(c, ownSub), *d_ors = upload_tmp(c, ownRowStart),
+            *d_ers = upload_tmp(c, extRowStart);
+        if (!R.ownRowPtr || !R.ownRowDof || !R.zBase || !R.extRowPtr || !R.extRowDof ||
+            !R.wBase || !Zcm || !Wcm || !d_ownSub || !d_ors || !d_ers)
+            return XDCG_OOM;
+        // balanced work units: per box, own rows then coupled rows, <= kUnitRows each
+        std::vector<int> unitBox, unitKind, unitBegin, unitEnd, boxUnit(S + 1, 0), ownUnit;
+        for (int sb2 = 0; sb2 < S; ++sb2) {
+            boxUnit[sb2] = (int)unitBox.size();
+            for (int kind = 0; kind < 2; ++kind) {
+                const int r0 = kind ? extRowPtr[sb2] : ownRowPtr[sb2];
+                const int r1 = kind ? extRowPtr[sb2 + 1] : ownRowPtr[sb2 + 1];
+                for (int rb = r0; rb < r1 || (rb == r0 && kind == 0); rb += kUnitRows) {
+                    if (kind == 0) ownUnit.push_back((int)unitBox.size());
+                    unitBox.push_back(sb2);
+                    unitKind.push_back(kind);
+                    unitBegin.push_back(rb);
+                    unitEnd.push_back(std::min(r1, rb + kUnitRows));
+                    if (r1 == r0) break;
+                }
+            }
+        }
+        boxUnit[S] = (int)unitBox.size();
+        R.nUnits = (int)unitBox.size();
+        R.nOwnUnits = (int)ownUnit.size();
+        R.unitBox = upload(c, unitBox);
+        R.unitKind = upload(c, unitKind);
+        R.unitBegin = upload(c, unitBegin);
+        R.unitEnd = upload(c, unitEnd);
+        R.boxUnit = upload(c, boxUnit);
+        R.ownUnit = upload(c, ownUnit);
+        R.unitPart = dalloc<double>(c, 12 * (size_t)R.nUnits);
+        R.boxTicket = dalloc<unsigned int>(c, S);
+        if (!R.unitBox || !R.unitKind || !R.unitBegin || !R.unitEnd || !R.boxUnit || !R.ownUnit ||
+            !R.unitPart || !R.boxTicket || R.nUnits > kMaxGrid)
+            return XDCG_OOM;
+        CK(cudaMemsetAsync(R.boxTicket, 0, S * sizeof(unsigned int), st));
+        launch_to_colmajor(N, d_ownSub, d_ors, d_ownB, d_zOff, R.ownRowPtr, R.zBase, d_menr, d_Zt,
+                           Zcm, st);
+        launch_to_colmajor(nExt, d_extBox, d_ers, d_extB, d_wOff, R.extRowPtr, R.wBase, d_menr,
+                           d_Wt, Wcm, st);
+        R.Z = Zcm;
+        R.W = Wcm;
         c->L32.dofStart = d_dof;
     }
     int hbad[2];
@@ -897,13 +1041,14 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     CK(cudaEventCreateWithFlags(&c->evb[0], cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->evb[1], cudaEventDisableTiming));
     CK(cudaStreamSynchronize(st));
-    if (spmv_grid(nSlices, nX) > kMaxGrid) return XDCG_INVALID_ARG;
+    if (spmv_grid(HS.nSlices, HX.nSlices) > kMaxGrid) return XDCG_INVALID_ARG;
 
     // ---- algorithmic byte counts (see the roofline notes of the design)
     long long nStdN = (long long)lists[0].size(), nHN = (long long)lists[1].size(),
               nTN = (long long)lists[2].size();
     auto spmv_bytes = [&](int s) {
-        return 9LL * nnzb3 * s + 4LL * nnzb3 + 8LL * nS + 8LL * nSlices + 16LL * nX + 2LL * n * s;
+        return 9LL * nnzb3 * s + 4LL * nnzb3 + 8LL * (nS + nX) + 8LL * (HS.nSlices + HX.nSlices)
+               + 2LL * n * s;
     };
     const long long fac = 6 * nStdN + 21 * nHN + 120 * nTN;
     long long nZt = 0;

@@ -16,7 +16,7 @@
 
 namespace xdcg {
 
-constexpr int kBoxThreads = 512;
+constexpr int kBoxThreads = 128;   // small CTAs: all boxes of an 8^3 split resident at once
 
 // column c (0..5) of R(x)^T a, R the rigid block of Eq. dcg_deflation_space
 template <typename A>
@@ -144,7 +144,7 @@ __device__ __forceinline__ void restrict_box(const BoxDev<T> &B, int s, const T 
 }
 
 template <typename T, typename A, bool EXPL>
-__global__ void __launch_bounds__(kBoxThreads)
+__global__ void __launch_bounds__(kBoxThreads, 4)
 k_restrict(BoxDev<T> B, const T *a, const T *b, int withW, double *g, double *zr,
            const Scalars *sc) {
     if (sc && sc->done != kRunning) return;
@@ -160,10 +160,6 @@ void launch_restrict(const BoxDev<double> &B, const double *a, const double *b, 
     k_restrict<double, double, false><<<B.nBox, kBoxThreads, 0, st>>>(B, a, b, withW, g, zr, sc);
 }
 
-void launch_restrict_z(const BoxDev<float> &B, const float *a, const float *b, int withW,
-                       double *g, double *zr, const Scalars *sc, cudaStream_t st) {
-    k_restrict<float, float, true><<<B.nBox, kBoxThreads, 0, st>>>(B, a, b, withW, g, zr, sc);
-}
 
 // ---- prolongation ----------------------------------------------------------
 
@@ -246,7 +242,7 @@ __device__ __forceinline__ void prolong_box(const BoxDev<T> &B, int s, const T *
 }
 
 template <typename T, bool EXPL>
-__global__ void __launch_bounds__(kBoxThreads)
+__global__ void __launch_bounds__(kBoxThreads, 4)
 k_prolong(BoxDev<T> B, const T *nu, const T *y, T *p, int mode, Scalars *sc) {
     if (sc->done != kRunning) return;
     const int s = blockIdx.x;
@@ -262,9 +258,174 @@ void launch_prolong(const BoxDev<double> &B, const double *nu, const double *y, 
     k_prolong<double, false><<<B.nBox, kBoxThreads, 0, st>>>(B, nu, y, p, mode, sc);
 }
 
-void launch_prolong_z(const BoxDev<float> &B, const float *nu32, const float *y, float *p,
-                      int mode, Scalars *sc, cudaStream_t st) {
-    k_prolong<float, true><<<B.nBox, kBoxThreads, 0, st>>>(B, nu32, y, p, mode, sc);
+
+// ---- row-parallel box kernels of the block-scaled FP32 path -----------------
+
+constexpr int kRowThreads = 256;
+
+// acc[0..M) collects the unit's coarse partials, acc[M] its share of ||r||^2;
+// returns (in thread 0) the unit's ||r||^2 after one block reduction.
+template <int M>
+__device__ __forceinline__ float restrict_update_unit(const RowBoxDev &B, int unit, float *u,
+                                                      const float *r_cur, float *r_next,
+                                                      const float *p, const float *q, int mode,
+                                                      float alpha, double *g, double *zr) {
+    const int s = B.unitBox[unit], kind = B.unitKind[unit];
+    const int rb = B.unitBegin[unit], re = B.unitEnd[unit];
+    float acc[M + 1];
+#pragma unroll
+    for (int c = 0; c <= M; ++c) acc[c] = 0.0f;
+    if (kind == 0) {
+        const int r0 = B.ownRowPtr[s], R = B.ownRowPtr[s + 1] - r0;
+        const float *Z = B.Z + B.zBase[s];
+#pragma unroll 4
+        for (int r = rb + threadIdx.x; r < re; r += blockDim.x) {
+            const int d = B.ownRowDof[r];
+            float rn = r_cur[d];
+            if (mode == 0) {
+                rn = fmaf(-alpha, q[d], rn);
+                r_next[d] = rn;
+                u[d] = fmaf(alpha, p[d], u[d]);
+            }
+            acc[M] = fmaf(rn, rn, acc[M]);
+            const int rl = r - r0;
+#pragma unroll
+            for (int c = 0; c < M; ++c) acc[c] = fmaf(Z[(size_t)c * R + rl], rn, acc[c]);
+        }
+    } else if (mode != 2) {
+        const int r0 = B.extRowPtr[s], R = B.extRowPtr[s + 1] - r0;
+        const float *W = B.W + B.wBase[s];
+#pragma unroll 4
+        for (int r = rb + threadIdx.x; r < re; r += blockDim.x) {
+            const int d = B.extRowDof[r];
+            const float rn = (mode == 0) ? fmaf(-alpha, q[d], r_cur[d]) : r_cur[d];
+            const int rl = r - r0;
+#pragma unroll
+            for (int c = 0; c < M; ++c) acc[c] = fmaf(W[(size_t)c * R + rl], rn, acc[c]);
+        }
+    }
+    block_sum<float, M + 1>(acc);
+    __shared__ bool lastUnit;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int c = 0; c < M; ++c) B.unitPart[(size_t)unit * 12 + c] = (double)acc[c];
+        __threadfence();
+        const unsigned int nu = (unsigned int)(B.boxUnit[s + 1] - B.boxUnit[s]);
+        lastUnit = atomicAdd(&B.boxTicket[s], 1u) == nu - 1;
+    }
+    __syncthreads();
+    if (lastUnit) {
+        __threadfence();
+        if (threadIdx.x < M) {
+            const int c = threadIdx.x;
+            double zs = 0.0, ws = 0.0;
+            for (int v = B.boxUnit[s]; v < B.boxUnit[s + 1]; ++v) {
+                const double x = __ldcg(B.unitPart + (size_t)v * 12 + c);
+                if (B.unitKind[v] == 0) zs += x; else ws += x;
+            }
+            const int c0 = B.col0[s];
+            g[c0 + c] = zs - ws;
+            if (zr) zr[c0 + c] = zs;
+        }
+        if (threadIdx.x == 0) B.boxTicket[s] = 0u;
+    }
+    return acc[M];
+}
+
+__global__ void __launch_bounds__(kRowThreads)
+k_restrict_update(RowBoxDev B, float *u, const float *r_cur, float *r_next, const float *p,
+                  const float *q, int mode, double *g, double *zr, double *partials,
+                  Scalars *sc) {
+    if (sc->done != kRunning) return;
+    const int unit = blockIdx.x;
+    const float alpha = (mode == 0) ? (float)sc->alpha : 0.0f;
+    float rr;
+    if (B.menr[B.unitBox[unit]])
+        rr = restrict_update_unit<12>(B, unit, u, r_cur, r_next, p, q, mode, alpha, g, zr);
+    else
+        rr = restrict_update_unit<6>(B, unit, u, r_cur, r_next, p, q, mode, alpha, g, zr);
+    if (mode == 2) return;
+    double tot;
+    if (grid_sum_t0((double)rr, partials, &sc->ticket[2], tot) && threadIdx.x == 0) {
+        sc->rr = tot;
+        sc->ry = tot;
+        if (tot <= sc->tol2ff)
+            sc->done = kConverged;
+        else if (sc->its >= sc->max_it)
+            sc->done = kMaxIter;
+        else if (!isfinite(tot))
+            sc->done = kBreakdown;
+    }
+}
+
+void launch_restrict_update(const RowBoxDev &B, float *u, const float *r_cur, float *r_next,
+                            const float *p, const float *q, int mode, double *g, double *zr,
+                            double *partials, Scalars *sc, cudaStream_t st) {
+    k_restrict_update<<<B.nUnits, kRowThreads, 0, st>>>(B, u, r_cur, r_next, p, q, mode, g, zr,
+                                                         partials, sc);
+}
+
+template <int M>
+__device__ __forceinline__ void prolong_rows_unit(const RowBoxDev &B, int unit,
+                                                  const float *nu32, const float *y, float *p,
+                                                  int mode, float beta) {
+    const int s = B.unitBox[unit];
+    const int c0 = B.col0[s];
+    float n[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) n[c] = nu32[c0 + c];
+    const int r0 = B.ownRowPtr[s], R = B.ownRowPtr[s + 1] - r0;
+    const float *Z = B.Z + B.zBase[s];
+    const int re = B.unitEnd[unit];
+#pragma unroll 2
+    for (int r = B.unitBegin[unit] + threadIdx.x; r < re; r += blockDim.x) {
+        const int rl = r - r0;
+        float zv = 0.0f;
+#pragma unroll
+        for (int c = 0; c < M; ++c) zv = fmaf(Z[(size_t)c * R + rl], n[c], zv);
+        emit(p, y, B.ownRowDof[r], zv, mode, beta);
+    }
+}
+
+__global__ void __launch_bounds__(kRowThreads)
+k_prolong_rows(RowBoxDev B, const float *nu32, const float *y, float *p, int mode, Scalars *sc) {
+    if (sc->done != kRunning) return;
+    const int unit = B.ownUnit[blockIdx.x];
+    const float beta = (float)sc->beta;
+    if (B.menr[B.unitBox[unit]])
+        prolong_rows_unit<12>(B, unit, nu32, y, p, mode, beta);
+    else
+        prolong_rows_unit<6>(B, unit, nu32, y, p, mode, beta);
+}
+
+void launch_prolong_rows(const RowBoxDev &B, const float *nu32, const float *y, float *p,
+                         int mode, Scalars *sc, cudaStream_t st) {
+    k_prolong_rows<<<B.nOwnUnits, kRowThreads, 0, st>>>(B, nu32, y, p, mode, sc);
+}
+
+// set-up: row-major per-item blocks (b x M at srcOff) to the per-box
+// column-major layout
+__global__ void k_to_colmajor(int nItems, const int *itemBox, const int *rowStart,
+                              const unsigned char *itemB, const long long *srcOff,
+                              const int *boxRowPtr, const long long *boxBase, const int *menr,
+                              const float *src, float *dst) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nItems) return;
+    const int s = itemBox[t], M = menr[s] ? 12 : 6, b = itemB[t];
+    const int R = boxRowPtr[s + 1] - boxRowPtr[s];
+    const int rl0 = rowStart[t] - boxRowPtr[s];
+    for (int i = 0; i < b; ++i)
+        for (int c = 0; c < M; ++c)
+            dst[boxBase[s] + (long long)c * R + rl0 + i] = src[srcOff[t] + i * M + c];
+}
+
+void launch_to_colmajor(int nItems, const int *itemBox, const int *rowStart,
+                        const unsigned char *itemB, const long long *srcOff,
+                        const int *boxRowPtr, const long long *boxBase, const int *menr,
+                        const float *src, float *dst, cudaStream_t st) {
+    if (nItems == 0) return;
+    k_to_colmajor<<<(nItems + 127) / 128, 128, 0, st>>>(nItems, itemBox, rowStart, itemB, srcOff,
+                                                        boxRowPtr, boxBase, menr, src, dst);
 }
 
 }  // namespace xdcg

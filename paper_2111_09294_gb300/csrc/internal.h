@@ -11,6 +11,8 @@ namespace xdcg {
 
 constexpr int kThreads = 256;      // threads per block of the streaming kernels
 constexpr int kWarps = kThreads / 32;
+constexpr int kSpmvThreads = 512;  // threads per block of the SpMV
+constexpr int kSpmvWarps = kSpmvThreads / 32;
 
 // done flags written by the kernels
 enum : int { kRunning = 0, kConverged = 1, kBreakdown = 2, kMaxIter = 3 };
@@ -39,27 +41,37 @@ struct Scalars {
     unsigned int ticket[4];   // last-block tickets, reset by the last block
 };
 
-// Chunked 3x3 BSR over the chunk rows (3 consecutive dofs).  Rows whose
-// blocks all couple standard dofs of standard nodes ("S" rows) use a
-// sliced-ELL layout, one thread per row, 32 rows per slice, slot-major with
-// the 9 values of a slot stored as 9 separate 32-wide runs.  The remaining
-// rows ("X": enriched chunks and standard chunks next to enriched nodes)
-// use one warp per row, lanes over the row's blocks, blocks in groups of 32
-// laid out the same way.
+// Chunked 3x3 BSR over the chunk rows (3 consecutive dofs) in sliced-ELL
+// form with TPR threads per row: a warp holds 32 / TPR rows; at step s,
+// lane (rr + (32 / TPR) h) handles slot s * TPR + h of row rr of its slice,
+// and the slot's column index and its 9 values sit in 32-wide runs, so
+// every load instruction of a warp reads one contiguous 128-byte (FP32) or
+// 256-byte (FP64) segment.  Partial rows are combined by shuffles.
+// With ilvSteps > 0 the part is interleaved: every slice has ilvSteps steps
+// and step st / value e of slice sl sits at ((st * 9 + e) * nSlices + sl) * 32
+// (columns at (st * nSlices + sl) * 32), so at any step all warps read one
+// contiguous band of memory, as a plain copy does.
+template <typename T>
+struct SellDev {
+    int nRows, nSlices, ilvSteps;
+    const int *row;            // [nRows] chunk row
+    const int *len;            // [nRows] blocks in the row
+    const long long *slicePtr; // [nSlices + 1] first slot (lane-slot) of each slice
+    const int *col;            // [slots] chunk column
+    const T *val;              // [9 slots]
+};
+
+// Rows whose blocks all couple standard dofs of standard nodes ("S": 27 or
+// fewer blocks, natural order, 2 threads per row) and the remaining rows
+// ("X": enriched chunks and standard chunks next to enriched nodes, sorted
+// by length, 16 threads per row).
+constexpr int kTprS = 2;
+constexpr int kTprX = 16;
+constexpr int kXBucket = 8;     // X rows are grouped by len / kXBucket
+
 template <typename T>
 struct SpmvDev {
-    int nS, nSlices;
-    const int *rowS;          // [nS] chunk row
-    const int *lenS;          // [nS] blocks in the row
-    const long long *slicePtr;// [nSlices] first slot of the slice
-    const int *colS;          // [slots] chunk column
-    const T *valS;            // [9 slots]
-    int nX;
-    const int *rowX;          // [nX]
-    const int *lenX;          // [nX]
-    const long long *ptrX;    // [nX] first slot (multiple of 32)
-    const int *colX;
-    const T *valX;
+    SellDev<T> S, X;
 };
 
 // Node-level data: node lists per block size, packed Cholesky factors of
@@ -108,20 +120,56 @@ struct BoxDev {
 template <typename T>
 void launch_spmv(const SpmvDev<T> &A, const T *x, T *y, const T *b, int residual_mode,
                  double *partials, Scalars *sc, int fin, int slot, cudaStream_t st);
-int spmv_grid(int nSlices, int nX);
+int spmv_grid(int nSlicesS, int nSlicesX);
 
 template <typename T>
 void launch_update(const NodeDev<T> &N, T *u, T *r, const T *p, const T *q, T *y, int mode,
                    double *partials, Scalars *sc, cudaStream_t st);
 
+// Row-parallel form of the block-scaled FP32 path: per box, the rows of its
+// own nodes (Z~, column-major: column c of box s at Z + zBase[s] + c * R_s)
+// and the rows of the nodes coupled to it (W~, column-major likewise), each
+// row mapped to its dof.
+// Work is split into balanced units of at most kUnitRows rows (a box near
+// the crack front holds several times the rows of an average box): units of
+// a box are contiguous, its own-row units first; the last unit of a box to
+// finish (per-box ticket) adds the units' partial sums in unit order.
+struct RowBoxDev {
+    int nBox;
+    const int *col0, *menr;
+    const int *ownRowPtr, *ownRowDof;   // [nBox + 1], [own rows]
+    const long long *zBase;             // [nBox]
+    const float *Z;
+    const int *extRowPtr, *extRowDof;   // [nBox + 1], [coupled rows]
+    const long long *wBase;             // [nBox]
+    const float *W;
+    int nUnits, nOwnUnits;
+    const int *unitBox, *unitKind, *unitBegin, *unitEnd;   // [nUnits]; kind 0: own, 1: coupled
+    const int *boxUnit;                 // [nBox + 1] first unit of each box
+    const int *ownUnit;                 // [nOwnUnits] the own-row units, in order
+    double *unitPart;                   // [nUnits * 12] partial sums (scratch)
+    unsigned int *boxTicket;            // [nBox] (scratch, kept at zero between launches)
+};
+constexpr int kUnitRows = 2048;
+
 void launch_restrict(const BoxDev<double> &B, const double *a, const double *b, int withW,
                      double *g, double *zr, const Scalars *sc, cudaStream_t st);
-void launch_restrict_z(const BoxDev<float> &B, const float *a, const float *b, int withW,
-                       double *g, double *zr, const Scalars *sc, cudaStream_t st);
 void launch_prolong(const BoxDev<double> &B, const double *nu, const double *y, double *p,
                     int mode, Scalars *sc, cudaStream_t st);
-void launch_prolong_z(const BoxDev<float> &B, const float *nu32, const float *y, float *p,
-                      int mode, Scalars *sc, cudaStream_t st);
+// mode 0 (iteration): r' = r - alpha q and u += alpha p on own rows (r' written
+// to r_next), g = Z~^T r' - W~^T r', zr = Z~^T r', ||r'||^2 with the
+// convergence and iteration-cap tests; mode 1 (start): the same without the
+// update (alpha = 0, nothing written but g, zr, ||r||^2); mode 2 (Algorithm
+// 2): g = Z~^T r only.
+void launch_restrict_update(const RowBoxDev &B, float *u, const float *r_cur, float *r_next,
+                            const float *p, const float *q, int mode, double *g, double *zr,
+                            double *partials, Scalars *sc, cudaStream_t st);
+void launch_prolong_rows(const RowBoxDev &B, const float *nu32, const float *y, float *p,
+                         int mode, Scalars *sc, cudaStream_t st);
+void launch_to_colmajor(int nItems, const int *itemBox, const int *rowStart,
+                        const unsigned char *itemB, const long long *srcOff,
+                        const int *boxRowPtr, const long long *boxBase, const int *menr,
+                        const float *src, float *dst, cudaStream_t st);
 
 // nu = E^-1 g (FP64; nu32 optional FP32 copy)
 void launch_coarse(const double *Einv, int k, const double *g, const double *zr, double *nu,

@@ -74,6 +74,30 @@ __device__ __forceinline__ bool grid_sum(A (&v)[NV], double *partials, unsigned 
     return true;
 }
 
+// Grid-wide sum of one value already reduced to thread 0 of each block:
+// returns true in the last block to finish, where thread 0 holds the FP64
+// total (block partials added in block order).
+__device__ __forceinline__ bool grid_sum_t0(double v, double *partials, unsigned int *ticket,
+                                            double &tot) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = v;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double s[1] = {0.0};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s[0] += __ldcg(partials + b);
+    block_sum<double, 1>(s);
+    if (threadIdx.x == 0) {
+        tot = s[0];
+        *ticket = 0u;
+    }
+    return true;
+}
+
 // Shared last-block actions on the scalar block.
 __device__ __forceinline__ void finalize(Scalars *sc, int fin, int slot, double val) {
     if (fin == kFinAlpha) {

@@ -13,116 +13,106 @@ namespace xdcg {
 template <typename T>
 __device__ __forceinline__ T ldcs(const T *p) { return __ldcs(p); }
 
+// One slice of TPR-threads-per-row sliced ELL; returns this lane's share of
+// the fused dot (x^T y, or y^T y in residual mode) in part.
+template <typename T, bool RES, int TPR>
+__device__ __forceinline__ void sell_slice(const SellDev<T> &P, int slice, int lane,
+                                           const T *__restrict__ x, T *__restrict__ y,
+                                           const T *__restrict__ b, T &part) {
+    constexpr int RPW = 32 / TPR;
+    const int rr = lane % RPW, h = lane / RPW;
+    const int rl = slice * RPW + rr;
+    const bool valid = rl < P.nRows;
+    const int len = valid ? P.len[rl] : 0;
+    long long base, cstep, vstep, ve;
+    int steps;
+    if (P.ilvSteps > 0) {             // interleaved: all slices step together
+        base = 32LL * slice;
+        steps = P.ilvSteps;
+        cstep = 32LL * P.nSlices;
+        ve = cstep;
+        vstep = 9 * cstep;
+    } else {                          // slice-blocked
+        base = P.slicePtr[slice];
+        steps = (int)((P.slicePtr[slice + 1] - base) >> 5);
+        cstep = 32;
+        ve = 32;
+        vstep = 288;
+    }
+    const int *cp = P.col + base + lane;
+    const T *vp = P.val + (P.ilvSteps > 0 ? base : 9 * base) + lane;
+    T a0 = T(0), a1 = T(0), a2 = T(0);
+#pragma unroll 4
+    for (int st = 0; st < steps; ++st) {
+        if (st * TPR + h < len) {
+            const int c = __ldcs(cp + cstep * st);
+            const T *v = vp + vstep * st;
+            const T x0 = __ldg(x + 3 * c), x1 = __ldg(x + 3 * c + 1), x2 = __ldg(x + 3 * c + 2);
+            a0 = fma(ldcs(v), x0, a0);
+            a0 = fma(ldcs(v + ve), x1, a0);
+            a0 = fma(ldcs(v + 2 * ve), x2, a0);
+            a1 = fma(ldcs(v + 3 * ve), x0, a1);
+            a1 = fma(ldcs(v + 4 * ve), x1, a1);
+            a1 = fma(ldcs(v + 5 * ve), x2, a1);
+            a2 = fma(ldcs(v + 6 * ve), x0, a2);
+            a2 = fma(ldcs(v + 7 * ve), x1, a2);
+            a2 = fma(ldcs(v + 8 * ve), x2, a2);
+        }
+    }
+#pragma unroll
+    for (int o = RPW; o < 32; o <<= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+    if (valid && h == 0) {
+        const long long r3 = 3 * (long long)P.row[rl];
+        if (RES) {
+            a0 = b[r3] - a0;
+            a1 = b[r3 + 1] - a1;
+            a2 = b[r3 + 2] - a2;
+            part = a0 * a0 + a1 * a1 + a2 * a2;
+        } else {
+            part = x[r3] * a0 + x[r3 + 1] * a1 + x[r3 + 2] * a2;
+        }
+        y[r3] = a0;
+        y[r3 + 1] = a1;
+        y[r3 + 2] = a2;
+    }
+}
+
 template <typename T, bool RES>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kSpmvThreads)
 k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__restrict__ b,
        int nbS, double *partials, Scalars *sc, int fin, int slot) {
     if (sc->done != kRunning) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T part[1] = {T(0)};
     if ((int)blockIdx.x < nbS) {
-        const int slice = blockIdx.x * kWarps + warp;
-        const int rl = slice * 32 + lane;
-        if (slice < A.nSlices && rl < A.nS) {
-            const int row = A.rowS[rl];
-            const int len = A.lenS[rl];
-            const long long base = A.slicePtr[slice];
-            const int *cp = A.colS + base + lane;
-            const T *vp = A.valS + 9 * base + lane;
-            T a0 = T(0), a1 = T(0), a2 = T(0);
-#pragma unroll 4
-            for (int j = 0; j < len; ++j) {
-                const int c = __ldcs(cp + 32 * j);
-                const T *v = vp + 288 * j;
-                const T x0 = __ldg(x + 3 * c), x1 = __ldg(x + 3 * c + 1), x2 = __ldg(x + 3 * c + 2);
-                a0 = fma(ldcs(v), x0, a0);
-                a0 = fma(ldcs(v + 32), x1, a0);
-                a0 = fma(ldcs(v + 64), x2, a0);
-                a1 = fma(ldcs(v + 96), x0, a1);
-                a1 = fma(ldcs(v + 128), x1, a1);
-                a1 = fma(ldcs(v + 160), x2, a1);
-                a2 = fma(ldcs(v + 192), x0, a2);
-                a2 = fma(ldcs(v + 224), x1, a2);
-                a2 = fma(ldcs(v + 256), x2, a2);
-            }
-            T *yr = y + 3 * (long long)row;
-            if (RES) {
-                const T *br = b + 3 * (long long)row;
-                a0 = br[0] - a0;
-                a1 = br[1] - a1;
-                a2 = br[2] - a2;
-                part[0] = a0 * a0 + a1 * a1 + a2 * a2;
-            } else {
-                const T *xr = x + 3 * (long long)row;
-                part[0] = xr[0] * a0 + xr[1] * a1 + xr[2] * a2;
-            }
-            yr[0] = a0;
-            yr[1] = a1;
-            yr[2] = a2;
-        }
+        const int slice = blockIdx.x * kSpmvWarps + warp;
+        if (slice < A.S.nSlices) sell_slice<T, RES, kTprS>(A.S, slice, lane, x, y, b, part[0]);
     } else {
-        const int xi = (blockIdx.x - nbS) * kWarps + warp;
-        if (xi < A.nX) {
-            const int row = A.rowX[xi];
-            const int len = A.lenX[xi];
-            const long long base = A.ptrX[xi];
-            T a0 = T(0), a1 = T(0), a2 = T(0);
-            for (int t = lane; t < len; t += 32) {
-                const int c = __ldcs(A.colX + base + t);
-                const T *v = A.valX + 9 * base + 288 * (t >> 5) + (t & 31);
-                const T x0 = __ldg(x + 3 * c), x1 = __ldg(x + 3 * c + 1), x2 = __ldg(x + 3 * c + 2);
-                a0 = fma(ldcs(v), x0, a0);
-                a0 = fma(ldcs(v + 32), x1, a0);
-                a0 = fma(ldcs(v + 64), x2, a0);
-                a1 = fma(ldcs(v + 96), x0, a1);
-                a1 = fma(ldcs(v + 128), x1, a1);
-                a1 = fma(ldcs(v + 160), x2, a1);
-                a2 = fma(ldcs(v + 192), x0, a2);
-                a2 = fma(ldcs(v + 224), x1, a2);
-                a2 = fma(ldcs(v + 256), x2, a2);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-                a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-                a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-            }
-            if (lane == 0) {
-                T *yr = y + 3 * (long long)row;
-                if (RES) {
-                    const T *br = b + 3 * (long long)row;
-                    a0 = br[0] - a0;
-                    a1 = br[1] - a1;
-                    a2 = br[2] - a2;
-                    part[0] = a0 * a0 + a1 * a1 + a2 * a2;
-                } else {
-                    const T *xr = x + 3 * (long long)row;
-                    part[0] = xr[0] * a0 + xr[1] * a1 + xr[2] * a2;
-                }
-                yr[0] = a0;
-                yr[1] = a1;
-                yr[2] = a2;
-            }
-        }
+        const int slice = (blockIdx.x - nbS) * kSpmvWarps + warp;
+        if (slice < A.X.nSlices) sell_slice<T, RES, kTprX>(A.X, slice, lane, x, y, b, part[0]);
     }
     double tot[1];
     if (grid_sum<T, 1>(part, partials, &sc->ticket[0], tot) && threadIdx.x == 0)
         finalize(sc, fin, slot, tot[0]);
 }
 
-int spmv_grid(int nSlices, int nX) {
-    return (nSlices + kWarps - 1) / kWarps + (nX + kWarps - 1) / kWarps;
+int spmv_grid(int nSlicesS, int nSlicesX) {
+    return (nSlicesS + kSpmvWarps - 1) / kSpmvWarps + (nSlicesX + kSpmvWarps - 1) / kSpmvWarps;
 }
 
 template <typename T>
 void launch_spmv(const SpmvDev<T> &A, const T *x, T *y, const T *b, int residual_mode,
                  double *partials, Scalars *sc, int fin, int slot, cudaStream_t st) {
-    const int nbS = (A.nSlices + kWarps - 1) / kWarps;
-    const int grid = spmv_grid(A.nSlices, A.nX);
+    const int nbS = (A.S.nSlices + kSpmvWarps - 1) / kSpmvWarps;
+    const int grid = spmv_grid(A.S.nSlices, A.X.nSlices);
     if (residual_mode)
-        k_spmv<T, true><<<grid, kThreads, 0, st>>>(A, x, y, b, nbS, partials, sc, fin, slot);
+        k_spmv<T, true><<<grid, kSpmvThreads, 0, st>>>(A, x, y, b, nbS, partials, sc, fin, slot);
     else
-        k_spmv<T, false><<<grid, kThreads, 0, st>>>(A, x, y, b, nbS, partials, sc, fin, slot);
+        k_spmv<T, false><<<grid, kSpmvThreads, 0, st>>>(A, x, y, b, nbS, partials, sc, fin, slot);
 }
 
 template void launch_spmv<double>(const SpmvDev<double> &, const double *, double *,
