@@ -992,6 +992,18 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         R.unitEnd = upload(c, unitEnd);
         R.boxUnit = upload(c, boxUnit);
         R.ownUnit = upload(c, ownUnit);
+        std::vector<int> pBox, pBegin, pEnd;
+        for (int sb2 = 0; sb2 < S; ++sb2)
+            for (int rb = ownRowPtr[sb2]; rb < ownRowPtr[sb2 + 1]; rb += kProlongRows) {
+                pBox.push_back(sb2);
+                pBegin.push_back(rb);
+                pEnd.push_back(std::min(ownRowPtr[sb2 + 1], rb + kProlongRows));
+            }
+        R.nPUnits = (int)pBox.size();
+        R.pUnitBox = upload(c, pBox);
+        R.pUnitBegin = upload(c, pBegin);
+        R.pUnitEnd = upload(c, pEnd);
+        if (!R.pUnitBox || !R.pUnitBegin || !R.pUnitEnd || R.nPUnits == 0) return XDCG_OOM;
         R.unitPart = dalloc<double>(c, 12 * (size_t)R.nUnits);
         R.boxTicket = dalloc<unsigned int>(c, S);
         if (!R.unitBox || !R.unitKind || !R.unitBegin || !R.unitEnd || !R.boxUnit || !R.ownUnit ||

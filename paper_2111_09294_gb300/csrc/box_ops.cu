@@ -369,16 +369,16 @@ template <int M>
 __device__ __forceinline__ void prolong_rows_unit(const RowBoxDev &B, int unit,
                                                   const float *nu32, const float *y, float *p,
                                                   int mode, float beta) {
-    const int s = B.unitBox[unit];
+    const int s = B.pUnitBox[unit];
     const int c0 = B.col0[s];
     float n[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) n[c] = nu32[c0 + c];
     const int r0 = B.ownRowPtr[s], R = B.ownRowPtr[s + 1] - r0;
     const float *Z = B.Z + B.zBase[s];
-    const int re = B.unitEnd[unit];
+    const int re = B.pUnitEnd[unit];
 #pragma unroll 2
-    for (int r = B.unitBegin[unit] + threadIdx.x; r < re; r += blockDim.x) {
+    for (int r = B.pUnitBegin[unit] + threadIdx.x; r < re; r += blockDim.x) {
         const int rl = r - r0;
         float zv = 0.0f;
 #pragma unroll
@@ -390,9 +390,9 @@ __device__ __forceinline__ void prolong_rows_unit(const RowBoxDev &B, int unit,
 __global__ void __launch_bounds__(kRowThreads)
 k_prolong_rows(RowBoxDev B, const float *nu32, const float *y, float *p, int mode, Scalars *sc) {
     if (sc->done != kRunning) return;
-    const int unit = B.ownUnit[blockIdx.x];
+    const int unit = blockIdx.x;
     const float beta = (float)sc->beta;
-    if (B.menr[B.unitBox[unit]])
+    if (B.menr[B.pUnitBox[unit]])
         prolong_rows_unit<12>(B, unit, nu32, y, p, mode, beta);
     else
         prolong_rows_unit<6>(B, unit, nu32, y, p, mode, beta);
@@ -400,7 +400,7 @@ k_prolong_rows(RowBoxDev B, const float *nu32, const float *y, float *p, int mod
 
 void launch_prolong_rows(const RowBoxDev &B, const float *nu32, const float *y, float *p,
                          int mode, Scalars *sc, cudaStream_t st) {
-    k_prolong_rows<<<B.nOwnUnits, kRowThreads, 0, st>>>(B, nu32, y, p, mode, sc);
+    k_prolong_rows<<<B.nPUnits, kRowThreads, 0, st>>>(B, nu32, y, p, mode, sc);
 }
 
 // set-up: row-major per-item blocks (b x M at srcOff) to the per-box

@@ -147,10 +147,13 @@ struct RowBoxDev {
     const int *unitBox, *unitKind, *unitBegin, *unitEnd;   // [nUnits]; kind 0: own, 1: coupled
     const int *boxUnit;                 // [nBox + 1] first unit of each box
     const int *ownUnit;                 // [nOwnUnits] the own-row units, in order
+    int nPUnits;                        // prolongation units (own rows, <= kProlongRows)
+    const int *pUnitBox, *pUnitBegin, *pUnitEnd;
     double *unitPart;                   // [nUnits * 12] partial sums (scratch)
     unsigned int *boxTicket;            // [nBox] (scratch, kept at zero between launches)
 };
 constexpr int kUnitRows = 2048;
+constexpr int kProlongRows = 512;
 
 void launch_restrict(const BoxDev<double> &B, const double *a, const double *b, int withW,
                      double *g, double *zr, const Scalars *sc, cudaStream_t st);
