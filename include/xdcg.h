@@ -46,7 +46,9 @@ typedef enum {
     XDCG_BREAKDOWN = 4,        /* p^T K p <= 0 or not finite during the iteration */
     XDCG_NO_CONVERGENCE = 5,   /* max_iter reached; u holds the last iterate */
     XDCG_CUDA_ERROR = 6,       /* a CUDA runtime call failed */
-    XDCG_OOM = 7               /* device allocation failed */
+    XDCG_OOM = 7,              /* device allocation failed */
+    XDCG_TOO_LARGE = 8         /* the problem needs more than the fixed scratch of
+                                  xdcg_spmv_noalloc */
 } xdcg_status;
 
 enum { XDCG_HOST = 0, XDCG_DEVICE = 1 };       /* memory space of input arrays */
@@ -155,6 +157,31 @@ xdcg_status xdcg_get_info(const xdcg_ctx *ctx, xdcg_info_t *info);
  * x, y: device, length n.  If xty is not NULL it receives x^T y (FP64
  * reduction) on the host. */
 xdcg_status xdcg_spmv(xdcg_ctx *ctx, int32_t precision, const void *x, void *y, double *xty);
+
+/* Same result as xdcg_spmv, for callers that must not allocate device
+ * memory: code that records into a CUDA stream capture (an allocation there
+ * would break the capture), or that runs where another allocator owns the
+ * whole device memory budget.  The paper has no counterpart; this is a
+ * property of the library, not of the method.
+ *
+ * It allocates nothing.  The SpMV's reduction scratch (block partial sums
+ * and its scalar block) lives in one file-scope device array of
+ * XDCG_NOALLOC_MAX_BLOCKS doubles plus one scalar block (about 33 KB), which
+ * every GPU that loads the library keeps until the process exits.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current, so make that first call
+ * before any stream capture.  All calls share the array, which keeps the
+ * last call's contents; each call clears what must start at zero, but calls
+ * that overlap on the GPU (other streams, other contexts) race on it.
+ *
+ * x, y: device arrays of n values (double for XDCG_FP64, float for
+ * XDCG_MIXED, as in xdcg_spmv).  xty_dev: NULL or a device double that
+ * receives x^T y.  Asynchronous on the context stream.  Returns
+ * XDCG_TOO_LARGE when the context's SpMV grid exceeds
+ * XDCG_NOALLOC_MAX_BLOCKS blocks (the 48^3 case needs 933). */
+#define XDCG_NOALLOC_MAX_BLOCKS 4096
+xdcg_status xdcg_spmv_noalloc(xdcg_ctx *ctx, int32_t precision, const void *x, void *y,
+                              double *xty_dev);
 
 /* z = A-DEF2 preconditioner applied to r (Algorithm 3, one merged coarse
  * solve), FP64.  r, z: device, length n. */

@@ -16,11 +16,11 @@ XDCG_FP64, XDCG_MIXED = 0, 1
 
 STATUS = {0: "XDCG_OK", 1: "XDCG_INVALID_ARG", 2: "XDCG_NOT_SPD_BLOCK",
           3: "XDCG_COARSE_NOT_SPD", 4: "XDCG_BREAKDOWN", 5: "XDCG_NO_CONVERGENCE",
-          6: "XDCG_CUDA_ERROR", 7: "XDCG_OOM"}
+          6: "XDCG_CUDA_ERROR", 7: "XDCG_OOM", 8: "XDCG_TOO_LARGE"}
 
 # every function the header declares
 EXPORTS = ["xdcg_default_options", "xdcg_setup", "xdcg_solve", "xdcg_solve_host",
-           "xdcg_get_info", "xdcg_spmv", "xdcg_precond", "xdcg_coarse_matrix",
+           "xdcg_get_info", "xdcg_spmv", "xdcg_spmv_noalloc", "xdcg_precond", "xdcg_coarse_matrix",
            "xdcg_destroy", "xdcg_status_string"]
 
 
@@ -79,6 +79,7 @@ def load():
     lib.xdcg_solve_host.argtypes = [c_void_p, c_void_p, c_void_p, c_double, POINTER(Result)]
     lib.xdcg_get_info.argtypes = [c_void_p, POINTER(Info)]
     lib.xdcg_spmv.argtypes = [c_void_p, c_int32, c_void_p, c_void_p, POINTER(c_double)]
+    lib.xdcg_spmv_noalloc.argtypes = [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]
     lib.xdcg_precond.argtypes = [c_void_p, c_void_p, c_void_p]
     lib.xdcg_coarse_matrix.argtypes = [c_void_p, c_void_p]
     lib.xdcg_destroy.argtypes = [c_void_p]

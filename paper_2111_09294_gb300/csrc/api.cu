@@ -7,6 +7,7 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -1182,6 +1183,67 @@ xdcg_status xdcg_spmv(xdcg_ctx *c, int32_t precision, const void *x, void *y, do
     return XDCG_OK;
 }
 
+// ---- no-allocation SpMV: reduction scratch in one static device array ------
+
+namespace {
+
+// [Scalars block | XDCG_NOALLOC_MAX_BLOCKS partial sums]; zero at load time
+constexpr int kNoallocScalarsDoubles = (int)((sizeof(Scalars) + 255) / 256 * 256 / sizeof(double));
+static __device__ __align__(256) double
+    g_noalloc_scratch[kNoallocScalarsDoubles + XDCG_NOALLOC_MAX_BLOCKS];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+__global__ void k_noalloc_result(const Scalars *sc, int slot, double *out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *out = sc->scratch[slot];
+}
+
+}  // namespace
+
+xdcg_status xdcg_spmv_noalloc(xdcg_ctx *c, int32_t precision, const void *x, void *y,
+                              double *xty_dev) {
+    if (!c || !x || !y || x == y) return XDCG_INVALID_ARG;
+    if (precision != XDCG_FP64 && precision != XDCG_MIXED) return XDCG_INVALID_ARG;
+    if (precision == XDCG_MIXED && !c->mixed) return XDCG_INVALID_ARG;
+    const int grid = precision == XDCG_FP64 ? spmv_grid(c->L64.A.S.nSlices, c->L64.A.X.nSlices)
+                                            : spmv_grid(c->L32.A.S.nSlices, c->L32.A.X.nSlices);
+    if (grid > XDCG_NOALLOC_MAX_BLOCKS) return XDCG_TOO_LARGE;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return XDCG_INVALID_ARG;
+    double *base = nullptr;
+    {
+        // first call on this device: resolve the array's device address
+        // (the host-side name is only a stand-in, not a device pointer)
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+            g_noalloc_ptr[dev] = (double *)p;
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    Scalars *sc = reinterpret_cast<Scalars *>(base);
+    double *partials = base + kNoallocScalarsDoubles;
+    // clear the scalar block (done flag, tickets) left by the previous call
+    init_scalars(c, sc, -1.0, nullptr, INT_MAX);
+    if (precision == XDCG_FP64)
+        launch_spmv<double>(c->L64.A, (const double *)x, (double *)y, nullptr, 0, partials, sc,
+                            kFinStore, 2, c->st);
+    else
+        launch_spmv<float>(c->L32.A, (const float *)x, (float *)y, nullptr, 0, partials, sc,
+                           kFinStore, 2, c->st);
+    c->launches++;
+    if (xty_dev) {
+        k_noalloc_result<<<1, 32, 0, c->st>>>(sc, 2, xty_dev);
+        c->launches++;
+    }
+    CK(cudaGetLastError());
+    return XDCG_OK;
+}
+
 xdcg_status xdcg_precond(xdcg_ctx *c, const double *r, double *z) {
     if (!c || !r || !z || r == z) return XDCG_INVALID_ARG;
     cudaStream_t st = c->st;
@@ -1223,6 +1285,8 @@ const char *xdcg_status_string(xdcg_status s) {
         case XDCG_NO_CONVERGENCE: return "no convergence within max_iter";
         case XDCG_CUDA_ERROR: return "CUDA error";
         case XDCG_OOM: return "out of device memory";
+        case XDCG_TOO_LARGE:
+            return "problem exceeds the fixed scratch of xdcg_spmv_noalloc (XDCG_NOALLOC_MAX_BLOCKS)";
     }
     return "unknown status";
 }
