@@ -1,10 +1,10 @@
 """Benchmark: time to ||f - K u|| / ||f|| <= 1e-8 on the 48^3 two-crack cube.
 
 Default arm: the GPU library.  One step = one full solve (all steps of the
-hot path: Algorithm 2 start, A-DEF2 PCG iterations, FP64 refinement for the
-mixed path) with the load vector already resident in HBM; L2 is flushed
+hot path: Algorithm 2 start, A-DEF2 PCG iterations, FP64 residual replacement
+for the mixed path) with the load vector already resident in HBM; L2 is flushed
 (a 256 MiB write) before every timed step, outside the step's events.
-Reported: mixed (FP32 inner / FP64 refinement) solve time as the value, the
+Reported: mixed (FP32 PCG / FP64 residual replacement) solve time as the value, the
 plain FP64 solve time beside it, iterations, SpMV bandwidth against the
 measured HBM copy bandwidth, the FP64 CPU oracle on a bounded sample, and an
 end-to-end figure through the host-memory entry point.
@@ -281,7 +281,7 @@ def run_ours(args):
         "metric": METRIC, "value": t_mixed, "unit": "ms", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_mixed,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 inner / f64 refinement", "data": "synthetic",
+        "dtype": "f32 PCG / f64 residual replacement", "data": "synthetic",
         "config": config_dict(P, info["k"]),
         "fp64_ms": t_fp64, "speedup_mixed_vs_fp64": t_fp64 / t_mixed,
         "iterations_mixed": inf_mixed[-1]["iterations"],
@@ -332,7 +332,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--inner-tol", type=float, default=1e-5)
+    ap.add_argument("--inner-tol", type=float, default=1e-3)
     ap.add_argument("--sample-iters", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", choices=["mixed", "fp64"], default=None,

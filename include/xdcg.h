@@ -94,15 +94,18 @@ typedef struct {
     double tol;              /* relative residual target, default 1e-8 */
     int32_t max_iter;        /* total CG iterations (inner ones for MIXED), default 10000 */
     int32_t precision;       /* XDCG_FP64 (default) or XDCG_MIXED */
-    double inner_tol;        /* MIXED: inner FP32 solve stops at inner_tol * ||r||, default 1e-5 */
-    int32_t max_outer;       /* MIXED: refinement cycles, default 30 */
+    double inner_tol;        /* MIXED: residual replacement each time the FP32 recursive
+                                residual has dropped by this factor, default 1e-3 */
+    int32_t max_outer;       /* MIXED: residual replacements (FP64 residual evaluations),
+                                default 30 */
     int32_t time_spmv;       /* 1: bracket every SpMV launch by CUDA events */
 } xdcg_options;
 
 typedef struct {
     int32_t iterations;          /* loop bodies run (products K p), summed over cycles */
-    int32_t outer_cycles;        /* MIXED: refinement cycles; FP64: 1 */
-    double rel_res_recursive;    /* last recursive ||r|| / ||f|| */
+    int32_t outer_cycles;        /* MIXED: FP64 residual evaluations; FP64: 1 */
+    double rel_res_recursive;    /* FP64: last recursive ||r|| / ||f||; MIXED: ||L^-1 r|| / ||f||
+                                    of the FP32 recursive residual before the last replacement */
     double rel_res_true;         /* ||f - K u|| / ||f|| in FP64 after the solve */
     double t_solve_ms;           /* CUDA-event time of the solve on the context stream */
     int32_t bad_index;           /* failing node or coarse pivot, else -1 */

@@ -267,31 +267,56 @@ xdcg_status run_pcg(xdcg_ctx *c, Path path, const T *f, T *u, T *r, T *p, T *q, 
 // iteration (SpMV with p^T q; restriction fused with the u, r update and
 // ||r||^2; coarse solve; prolongation), the residual double-buffered so that
 // the restriction can read the old residual of neighbouring boxes while it
-// writes the new one of its own.
-xdcg_status run_pcg_scaled(xdcg_ctx *c, const float *f, float *u, float *rA, float *rB, float *p,
-                           float *q, Scalars *sc, int max_it, bool time_spmv, int *its_out,
-                           int *done_out, double *t_spmv, int *n_spmv) {
+// writes the new one of its own.  Iteration i reads residual buffer
+// (i & 1 ? rB : rA) and writes the other.
+
+constexpr double kMinGroupDrop2 = 1e-2;   // (1/10)^2
+
+__global__ void k_set_trigger(Scalars *sc, int mode, double delta2, double floor2) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        if (mode == 0) {            // re-arm without a convergence test; keep the
+            sc->done = kRunning;    // recursive ||r||^2 for the restart test
+            sc->tol2ff = -1.0;
+            sc->scratch[3] = sc->rr;
+        } else {                    // next residual replacement when ||r||^2 drops below this
+            sc->tol2ff = fmax(delta2 * sc->rr, floor2);
+        }
+    }
+}
+
+// Algorithm 2 and the first direction: u~ = Z~ E^-1 Z~^T f~, r = f~ - K~ u~ (rA),
+// z = r + Z~ nu, p = z.
+void scaled_init(xdcg_ctx *c, const float *f, float *u, float *rA, float *p, Scalars *sc) {
     cudaStream_t st = c->st;
     Level32 &L = c->L32;
-    // Algorithm 2 with u_-1 = 0: u_0 = Z~ E^-1 Z~^T f
     launch_restrict_update(L.R, nullptr, f, nullptr, nullptr, nullptr, 2, c->g, nullptr,
                            c->partials, sc, st);
     launch_coarse(c->Einv, c->k, c->g, nullptr, c->nu, c->nu32, 0, c->partials, sc, st);
     launch_prolong_rows(L.R, c->nu32, nullptr, u, 1, sc, st);
-    // r_0 = f - K~ u_0 (into rA), z_0 by Algorithm 3 (identity block Jacobi), p_0 = z_0
     launch_spmv<float>(L.A, u, rA, f, 1, c->partials, sc, kFinRR, 0, st);
     launch_restrict_update(L.R, nullptr, rA, nullptr, nullptr, nullptr, 1, c->g, c->zr,
                            c->partials, sc, st);
     launch_coarse(c->Einv, c->k, c->g, c->zr, c->nu, c->nu32, 1, c->partials, sc, st);
     launch_prolong_rows(L.R, c->nu32, rA, p, 2, sc, st);
     c->launches += 7;
+}
 
-    int launched = 0;
-    const int max_batches = max_it / kBatch + 2;
+// Run iterations (in batches, polling the device flag) until a kernel stops
+// the run: the replacement trigger, breakdown, or the iteration cap.
+xdcg_status scaled_iterate(xdcg_ctx *c, float *u, float *rA, float *rB, float *p, float *q,
+                           Scalars *sc, int max_it, bool time_spmv, int *its_out, int *done_out,
+                           double *t_spmv, int *n_spmv) {
+    cudaStream_t st = c->st;
+    Level32 &L = c->L32;
+    CK(cudaMemcpyAsync(c->h_sc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int it0 = c->h_sc->its;
+    int i = it0, launched = 0;
+    const int max_batches = (max_it - it0) / kBatch + 2;
     for (int b = 0; b < max_batches; ++b) {
-        for (int i = 0; i < kBatch; ++i) {
-            float *rc = (launched & 1) ? rB : rA;
-            float *rn = (launched & 1) ? rA : rB;
+        for (int j = 0; j < kBatch; ++j, ++i, ++launched) {
+            float *rc = (i & 1) ? rB : rA;
+            float *rn = (i & 1) ? rA : rB;
             if (time_spmv) {
                 if ((int)c->evS.size() <= launched) {
                     cudaEvent_t e0, e1;
@@ -308,7 +333,6 @@ xdcg_status run_pcg_scaled(xdcg_ctx *c, const float *f, float *u, float *rA, flo
             launch_coarse(c->Einv, c->k, c->g, c->zr, c->nu, c->nu32, 2, c->partials, sc, st);
             launch_prolong_rows(L.R, c->nu32, rn, p, 0, sc, st);
             c->launches += 4;
-            ++launched;
         }
         CK(cudaMemcpyAsync(&c->h_done[b & 1], &sc->done, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaEventRecord(c->evb[b & 1], st));
@@ -323,10 +347,10 @@ xdcg_status run_pcg_scaled(xdcg_ctx *c, const float *f, float *u, float *rA, flo
     *its_out = c->h_sc->its;
     *done_out = c->h_sc->done;
     if (time_spmv) {
-        const int nt = std::min(launched, c->h_sc->its);
-        for (int i = 0; i < nt; ++i) {
+        const int nt = std::min(launched, c->h_sc->its - it0);
+        for (int e = 0; e < nt; ++e) {
             float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, c->evS[i], c->evE[i]));
+            CK(cudaEventElapsedTime(&ms, c->evS[e], c->evE[e]));
             *t_spmv += ms;
         }
         *n_spmv += nt;
@@ -366,8 +390,16 @@ xdcg_status solve_fp64(xdcg_ctx *c, const double *f, double *u, double tol, xdcg
     return map_done(done);
 }
 
+// FP32-inner / FP64-refinement solve with residual replacement ("reliable
+// updates"): one FP32 A-DEF2 CG run on the block-scaled system; whenever its
+// recursive residual has dropped by the factor inner_tol since the last
+// replacement, the FP32 correction is added to the FP64 solution, the true
+// residual f - K u is recomputed in FP64, and its scaled image replaces the
+// recursive residual while the search direction and rho carry on, so the
+// Krylov space is not restarted.
 xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, xdcg_result *res) {
     cudaStream_t st = c->st;
+    Level32 &L = c->L32;
     init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
     launch_dot<double>(f, f, c->n, c->partials, c->aux, kFinStore, 0, st);
     c->launches += 1;
@@ -376,44 +408,76 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, xdc
     if ((s = read_aux(c, v, 1)) != XDCG_OK) return s;
     const double ff = v[0];
     CK(cudaMemsetAsync(u, 0, c->n * sizeof(double), st));
-    CK(cudaMemcpyAsync(c->r64, f, c->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    double rn2 = ff;
-    int total = 0, cycles = 0;
+    res->iterations = 0;
+    res->outer_cycles = 0;
+    res->rel_res_recursive = 0.0;
+    res->rel_res_true = 0.0;
+    if (ff == 0.0) return XDCG_OK;
+    if (!std::isfinite(ff)) return XDCG_BREAKDOWN;
+    const double s0 = 1.0 / std::sqrt(ff);
+    const double delta2 = c->opt.inner_tol * c->opt.inner_tol;
+    float *rA = c->r32, *rB = c->y32;
+    // f~ = s0 L^-1 f, and the FP32 run from Algorithm 2
+    launch_fwd_scale(c->nNodes, L.dofStart, L.F, f, s0, c->f32, st);
+    CK(cudaMemsetAsync(c->u32, 0, c->n * sizeof(float), st));
+    init_scalars(c, c->sc32, -1.0, nullptr, c->opt.max_iter);
+    scaled_init(c, c->f32, c->u32, rA, c->p32, c->sc32);
+    k_set_trigger<<<1, 32, 0, st>>>(c->sc32, 1, delta2, 0.0);
+    c->launches += 2;
+    double rn2 = ff, last_rec = 1.0;
+    int cycles = 0, its = 0, done = 0, breakdowns = 0;
     xdcg_status status = XDCG_NO_CONVERGENCE;
-    double last_inner_rel = 1.0;
     while (true) {
-        if (ff == 0.0 || rn2 <= tol * tol * ff) { status = XDCG_OK; break; }
-        if (cycles >= c->opt.max_outer || total >= c->opt.max_iter) break;
-        const double rn = std::sqrt(rn2);
-        // scaled inner right-hand side f~ = L^-1 r / ||r||
-        launch_fwd_scale(c->nNodes, c->L32.dofStart, c->L32.F, c->r64, 1.0 / rn, c->f32, st);
-        init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
-        launch_dot<float>(c->f32, c->f32, c->n, c->partials, c->aux, kFinStore, 0, st);
-        const double eta = c->opt.inner_tol;
-        init_scalars(c, c->sc32, eta * eta, &c->aux->scratch[0], c->opt.max_iter - total);
-        c->launches += 3;
-        int its = 0, done = 0;
-        s = run_pcg_scaled(c, c->f32, c->u32, c->r32, c->y32, c->p32, c->q32, c->sc32,
-                           c->opt.max_iter - total, c->opt.time_spmv != 0, &its, &done,
-                           &res->t_spmv_ms, &res->n_spmv_timed);
+        s = scaled_iterate(c, c->u32, rA, rB, c->p32, c->q32, c->sc32, c->opt.max_iter,
+                           c->opt.time_spmv != 0, &its, &done, &res->t_spmv_ms,
+                           &res->n_spmv_timed);
         if (s != XDCG_OK) return s;
-        total += its;
-        cycles++;
-        last_inner_rel = std::sqrt(c->h_sc->rr);
-        launch_bwd_accum(c->nNodes, c->L32.dofStart, c->L32.F, c->u32, rn, u, st);
+        last_rec = std::sqrt(c->h_sc->rr);
+        // fold the FP32 correction into u (FP64): u += L^-T u~ / s0
+        launch_bwd_accum(c->nNodes, L.dofStart, L.F, c->u32, 1.0 / s0, u, st);
+        CK(cudaMemsetAsync(c->u32, 0, c->n * sizeof(float), st));
         init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
         launch_spmv<double>(c->L64.A, u, c->r64, f, 1, c->partials, c->aux, kFinStore, 0, st);
         c->launches += 3;
         if ((s = read_aux(c, v, 1)) != XDCG_OK) return s;
         const double prev = rn2;
         rn2 = v[0];
+        cycles++;
         if (!std::isfinite(rn2)) { status = XDCG_BREAKDOWN; break; }
-        if (done == kBreakdown && rn2 >= prev) { status = XDCG_BREAKDOWN; break; }
+        if (rn2 <= tol * tol * ff) { status = XDCG_OK; break; }
+        if (done == kMaxIter || cycles >= c->opt.max_outer) { status = XDCG_NO_CONVERGENCE; break; }
+        if (done == kBreakdown) {
+            if (rn2 >= prev || ++breakdowns > 2) { status = XDCG_BREAKDOWN; break; }
+        }
+        // replace the recursive residual by the scaled true residual and finish
+        // the interrupted iteration: z = r + Z~ nu, beta, p = z + beta p (beta =
+        // 0 if the replacement moved the residual far: see k_coarse mode 3)
+        float *rbuf = (its & 1) ? rB : rA;
+        launch_fwd_scale(c->nNodes, L.dofStart, L.F, c->r64, s0, rbuf, st);
+        k_set_trigger<<<1, 32, 0, st>>>(c->sc32, 0, 0.0, 0.0);
+        launch_restrict_update(L.R, nullptr, rbuf, nullptr, nullptr, nullptr, 1, c->g, c->zr,
+                               c->partials, c->sc32, st);
+        launch_coarse(c->Einv, c->k, c->g, c->zr, c->nu, c->nu32, done == kBreakdown ? 1 : 3,
+                      c->partials, c->sc32, st);
+        launch_prolong_rows(L.R, c->nu32, rbuf, c->p32, done == kBreakdown ? 2 : 0, c->sc32, st);
+        c->launches += 5;
+        CK(cudaMemcpyAsync(c->h_sc, c->sc32, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        // next replacement: a further factor inner_tol, or sooner when the
+        // scaled residual, at the ratio just observed between the scaled and
+        // the true norm, should be at half the target -- but not before it has
+        // dropped by a factor 10: near the target a few CG steps shorten the
+        // scaled residual without shortening the true one
+        const double gamma2 = c->h_sc->rr / (s0 * s0 * rn2);
+        const double floor2 = std::min(0.25 * tol * tol * ff * s0 * s0 * gamma2,
+                                       kMinGroupDrop2 * c->h_sc->rr);
+        k_set_trigger<<<1, 32, 0, st>>>(c->sc32, 1, delta2, floor2);
+        c->launches += 1;
     }
-    res->iterations = total;
+    res->iterations = its;
     res->outer_cycles = cycles;
-    res->rel_res_recursive = last_inner_rel;
-    res->rel_res_true = ff > 0 ? std::sqrt(rn2 / ff) : 0.0;
+    res->rel_res_recursive = last_rec;
+    res->rel_res_true = std::sqrt(rn2 / ff);
     return status;
 }
 
@@ -1098,7 +1162,7 @@ xdcg_status xdcg_default_options(xdcg_options *opt) {
     opt->tol = 1e-8;
     opt->max_iter = 10000;
     opt->precision = XDCG_FP64;
-    opt->inner_tol = 1e-5;
+    opt->inner_tol = 1e-3;
     opt->max_outer = 30;
     opt->time_spmv = 0;
     return XDCG_OK;

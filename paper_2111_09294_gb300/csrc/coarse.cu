@@ -176,7 +176,11 @@ void launch_sweep_inverse(double *A, int k, double *colbuf, int *bad, double thr
 // 16-byte loads when rows are 16-byte aligned (k even).  nu32, if given,
 // receives an FP32 copy for the FP32 prolongation.  mode 0: nothing else
 // (Algorithm 2); mode 1: rho = r^T y + nu^T (Z^T r), beta = 0 (start);
-// mode 2: the same rho_new, beta = rho_new / rho, rho = rho_new (iteration).
+// mode 2: the same rho_new, beta = rho_new / rho, rho = rho_new (iteration);
+// mode 3: as mode 2 after a residual replacement, except that beta = 0 (a
+// restart) when the replaced residual is more than twice as long as the
+// recursive one it replaced (kept in scratch[3]): the recursion had drifted
+// too far from the true residual for the old direction to stay conjugate.
 __global__ void __launch_bounds__(kThreads)
 k_coarse(const double *__restrict__ Einv, int k, const double *__restrict__ g,
          const double *__restrict__ zr, double *nu, float *nu32, int mode, double *partials,
@@ -228,9 +232,10 @@ k_coarse(const double *__restrict__ Einv, int k, const double *__restrict__ g,
         if (mode == 1) {
             sc->rho = sc->ry + tot[0];
             sc->beta = 0.0;
-        } else if (mode == 2) {
+        } else {
             const double rho_new = sc->ry + tot[0];
-            sc->beta = rho_new / sc->rho;
+            const bool restart = mode == 3 && sc->rr > 4.0 * sc->scratch[3];
+            sc->beta = restart ? 0.0 : rho_new / sc->rho;
             sc->rho = rho_new;
         }
     }

@@ -20,11 +20,11 @@ class Solver:
 
     K: node-blocked CSR arrays (dof_ptr, row_ptr, col, val_ptr, val) in host memory;
     Z: box subdomains (sub_of_node, coords, hsign, centres).
-    precision: "fp64" or "mixed" (FP32 inner PCG inside FP64 iterative refinement).
+    precision: "fp64" or "mixed" (FP32 PCG on the block-scaled system with FP64 residual replacement).
     """
 
     def __init__(self, dof_ptr, row_ptr, col, val_ptr, val, sub_of_node, coords, hsign, centres,
-                 precision="fp64", tol=1e-8, max_iter=10000, inner_tol=1e-5, max_outer=30,
+                 precision="fp64", tol=1e-8, max_iter=10000, inner_tol=1e-3, max_outer=30,
                  time_spmv=False, enriched_modes=True, stream=None):
         lib = L.load()
         self._lib = lib
