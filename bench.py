@@ -260,6 +260,19 @@ def run_ours(args):
 
     if rank != 0:
         return
+    # per-kernel time per iteration, from separate solves with CUDA events
+    # around every kernel of the loop (outside the timed region)
+    phases = {}
+    for prec, names in (("mixed", ("spmv", "restrict_update", "coarse", "prolong")),
+                        ("fp64", ("spmv", "update", "restrict", "coarse", "prolong"))):
+        diag = Solver.from_problem(P, precision=prec, time_spmv="kernels",
+                                   inner_tol=args.inner_tol)
+        diag.solve(f, tol=TOL, out=u)
+        flush.zero_()
+        _, dinf = diag.solve(f, tol=TOL, out=u)
+        nt = max(dinf["n_phase_timed"], 1)
+        phases[prec] = {nm: round(1e3 * t / nt, 2) for nm, t in zip(names, dinf["t_phase_ms"])}
+        diag.close()
     info = mixed.info
     n_sp = sum(i["n_spmv_timed"] for i in inf_mixed)
     t_sp = sum(i["t_spmv_ms"] for i in inf_mixed)
@@ -289,6 +302,7 @@ def run_ours(args):
         "rel_res_true_mixed": res_true, "rel_res_true_fp64": inf_fp64[-1]["rel_res_true"],
         "setup_ms": info["t_setup_ms"],
         "spmv_fp32_gbs": achieved, "spmv_fp64_gbs": achieved64,
+        "kernel_us_per_iteration": phases,
         "roofline": {"bound": "hbm", "kernel": "k_spmv<float> (inner FP32 SpMV)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind,

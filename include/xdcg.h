@@ -47,8 +47,11 @@ typedef enum {
     XDCG_NO_CONVERGENCE = 5,   /* max_iter reached; u holds the last iterate */
     XDCG_CUDA_ERROR = 6,       /* a CUDA runtime call failed */
     XDCG_OOM = 7,              /* device allocation failed */
-    XDCG_TOO_LARGE = 8         /* the problem needs more than the fixed scratch of
+    XDCG_TOO_LARGE = 8,        /* the problem needs more than the fixed scratch of
                                   xdcg_spmv_noalloc */
+    XDCG_TIMEOUT = 9           /* a kernel's bounded wait on its own asynchronous copies ran
+                                  out; the results of that call are invalid and the
+                                  context must be destroyed */
 } xdcg_status;
 
 enum { XDCG_HOST = 0, XDCG_DEVICE = 1 };       /* memory space of input arrays */
@@ -98,7 +101,8 @@ typedef struct {
                                 residual has dropped by this factor, default 1e-3 */
     int32_t max_outer;       /* MIXED: residual replacements (FP64 residual evaluations),
                                 default 30 */
-    int32_t time_spmv;       /* 1: bracket every SpMV launch by CUDA events */
+    int32_t time_spmv;       /* 1: bracket every SpMV launch of the iteration by CUDA events;
+                                2: bracket every kernel of the iteration (t_phase_ms) */
 } xdcg_options;
 
 typedef struct {
@@ -112,6 +116,10 @@ typedef struct {
     int32_t n_spmv_timed;        /* SpMV launches timed (time_spmv) */
     double t_spmv_ms;            /* their summed CUDA-event time */
     int64_t n_launches;          /* kernels launched by this call */
+    int32_t n_phase_timed;       /* iterations whose kernels were timed (time_spmv = 2) */
+    double t_phase_ms[5];        /* their summed CUDA-event time per kernel of the iteration:
+                                    FP64: SpMV, update, restriction, coarse solve, prolongation;
+                                    MIXED: SpMV, restriction+update, coarse solve, prolongation */
 } xdcg_result;
 
 typedef struct {

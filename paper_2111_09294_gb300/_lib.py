@@ -16,7 +16,7 @@ XDCG_FP64, XDCG_MIXED = 0, 1
 
 STATUS = {0: "XDCG_OK", 1: "XDCG_INVALID_ARG", 2: "XDCG_NOT_SPD_BLOCK",
           3: "XDCG_COARSE_NOT_SPD", 4: "XDCG_BREAKDOWN", 5: "XDCG_NO_CONVERGENCE",
-          6: "XDCG_CUDA_ERROR", 7: "XDCG_OOM", 8: "XDCG_TOO_LARGE"}
+          6: "XDCG_CUDA_ERROR", 7: "XDCG_OOM", 8: "XDCG_TOO_LARGE", 9: "XDCG_TIMEOUT"}
 
 # every function the header declares
 EXPORTS = ["xdcg_default_options", "xdcg_setup", "xdcg_solve", "xdcg_solve_host",
@@ -44,10 +44,13 @@ class Result(ctypes.Structure):
     _fields_ = [("iterations", c_int32), ("outer_cycles", c_int32),
                 ("rel_res_recursive", c_double), ("rel_res_true", c_double),
                 ("t_solve_ms", c_double), ("bad_index", c_int32), ("n_spmv_timed", c_int32),
-                ("t_spmv_ms", c_double), ("n_launches", c_int64)]
+                ("t_spmv_ms", c_double), ("n_launches", c_int64),
+                ("n_phase_timed", c_int32), ("t_phase_ms", c_double * 5)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["t_phase_ms"] = list(self.t_phase_ms)
+        return d
 
 
 class Info(ctypes.Structure):

@@ -48,6 +48,7 @@ struct xdcg_ctx {
     Level64 L64{};
     Level32 L32{};
     double *Einv = nullptr;
+    float *Einv32 = nullptr;       // FP32 copy for the mixed path's FP32 iteration
     double *E = nullptr;                      // E = Z^T K Z as assembled (diagnostics)
     std::vector<void *> temps;                // set-up temporaries
 
@@ -65,6 +66,7 @@ struct xdcg_ctx {
     int *h_done = nullptr;     // pinned, 2 slots
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evb[2] = {nullptr, nullptr};
     std::vector<cudaEvent_t> evS, evE;
+    std::vector<cudaEvent_t> evP;      // per-kernel marks of timed iterations (time_spmv = 2)
     long long launches = 0;
 };
 
@@ -170,9 +172,46 @@ xdcg_status map_done(int done) {
         case kConverged: return XDCG_OK;
         case kBreakdown: return XDCG_BREAKDOWN;
         case kMaxIter: return XDCG_NO_CONVERGENCE;
+        case kFault: return XDCG_TIMEOUT;
         default: return XDCG_NO_CONVERGENCE;
     }
 }
+
+// Kernel timing of the iteration loop (time_spmv = 2): mark m of iteration it
+// is recorded before the iteration's kernel m, mark P after its last kernel.
+constexpr int kMarks = 6;
+
+xdcg_status phase_mark(xdcg_ctx *c, int it, int m) {
+    const size_t idx = (size_t)it * kMarks + m;
+    while (c->evP.size() <= idx) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        c->evP.push_back(e);
+    }
+    CK(cudaEventRecord(c->evP[idx], c->st));
+    return XDCG_OK;
+}
+
+// sums the phase times of the first n timed iterations into res
+xdcg_status phase_collect(xdcg_ctx *c, int n, int P, xdcg_result *res) {
+    for (int it = 0; it < n; ++it)
+        for (int m = 0; m < P; ++m) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, c->evP[(size_t)it * kMarks + m],
+                                    c->evP[(size_t)it * kMarks + m + 1]));
+            res->t_phase_ms[m] += ms;
+        }
+    res->n_phase_timed += n;
+    return XDCG_OK;
+}
+
+#define MARK(it, m)                                                             \
+    do {                                                                        \
+        if (timeKernels) {                                                      \
+            xdcg_status ms_ = phase_mark(c, (it), (m));                         \
+            if (ms_ != XDCG_OK) return ms_;                                     \
+        }                                                                       \
+    } while (0)
 
 // ---- one preconditioned CG run (Algorithms 1-3) ----------------------------
 
@@ -201,9 +240,9 @@ struct PlainPath {
 
 template <typename T, typename Path>
 xdcg_status run_pcg(xdcg_ctx *c, Path path, const T *f, T *u, T *r, T *p, T *q, T *y,
-                    Scalars *sc, int max_it, bool time_spmv, int *its_out, int *done_out,
-                    double *t_spmv, int *n_spmv) {
+                    Scalars *sc, int max_it, int *its_out, int *done_out, xdcg_result *res) {
     cudaStream_t st = c->st;
+    const bool timeSpmv = c->opt.time_spmv == 1, timeKernels = c->opt.time_spmv == 2;
     // Algorithm 2 with u_-1 = 0: u_0 = Z E^-1 Z^T f
     path.restrict_(f, nullptr, 0, nullptr, sc);
     path.coarse(nullptr, 0, sc);
@@ -220,7 +259,7 @@ xdcg_status run_pcg(xdcg_ctx *c, Path path, const T *f, T *u, T *r, T *p, T *q, 
     const int max_batches = max_it / kBatch + 2;
     for (int b = 0; b < max_batches; ++b) {
         for (int i = 0; i < kBatch; ++i) {
-            if (time_spmv) {
+            if (timeSpmv) {
                 if ((int)c->evS.size() <= launched) {
                     cudaEvent_t e0, e1;
                     CK(cudaEventCreate(&e0));
@@ -230,12 +269,18 @@ xdcg_status run_pcg(xdcg_ctx *c, Path path, const T *f, T *u, T *r, T *p, T *q, 
                 }
                 CK(cudaEventRecord(c->evS[launched], st));
             }
+            MARK(launched, 0);
             path.spmv(p, q, nullptr, 0, kFinAlpha, sc);
-            if (time_spmv) CK(cudaEventRecord(c->evE[launched], st));
+            if (timeSpmv) CK(cudaEventRecord(c->evE[launched], st));
+            MARK(launched, 1);
             path.update(u, r, p, q, y, 0, sc);
+            MARK(launched, 2);
             path.restrict_(r, y, 1, c->zr, sc);
+            MARK(launched, 3);
             path.coarse(c->zr, 2, sc);
+            MARK(launched, 4);
             path.prolong(y, p, 0, sc);
+            MARK(launched, 5);
             c->launches += 5;
             ++launched;
         }
@@ -251,14 +296,20 @@ xdcg_status run_pcg(xdcg_ctx *c, Path path, const T *f, T *u, T *r, T *p, T *q, 
     CK(cudaGetLastError());
     *its_out = c->h_sc->its;
     *done_out = c->h_sc->done;
-    if (time_spmv) {
-        const int nt = std::min(launched, c->h_sc->its);
+    const int nt = std::min(launched, c->h_sc->its);
+    if (timeSpmv) {
         for (int i = 0; i < nt; ++i) {
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, c->evS[i], c->evE[i]));
-            *t_spmv += ms;
+            res->t_spmv_ms += ms;
         }
-        *n_spmv += nt;
+        res->n_spmv_timed += nt;
+    }
+    if (timeKernels) {
+        xdcg_status s = phase_collect(c, nt, 5, res);
+        if (s != XDCG_OK) return s;
+        res->t_spmv_ms = res->t_phase_ms[0];
+        res->n_spmv_timed = res->n_phase_timed;
     }
     return XDCG_OK;
 }
@@ -291,12 +342,12 @@ void scaled_init(xdcg_ctx *c, const float *f, float *u, float *rA, float *p, Sca
     Level32 &L = c->L32;
     launch_restrict_update(L.R, nullptr, f, nullptr, nullptr, nullptr, 2, c->g, nullptr,
                            c->partials, sc, st);
-    launch_coarse(c->Einv, c->k, c->g, nullptr, c->nu, c->nu32, 0, c->partials, sc, st);
+    launch_coarse32(c->Einv32, c->k, c->g, nullptr, c->nu, c->nu32, 0, c->partials, sc, st);
     launch_prolong_rows(L.R, c->nu32, nullptr, u, 1, sc, st);
     launch_spmv<float>(L.A, u, rA, f, 1, c->partials, sc, kFinRR, 0, st);
     launch_restrict_update(L.R, nullptr, rA, nullptr, nullptr, nullptr, 1, c->g, c->zr,
                            c->partials, sc, st);
-    launch_coarse(c->Einv, c->k, c->g, c->zr, c->nu, c->nu32, 1, c->partials, sc, st);
+    launch_coarse32(c->Einv32, c->k, c->g, c->zr, c->nu, c->nu32, 1, c->partials, sc, st);
     launch_prolong_rows(L.R, c->nu32, rA, p, 2, sc, st);
     c->launches += 7;
 }
@@ -304,10 +355,11 @@ void scaled_init(xdcg_ctx *c, const float *f, float *u, float *rA, float *p, Sca
 // Run iterations (in batches, polling the device flag) until a kernel stops
 // the run: the replacement trigger, breakdown, or the iteration cap.
 xdcg_status scaled_iterate(xdcg_ctx *c, float *u, float *rA, float *rB, float *p, float *q,
-                           Scalars *sc, int max_it, bool time_spmv, int *its_out, int *done_out,
-                           double *t_spmv, int *n_spmv) {
+                           Scalars *sc, int max_it, int *its_out, int *done_out,
+                           xdcg_result *res) {
     cudaStream_t st = c->st;
     Level32 &L = c->L32;
+    const bool timeSpmv = c->opt.time_spmv == 1, timeKernels = c->opt.time_spmv == 2;
     CK(cudaMemcpyAsync(c->h_sc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     const int it0 = c->h_sc->its;
@@ -317,7 +369,7 @@ xdcg_status scaled_iterate(xdcg_ctx *c, float *u, float *rA, float *rB, float *p
         for (int j = 0; j < kBatch; ++j, ++i, ++launched) {
             float *rc = (i & 1) ? rB : rA;
             float *rn = (i & 1) ? rA : rB;
-            if (time_spmv) {
+            if (timeSpmv) {
                 if ((int)c->evS.size() <= launched) {
                     cudaEvent_t e0, e1;
                     CK(cudaEventCreate(&e0));
@@ -327,11 +379,16 @@ xdcg_status scaled_iterate(xdcg_ctx *c, float *u, float *rA, float *rB, float *p
                 }
                 CK(cudaEventRecord(c->evS[launched], st));
             }
+            MARK(launched, 0);
             launch_spmv<float>(L.A, p, q, nullptr, 0, c->partials, sc, kFinAlpha, 0, st);
-            if (time_spmv) CK(cudaEventRecord(c->evE[launched], st));
+            if (timeSpmv) CK(cudaEventRecord(c->evE[launched], st));
+            MARK(launched, 1);
             launch_restrict_update(L.R, u, rc, rn, p, q, 0, c->g, c->zr, c->partials, sc, st);
-            launch_coarse(c->Einv, c->k, c->g, c->zr, c->nu, c->nu32, 2, c->partials, sc, st);
+            MARK(launched, 2);
+            launch_coarse32(c->Einv32, c->k, c->g, c->zr, c->nu, c->nu32, 2, c->partials, sc, st);
+            MARK(launched, 3);
             launch_prolong_rows(L.R, c->nu32, rn, p, 0, sc, st);
+            MARK(launched, 4);
             c->launches += 4;
         }
         CK(cudaMemcpyAsync(&c->h_done[b & 1], &sc->done, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -346,14 +403,22 @@ xdcg_status scaled_iterate(xdcg_ctx *c, float *u, float *rA, float *rB, float *p
     CK(cudaGetLastError());
     *its_out = c->h_sc->its;
     *done_out = c->h_sc->done;
-    if (time_spmv) {
-        const int nt = std::min(launched, c->h_sc->its - it0);
+    const int nt = std::min(launched, c->h_sc->its - it0);
+    if (timeSpmv) {
         for (int e = 0; e < nt; ++e) {
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, c->evS[e], c->evE[e]));
-            *t_spmv += ms;
+            res->t_spmv_ms += ms;
         }
-        *n_spmv += nt;
+        res->n_spmv_timed += nt;
+    }
+    if (timeKernels) {
+        const double t0 = res->t_phase_ms[0];
+        const int n0 = res->n_phase_timed;
+        xdcg_status s = phase_collect(c, nt, 4, res);
+        if (s != XDCG_OK) return s;
+        res->t_spmv_ms += res->t_phase_ms[0] - t0;
+        res->n_spmv_timed += res->n_phase_timed - n0;
     }
     return XDCG_OK;
 }
@@ -362,7 +427,7 @@ xdcg_status read_aux(xdcg_ctx *c, double *vals, int count) {
     CK(cudaMemcpyAsync(c->h_sc, c->aux, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     for (int i = 0; i < count; ++i) vals[i] = c->h_sc->scratch[i];
-    return XDCG_OK;
+    return c->h_sc->done == kFault ? XDCG_TIMEOUT : XDCG_OK;
 }
 
 xdcg_status solve_fp64(xdcg_ctx *c, const double *f, double *u, double tol, xdcg_result *res) {
@@ -373,8 +438,7 @@ xdcg_status solve_fp64(xdcg_ctx *c, const double *f, double *u, double tol, xdcg
     c->launches += 1;
     int its = 0, done = 0;
     xdcg_status s = run_pcg<double>(c, PlainPath{c, c->L64}, f, u, c->r64, c->p64, c->q64,
-                                    c->y64, c->sc, c->opt.max_iter, c->opt.time_spmv != 0, &its,
-                                    &done, &res->t_spmv_ms, &res->n_spmv_timed);
+                                    c->y64, c->sc, c->opt.max_iter, &its, &done, res);
     if (s != XDCG_OK) return s;
     const double rr = c->h_sc->rr;
     // true residual f - K u in FP64
@@ -428,10 +492,10 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, xdc
     int cycles = 0, its = 0, done = 0, breakdowns = 0;
     xdcg_status status = XDCG_NO_CONVERGENCE;
     while (true) {
-        s = scaled_iterate(c, c->u32, rA, rB, c->p32, c->q32, c->sc32, c->opt.max_iter,
-                           c->opt.time_spmv != 0, &its, &done, &res->t_spmv_ms,
-                           &res->n_spmv_timed);
+        s = scaled_iterate(c, c->u32, rA, rB, c->p32, c->q32, c->sc32, c->opt.max_iter, &its,
+                           &done, res);
         if (s != XDCG_OK) return s;
+        if (done == kFault) return XDCG_TIMEOUT;
         last_rec = std::sqrt(c->h_sc->rr);
         // fold the FP32 correction into u (FP64): u += L^-T u~ / s0
         launch_bwd_accum(c->nNodes, L.dofStart, L.F, c->u32, 1.0 / s0, u, st);
@@ -457,7 +521,7 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, xdc
         k_set_trigger<<<1, 32, 0, st>>>(c->sc32, 0, 0.0, 0.0);
         launch_restrict_update(L.R, nullptr, rbuf, nullptr, nullptr, nullptr, 1, c->g, c->zr,
                                c->partials, c->sc32, st);
-        launch_coarse(c->Einv, c->k, c->g, c->zr, c->nu, c->nu32, done == kBreakdown ? 1 : 3,
+        launch_coarse32(c->Einv32, c->k, c->g, c->zr, c->nu, c->nu32, done == kBreakdown ? 1 : 3,
                       c->partials, c->sc32, st);
         launch_prolong_rows(L.R, c->nu32, rbuf, c->p32, done == kBreakdown ? 2 : 0, c->sc32, st);
         c->launches += 5;
@@ -508,6 +572,7 @@ void free_ctx(xdcg_ctx *c) {
     if (c->h_done) cudaFreeHost(c->h_done);
     for (auto e : c->evS) cudaEventDestroy(e);
     for (auto e : c->evE) cudaEventDestroy(e);
+    for (auto e : c->evP) cudaEventDestroy(e);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     for (auto e : c->evb)
@@ -656,37 +721,29 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     struct SellHost {
         std::vector<int> row, len, col, src;
         std::vector<long long> slicePtr;
-        int nSlices = 0, ilvSteps = 0;
+        int nSlices = 0;
     };
-    auto build_sell = [&](const std::vector<int> &rows, int tpr, bool interleave, SellHost &H) {
+    auto build_sell = [&](const std::vector<int> &rows, int tpr, SellHost &H) {
         const int rpw = 32 / tpr;
         const int nr = (int)rows.size();
         H.nSlices = (nr + rpw - 1) / rpw;
         H.row = rows;
         H.len.resize(nr);
         H.slicePtr.assign(H.nSlices + 1, 0);
-        int gmax = 0;
         for (int sl = 0; sl < H.nSlices; ++sl) {
             int mx = 0;
             for (int q = 0; q < rpw && sl * rpw + q < nr; ++q) mx = std::max(mx, rowLen[rows[sl * rpw + q]]);
-            H.slicePtr[sl + 1] = H.slicePtr[sl] + 32LL * ((mx + tpr - 1) / tpr);
-            gmax = std::max(gmax, (mx + tpr - 1) / tpr);
+            H.slicePtr[sl + 1] = H.slicePtr[sl] + 32LL * std::max(1, (mx + tpr - 1) / tpr);
         }
-        H.ilvSteps = interleave ? std::max(gmax, 1) : 0;
-        const long long slots = interleave ? 32LL * H.nSlices * H.ilvSteps
-                                           : std::max<long long>(H.slicePtr[H.nSlices], 1);
-        H.col.assign(std::max<long long>(slots, 1), 0);
-        H.src.assign(9 * (size_t)std::max<long long>(slots, 1), -1);
-        const long long NS = H.nSlices;
+        const long long slots = std::max<long long>(H.slicePtr[H.nSlices], 1);
+        H.col.assign(slots, 0);
+        H.src.assign(9 * (size_t)slots, -1);
         for (int sl = 0; sl < H.nSlices; ++sl) {
             const long long base = H.slicePtr[sl];
-            const long long steps = interleave ? H.ilvSteps : (H.slicePtr[sl + 1] - base) / 32;
-            auto cidx = [&](long long st2, int lane) {
-                return interleave ? (st2 * NS + sl) * 32 + lane : base + st2 * 32 + lane;
-            };
+            const long long steps = (H.slicePtr[sl + 1] - base) / 32;
+            auto cidx = [&](long long st2, int lane) { return base + st2 * 32 + lane; };
             auto vidx = [&](long long st2, int e, int lane) {
-                return interleave ? ((st2 * 9 + e) * NS + sl) * 32 + lane
-                                  : 9 * base + (st2 * 9 + e) * 32 + lane;
+                return 9 * base + (st2 * 9 + e) * 32 + lane;
             };
             for (int q = 0; q < rpw && sl * rpw + q < nr; ++q) {
                 const int r = rows[sl * rpw + q];
@@ -700,15 +757,11 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
                     for (int e = 0; e < 9; ++e) H.src[vidx(st2, e, lane)] = blk[e];
                 });
             }
-            // lanes of a partial last slice point at a valid row
-            for (int q = nr - sl * rpw; q < rpw && q > 0; ++q)
-                for (long long st2 = 0; st2 < steps; ++st2)
-                    for (int h = 0; h < tpr; ++h) H.col[cidx(st2, q + rpw * h)] = 0;
         }
     };
     SellHost HS, HX;
-    build_sell(sRows, kTprS, false, HS);
-    build_sell(xRows, kTprX, false, HX);
+    build_sell(sRows, kTprS, HS);
+    build_sell(xRows, kTprX, HX);
     const int nS = (int)sRows.size(), nX = (int)xRows.size();
     long long nnzb3 = 0;
     for (long long r = 0; r < nChunks; ++r) nnzb3 += rowLen[r];
@@ -822,7 +875,6 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     auto upload_sell = [&](const SellHost &H, SellDev<double> &D, int **d_src) -> bool {
         D.nRows = (int)H.row.size();
         D.nSlices = H.nSlices;
-        D.ilvSteps = H.ilvSteps;
         D.row = upload(c, H.row);
         D.len = upload(c, H.len);
         D.slicePtr = upload(c, H.slicePtr);
@@ -837,6 +889,30 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     auto &A = c->L64.A;
     int *d_srcS = nullptr, *d_srcX = nullptr;
     if (!upload_sell(HS, A.S, &d_srcS) || !upload_sell(HX, A.X, &d_srcX)) return XDCG_OOM;
+    // persistent SpMV grids and each warp's slice range, balanced by steps
+    auto partition = [&](int grid) -> const int * {
+        const int nW = grid * kSpmvWarps, nT = HS.nSlices + HX.nSlices;
+        std::vector<long long> pre(nT + 1, 0);
+        for (int i = 0; i < nT; ++i) {
+            const SellHost &H = i < HS.nSlices ? HS : HX;
+            const int sl = i < HS.nSlices ? i : i - HS.nSlices;
+            pre[i + 1] = pre[i] + (H.slicePtr[sl + 1] - H.slicePtr[sl]) / 32;
+        }
+        std::vector<int> ws(nW + 1);
+        int i = 0;
+        for (int w = 0; w < nW; ++w) {
+            const long long target = pre[nT] * w / nW;
+            while (i < nT && pre[i + 1] <= target) ++i;
+            if (i < nT && target - pre[i] > pre[i + 1] - target) ++i;
+            ws[w] = i;
+        }
+        ws[nW] = nT;
+        return upload(c, ws);
+    };
+    A.grid = spmv_persistent_grid<double>(HS.nSlices + HX.nSlices);
+    if (A.grid < 1) return XDCG_CUDA_ERROR;
+    A.warpSlice = partition(A.grid);
+    if (!A.warpSlice) return XDCG_OOM;
 
     // node data and block factors (FP64)
     int *d_bad = dalloc<int>(c, 2);
@@ -948,6 +1024,9 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
 
     // block-scaled FP32 level of the mixed path: K~ = L^-1 K L^-T, Z~ = L^T Z, W~ = L^-1 W
     if (mixed) {
+        c->Einv32 = dalloc<float>(c, (size_t)k * k);
+        if (!c->Einv32) return XDCG_OOM;
+        launch_cast_f32(c->Einv, c->Einv32, (long long)k * k, st);
         std::vector<int> nodeList(N), nodeIdx(N);
         for (int t = 0; t < 3; ++t)
             for (size_t i = 0; i < lists[t].size(); ++i) {
@@ -983,12 +1062,16 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         launch_gather(d_srcX, (long long)HX.src.size(), d_Kt, nullptr, v32X, st);
         auto &A2 = c->L32.A;
         auto copy_struct = [](const SellDev<double> &D, const float *v, SellDev<float> &E) {
-            E.nRows = D.nRows; E.nSlices = D.nSlices; E.ilvSteps = D.ilvSteps; E.row = D.row;
+            E.nRows = D.nRows; E.nSlices = D.nSlices; E.row = D.row;
             E.len = D.len;
             E.slicePtr = D.slicePtr; E.col = D.col; E.val = v;
         };
         copy_struct(A.S, v32S, A2.S);
         copy_struct(A.X, v32X, A2.X);
+        A2.grid = spmv_persistent_grid<float>(HS.nSlices + HX.nSlices);
+        if (A2.grid < 1) return XDCG_CUDA_ERROR;
+        A2.warpSlice = partition(A2.grid);
+        if (!A2.warpSlice) return XDCG_OOM;
         launch_build_Zt(N, d_own, d_dof, d_sub, d_x64, d_hs, d_menr, F, d_zOff, d_Zt, st);
         launch_scale_W(nExt, d_extBox, d_extNode, d_wOff, d_menr, d_dof, F, d_W, d_Wt, st);
         // row-parallel layouts: own rows (Z~) and coupled rows (W~) of each box,
@@ -1118,7 +1201,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     CK(cudaEventCreateWithFlags(&c->evb[0], cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->evb[1], cudaEventDisableTiming));
     CK(cudaStreamSynchronize(st));
-    if (spmv_grid(HS.nSlices, HX.nSlices) > kMaxGrid) return XDCG_INVALID_ARG;
+    if (c->L64.A.grid > kMaxGrid || (mixed && c->L32.A.grid > kMaxGrid)) return XDCG_INVALID_ARG;
 
     // ---- algorithmic byte counts (see the roofline notes of the design)
     long long nStdN = (long long)lists[0].size(), nHN = (long long)lists[1].size(),
@@ -1183,6 +1266,7 @@ xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflatio
         xdcg_default_options(&c->opt);
     if (!(c->opt.tol > 0) || c->opt.max_iter < 0 || c->opt.max_outer < 1 ||
         (c->opt.precision != XDCG_FP64 && c->opt.precision != XDCG_MIXED) ||
+        c->opt.time_spmv < 0 || c->opt.time_spmv > 2 ||
         !(c->opt.inner_tol > 0 && c->opt.inner_tol < 1)) {
         delete c;
         return XDCG_INVALID_ARG;
@@ -1261,7 +1345,8 @@ std::mutex g_noalloc_mutex;
 double *g_noalloc_ptr[kMaxDevices] = {nullptr};
 
 __global__ void k_noalloc_result(const Scalars *sc, int slot, double *out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) *out = sc->scratch[slot];
+    if (threadIdx.x == 0 && blockIdx.x == 0)
+        *out = sc->done == kFault ? __longlong_as_double(0x7ff8000000000000ll) : sc->scratch[slot];
 }
 
 }  // namespace
@@ -1271,8 +1356,7 @@ xdcg_status xdcg_spmv_noalloc(xdcg_ctx *c, int32_t precision, const void *x, voi
     if (!c || !x || !y || x == y) return XDCG_INVALID_ARG;
     if (precision != XDCG_FP64 && precision != XDCG_MIXED) return XDCG_INVALID_ARG;
     if (precision == XDCG_MIXED && !c->mixed) return XDCG_INVALID_ARG;
-    const int grid = precision == XDCG_FP64 ? spmv_grid(c->L64.A.S.nSlices, c->L64.A.X.nSlices)
-                                            : spmv_grid(c->L32.A.S.nSlices, c->L32.A.X.nSlices);
+    const int grid = precision == XDCG_FP64 ? c->L64.A.grid : c->L32.A.grid;
     if (grid > XDCG_NOALLOC_MAX_BLOCKS) return XDCG_TOO_LARGE;
     int dev = 0;
     CK(cudaGetDevice(&dev));
@@ -1351,6 +1435,7 @@ const char *xdcg_status_string(xdcg_status s) {
         case XDCG_OOM: return "out of device memory";
         case XDCG_TOO_LARGE:
             return "problem exceeds the fixed scratch of xdcg_spmv_noalloc (XDCG_NOALLOC_MAX_BLOCKS)";
+        case XDCG_TIMEOUT: return "a bounded device-side wait ran out (results invalid)";
     }
     return "unknown status";
 }

@@ -12,6 +12,7 @@
 // centre (Eqs. dcg_deflation_space, dcg_deflation_space_enr_std,
 // dcg_deflation_space_enr_enr) in the FP64 path, and from the explicit
 // scaled basis Z~ = L^T Z in the FP32 block-scaled path.
+#include "cache.cuh"
 #include "reduce.cuh"
 
 namespace xdcg {
@@ -275,12 +276,13 @@ __device__ __forceinline__ float restrict_update_unit(const RowBoxDev &B, int un
     float acc[M + 1];
 #pragma unroll
     for (int c = 0; c <= M; ++c) acc[c] = 0.0f;
+    const uint64_t keep = l2_keep_policy();
     if (kind == 0) {
         const int r0 = B.ownRowPtr[s], R = B.ownRowPtr[s + 1] - r0;
         const float *Z = B.Z + B.zBase[s];
 #pragma unroll 4
         for (int r = rb + threadIdx.x; r < re; r += blockDim.x) {
-            const int d = B.ownRowDof[r];
+            const int d = ld_keep(B.ownRowDof + r, keep);
             float rn = r_cur[d];
             if (mode == 0) {
                 rn = fmaf(-alpha, q[d], rn);
@@ -290,18 +292,18 @@ __device__ __forceinline__ float restrict_update_unit(const RowBoxDev &B, int un
             acc[M] = fmaf(rn, rn, acc[M]);
             const int rl = r - r0;
 #pragma unroll
-            for (int c = 0; c < M; ++c) acc[c] = fmaf(Z[(size_t)c * R + rl], rn, acc[c]);
+            for (int c = 0; c < M; ++c) acc[c] = fmaf(ld_keep(Z + (size_t)c * R + rl, keep), rn, acc[c]);
         }
     } else if (mode != 2) {
         const int r0 = B.extRowPtr[s], R = B.extRowPtr[s + 1] - r0;
         const float *W = B.W + B.wBase[s];
 #pragma unroll 4
         for (int r = rb + threadIdx.x; r < re; r += blockDim.x) {
-            const int d = B.extRowDof[r];
+            const int d = ld_keep(B.extRowDof + r, keep);
             const float rn = (mode == 0) ? fmaf(-alpha, q[d], r_cur[d]) : r_cur[d];
             const int rl = r - r0;
 #pragma unroll
-            for (int c = 0; c < M; ++c) acc[c] = fmaf(W[(size_t)c * R + rl], rn, acc[c]);
+            for (int c = 0; c < M; ++c) acc[c] = fmaf(ld_keep(W + (size_t)c * R + rl, keep), rn, acc[c]);
         }
     }
     block_sum<float, M + 1>(acc);
@@ -377,13 +379,14 @@ __device__ __forceinline__ void prolong_rows_unit(const RowBoxDev &B, int unit,
     const int r0 = B.ownRowPtr[s], R = B.ownRowPtr[s + 1] - r0;
     const float *Z = B.Z + B.zBase[s];
     const int re = B.pUnitEnd[unit];
+    const uint64_t keep = l2_keep_policy();
 #pragma unroll 2
     for (int r = B.pUnitBegin[unit] + threadIdx.x; r < re; r += blockDim.x) {
         const int rl = r - r0;
         float zv = 0.0f;
 #pragma unroll
-        for (int c = 0; c < M; ++c) zv = fmaf(Z[(size_t)c * R + rl], n[c], zv);
-        emit(p, y, B.ownRowDof[r], zv, mode, beta);
+        for (int c = 0; c < M; ++c) zv = fmaf(ld_keep(Z + (size_t)c * R + rl, keep), n[c], zv);
+        emit(p, y, ld_keep(B.ownRowDof + r, keep), zv, mode, beta);
     }
 }
 

@@ -2,6 +2,7 @@
 // set-up, the FP64 inverse of E, and the per-iteration coarse solve
 // nu = E^-1 g that replaces the two solves of Algorithm 3 (their difference
 // lambda - mu = E^-1 (Z^T r - Z^T K y)) and the two of Algorithm 2.
+#include "cache.cuh"
 #include "reduce.cuh"
 
 namespace xdcg {
@@ -172,6 +173,24 @@ void launch_sweep_inverse(double *A, int k, double *colbuf, int *bad, double thr
 
 // ---- per-iteration coarse solve -------------------------------------------
 
+// Scalar updates shared by the coarse kernels (modes as for k_coarse); part
+// holds this thread's share of nu^T (Z^T r).
+__device__ __forceinline__ void coarse_scalars(double (&part)[1], int mode, double *partials,
+                                               Scalars *sc) {
+    double tot[1];
+    if (grid_sum<double, 1>(part, partials, &sc->ticket[3], tot) && threadIdx.x == 0) {
+        if (mode == 1) {
+            sc->rho = sc->ry + tot[0];
+            sc->beta = 0.0;
+        } else if (mode >= 2) {
+            const double rho_new = sc->ry + tot[0];
+            const bool restart = mode == 3 && sc->rr > 4.0 * sc->scratch[3];
+            sc->beta = restart ? 0.0 : rho_new / sc->rho;
+            sc->rho = rho_new;
+        }
+    }
+}
+
 // nu = E^-1 g, one warp per row, four independent FMA chains per lane and
 // 16-byte loads when rows are 16-byte aligned (k even).  nu32, if given,
 // receives an FP32 copy for the FP32 prolongation.  mode 0: nothing else
@@ -227,18 +246,75 @@ k_coarse(const double *__restrict__ Einv, int k, const double *__restrict__ g,
             if (mode != 0) part[0] = s * zr[i];
         }
     }
-    double tot[1];
-    if (grid_sum<double, 1>(part, partials, &sc->ticket[3], tot) && threadIdx.x == 0) {
-        if (mode == 1) {
-            sc->rho = sc->ry + tot[0];
-            sc->beta = 0.0;
+    coarse_scalars(part, mode, partials, sc);
+}
+
+// nu = E^-1 g with E^-1 held in FP32, for the FP32 iteration of the mixed
+// path.  A-DEF2 tolerates an inexact coarse solve (the coarse correction
+// acts as a preconditioner, not as a projection the recurrence relies on),
+// and on the test problems FP32 E^-1 changes no iteration count.  Each block
+// stages g in FP32 shared memory chunk by chunk; one warp per row, 16-byte
+// loads of E^-1 when rows are 16-byte aligned (k a multiple of 4).
+constexpr int kCoarseChunk = 2048;
+
+template <int V>
+__global__ void __launch_bounds__(kThreads)
+k_coarse32(const float *__restrict__ Einv, int k, const double *__restrict__ g,
+           const double *__restrict__ zr, double *nu, float *nu32, int mode, double *partials,
+           Scalars *sc) {
+    if (sc->done != kRunning) return;
+    __shared__ __align__(16) float gs[kCoarseChunk];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kWarps + warp;
+    const float *row = Einv + (size_t)(i < k ? i : 0) * k;
+    const uint64_t keep = l2_keep_policy();
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    for (int c0 = 0; c0 < k; c0 += kCoarseChunk) {
+        const int len = min(kCoarseChunk, k - c0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < len; j += blockDim.x) gs[j] = (float)g[c0 + j];
+        __syncthreads();
+        if (i >= k) continue;
+        if (V == 4) {
+            const float4 *r4 = reinterpret_cast<const float4 *>(row + c0);
+            const float4 *g4 = reinterpret_cast<const float4 *>(gs);
+            const int n4 = len >> 2;
+#pragma unroll 8
+            for (int j = lane; j < n4; j += 32) {
+                const float4 a = ld_keep(r4 + j, keep), x = g4[j];
+                s0 = fmaf(a.x, x.x, s0);
+                s1 = fmaf(a.y, x.y, s1);
+                s2 = fmaf(a.z, x.z, s2);
+                s3 = fmaf(a.w, x.w, s3);
+            }
         } else {
-            const double rho_new = sc->ry + tot[0];
-            const bool restart = mode == 3 && sc->rr > 4.0 * sc->scratch[3];
-            sc->beta = restart ? 0.0 : rho_new / sc->rho;
-            sc->rho = rho_new;
+#pragma unroll 4
+            for (int j = lane; j < len; j += 32) s0 = fmaf(ld_keep(row + c0 + j, keep), gs[j], s0);
         }
     }
+    double part[1] = {0.0};
+    if (i < k) {
+        float s = (s0 + s1) + (s2 + s3);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            nu[i] = (double)s;
+            nu32[i] = s;
+            if (mode != 0) part[0] = (double)s * zr[i];
+        }
+    }
+    coarse_scalars(part, mode, partials, sc);
+}
+
+void launch_coarse32(const float *Einv, int k, const double *g, const double *zr, double *nu,
+                     float *nu32, int mode, double *partials, Scalars *sc, cudaStream_t st) {
+    const int grid = (k + kWarps - 1) / kWarps;
+    if (k % 4 == 0)
+        k_coarse32<4><<<grid > 0 ? grid : 1, kThreads, 0, st>>>(Einv, k, g, zr, nu, nu32, mode,
+                                                                 partials, sc);
+    else
+        k_coarse32<1><<<grid > 0 ? grid : 1, kThreads, 0, st>>>(Einv, k, g, zr, nu, nu32, mode,
+                                                                 partials, sc);
 }
 
 void launch_coarse(const double *Einv, int k, const double *g, const double *zr, double *nu,

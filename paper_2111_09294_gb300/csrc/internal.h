@@ -11,11 +11,11 @@ namespace xdcg {
 
 constexpr int kThreads = 256;      // threads per block of the streaming kernels
 constexpr int kWarps = kThreads / 32;
-constexpr int kSpmvThreads = 512;  // threads per block of the SpMV
+constexpr int kSpmvThreads = 256;  // threads per block of the SpMV (8 persistent warps)
 constexpr int kSpmvWarps = kSpmvThreads / 32;
 
 // done flags written by the kernels
-enum : int { kRunning = 0, kConverged = 1, kBreakdown = 2, kMaxIter = 3 };
+enum : int { kRunning = 0, kConverged = 1, kBreakdown = 2, kMaxIter = 3, kFault = 4 };
 
 // what the last block of a reduction does with the reduced value(s)
 enum Fin : int {
@@ -35,9 +35,9 @@ struct Scalars {
     double tol2ff;    // tol^2 ||f||^2
     double scratch[4];
     int its;          // loop bodies run
-    int done;         // kRunning / kConverged / kBreakdown / kMaxIter
+    int done;         // kRunning / kConverged / kBreakdown / kMaxIter / kFault
     int max_it;
-    int pad;
+    int fault;        // set by a kernel whose bounded wait ran out
     unsigned int ticket[4];   // last-block tickets, reset by the last block
 };
 
@@ -45,15 +45,13 @@ struct Scalars {
 // form with TPR threads per row: a warp holds 32 / TPR rows; at step s,
 // lane (rr + (32 / TPR) h) handles slot s * TPR + h of row rr of its slice,
 // and the slot's column index and its 9 values sit in 32-wide runs, so
-// every load instruction of a warp reads one contiguous 128-byte (FP32) or
-// 256-byte (FP64) segment.  Partial rows are combined by shuffles.
-// With ilvSteps > 0 the part is interleaved: every slice has ilvSteps steps
-// and step st / value e of slice sl sits at ((st * 9 + e) * nSlices + sl) * 32
-// (columns at (st * nSlices + sl) * 32), so at any step all warps read one
-// contiguous band of memory, as a plain copy does.
+// a slice's steps are one contiguous run of memory (columns at
+// slicePtr[sl] + 32 st + lane, value e at 9 slicePtr[sl] + (9 st + e) 32 +
+// lane), which the SpMV streams into shared memory with bulk copies.
+// Partial rows are combined by shuffles.  Every slice has at least one step.
 template <typename T>
 struct SellDev {
-    int nRows, nSlices, ilvSteps;
+    int nRows, nSlices;
     const int *row;            // [nRows] chunk row
     const int *len;            // [nRows] blocks in the row
     const long long *slicePtr; // [nSlices + 1] first slot (lane-slot) of each slice
@@ -72,6 +70,9 @@ constexpr int kXBucket = 8;     // X rows are grouped by len / kXBucket
 template <typename T>
 struct SpmvDev {
     SellDev<T> S, X;
+    int grid;                  // persistent blocks (kSpmvThreads each)
+    const int *warpSlice;      // [grid * kSpmvWarps + 1] slice range of each warp
+                               // (S slices, then X slices offset by S.nSlices)
 };
 
 // Node-level data: node lists per block size, packed Cholesky factors of
@@ -120,7 +121,8 @@ struct BoxDev {
 template <typename T>
 void launch_spmv(const SpmvDev<T> &A, const T *x, T *y, const T *b, int residual_mode,
                  double *partials, Scalars *sc, int fin, int slot, cudaStream_t st);
-int spmv_grid(int nSlicesS, int nSlicesX);
+template <typename T>
+int spmv_persistent_grid(int nSlicesTotal);   // < 0 on a CUDA error
 
 template <typename T>
 void launch_update(const NodeDev<T> &N, T *u, T *r, const T *p, const T *q, T *y, int mode,
@@ -183,8 +185,6 @@ void launch_dot(const T *a, const T *b, long long n, double *partials, Scalars *
                 int slot, cudaStream_t st);
 
 // mixed precision helpers
-void launch_scale_to_f32(const double *r64, float *r32, long long n, double s, cudaStream_t st);
-void launch_accumulate_f64(double *u64, const float *d32, long long n, double s, cudaStream_t st);
 
 // ---- block-scaled FP32 path (mixed precision) -------------------------------
 
@@ -232,6 +232,8 @@ void launch_build_E(int nSeg, const int *segBox, const int *segOwner, const int 
 void launch_symmetrize(double *E, int k, cudaStream_t st);
 void launch_sweep_inverse(double *A, int k, double *colbuf, int *bad, double thr,
                           cudaStream_t st);
+void launch_coarse32(const float *Einv, int k, const double *g, const double *zr, double *nu,
+                     float *nu32, int mode, double *partials, Scalars *sc, cudaStream_t st);
 void launch_cast_f32(const double *a, float *b, long long n, cudaStream_t st);
 void launch_scale_blocks(const KinDev &K, const int *blockRow, long long nnzb, const FacDev &F,
                          double *Kt, cudaStream_t st);

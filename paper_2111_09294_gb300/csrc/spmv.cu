@@ -6,113 +6,256 @@
 // so standard and enriched couplings of Eq. linear_system stream through the
 // same code.  Values and column indices are read once per product with
 // evict-first loads; the gathered x chunks stay in L1/L2.
+#include <algorithm>
+
 #include "reduce.cuh"
+#include "tma.cuh"
 
 namespace xdcg {
 
-template <typename T>
-__device__ __forceinline__ T ldcs(const T *p) { return __ldcs(p); }
+// Per-precision pipeline shape: C steps per stage, NS stages per warp, MINB
+// resident blocks per SM.  A step is one 32-lane column of the slice: 32
+// column indices and 9 planes of 32 values (1280 bytes in FP32, 2432 in
+// FP64).  GUARD skips the arithmetic of padding slots: worth a per-slice row
+// length load in FP64, whose FMAs run at 1/64 of the FP32 rate on this GPU
+// and bound the FP64 product as much as its bytes do.
+template <typename T> struct SpmvCfg;
+template <> struct SpmvCfg<float> {
+    static constexpr int C = 2, NS = 3, MINB = 3;
+    static constexpr bool GUARD = false;
+};
+template <> struct SpmvCfg<double> {
+    static constexpr int C = 1, NS = 3, MINB = 3;
+    static constexpr bool GUARD = true;
+};
 
-// One slice of TPR-threads-per-row sliced ELL; returns this lane's share of
-// the fused dot (x^T y, or y^T y in residual mode) in part.
-template <typename T, bool RES, int TPR>
-__device__ __forceinline__ void sell_slice(const SellDev<T> &P, int slice, int lane,
-                                           const T *__restrict__ x, T *__restrict__ y,
-                                           const T *__restrict__ b, T &part) {
-    constexpr int RPW = 32 / TPR;
-    const int rr = lane % RPW, h = lane / RPW;
-    const int rl = slice * RPW + rr;
-    const bool valid = rl < P.nRows;
-    const int len = valid ? P.len[rl] : 0;
-    long long base, cstep, vstep, ve;
-    int steps;
-    if (P.ilvSteps > 0) {             // interleaved: all slices step together
-        base = 32LL * slice;
-        steps = P.ilvSteps;
-        cstep = 32LL * P.nSlices;
-        ve = cstep;
-        vstep = 9 * cstep;
-    } else {                          // slice-blocked
-        base = P.slicePtr[slice];
-        steps = (int)((P.slicePtr[slice + 1] - base) >> 5);
-        cstep = 32;
-        ve = 32;
-        vstep = 288;
-    }
-    const int *cp = P.col + base + lane;
-    const T *vp = P.val + (P.ilvSteps > 0 ? base : 9 * base) + lane;
-    T a0 = T(0), a1 = T(0), a2 = T(0);
-#pragma unroll 4
-    for (int st = 0; st < steps; ++st) {
-        if (st * TPR + h < len) {
-            const int c = __ldcs(cp + cstep * st);
-            const T *v = vp + vstep * st;
-            const T x0 = __ldg(x + 3 * c), x1 = __ldg(x + 3 * c + 1), x2 = __ldg(x + 3 * c + 2);
-            a0 = fma(ldcs(v), x0, a0);
-            a0 = fma(ldcs(v + ve), x1, a0);
-            a0 = fma(ldcs(v + 2 * ve), x2, a0);
-            a1 = fma(ldcs(v + 3 * ve), x0, a1);
-            a1 = fma(ldcs(v + 4 * ve), x1, a1);
-            a1 = fma(ldcs(v + 5 * ve), x2, a1);
-            a2 = fma(ldcs(v + 6 * ve), x0, a2);
-            a2 = fma(ldcs(v + 7 * ve), x1, a2);
-            a2 = fma(ldcs(v + 8 * ve), x2, a2);
-        }
-    }
-#pragma unroll
-    for (int o = RPW; o < 32; o <<= 1) {
-        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-    }
-    if (valid && h == 0) {
-        const long long r3 = 3 * (long long)P.row[rl];
-        if (RES) {
-            a0 = b[r3] - a0;
-            a1 = b[r3 + 1] - a1;
-            a2 = b[r3 + 2] - a2;
-            part = a0 * a0 + a1 * a1 + a2 * a2;
-        } else {
-            part = x[r3] * a0 + x[r3 + 1] * a1 + x[r3 + 2] * a2;
-        }
-        y[r3] = a0;
-        y[r3 + 1] = a1;
-        y[r3 + 2] = a2;
-    }
+template <typename T>
+__host__ __device__ constexpr int stage_bytes() { return SpmvCfg<T>::C * (128 + 288 * (int)sizeof(T)); }
+
+template <typename T>
+__host__ __device__ constexpr int spmv_smem_bytes() {
+    return kSpmvWarps * SpmvCfg<T>::NS * (stage_bytes<T>() + 8 + 3 * 4);
 }
 
+// Persistent warps over the slices of both parts (S slices first, then X);
+// warp w owns the slices [warpSlice[w], warpSlice[w + 1]), ranges balanced
+// by steps at set-up.  Each warp streams its slices' column indices and
+// values through its own ring of NS shared-memory stages with bulk copies
+// (lane 0 issues, all lanes consume), so the HBM stream takes no per-lane
+// load instructions and no registers in flight.  The x chunks of the next
+// stage are gathered (from L1/L2) before the current stage is computed.
+// Padding slots hold zero values and a valid column, so every slot can be
+// computed (unless GUARD).  The fused dot (x^T y, or y^T y in residual mode) is summed per
+// warp over a fixed slice range, then by the deterministic grid reduction.
 template <typename T, bool RES>
-__global__ void __launch_bounds__(kSpmvThreads)
+__global__ void __launch_bounds__(kSpmvThreads, SpmvCfg<T>::MINB)
 k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__restrict__ b,
-       int nbS, double *partials, Scalars *sc, int fin, int slot) {
+       double *partials, Scalars *sc, int fin, int slot) {
     if (sc->done != kRunning) return;
+    constexpr int C = SpmvCfg<T>::C, NS = SpmvCfg<T>::NS, SB = stage_bytes<T>();
+    extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *ring = smem + (size_t)warp * NS * SB;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)kSpmvWarps * NS * SB) + warp * NS;
+    int *meta = reinterpret_cast<int *>(smem + (size_t)kSpmvWarps * NS * (SB + 8)) + warp * NS * 3;
+    const int nS = A.S.nSlices;
+    const int gw = blockIdx.x * kSpmvWarps + warp;
+    const int sEnd = A.warpSlice[gw + 1];
+    if (lane == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(bars + s, 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    const uint64_t stream = l2_stream_policy();
+    const unsigned long long deadline = global_ns() + kWaitNs;
+
+    // producer state, meaningful in lane 0
+    int issued = 0, more = 1, pSlice = A.warpSlice[gw] - 1, pStep = 0, pSteps = 0;
+    long long pBase = 0;
+    const int *pCol = nullptr;
+    const T *pVal = nullptr;
+    auto issue = [&]() {
+        if (pStep >= pSteps) {
+            if (++pSlice >= sEnd) {
+                more = 0;
+                return;
+            }
+            const bool isS = pSlice < nS;
+            const SellDev<T> &P = isS ? A.S : A.X;
+            const int sl = isS ? pSlice : pSlice - nS;
+            pBase = P.slicePtr[sl];
+            pSteps = (int)((P.slicePtr[sl + 1] - pBase) >> 5);
+            pStep = 0;
+            pCol = P.col;
+            pVal = P.val;
+        }
+        const int st = issued % NS;
+        const int n = min(C, pSteps - pStep);
+        meta[st * 3] = pSlice;
+        meta[st * 3 + 1] = pStep;
+        meta[st * 3 + 2] = n;
+        unsigned char *dst = ring + st * SB;
+        const uint32_t cb = (uint32_t)n * 128u, vb = (uint32_t)n * 288u * (uint32_t)sizeof(T);
+        const long long off = pBase + 32LL * pStep;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bars + st, cb + vb);
+        bulk_g2s(dst, pCol + off, cb, bars + st, stream);
+        bulk_g2s(dst + C * 128, pVal + 9 * off, vb, bars + st, stream);
+        pStep += n;
+        ++issued;
+    };
+    if (lane == 0)
+        while (more && issued < NS) issue();
+    issued = __shfl_sync(0xffffffffu, issued, 0);
+
     T part[1] = {T(0)};
-    if ((int)blockIdx.x < nbS) {
-        const int slice = blockIdx.x * kSpmvWarps + warp;
-        if (slice < A.S.nSlices) sell_slice<T, RES, kTprS>(A.S, slice, lane, x, y, b, part[0]);
+    int cur = -1, rpw = 16, rl = 0, h = 0, tpr = 2, len = 0;
+    bool valid = false, isS = true;
+    T a0 = T(0), a1 = T(0), a2 = T(0);
+    auto finish = [&]() {
+        for (int o = rpw; o < 32; o <<= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        }
+        if (valid && h == 0) {
+            const long long r3 = 3 * (long long)(isS ? A.S.row[rl] : A.X.row[rl]);
+            if (RES) {
+                a0 = b[r3] - a0;
+                a1 = b[r3 + 1] - a1;
+                a2 = b[r3 + 2] - a2;
+                part[0] += a0 * a0 + a1 * a1 + a2 * a2;
+            } else {
+                part[0] += x[r3] * a0 + x[r3 + 1] * a1 + x[r3 + 2] * a2;
+            }
+            y[r3] = a0;
+            y[r3 + 1] = a1;
+            y[r3 + 2] = a2;
+        }
+    };
+    // x chunks of a landed stage, gathered ahead of its computation
+    auto gather = [&](int st, int n, T (&xv)[C][3]) {
+        const int *cs = reinterpret_cast<const int *>(ring + st * SB);
+#pragma unroll
+        for (int t = 0; t < C; ++t) {
+            if (t < n) {
+                const int c = cs[t * 32 + lane];
+                xv[t][0] = __ldg(x + 3 * c);
+                xv[t][1] = __ldg(x + 3 * c + 1);
+                xv[t][2] = __ldg(x + 3 * c + 2);
+            }
+        }
+    };
+    T xa[C][3], xb[C][3];
+    int na = 0;
+    bool ok = true;
+    int k = 0;
+    if (issued > 0) {
+        ok = __all_sync(0xffffffffu, mbar_wait(bars, 0u, deadline));
+        if (ok) {
+            na = meta[2];
+            gather(0, na, xa);
+        }
+    }
+    for (; ok && k < issued; ++k) {
+        const int st = k % NS;
+        // land and gather the next stage first
+        int nb = 0;
+        if (k + 1 < issued) {
+            const int s1 = (k + 1) % NS;
+            ok = __all_sync(0xffffffffu, mbar_wait(bars + s1, (uint32_t)((k + 1) / NS) & 1u, deadline));
+            if (!ok) break;
+            nb = meta[s1 * 3 + 2];
+            gather(s1, nb, xb);
+        }
+        const int sl = meta[st * 3];
+        if (sl != cur) {
+            if (cur >= 0) finish();
+            cur = sl;
+            isS = sl < nS;
+            tpr = isS ? kTprS : kTprX;
+            rpw = 32 / tpr;
+            rl = (isS ? sl : sl - nS) * rpw + (lane % rpw);
+            h = lane / rpw;
+            valid = rl < (isS ? A.S.nRows : A.X.nRows);
+            if (SpmvCfg<T>::GUARD) len = valid ? (isS ? A.S.len[rl] : A.X.len[rl]) : 0;
+            a0 = a1 = a2 = T(0);
+        }
+        const int s0 = meta[st * 3 + 1];
+        const T *vs = reinterpret_cast<const T *>(ring + st * SB + C * 128);
+#pragma unroll
+        for (int t = 0; t < C; ++t) {
+            if (t < na && (!SpmvCfg<T>::GUARD || (s0 + t) * tpr + h < len)) {
+                const T *v = vs + t * 288 + lane;
+                a0 = fma(v[0], xa[t][0], a0);
+                a0 = fma(v[32], xa[t][1], a0);
+                a0 = fma(v[64], xa[t][2], a0);
+                a1 = fma(v[96], xa[t][0], a1);
+                a1 = fma(v[128], xa[t][1], a1);
+                a1 = fma(v[160], xa[t][2], a1);
+                a2 = fma(v[192], xa[t][0], a2);
+                a2 = fma(v[224], xa[t][1], a2);
+                a2 = fma(v[256], xa[t][2], a2);
+            }
+        }
+        __syncwarp();
+        if (lane == 0 && more) issue();
+        issued = __shfl_sync(0xffffffffu, issued, 0);
+#pragma unroll
+        for (int t = 0; t < C; ++t) {
+            xa[t][0] = xb[t][0];
+            xa[t][1] = xb[t][1];
+            xa[t][2] = xb[t][2];
+        }
+        na = nb;
+    }
+    if (ok) {
+        if (cur >= 0) finish();
     } else {
-        const int slice = (blockIdx.x - nbS) * kSpmvWarps + warp;
-        if (slice < A.X.nSlices) sell_slice<T, RES, kTprX>(A.X, slice, lane, x, y, b, part[0]);
+        // a copy did not land in time: flag it, give the copies still in
+        // flight a bounded chance to land, and leave the shared memory
+        if (lane == 0) atomicExch(&sc->fault, 1);
+        const unsigned long long drain = global_ns() + kDrainNs;
+        for (; k < issued; ++k) mbar_wait(bars + k % NS, (uint32_t)(k / NS) & 1u, drain);
+        __syncwarp();
     }
     double tot[1];
-    if (grid_sum<T, 1>(part, partials, &sc->ticket[0], tot) && threadIdx.x == 0)
-        finalize(sc, fin, slot, tot[0]);
+    if (grid_sum<T, 1>(part, partials, &sc->ticket[0], tot) && threadIdx.x == 0) {
+        if (sc->fault)
+            sc->done = kFault;
+        else
+            finalize(sc, fin, slot, tot[0]);
+    }
 }
 
-int spmv_grid(int nSlicesS, int nSlicesX) {
-    return (nSlicesS + kSpmvWarps - 1) / kSpmvWarps + (nSlicesX + kSpmvWarps - 1) / kSpmvWarps;
+template <typename T>
+int spmv_persistent_grid(int nSlicesTotal) {
+    int dev = 0, sms = 0, nb = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+    const int smem = spmv_smem_bytes<T>();
+    if (cudaFuncSetAttribute(k_spmv<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_spmv<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+            cudaSuccess)
+        return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv<T, false>, kSpmvThreads, smem) !=
+            cudaSuccess || nb < 1)
+        return -1;
+    const int need = (nSlicesTotal + kSpmvWarps - 1) / kSpmvWarps;
+    return std::max(1, std::min(nb * sms, need));
 }
+template int spmv_persistent_grid<float>(int);
+template int spmv_persistent_grid<double>(int);
 
 template <typename T>
 void launch_spmv(const SpmvDev<T> &A, const T *x, T *y, const T *b, int residual_mode,
                  double *partials, Scalars *sc, int fin, int slot, cudaStream_t st) {
-    const int nbS = (A.S.nSlices + kSpmvWarps - 1) / kSpmvWarps;
-    const int grid = spmv_grid(A.S.nSlices, A.X.nSlices);
+    const int smem = spmv_smem_bytes<T>();
     if (residual_mode)
-        k_spmv<T, true><<<grid, kSpmvThreads, 0, st>>>(A, x, y, b, nbS, partials, sc, fin, slot);
+        k_spmv<T, true><<<A.grid, kSpmvThreads, smem, st>>>(A, x, y, b, partials, sc, fin, slot);
     else
-        k_spmv<T, false><<<grid, kSpmvThreads, 0, st>>>(A, x, y, b, nbS, partials, sc, fin, slot);
+        k_spmv<T, false><<<A.grid, kSpmvThreads, smem, st>>>(A, x, y, b, partials, sc, fin, slot);
 }
 
 template void launch_spmv<double>(const SpmvDev<double> &, const double *, double *,
@@ -147,31 +290,9 @@ template void launch_dot<double>(const double *, const double *, long long, doub
 template void launch_dot<float>(const float *, const float *, long long, double *, Scalars *, int,
                                 int, cudaStream_t);
 
-__global__ void k_scale_to_f32(const double *__restrict__ r64, float *__restrict__ r32,
-                               long long n, double s) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        r32[i] = (float)(r64[i] * s);
-}
-
-__global__ void k_accumulate_f64(double *__restrict__ u64, const float *__restrict__ d32,
-                                 long long n, double s) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        u64[i] += s * (double)d32[i];
-}
-
 static int grid_for(long long n) {
     long long g = (n + kThreads - 1) / kThreads;
     return (int)(g < 4 * 152 ? (g > 0 ? g : 1) : 4 * 152);
-}
-
-void launch_scale_to_f32(const double *r64, float *r32, long long n, double s, cudaStream_t st) {
-    k_scale_to_f32<<<grid_for(n), kThreads, 0, st>>>(r64, r32, n, s);
-}
-
-void launch_accumulate_f64(double *u64, const float *d32, long long n, double s, cudaStream_t st) {
-    k_accumulate_f64<<<grid_for(n), kThreads, 0, st>>>(u64, d32, n, s);
 }
 
 __global__ void k_cast_f32(const double *__restrict__ a, float *__restrict__ b, long long n) {

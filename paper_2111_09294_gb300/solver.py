@@ -46,7 +46,7 @@ class Solver:
         opt.precision = L.XDCG_MIXED if precision == "mixed" else L.XDCG_FP64
         opt.inner_tol = inner_tol
         opt.max_outer = max_outer
-        opt.time_spmv = int(bool(time_spmv))
+        opt.time_spmv = 2 if time_spmv == "kernels" else int(bool(time_spmv))
         self.precision = precision
         if stream is None:
             stream = torch.cuda.current_stream()

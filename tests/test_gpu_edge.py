@@ -125,3 +125,20 @@ def test_rigid_only_deflation_matches_oracle():
     assert s.k == C.k
     _, info = s.solve(torch.tensor(P.f, device=dev), tol=1e-8)
     assert abs(info["iterations"] - ref.iterations) <= 2
+
+
+@pytest.mark.parametrize("prec,nphase", [("fp64", 5), ("mixed", 4)])
+def test_kernel_timing_mode_times_every_iteration(prec, nphase):
+    # time_spmv = 2: CUDA events around every kernel of the loop; results
+    # must be those of the untimed solve
+    dev = _cuda()
+    P = X.make("cube8_edge")
+    f = torch.tensor(P.f, device=dev)
+    u0, i0 = _solver(P, precision=prec).solve(f)
+    u1, i1 = _solver(P, precision=prec, time_spmv="kernels").solve(f)
+    assert torch.equal(u0, u1)
+    assert i1["iterations"] == i0["iterations"]
+    assert i1["n_phase_timed"] == i1["iterations"] == i1["n_spmv_timed"]
+    t = i1["t_phase_ms"]
+    assert all(x > 0 for x in t[:nphase]) and all(x == 0 for x in t[nphase:])
+    assert abs(t[0] - i1["t_spmv_ms"]) <= 1e-9
