@@ -131,8 +131,11 @@ typedef struct {
     int64_t spmv_bytes_fp64;     /* algorithmic bytes of one FP64 SpMV */
     int64_t spmv_bytes_fp32;     /* algorithmic bytes of one FP32 SpMV */
     int64_t iter_bytes_fp64;     /* algorithmic bytes of one FP64 iteration */
-    int64_t iter_bytes_fp32;     /* algorithmic bytes of one FP32 inner iteration */
+    int64_t iter_bytes_fp32;     /* algorithmic bytes of one FP32 inner iteration (MIXED) */
     double t_setup_ms;           /* wall time of xdcg_setup */
+    int64_t restrict_bytes_fp32; /* ... of its restriction + update kernel (MIXED) */
+    int64_t coarse_bytes_fp32;   /* ... of its coarse solve kernel (MIXED) */
+    int64_t prolong_bytes_fp32;  /* ... of its prolongation kernel (MIXED) */
 } xdcg_info_t;
 
 /* Fill *opt with the defaults listed above. */
@@ -141,8 +144,10 @@ xdcg_status xdcg_default_options(xdcg_options *opt);
 /* Validate K and the deflation description, copy them to the device, lay K
  * out for the SpMV (FP64 and, for MIXED, FP32 copies), factor the node
  * blocks (FP64 Cholesky), build Z, W = K Z and E = Z^T K Z, and invert E in
- * FP64.  stream: a cudaStream_t (NULL = legacy default stream).  blocks must
- * be NULL (one block per node).  On error *out is NULL and, if bad_index is
+ * FP64 (MIXED also keeps an FP32 copy of E^-1 and needs a coarse dimension
+ * k <= 49152, else XDCG_INVALID_ARG).  stream: a cudaStream_t (NULL = legacy
+ * default stream).  blocks must be NULL (one block per node).  On error *out
+ * is NULL and, if bad_index is
  * not NULL, *bad_index names the failing node (XDCG_NOT_SPD_BLOCK) or coarse
  * pivot (XDCG_COARSE_NOT_SPD), else -1. */
 xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflation *Z,
@@ -165,8 +170,10 @@ xdcg_status xdcg_get_info(const xdcg_ctx *ctx, xdcg_info_t *info);
  * double arrays.  XDCG_MIXED: y = K~ x with float arrays, where
  * K~ = L^-1 K L^-T is the block-scaled matrix of the FP32 inner solve (L the
  * FP64 Cholesky factors of the node blocks), stored and accumulated in FP32.
- * x, y: device, length n.  If xty is not NULL it receives x^T y (FP64
- * reduction) on the host. */
+ * x, y: device, length n, in the caller's dof numbering (the FP32 operator
+ * is stored box by box; x and y are renumbered through the context's FP32
+ * work vectors).  If xty is not NULL it receives x^T y (FP64 reduction) on
+ * the host. */
 xdcg_status xdcg_spmv(xdcg_ctx *ctx, int32_t precision, const void *x, void *y, double *xty);
 
 /* Same result as xdcg_spmv, for callers that must not allocate device
@@ -183,13 +190,17 @@ xdcg_status xdcg_spmv(xdcg_ctx *ctx, int32_t precision, const void *x, void *y, 
  * (cudaGetSymbolAddress) with that device current, so make that first call
  * before any stream capture.  All calls share the array, which keeps the
  * last call's contents; each call clears what must start at zero, but calls
- * that overlap on the GPU (other streams, other contexts) race on it.
+ * that overlap on the GPU (other streams, other contexts) race on it.  The
+ * XDCG_MIXED product also uses the context's own FP32 work vectors (it
+ * renumbers x and y, see xdcg_spmv), so it must not overlap another call on
+ * the same context.
  *
  * x, y: device arrays of n values (double for XDCG_FP64, float for
  * XDCG_MIXED, as in xdcg_spmv).  xty_dev: NULL or a device double that
  * receives x^T y.  Asynchronous on the context stream.  Returns
  * XDCG_TOO_LARGE when the context's SpMV grid exceeds
- * XDCG_NOALLOC_MAX_BLOCKS blocks (the 48^3 case needs 933). */
+ * XDCG_NOALLOC_MAX_BLOCKS blocks (the SpMV runs a persistent grid of at
+ * most a few blocks per SM, so this does not happen on current GPUs). */
 #define XDCG_NOALLOC_MAX_BLOCKS 4096
 xdcg_status xdcg_spmv_noalloc(xdcg_ctx *ctx, int32_t precision, const void *x, void *y,
                               double *xty_dev);

@@ -57,7 +57,8 @@ class Info(ctypes.Structure):
     _fields_ = [("n", c_int64), ("n_nodes", c_int32), ("k", c_int32), ("nnz", c_int64),
                 ("nnzb3", c_int64), ("spmv_bytes_fp64", c_int64), ("spmv_bytes_fp32", c_int64),
                 ("iter_bytes_fp64", c_int64), ("iter_bytes_fp32", c_int64),
-                ("t_setup_ms", c_double)]
+                ("t_setup_ms", c_double), ("restrict_bytes_fp32", c_int64),
+                ("coarse_bytes_fp32", c_int64), ("prolong_bytes_fp32", c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -29,7 +29,8 @@ struct Level32 {          // block-scaled system K~ = L^-1 K L^-T in FP32
     SpmvDev<float> A;
     RowBoxDev R;
     FacDev F;
-    const int *dofStart;
+    const int *dofStart64;    // [nNodes + 1] node dofs in the FP64 (caller's) numbering
+    const int *dofStart32;    // [nNodes + 1] node dofs in the box-major FP32 numbering
 };
 
 }  // namespace
@@ -49,6 +50,7 @@ struct xdcg_ctx {
     Level32 L32{};
     double *Einv = nullptr;
     float *Einv32 = nullptr;       // FP32 copy for the mixed path's FP32 iteration
+    long long extRows32 = 0, zEnt32 = 0, wEnt32 = 0;   // sizes of the FP32 box layouts
     double *E = nullptr;                      // E = Z^T K Z as assembled (diagnostics)
     std::vector<void *> temps;                // set-up temporaries
 
@@ -482,7 +484,7 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, xdc
     const double delta2 = c->opt.inner_tol * c->opt.inner_tol;
     float *rA = c->r32, *rB = c->y32;
     // f~ = s0 L^-1 f, and the FP32 run from Algorithm 2
-    launch_fwd_scale(c->nNodes, L.dofStart, L.F, f, s0, c->f32, st);
+    launch_fwd_scale(c->nNodes, L.dofStart64, L.dofStart64, L.dofStart32, L.F, f, s0, c->f32, st);
     CK(cudaMemsetAsync(c->u32, 0, c->n * sizeof(float), st));
     init_scalars(c, c->sc32, -1.0, nullptr, c->opt.max_iter);
     scaled_init(c, c->f32, c->u32, rA, c->p32, c->sc32);
@@ -498,7 +500,8 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, xdc
         if (done == kFault) return XDCG_TIMEOUT;
         last_rec = std::sqrt(c->h_sc->rr);
         // fold the FP32 correction into u (FP64): u += L^-T u~ / s0
-        launch_bwd_accum(c->nNodes, L.dofStart, L.F, c->u32, 1.0 / s0, u, st);
+        launch_bwd_accum(c->nNodes, L.dofStart64, L.dofStart32, L.dofStart64, L.F, c->u32, 1.0 / s0,
+                         u, st);
         CK(cudaMemsetAsync(c->u32, 0, c->n * sizeof(float), st));
         init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
         launch_spmv<double>(c->L64.A, u, c->r64, f, 1, c->partials, c->aux, kFinStore, 0, st);
@@ -517,7 +520,8 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, xdc
         // the interrupted iteration: z = r + Z~ nu, beta, p = z + beta p (beta =
         // 0 if the replacement moved the residual far: see k_coarse mode 3)
         float *rbuf = (its & 1) ? rB : rA;
-        launch_fwd_scale(c->nNodes, L.dofStart, L.F, c->r64, s0, rbuf, st);
+        launch_fwd_scale(c->nNodes, L.dofStart64, L.dofStart64, L.dofStart32, L.F, c->r64, s0, rbuf,
+                         st);
         k_set_trigger<<<1, 32, 0, st>>>(c->sc32, 0, 0.0, 0.0);
         launch_restrict_update(L.R, nullptr, rbuf, nullptr, nullptr, nullptr, 1, c->g, c->zr,
                                c->partials, c->sc32, st);
@@ -723,11 +727,15 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         std::vector<long long> slicePtr;
         int nSlices = 0;
     };
-    auto build_sell = [&](const std::vector<int> &rows, int tpr, SellHost &H) {
+    // chunkMap (may be null) renumbers the chunk rows and columns written
+    auto build_sell = [&](const std::vector<int> &rows, int tpr, SellHost &H,
+                          const std::vector<int> *chunkMap) {
         const int rpw = 32 / tpr;
         const int nr = (int)rows.size();
         H.nSlices = (nr + rpw - 1) / rpw;
         H.row = rows;
+        if (chunkMap)
+            for (int &r : H.row) r = (*chunkMap)[r];
         H.len.resize(nr);
         H.slicePtr.assign(H.nSlices + 1, 0);
         for (int sl = 0; sl < H.nSlices; ++sl) {
@@ -748,20 +756,21 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
             for (int q = 0; q < rpw && sl * rpw + q < nr; ++q) {
                 const int r = rows[sl * rpw + q];
                 H.len[sl * rpw + q] = rowLen[r];
+                const int rOut = chunkMap ? (*chunkMap)[r] : r;
                 for (long long st2 = 0; st2 < steps; ++st2)
-                    for (int h = 0; h < tpr; ++h) H.col[cidx(st2, q + rpw * h)] = r;
+                    for (int h = 0; h < tpr; ++h) H.col[cidx(st2, q + rpw * h)] = rOut;
                 for_blocks(r, [&](int t, int cc, const int *blk) {
                     const long long st2 = t / tpr;
                     const int lane = q + rpw * (t % tpr);
-                    H.col[cidx(st2, lane)] = cc;
+                    H.col[cidx(st2, lane)] = chunkMap ? (*chunkMap)[cc] : cc;
                     for (int e = 0; e < 9; ++e) H.src[vidx(st2, e, lane)] = blk[e];
                 });
             }
         }
     };
     SellHost HS, HX;
-    build_sell(sRows, kTprS, HS);
-    build_sell(xRows, kTprX, HX);
+    build_sell(sRows, kTprS, HS, nullptr);
+    build_sell(xRows, kTprX, HX, nullptr);
     const int nS = (int)sRows.size(), nX = (int)xRows.size();
     long long nnzb3 = 0;
     for (long long r = 0; r < nChunks; ++r) nnzb3 += rowLen[r];
@@ -872,17 +881,22 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     kin.val = d_val;
     if (!kin.rowPtr || !kin.col || !kin.valPtr || !kin.val) return XDCG_OOM;
     // SpMV layouts: values gathered on the device through the index maps
-    auto upload_sell = [&](const SellHost &H, SellDev<double> &D, int **d_src) -> bool {
+    // structure of a SELL part; the values are gathered through *d_src
+    auto upload_sell_structure = [&](const SellHost &H, auto &D, int **d_src) -> bool {
         D.nRows = (int)H.row.size();
         D.nSlices = H.nSlices;
         D.row = upload(c, H.row);
         D.len = upload(c, H.len);
         D.slicePtr = upload(c, H.slicePtr);
         D.col = upload(c, H.col);
-        double *v = dalloc<double>(c, H.src.size());
         *d_src = upload_tmp(c, H.src);
+        return D.row && D.len && D.slicePtr && D.col && *d_src;
+    };
+    auto upload_sell = [&](const SellHost &H, SellDev<double> &D, int **d_src) -> bool {
+        if (!upload_sell_structure(H, D, d_src)) return false;
+        double *v = dalloc<double>(c, H.src.size());
         D.val = v;
-        if (!D.row || !D.len || !D.slicePtr || !D.col || !v || !*d_src) return false;
+        if (!v) return false;
         launch_gather(*d_src, (long long)H.src.size(), d_val, v, nullptr, st);
         return true;
     };
@@ -890,12 +904,12 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     int *d_srcS = nullptr, *d_srcX = nullptr;
     if (!upload_sell(HS, A.S, &d_srcS) || !upload_sell(HX, A.X, &d_srcX)) return XDCG_OOM;
     // persistent SpMV grids and each warp's slice range, balanced by steps
-    auto partition = [&](int grid) -> const int * {
-        const int nW = grid * kSpmvWarps, nT = HS.nSlices + HX.nSlices;
+    auto partition = [&](const SellHost &PS, const SellHost &PX, int grid) -> const int * {
+        const int nW = grid * kSpmvWarps, nT = PS.nSlices + PX.nSlices;
         std::vector<long long> pre(nT + 1, 0);
         for (int i = 0; i < nT; ++i) {
-            const SellHost &H = i < HS.nSlices ? HS : HX;
-            const int sl = i < HS.nSlices ? i : i - HS.nSlices;
+            const SellHost &H = i < PS.nSlices ? PS : PX;
+            const int sl = i < PS.nSlices ? i : i - PS.nSlices;
             pre[i + 1] = pre[i] + (H.slicePtr[sl + 1] - H.slicePtr[sl]) / 32;
         }
         std::vector<int> ws(nW + 1);
@@ -911,7 +925,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     };
     A.grid = spmv_persistent_grid<double>(HS.nSlices + HX.nSlices);
     if (A.grid < 1) return XDCG_CUDA_ERROR;
-    A.warpSlice = partition(A.grid);
+    A.warpSlice = partition(HS, HX, A.grid);
     if (!A.warpSlice) return XDCG_OOM;
 
     // node data and block factors (FP64)
@@ -1024,6 +1038,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
 
     // block-scaled FP32 level of the mixed path: K~ = L^-1 K L^-T, Z~ = L^T Z, W~ = L^-1 W
     if (mixed) {
+        if (!coarse32_prepare(k)) return XDCG_INVALID_ARG;
         c->Einv32 = dalloc<float>(c, (size_t)k * k);
         if (!c->Einv32) return XDCG_OOM;
         launch_cast_f32(c->Einv, c->Einv32, (long long)k * k, st);
@@ -1051,39 +1066,60 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         long long *d_zOff = upload_tmp(c, zOff);
         float *d_Zt = dalloc_tmp<float>(c, zOff[N]);
         float *d_Wt = dalloc_tmp<float>(c, nW);
-        float *v32S = dalloc<float>(c, HS.src.size()), *v32X = dalloc<float>(c, HX.src.size());
-        if (!F.nodeList || !F.nodeIdx || !d_brow || !d_Kt || !d_zOff || !d_Zt || !d_Wt || !v32S ||
-            !v32X)
+        // The FP32 system is numbered box by box: node slots in box order,
+        // each node's dofs together, so box s owns the contiguous dof range
+        // [ownRowPtr[s], ownRowPtr[s + 1]) and own row r is dof r.
+        std::vector<int> dof32(N + 1, 0);
+        {
+            int off = 0;
+            for (int t = 0; t < N; ++t) {
+                dof32[ownNodes[t]] = off;
+                off += kindb[ownNodes[t]];
+            }
+            dof32[N] = off;
+        }
+        std::vector<int> chunkMap(nChunks);
+        for (long long r = 0; r < nChunks; ++r) chunkMap[r] = dof32[rowNode[r]] / 3 + rowPart[r];
+        std::vector<int> sRows32(sRows), xRows32(xRows);
+        std::stable_sort(sRows32.begin(), sRows32.end(),
+                         [&](int a, int b) { return chunkMap[a] < chunkMap[b]; });
+        std::stable_sort(xRows32.begin(), xRows32.end(), [&](int a, int b) {
+            const int ba = rowLen[a] / kXBucket, bb = rowLen[b] / kXBucket;
+            return ba != bb ? ba > bb : chunkMap[a] < chunkMap[b];
+        });
+        SellHost HS32, HX32;
+        build_sell(sRows32, kTprS, HS32, &chunkMap);
+        build_sell(xRows32, kTprX, HX32, &chunkMap);
+        auto &A2 = c->L32.A;
+        int *d_src32S = nullptr, *d_src32X = nullptr;
+        if (!upload_sell_structure(HS32, A2.S, &d_src32S) ||
+            !upload_sell_structure(HX32, A2.X, &d_src32X))
             return XDCG_OOM;
+        float *v32S = dalloc<float>(c, HS32.src.size()), *v32X = dalloc<float>(c, HX32.src.size());
+        const int *d_dof32 = upload(c, dof32);
+        if (!F.nodeList || !F.nodeIdx || !d_brow || !d_Kt || !d_zOff || !d_Zt || !d_Wt || !v32S ||
+            !v32X || !d_dof32)
+            return XDCG_OOM;
+        A2.S.val = v32S;
+        A2.X.val = v32X;
         c->L32.F = F;
         CK(cudaMemcpyAsync(d_Kt, d_val, val.size() * sizeof(double), cudaMemcpyDeviceToDevice, st));
         launch_scale_blocks(kin, d_brow, nnzb, F, d_Kt, st);
-        launch_gather(d_srcS, (long long)HS.src.size(), d_Kt, nullptr, v32S, st);
-        launch_gather(d_srcX, (long long)HX.src.size(), d_Kt, nullptr, v32X, st);
-        auto &A2 = c->L32.A;
-        auto copy_struct = [](const SellDev<double> &D, const float *v, SellDev<float> &E) {
-            E.nRows = D.nRows; E.nSlices = D.nSlices; E.row = D.row;
-            E.len = D.len;
-            E.slicePtr = D.slicePtr; E.col = D.col; E.val = v;
-        };
-        copy_struct(A.S, v32S, A2.S);
-        copy_struct(A.X, v32X, A2.X);
-        A2.grid = spmv_persistent_grid<float>(HS.nSlices + HX.nSlices);
+        launch_gather(d_src32S, (long long)HS32.src.size(), d_Kt, nullptr, v32S, st);
+        launch_gather(d_src32X, (long long)HX32.src.size(), d_Kt, nullptr, v32X, st);
+        A2.grid = spmv_persistent_grid<float>(HS32.nSlices + HX32.nSlices);
         if (A2.grid < 1) return XDCG_CUDA_ERROR;
-        A2.warpSlice = partition(A2.grid);
+        A2.warpSlice = partition(HS32, HX32, A2.grid);
         if (!A2.warpSlice) return XDCG_OOM;
         launch_build_Zt(N, d_own, d_dof, d_sub, d_x64, d_hs, d_menr, F, d_zOff, d_Zt, st);
         launch_scale_W(nExt, d_extBox, d_extNode, d_wOff, d_menr, d_dof, F, d_W, d_Wt, st);
         // row-parallel layouts: own rows (Z~) and coupled rows (W~) of each box,
         // column-major per box
-        std::vector<int> ownRowPtr(S + 1, 0), ownRowStart(N), ownRowDof;
+        std::vector<int> ownRowPtr(S + 1, 0), ownRowStart(N);
         std::vector<long long> zBase(S + 1, 0);
         for (int sb2 = 0; sb2 < S; ++sb2) {
-            for (int t = ownPtr[sb2]; t < ownPtr[sb2 + 1]; ++t) {
-                ownRowStart[t] = (int)ownRowDof.size();
-                for (int i = 0; i < ownB[t]; ++i) ownRowDof.push_back(ownDof[t] + i);
-            }
-            ownRowPtr[sb2 + 1] = (int)ownRowDof.size();
+            for (int t = ownPtr[sb2]; t < ownPtr[sb2 + 1]; ++t) ownRowStart[t] = dof32[ownNodes[t]];
+            ownRowPtr[sb2 + 1] = ownPtr[sb2 + 1] < N ? dof32[ownNodes[ownPtr[sb2 + 1]]] : dof32[N];
             zBase[sb2 + 1] = zBase[sb2] + (long long)(menr[sb2] ? 12 : 6) *
                                               (ownRowPtr[sb2 + 1] - ownRowPtr[sb2]);
         }
@@ -1092,18 +1128,20 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         for (int sb2 = 0; sb2 < S; ++sb2) {
             for (int e = extPtr[sb2]; e < extPtr[sb2 + 1]; ++e) {
                 extRowStart[e] = (int)extRowDof.size();
-                for (int i = 0; i < extB[e]; ++i) extRowDof.push_back(extDof[e] + i);
+                for (int i = 0; i < extB[e]; ++i) extRowDof.push_back(dof32[extNode[e]] + i);
             }
             extRowPtr[sb2 + 1] = (int)extRowDof.size();
             wBase[sb2 + 1] = wBase[sb2] + (long long)(menr[sb2] ? 12 : 6) *
                                               (extRowPtr[sb2 + 1] - extRowPtr[sb2]);
         }
+        c->extRows32 = extRowPtr[S];
+        c->zEnt32 = zBase[S];
+        c->wEnt32 = wBase[S];
         RowBoxDev &R = c->L32.R;
         R.nBox = S;
         R.col0 = d_col0;
         R.menr = d_menr;
         R.ownRowPtr = upload(c, ownRowPtr);
-        R.ownRowDof = upload(c, ownRowDof);
         R.zBase = upload(c, zBase);
         R.extRowPtr = upload(c, extRowPtr);
         R.extRowDof = upload(c, extRowDof);
@@ -1111,7 +1149,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         float *Zcm = dalloc<float>(c, zBase[S]), *Wcm = dalloc<float>(c, wBase[S]);
         int *d_ownSub = upload_tmp(c, ownSub), *d_ors = upload_tmp(c, ownRowStart),
             *d_ers = upload_tmp(c, extRowStart);
-        if (!R.ownRowPtr || !R.ownRowDof || !R.zBase || !R.extRowPtr || !R.extRowDof ||
+        if (!R.ownRowPtr || !R.zBase || !R.extRowPtr || !R.extRowDof ||
             !R.wBase || !Zcm || !Wcm || !d_ownSub || !d_ors || !d_ers)
             return XDCG_OOM;
         // balanced work units: per box, own rows then coupled rows, <= kUnitRows each
@@ -1164,7 +1202,8 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
                            d_Wt, Wcm, st);
         R.Z = Zcm;
         R.W = Wcm;
-        c->L32.dofStart = d_dof;
+        c->L32.dofStart64 = d_dof;
+        c->L32.dofStart32 = d_dof32;
     }
     int hbad[2];
     CK(cudaMemcpyAsync(hbad, d_bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1211,19 +1250,23 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
                + 2LL * n * s;
     };
     const long long fac = 6 * nStdN + 21 * nHN + 120 * nTN;
-    long long nZt = 0;
-    for (int I = 0; I < N; ++I) nZt += (long long)kindb[I] * (menr[sub[I]] ? 12 : 6);
     // FP64 path: SpMV; update (u, p, r, q read, u, r, y written, factors);
     // restriction (r, y, W, box lists); coarse GEMV (E^-1 and k-vectors);
     // prolongation (y, p read, p written, node geometry)
     const long long iter64 = spmv_bytes(8) + 7LL * n * 8 + fac * 8 + 4LL * N
                              + 2LL * n * 8 + nW * 8 + 12LL * nExt + 16LL * k
                              + 8LL * k * k + 24LL * k + 3LL * n * 8 + 33LL * N;
-    // FP32 scaled path: identity preconditioner (no y), explicit Z~ read by
-    // the restriction and the prolongation
-    const long long iter32 = spmv_bytes(4) + 6LL * n * 4
-                             + n * 4 + nZt * 4 + nW * 4 + 12LL * nExt + 16LL * k
-                             + 8LL * k * k + 24LL * k + 3LL * n * 4 + nZt * 4 + 20LL * N;
+    // FP32 scaled path (identity block preconditioner), per kernel:
+    // restriction + update: own rows read map, r, q, p, u and write r', u,
+    // plus Z~; coupled rows read map, r, q, plus W~; g and Z~^T r written;
+    // coarse: E^-1 in FP32 and the k-vectors; prolongation: own rows read
+    // map, r', p and write p, plus Z~ and nu
+    const long long restrict32 = mixed ? 28LL * n + 4LL * c->zEnt32 + 12LL * c->extRows32 +
+                                             4LL * c->wEnt32 + 16LL * k
+                                       : 0;
+    const long long coarse32 = mixed ? 4LL * k * k + 28LL * k : 0;
+    const long long prolong32 = mixed ? 16LL * n + 4LL * c->zEnt32 + 4LL * k : 0;
+    const long long iter32 = mixed ? spmv_bytes(4) + restrict32 + coarse32 + prolong32 : 0;
     c->info.n = n;
     c->info.n_nodes = N;
     c->info.k = k;
@@ -1233,6 +1276,9 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     c->info.spmv_bytes_fp32 = spmv_bytes(4);
     c->info.iter_bytes_fp64 = iter64;
     c->info.iter_bytes_fp32 = iter32;
+    c->info.restrict_bytes_fp32 = restrict32;
+    c->info.coarse_bytes_fp32 = coarse32;
+    c->info.prolong_bytes_fp32 = prolong32;
     return XDCG_OK;
 }
 
@@ -1310,19 +1356,29 @@ xdcg_status xdcg_get_info(const xdcg_ctx *c, xdcg_info_t *info) {
     return XDCG_OK;
 }
 
+// y = K~ x for caller-ordered x, y: the FP32 operator works in the box-major
+// numbering, so x is renumbered into p32 and the product back out of q32
+void spmv32_caller_order(xdcg_ctx *c, const float *x, float *y, double *partials, Scalars *sc) {
+    const int *nat = c->L32.dofStart64, *box = c->L32.dofStart32;
+    launch_renumber(c->nNodes, nat, nat, box, x, c->p32, c->st);
+    launch_spmv<float>(c->L32.A, c->p32, c->q32, nullptr, 0, partials, sc, kFinStore, 2, c->st);
+    launch_renumber(c->nNodes, nat, box, nat, c->q32, y, c->st);
+    c->launches += 3;
+}
+
 xdcg_status xdcg_spmv(xdcg_ctx *c, int32_t precision, const void *x, void *y, double *xty) {
     if (!c || !x || !y || x == y) return XDCG_INVALID_ARG;
     if (precision == XDCG_MIXED && !c->mixed) return XDCG_INVALID_ARG;
     init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
-    if (precision == XDCG_FP64)
+    if (precision == XDCG_FP64) {
         launch_spmv<double>(c->L64.A, (const double *)x, (double *)y, nullptr, 0, c->partials,
                             c->aux, kFinStore, 2, c->st);
-    else if (precision == XDCG_MIXED)
-        launch_spmv<float>(c->L32.A, (const float *)x, (float *)y, nullptr, 0, c->partials, c->aux,
-                           kFinStore, 2, c->st);
-    else
+        c->launches++;
+    } else if (precision == XDCG_MIXED) {
+        spmv32_caller_order(c, (const float *)x, (float *)y, c->partials, c->aux);
+    } else {
         return XDCG_INVALID_ARG;
-    c->launches++;
+    }
     CK(cudaGetLastError());
     double v[3];
     xdcg_status s = read_aux(c, v, 3);
@@ -1377,13 +1433,13 @@ xdcg_status xdcg_spmv_noalloc(xdcg_ctx *c, int32_t precision, const void *x, voi
     double *partials = base + kNoallocScalarsDoubles;
     // clear the scalar block (done flag, tickets) left by the previous call
     init_scalars(c, sc, -1.0, nullptr, INT_MAX);
-    if (precision == XDCG_FP64)
+    if (precision == XDCG_FP64) {
         launch_spmv<double>(c->L64.A, (const double *)x, (double *)y, nullptr, 0, partials, sc,
                             kFinStore, 2, c->st);
-    else
-        launch_spmv<float>(c->L32.A, (const float *)x, (float *)y, nullptr, 0, partials, sc,
-                           kFinStore, 2, c->st);
-    c->launches++;
+        c->launches++;
+    } else {
+        spmv32_caller_order(c, (const float *)x, (float *)y, partials, sc);
+    }
     if (xty_dev) {
         k_noalloc_result<<<1, 32, 0, c->st>>>(sc, 2, xty_dev);
         c->launches++;

@@ -148,6 +148,7 @@ template <typename T, typename A, bool EXPL>
 __global__ void __launch_bounds__(kBoxThreads, 4)
 k_restrict(BoxDev<T> B, const T *a, const T *b, int withW, double *g, double *zr,
            const Scalars *sc) {
+    pdl_wait();
     if (sc && sc->done != kRunning) return;
     const int s = blockIdx.x;
     if (B.menr[s])
@@ -158,7 +159,8 @@ k_restrict(BoxDev<T> B, const T *a, const T *b, int withW, double *g, double *zr
 
 void launch_restrict(const BoxDev<double> &B, const double *a, const double *b, int withW,
                      double *g, double *zr, const Scalars *sc, cudaStream_t st) {
-    k_restrict<double, double, false><<<B.nBox, kBoxThreads, 0, st>>>(B, a, b, withW, g, zr, sc);
+    launch_pdl(k_restrict<double, double, false>, B.nBox, kBoxThreads, 0, st, B, a, b, withW, g, zr,
+               sc);
 }
 
 
@@ -245,6 +247,7 @@ __device__ __forceinline__ void prolong_box(const BoxDev<T> &B, int s, const T *
 template <typename T, bool EXPL>
 __global__ void __launch_bounds__(kBoxThreads, 4)
 k_prolong(BoxDev<T> B, const T *nu, const T *y, T *p, int mode, Scalars *sc) {
+    pdl_wait();
     if (sc->done != kRunning) return;
     const int s = blockIdx.x;
     const T beta = (T)sc->beta;
@@ -256,7 +259,7 @@ k_prolong(BoxDev<T> B, const T *nu, const T *y, T *p, int mode, Scalars *sc) {
 
 void launch_prolong(const BoxDev<double> &B, const double *nu, const double *y, double *p,
                     int mode, Scalars *sc, cudaStream_t st) {
-    k_prolong<double, false><<<B.nBox, kBoxThreads, 0, st>>>(B, nu, y, p, mode, sc);
+    launch_pdl(k_prolong<double, false>, B.nBox, kBoxThreads, 0, st, B, nu, y, p, mode, sc);
 }
 
 
@@ -282,7 +285,7 @@ __device__ __forceinline__ float restrict_update_unit(const RowBoxDev &B, int un
         const float *Z = B.Z + B.zBase[s];
 #pragma unroll 4
         for (int r = rb + threadIdx.x; r < re; r += blockDim.x) {
-            const int d = ld_keep(B.ownRowDof + r, keep);
+            const int d = r;
             float rn = r_cur[d];
             if (mode == 0) {
                 rn = fmaf(-alpha, q[d], rn);
@@ -338,6 +341,7 @@ __global__ void __launch_bounds__(kRowThreads)
 k_restrict_update(RowBoxDev B, float *u, const float *r_cur, float *r_next, const float *p,
                   const float *q, int mode, double *g, double *zr, double *partials,
                   Scalars *sc) {
+    pdl_wait();
     if (sc->done != kRunning) return;
     const int unit = blockIdx.x;
     const float alpha = (mode == 0) ? (float)sc->alpha : 0.0f;
@@ -363,8 +367,8 @@ k_restrict_update(RowBoxDev B, float *u, const float *r_cur, float *r_next, cons
 void launch_restrict_update(const RowBoxDev &B, float *u, const float *r_cur, float *r_next,
                             const float *p, const float *q, int mode, double *g, double *zr,
                             double *partials, Scalars *sc, cudaStream_t st) {
-    k_restrict_update<<<B.nUnits, kRowThreads, 0, st>>>(B, u, r_cur, r_next, p, q, mode, g, zr,
-                                                         partials, sc);
+    launch_pdl(k_restrict_update, B.nUnits, kRowThreads, 0, st, B, u, r_cur, r_next, p, q, mode, g,
+               zr, partials, sc);
 }
 
 template <int M>
@@ -386,12 +390,13 @@ __device__ __forceinline__ void prolong_rows_unit(const RowBoxDev &B, int unit,
         float zv = 0.0f;
 #pragma unroll
         for (int c = 0; c < M; ++c) zv = fmaf(ld_keep(Z + (size_t)c * R + rl, keep), n[c], zv);
-        emit(p, y, ld_keep(B.ownRowDof + r, keep), zv, mode, beta);
+        emit(p, y, r, zv, mode, beta);
     }
 }
 
 __global__ void __launch_bounds__(kRowThreads)
 k_prolong_rows(RowBoxDev B, const float *nu32, const float *y, float *p, int mode, Scalars *sc) {
+    pdl_wait();
     if (sc->done != kRunning) return;
     const int unit = blockIdx.x;
     const float beta = (float)sc->beta;
@@ -403,7 +408,7 @@ k_prolong_rows(RowBoxDev B, const float *nu32, const float *y, float *p, int mod
 
 void launch_prolong_rows(const RowBoxDev &B, const float *nu32, const float *y, float *p,
                          int mode, Scalars *sc, cudaStream_t st) {
-    k_prolong_rows<<<B.nPUnits, kRowThreads, 0, st>>>(B, nu32, y, p, mode, sc);
+    launch_pdl(k_prolong_rows, B.nPUnits, kRowThreads, 0, st, B, nu32, y, p, mode, sc);
 }
 
 // set-up: row-major per-item blocks (b x M at srcOff) to the per-box

@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(kThreads)
 k_coarse(const double *__restrict__ Einv, int k, const double *__restrict__ g,
          const double *__restrict__ zr, double *nu, float *nu32, int mode, double *partials,
          Scalars *sc) {
+    pdl_wait();
     if (sc->done != kRunning) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kWarps + warp;
@@ -253,47 +254,42 @@ k_coarse(const double *__restrict__ Einv, int k, const double *__restrict__ g,
 // path.  A-DEF2 tolerates an inexact coarse solve (the coarse correction
 // acts as a preconditioner, not as a projection the recurrence relies on),
 // and on the test problems FP32 E^-1 changes no iteration count.  Each block
-// stages g in FP32 shared memory chunk by chunk; one warp per row, 16-byte
-// loads of E^-1 when rows are 16-byte aligned (k a multiple of 4).
-constexpr int kCoarseChunk = 2048;
-
+// stages all of g in FP32 shared memory once (k <= kMaxCoarse32); one warp
+// per row streams it with eight 16-byte loads in flight per lane (rows are
+// 16-byte aligned when k is a multiple of 4).
 template <int V>
 __global__ void __launch_bounds__(kThreads)
 k_coarse32(const float *__restrict__ Einv, int k, const double *__restrict__ g,
            const double *__restrict__ zr, double *nu, float *nu32, int mode, double *partials,
            Scalars *sc) {
+    pdl_wait();
     if (sc->done != kRunning) return;
-    __shared__ __align__(16) float gs[kCoarseChunk];
+    extern __shared__ float4 gs4[];
+    float *gs = reinterpret_cast<float *>(gs4);
+    for (int j = threadIdx.x; j < k; j += blockDim.x) gs[j] = (float)g[j];
+    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kWarps + warp;
-    const float *row = Einv + (size_t)(i < k ? i : 0) * k;
-    const uint64_t keep = l2_keep_policy();
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    for (int c0 = 0; c0 < k; c0 += kCoarseChunk) {
-        const int len = min(kCoarseChunk, k - c0);
-        __syncthreads();
-        for (int j = threadIdx.x; j < len; j += blockDim.x) gs[j] = (float)g[c0 + j];
-        __syncthreads();
-        if (i >= k) continue;
+    double part[1] = {0.0};
+    if (i < k) {
+        const float *row = Einv + (size_t)i * k;
+        const uint64_t keep = l2_keep_policy();
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
         if (V == 4) {
-            const float4 *r4 = reinterpret_cast<const float4 *>(row + c0);
-            const float4 *g4 = reinterpret_cast<const float4 *>(gs);
-            const int n4 = len >> 2;
+            const float4 *r4 = reinterpret_cast<const float4 *>(row);
+            const int n4 = k >> 2;
 #pragma unroll 8
             for (int j = lane; j < n4; j += 32) {
-                const float4 a = ld_keep(r4 + j, keep), x = g4[j];
+                const float4 a = ld_keep(r4 + j, keep), x = gs4[j];
                 s0 = fmaf(a.x, x.x, s0);
                 s1 = fmaf(a.y, x.y, s1);
                 s2 = fmaf(a.z, x.z, s2);
                 s3 = fmaf(a.w, x.w, s3);
             }
         } else {
-#pragma unroll 4
-            for (int j = lane; j < len; j += 32) s0 = fmaf(ld_keep(row + c0 + j, keep), gs[j], s0);
+#pragma unroll 8
+            for (int j = lane; j < k; j += 32) s0 = fmaf(ld_keep(row + j, keep), gs[j], s0);
         }
-    }
-    double part[1] = {0.0};
-    if (i < k) {
         float s = (s0 + s1) + (s2 + s3);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -309,19 +305,26 @@ k_coarse32(const float *__restrict__ Einv, int k, const double *__restrict__ g,
 void launch_coarse32(const float *Einv, int k, const double *g, const double *zr, double *nu,
                      float *nu32, int mode, double *partials, Scalars *sc, cudaStream_t st) {
     const int grid = (k + kWarps - 1) / kWarps;
-    if (k % 4 == 0)
-        k_coarse32<4><<<grid > 0 ? grid : 1, kThreads, 0, st>>>(Einv, k, g, zr, nu, nu32, mode,
-                                                                 partials, sc);
-    else
-        k_coarse32<1><<<grid > 0 ? grid : 1, kThreads, 0, st>>>(Einv, k, g, zr, nu, nu32, mode,
-                                                                 partials, sc);
+    const size_t smem = (size_t)((k + 3) / 4) * sizeof(float4);
+    launch_pdl(k % 4 == 0 ? k_coarse32<4> : k_coarse32<1>, grid > 0 ? grid : 1, kThreads, smem, st,
+               Einv, k, g, zr, nu, nu32, mode, partials, sc);
+}
+
+// opts the FP32 coarse kernel into the shared memory it needs for g
+bool coarse32_prepare(int k) {
+    const int smem = ((k + 3) / 4) * (int)sizeof(float4);
+    if (k > kMaxCoarse32) return false;
+    return cudaFuncSetAttribute(k_coarse32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(k_coarse32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+               cudaSuccess;
 }
 
 void launch_coarse(const double *Einv, int k, const double *g, const double *zr, double *nu,
                    float *nu32, int mode, double *partials, Scalars *sc, cudaStream_t st) {
     const int grid = (k + kWarps - 1) / kWarps;
-    k_coarse<<<grid > 0 ? grid : 1, kThreads, 0, st>>>(Einv, k, g, zr, nu, nu32, mode, partials,
-                                                       sc);
+    launch_pdl(k_coarse, grid > 0 ? grid : 1, kThreads, 0, st, Einv, k, g, zr, nu, nu32, mode,
+               partials, sc);
 }
 
 }  // namespace xdcg

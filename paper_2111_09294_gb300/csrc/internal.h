@@ -139,7 +139,7 @@ void launch_update(const NodeDev<T> &N, T *u, T *r, const T *p, const T *q, T *y
 struct RowBoxDev {
     int nBox;
     const int *col0, *menr;
-    const int *ownRowPtr, *ownRowDof;   // [nBox + 1], [own rows]
+    const int *ownRowPtr;               // [nBox + 1]: box s owns dofs [ownRowPtr[s], ownRowPtr[s + 1])
     const long long *zBase;             // [nBox]
     const float *Z;
     const int *extRowPtr, *extRowDof;   // [nBox + 1], [coupled rows]
@@ -201,10 +201,15 @@ void launch_gather(const int *src, long long n, const double *v, double *out64, 
 void launch_build_Zt(int nSlots, const int *slotNode, const int *dofStart, const int *sub,
                      const double *xrel, const signed char *hsign, const int *menr,
                      const FacDev &F, const long long *zOff, float *Zt, cudaStream_t st);
-void launch_fwd_scale(int nNodes, const int *dofStart, const FacDev &F, const double *r, double s,
-                      float *out, cudaStream_t st);
-void launch_bwd_accum(int nNodes, const int *dofStart, const FacDev &F, const float *ut,
-                      double scale, double *u, cudaStream_t st);
+// node-wise transforms between the caller's dof numbering (nat, which also
+// gives the node sizes) and the box-major FP32 numbering: in / ot are the
+// numberings of the input / output vector
+void launch_fwd_scale(int nNodes, const int *nat, const int *in, const int *ot, const FacDev &F,
+                      const double *r, double s, float *out, cudaStream_t st);
+void launch_bwd_accum(int nNodes, const int *nat, const int *in, const int *ot, const FacDev &F,
+                      const float *ut, double scale, double *u, cudaStream_t st);
+void launch_renumber(int nNodes, const int *nat, const int *in, const int *ot, const float *x,
+                     float *out, cudaStream_t st);
 void launch_update_id(float *u, float *r, const float *p, const float *q, long long n, int mode,
                       double *partials, Scalars *sc, cudaStream_t st);
 
@@ -234,6 +239,8 @@ void launch_sweep_inverse(double *A, int k, double *colbuf, int *bad, double thr
                           cudaStream_t st);
 void launch_coarse32(const float *Einv, int k, const double *g, const double *zr, double *nu,
                      float *nu32, int mode, double *partials, Scalars *sc, cudaStream_t st);
+constexpr int kMaxCoarse32 = 49152;   // FP32 coarse dimension limit (g staged in shared memory)
+bool coarse32_prepare(int k);
 void launch_cast_f32(const double *a, float *b, long long n, cudaStream_t st);
 void launch_scale_blocks(const KinDev &K, const int *blockRow, long long nnzb, const FacDev &F,
                          double *Kt, cudaStream_t st);

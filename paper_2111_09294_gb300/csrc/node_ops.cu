@@ -99,6 +99,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_update(NodeDev<T> N, T *u, T *r, const T *p, const T *q, T *y, int mode, int nb3, int nb6,
          double *partials, Scalars *sc) {
+    pdl_wait();
     if (sc->done != kRunning) return;
     const T alpha = (T)sc->alpha;
     double v[2] = {0.0, 0.0};
@@ -141,7 +142,7 @@ void launch_update(const NodeDev<T> &N, T *u, T *r, const T *p, const T *q, T *y
               nb15 = cdiv(N.nT, kWarps);
     int grid = nb3 + nb6 + nb15;
     if (grid == 0) grid = 1;
-    k_update<T><<<grid, kThreads, 0, st>>>(N, u, r, p, q, y, mode, nb3, nb6, partials, sc);
+    launch_pdl(k_update<T>, grid, kThreads, 0, st, N, u, r, p, q, y, mode, nb3, nb6, partials, sc);
 }
 template void launch_update<double>(const NodeDev<double> &, double *, double *, const double *,
                                     const double *, double *, int, double *, Scalars *,

@@ -9,6 +9,7 @@
 #pragma once
 
 #include "internal.h"
+#include "pdl.cuh"
 
 namespace xdcg {
 

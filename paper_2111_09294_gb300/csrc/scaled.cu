@@ -180,37 +180,56 @@ void launch_scale_W(int nExt, const int *extBox, const int *extNode, const long 
 // ---- outer-loop transforms (FP64) -----------------------------------------
 
 // out = (float)(s L^-1 r) per node
-__global__ void k_fwd_scale(int nNodes, const int *dofStart, FacDev F, const double *r, double s,
-                            float *out) {
+// Node I has nat[I + 1] - nat[I] dofs (nat: the caller's numbering, where
+// each node's dofs are consecutive and nodes follow one another); `in` and
+// `ot` give where its dofs start in the input and the output vector.
+
+// out = s L^-1 r per node
+__global__ void k_fwd_scale(int nNodes, const int *nat, const int *in, const int *ot, FacDev F,
+                            const double *r, double s, float *out) {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nNodes) return;
-    const int d0 = dofStart[I], b = dofStart[I + 1] - d0;
+    const int b = nat[I + 1] - nat[I], d0 = in[I], o0 = ot[I];
     double x[15];
     for (int i = 0; i < b; ++i) x[i] = r[d0 + i];
     fwd_solve(F, F.nodeList[I], F.nodeIdx[I], b, x, 1);
-    for (int i = 0; i < b; ++i) out[d0 + i] = (float)(s * x[i]);
+    for (int i = 0; i < b; ++i) out[o0 + i] = (float)(s * x[i]);
 }
 
-void launch_fwd_scale(int nNodes, const int *dofStart, const FacDev &F, const double *r, double s,
-                      float *out, cudaStream_t st) {
-    k_fwd_scale<<<(nNodes + 127) / 128, 128, 0, st>>>(nNodes, dofStart, F, r, s, out);
+void launch_fwd_scale(int nNodes, const int *nat, const int *in, const int *ot, const FacDev &F,
+                      const double *r, double s, float *out, cudaStream_t st) {
+    k_fwd_scale<<<(nNodes + 127) / 128, 128, 0, st>>>(nNodes, nat, in, ot, F, r, s, out);
 }
 
 // u += scale L^-T ut per node
-__global__ void k_bwd_accum(int nNodes, const int *dofStart, FacDev F, const float *ut,
-                            double scale, double *u) {
+__global__ void k_bwd_accum(int nNodes, const int *nat, const int *in, const int *ot, FacDev F,
+                            const float *ut, double scale, double *u) {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nNodes) return;
-    const int d0 = dofStart[I], b = dofStart[I + 1] - d0;
+    const int b = nat[I + 1] - nat[I], d0 = in[I], o0 = ot[I];
     double x[15];
     for (int i = 0; i < b; ++i) x[i] = (double)ut[d0 + i];
     bwd_solve(F, F.nodeList[I], F.nodeIdx[I], b, x, 1);
-    for (int i = 0; i < b; ++i) u[d0 + i] += scale * x[i];
+    for (int i = 0; i < b; ++i) u[o0 + i] += scale * x[i];
 }
 
-void launch_bwd_accum(int nNodes, const int *dofStart, const FacDev &F, const float *ut,
-                      double scale, double *u, cudaStream_t st) {
-    k_bwd_accum<<<(nNodes + 127) / 128, 128, 0, st>>>(nNodes, dofStart, F, ut, scale, u);
+void launch_bwd_accum(int nNodes, const int *nat, const int *in, const int *ot, const FacDev &F,
+                      const float *ut, double scale, double *u, cudaStream_t st) {
+    k_bwd_accum<<<(nNodes + 127) / 128, 128, 0, st>>>(nNodes, nat, in, ot, F, ut, scale, u);
+}
+
+// out = x renumbered node by node (FP32 vectors)
+__global__ void k_renumber(int nNodes, const int *nat, const int *in, const int *ot,
+                           const float *x, float *out) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nNodes) return;
+    const int b = nat[I + 1] - nat[I], d0 = in[I], o0 = ot[I];
+    for (int i = 0; i < b; ++i) out[o0 + i] = x[d0 + i];
+}
+
+void launch_renumber(int nNodes, const int *nat, const int *in, const int *ot, const float *x,
+                     float *out, cudaStream_t st) {
+    k_renumber<<<(nNodes + 127) / 128, 128, 0, st>>>(nNodes, nat, in, ot, x, out);
 }
 
 // ---- inner FP32 iteration kernels ------------------------------------------

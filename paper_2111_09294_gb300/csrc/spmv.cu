@@ -43,15 +43,16 @@ __host__ __device__ constexpr int spmv_smem_bytes() {
 // values through its own ring of NS shared-memory stages with bulk copies
 // (lane 0 issues, all lanes consume), so the HBM stream takes no per-lane
 // load instructions and no registers in flight.  The x chunks of the next
-// stage are gathered (from L1/L2) before the current stage is computed.
-// Padding slots hold zero values and a valid column, so every slot can be
-// computed (unless GUARD).  The fused dot (x^T y, or y^T y in residual mode) is summed per
-// warp over a fixed slice range, then by the deterministic grid reduction.
+// stage are gathered (from L1/L2) before the current stage is computed, and
+// the first stages are in flight before the wait for the kernel that wrote
+// x.  Padding slots hold zero values and a valid column, so every slot can
+// be computed (unless GUARD).  The fused dot (x^T y, or y^T y in residual
+// mode) is summed per warp over a fixed slice range, then by the
+// deterministic grid reduction.
 template <typename T, bool RES>
 __global__ void __launch_bounds__(kSpmvThreads, SpmvCfg<T>::MINB)
 k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__restrict__ b,
        double *partials, Scalars *sc, int fin, int slot) {
-    if (sc->done != kRunning) return;
     constexpr int C = SpmvCfg<T>::C, NS = SpmvCfg<T>::NS, SB = stage_bytes<T>();
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -104,9 +105,19 @@ k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__rest
         pStep += n;
         ++issued;
     };
+    // the first stages stream set-up data only: issue them before waiting
+    // for the kernel that produced x
     if (lane == 0)
         while (more && issued < NS) issue();
     issued = __shfl_sync(0xffffffffu, issued, 0);
+    pdl_wait();
+    if (sc->done != kRunning) {
+        // nothing to do: let the copies in flight land before leaving
+        const unsigned long long drain = global_ns() + kDrainNs;
+        for (int k = 0; k < issued; ++k) mbar_wait(bars + k % NS, (uint32_t)(k / NS) & 1u, drain);
+        __syncwarp();
+        return;
+    }
 
     T part[1] = {T(0)};
     int cur = -1, rpw = 16, rl = 0, h = 0, tpr = 2, len = 0;
@@ -252,10 +263,8 @@ template <typename T>
 void launch_spmv(const SpmvDev<T> &A, const T *x, T *y, const T *b, int residual_mode,
                  double *partials, Scalars *sc, int fin, int slot, cudaStream_t st) {
     const int smem = spmv_smem_bytes<T>();
-    if (residual_mode)
-        k_spmv<T, true><<<A.grid, kSpmvThreads, smem, st>>>(A, x, y, b, partials, sc, fin, slot);
-    else
-        k_spmv<T, false><<<A.grid, kSpmvThreads, smem, st>>>(A, x, y, b, partials, sc, fin, slot);
+    launch_pdl(residual_mode ? k_spmv<T, true> : k_spmv<T, false>, A.grid, kSpmvThreads, smem, st,
+               A, x, y, b, partials, sc, fin, slot);
 }
 
 template void launch_spmv<double>(const SpmvDev<double> &, const double *, double *,
