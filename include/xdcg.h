@@ -144,10 +144,9 @@ xdcg_status xdcg_default_options(xdcg_options *opt);
 /* Validate K and the deflation description, copy them to the device, lay K
  * out for the SpMV (FP64 and, for MIXED, FP32 copies), factor the node
  * blocks (FP64 Cholesky), build Z, W = K Z and E = Z^T K Z, and invert E in
- * FP64 (MIXED also keeps an FP32 copy of E^-1 and needs a coarse dimension
- * k <= 49152, else XDCG_INVALID_ARG).  stream: a cudaStream_t (NULL = legacy
- * default stream).  blocks must be NULL (one block per node).  On error *out
- * is NULL and, if bad_index is
+ * FP64 (MIXED also keeps an FP32 copy of E^-1).  stream: a cudaStream_t
+ * (NULL = legacy default stream).  blocks must be NULL (one block per node).
+ * On error *out is NULL and, if bad_index is
  * not NULL, *bad_index names the failing node (XDCG_NOT_SPD_BLOCK) or coarse
  * pivot (XDCG_COARSE_NOT_SPD), else -1. */
 xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflation *Z,

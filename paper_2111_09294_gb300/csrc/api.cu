@@ -50,6 +50,7 @@ struct xdcg_ctx {
     Level32 L32{};
     double *Einv = nullptr;
     float *Einv32 = nullptr;       // FP32 copy for the mixed path's FP32 iteration
+    float *g32 = nullptr;          // FP32 copy of the coarse right-hand side g
     long long extRows32 = 0, zEnt32 = 0, wEnt32 = 0;   // sizes of the FP32 box layouts
     double *E = nullptr;                      // E = Z^T K Z as assembled (diagnostics)
     std::vector<void *> temps;                // set-up temporaries
@@ -344,12 +345,12 @@ void scaled_init(xdcg_ctx *c, const float *f, float *u, float *rA, float *p, Sca
     Level32 &L = c->L32;
     launch_restrict_update(L.R, nullptr, f, nullptr, nullptr, nullptr, 2, c->g, nullptr,
                            c->partials, sc, st);
-    launch_coarse32(c->Einv32, c->k, c->g, nullptr, c->nu, c->nu32, 0, c->partials, sc, st);
+    launch_coarse32(c->Einv32, c->k, c->g32, nullptr, c->nu, c->nu32, 0, c->partials, sc, st);
     launch_prolong_rows(L.R, c->nu32, nullptr, u, 1, sc, st);
     launch_spmv<float>(L.A, u, rA, f, 1, c->partials, sc, kFinRR, 0, st);
     launch_restrict_update(L.R, nullptr, rA, nullptr, nullptr, nullptr, 1, c->g, c->zr,
                            c->partials, sc, st);
-    launch_coarse32(c->Einv32, c->k, c->g, c->zr, c->nu, c->nu32, 1, c->partials, sc, st);
+    launch_coarse32(c->Einv32, c->k, c->g32, c->zr, c->nu, c->nu32, 1, c->partials, sc, st);
     launch_prolong_rows(L.R, c->nu32, rA, p, 2, sc, st);
     c->launches += 7;
 }
@@ -387,7 +388,7 @@ xdcg_status scaled_iterate(xdcg_ctx *c, float *u, float *rA, float *rB, float *p
             MARK(launched, 1);
             launch_restrict_update(L.R, u, rc, rn, p, q, 0, c->g, c->zr, c->partials, sc, st);
             MARK(launched, 2);
-            launch_coarse32(c->Einv32, c->k, c->g, c->zr, c->nu, c->nu32, 2, c->partials, sc, st);
+            launch_coarse32(c->Einv32, c->k, c->g32, c->zr, c->nu, c->nu32, 2, c->partials, sc, st);
             MARK(launched, 3);
             launch_prolong_rows(L.R, c->nu32, rn, p, 0, sc, st);
             MARK(launched, 4);
@@ -525,7 +526,7 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, xdc
         k_set_trigger<<<1, 32, 0, st>>>(c->sc32, 0, 0.0, 0.0);
         launch_restrict_update(L.R, nullptr, rbuf, nullptr, nullptr, nullptr, 1, c->g, c->zr,
                                c->partials, c->sc32, st);
-        launch_coarse32(c->Einv32, c->k, c->g, c->zr, c->nu, c->nu32, done == kBreakdown ? 1 : 3,
+        launch_coarse32(c->Einv32, c->k, c->g32, c->zr, c->nu, c->nu32, done == kBreakdown ? 1 : 3,
                       c->partials, c->sc32, st);
         launch_prolong_rows(L.R, c->nu32, rbuf, c->p32, done == kBreakdown ? 2 : 0, c->sc32, st);
         c->launches += 5;
@@ -1038,7 +1039,6 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
 
     // block-scaled FP32 level of the mixed path: K~ = L^-1 K L^-T, Z~ = L^T Z, W~ = L^-1 W
     if (mixed) {
-        if (!coarse32_prepare(k)) return XDCG_INVALID_ARG;
         c->Einv32 = dalloc<float>(c, (size_t)k * k);
         if (!c->Einv32) return XDCG_OOM;
         launch_cast_f32(c->Einv, c->Einv32, (long long)k * k, st);
@@ -1138,6 +1138,9 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         c->zEnt32 = zBase[S];
         c->wEnt32 = wBase[S];
         RowBoxDev &R = c->L32.R;
+        c->g32 = dalloc<float>(c, std::max(k, 1));
+        if (!c->g32) return XDCG_OOM;
+        R.g32 = c->g32;
         R.nBox = S;
         R.col0 = d_col0;
         R.menr = d_menr;

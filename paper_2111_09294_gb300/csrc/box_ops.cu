@@ -330,6 +330,7 @@ __device__ __forceinline__ float restrict_update_unit(const RowBoxDev &B, int un
             }
             const int c0 = B.col0[s];
             g[c0 + c] = zs - ws;
+            B.g32[c0 + c] = (float)(zs - ws);
             if (zr) zr[c0 + c] = zs;
         }
         if (threadIdx.x == 0) B.boxTicket[s] = 0u;

@@ -253,71 +253,66 @@ k_coarse(const double *__restrict__ Einv, int k, const double *__restrict__ g,
 // nu = E^-1 g with E^-1 held in FP32, for the FP32 iteration of the mixed
 // path.  A-DEF2 tolerates an inexact coarse solve (the coarse correction
 // acts as a preconditioner, not as a projection the recurrence relies on),
-// and on the test problems FP32 E^-1 changes no iteration count.  Each block
-// stages all of g in FP32 shared memory once (k <= kMaxCoarse32); one warp
-// per row streams it with eight 16-byte loads in flight per lane (rows are
-// 16-byte aligned when k is a multiple of 4).
+// and on the test problems FP32 E^-1 changes no iteration count.  Two warps
+// per row, each streaming half of it with up to sixteen 16-byte loads in
+// flight per lane (rows are 16-byte aligned when k is a multiple of 4); g
+// comes as the FP32 copy the restriction writes, read through L1.  The two
+// halves are added in a fixed order.
 template <int V>
 __global__ void __launch_bounds__(kThreads)
-k_coarse32(const float *__restrict__ Einv, int k, const double *__restrict__ g,
+k_coarse32(const float *__restrict__ Einv, int k, const float *__restrict__ g32,
            const double *__restrict__ zr, double *nu, float *nu32, int mode, double *partials,
            Scalars *sc) {
     pdl_wait();
     if (sc->done != kRunning) return;
-    extern __shared__ float4 gs4[];
-    float *gs = reinterpret_cast<float *>(gs4);
-    for (int j = threadIdx.x; j < k; j += blockDim.x) gs[j] = (float)g[j];
-    __syncthreads();
+    __shared__ float upper[kWarps / 2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * kWarps + warp;
-    double part[1] = {0.0};
+    const int i = blockIdx.x * (kWarps / 2) + (warp >> 1), h = warp & 1;
+    float s = 0.f;
     if (i < k) {
-        const float *row = Einv + (size_t)i * k;
         const uint64_t keep = l2_keep_policy();
+        const float *row = Einv + (size_t)i * k;
         float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
         if (V == 4) {
+            const int n4 = k >> 2, mid = (n4 + 1) >> 1;
+            const int j1 = h ? n4 : mid;
             const float4 *r4 = reinterpret_cast<const float4 *>(row);
-            const int n4 = k >> 2;
-#pragma unroll 8
-            for (int j = lane; j < n4; j += 32) {
-                const float4 a = ld_keep(r4 + j, keep), x = gs4[j];
+            const float4 *g4 = reinterpret_cast<const float4 *>(g32);
+#pragma unroll 16
+            for (int j = (h ? mid : 0) + lane; j < j1; j += 32) {
+                const float4 a = ld_keep(r4 + j, keep), x = __ldg(g4 + j);
                 s0 = fmaf(a.x, x.x, s0);
                 s1 = fmaf(a.y, x.y, s1);
                 s2 = fmaf(a.z, x.z, s2);
                 s3 = fmaf(a.w, x.w, s3);
             }
         } else {
-#pragma unroll 8
-            for (int j = lane; j < k; j += 32) s0 = fmaf(ld_keep(row + j, keep), gs[j], s0);
+            const int mid = (k + 1) >> 1, j1 = h ? k : mid;
+#pragma unroll 16
+            for (int j = (h ? mid : 0) + lane; j < j1; j += 32)
+                s0 = fmaf(ld_keep(row + j, keep), __ldg(g32 + j), s0);
         }
-        float s = (s0 + s1) + (s2 + s3);
+        s = (s0 + s1) + (s2 + s3);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) {
-            nu[i] = (double)s;
-            nu32[i] = s;
-            if (mode != 0) part[0] = (double)s * zr[i];
-        }
+    }
+    if (lane == 0 && h == 1) upper[warp >> 1] = s;
+    __syncthreads();
+    double part[1] = {0.0};
+    if (i < k && lane == 0 && h == 0) {
+        const float v = s + upper[warp >> 1];
+        nu[i] = (double)v;
+        nu32[i] = v;
+        if (mode != 0) part[0] = (double)v * zr[i];
     }
     coarse_scalars(part, mode, partials, sc);
 }
 
-void launch_coarse32(const float *Einv, int k, const double *g, const double *zr, double *nu,
+void launch_coarse32(const float *Einv, int k, const float *g32, const double *zr, double *nu,
                      float *nu32, int mode, double *partials, Scalars *sc, cudaStream_t st) {
-    const int grid = (k + kWarps - 1) / kWarps;
-    const size_t smem = (size_t)((k + 3) / 4) * sizeof(float4);
-    launch_pdl(k % 4 == 0 ? k_coarse32<4> : k_coarse32<1>, grid > 0 ? grid : 1, kThreads, smem, st,
-               Einv, k, g, zr, nu, nu32, mode, partials, sc);
-}
-
-// opts the FP32 coarse kernel into the shared memory it needs for g
-bool coarse32_prepare(int k) {
-    const int smem = ((k + 3) / 4) * (int)sizeof(float4);
-    if (k > kMaxCoarse32) return false;
-    return cudaFuncSetAttribute(k_coarse32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
-               cudaSuccess &&
-           cudaFuncSetAttribute(k_coarse32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
-               cudaSuccess;
+    const int grid = (k + kWarps / 2 - 1) / (kWarps / 2);
+    launch_pdl(k % 4 == 0 ? k_coarse32<4> : k_coarse32<1>, grid > 0 ? grid : 1, kThreads, 0, st,
+               Einv, k, g32, zr, nu, nu32, mode, partials, sc);
 }
 
 void launch_coarse(const double *Einv, int k, const double *g, const double *zr, double *nu,

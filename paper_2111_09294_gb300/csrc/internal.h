@@ -143,6 +143,7 @@ struct RowBoxDev {
     const long long *zBase;             // [nBox]
     const float *Z;
     const int *extRowPtr, *extRowDof;   // [nBox + 1], [coupled rows]
+    float *g32;                         // [k] FP32 copy of g for the FP32 coarse solve
     const long long *wBase;             // [nBox]
     const float *W;
     int nUnits, nOwnUnits;
@@ -237,10 +238,8 @@ void launch_build_E(int nSeg, const int *segBox, const int *segOwner, const int 
 void launch_symmetrize(double *E, int k, cudaStream_t st);
 void launch_sweep_inverse(double *A, int k, double *colbuf, int *bad, double thr,
                           cudaStream_t st);
-void launch_coarse32(const float *Einv, int k, const double *g, const double *zr, double *nu,
+void launch_coarse32(const float *Einv, int k, const float *g32, const double *zr, double *nu,
                      float *nu32, int mode, double *partials, Scalars *sc, cudaStream_t st);
-constexpr int kMaxCoarse32 = 49152;   // FP32 coarse dimension limit (g staged in shared memory)
-bool coarse32_prepare(int k);
 void launch_cast_f32(const double *a, float *b, long long n, cudaStream_t st);
 void launch_scale_blocks(const KinDev &K, const int *blockRow, long long nnzb, const FacDev &F,
                          double *Kt, cudaStream_t st);
