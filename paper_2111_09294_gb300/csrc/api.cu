@@ -1155,32 +1155,32 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         if (!R.ownRowPtr || !R.zBase || !R.extRowPtr || !R.extRowDof ||
             !R.wBase || !Zcm || !Wcm || !d_ownSub || !d_ors || !d_ers)
             return XDCG_OOM;
-        // balanced work units: per box, own rows then coupled rows, <= kUnitRows each
-        std::vector<int> unitBox, unitKind, unitBegin, unitEnd, boxUnit(S + 1, 0), ownUnit;
+        // balanced restriction units: each box's own rows followed by its coupled
+        // rows, cut into ceil(total / kUnitRows) nearly equal pieces
+        std::vector<int> unitBox, uOb, uOe, uEb, uEe, boxUnit(S + 1, 0);
         for (int sb2 = 0; sb2 < S; ++sb2) {
             boxUnit[sb2] = (int)unitBox.size();
-            for (int kind = 0; kind < 2; ++kind) {
-                const int r0 = kind ? extRowPtr[sb2] : ownRowPtr[sb2];
-                const int r1 = kind ? extRowPtr[sb2 + 1] : ownRowPtr[sb2 + 1];
-                for (int rb = r0; rb < r1 || (rb == r0 && kind == 0); rb += kUnitRows) {
-                    if (kind == 0) ownUnit.push_back((int)unitBox.size());
-                    unitBox.push_back(sb2);
-                    unitKind.push_back(kind);
-                    unitBegin.push_back(rb);
-                    unitEnd.push_back(std::min(r1, rb + kUnitRows));
-                    if (r1 == r0) break;
-                }
+            const long long nOwn = ownRowPtr[sb2 + 1] - ownRowPtr[sb2];
+            const long long nCpl = extRowPtr[sb2 + 1] - extRowPtr[sb2];
+            const long long T = nOwn + nCpl;
+            const long long nu = std::max<long long>(1, (T + kUnitRows - 1) / kUnitRows);
+            for (long long j = 0; j < nu; ++j) {
+                const long long a0 = T * j / nu, a1 = T * (j + 1) / nu;   // [a0, a1) of own|coupled
+                unitBox.push_back(sb2);
+                uOb.push_back(ownRowPtr[sb2] + (int)std::min(a0, nOwn));
+                uOe.push_back(ownRowPtr[sb2] + (int)std::min(a1, nOwn));
+                uEb.push_back(extRowPtr[sb2] + (int)(std::max(a0, nOwn) - nOwn));
+                uEe.push_back(extRowPtr[sb2] + (int)(std::max(a1, nOwn) - nOwn));
             }
         }
         boxUnit[S] = (int)unitBox.size();
         R.nUnits = (int)unitBox.size();
-        R.nOwnUnits = (int)ownUnit.size();
         R.unitBox = upload(c, unitBox);
-        R.unitKind = upload(c, unitKind);
-        R.unitBegin = upload(c, unitBegin);
-        R.unitEnd = upload(c, unitEnd);
+        R.unitOwnBegin = upload(c, uOb);
+        R.unitOwnEnd = upload(c, uOe);
+        R.unitExtBegin = upload(c, uEb);
+        R.unitExtEnd = upload(c, uEe);
         R.boxUnit = upload(c, boxUnit);
-        R.ownUnit = upload(c, ownUnit);
         std::vector<int> pBox, pBegin, pEnd;
         for (int sb2 = 0; sb2 < S; ++sb2)
             for (int rb = ownRowPtr[sb2]; rb < ownRowPtr[sb2 + 1]; rb += kProlongRows) {
@@ -1193,10 +1193,10 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         R.pUnitBegin = upload(c, pBegin);
         R.pUnitEnd = upload(c, pEnd);
         if (!R.pUnitBox || !R.pUnitBegin || !R.pUnitEnd || R.nPUnits == 0) return XDCG_OOM;
-        R.unitPart = dalloc<double>(c, 12 * (size_t)R.nUnits);
+        R.unitPart = dalloc<double>(c, 24 * (size_t)R.nUnits);
         R.boxTicket = dalloc<unsigned int>(c, S);
-        if (!R.unitBox || !R.unitKind || !R.unitBegin || !R.unitEnd || !R.boxUnit || !R.ownUnit ||
-            !R.unitPart || !R.boxTicket || R.nUnits > kMaxGrid)
+        if (!R.unitBox || !R.unitOwnBegin || !R.unitOwnEnd || !R.unitExtBegin || !R.unitExtEnd ||
+            !R.boxUnit || !R.unitPart || !R.boxTicket || R.nUnits > kMaxGrid)
             return XDCG_OOM;
         CK(cudaMemsetAsync(R.boxTicket, 0, S * sizeof(unsigned int), st));
         launch_to_colmajor(N, d_ownSub, d_ors, d_ownB, d_zOff, R.ownRowPtr, R.zBase, d_menr, d_Zt,

@@ -267,56 +267,79 @@ void launch_prolong(const BoxDev<double> &B, const double *nu, const double *y, 
 
 constexpr int kRowThreads = 256;
 
-// acc[0..M) collects the unit's coarse partials, acc[M] its share of ||r||^2;
+// A unit covers own rows [ownBegin, ownEnd) and coupled rows [extBegin,
+// extEnd) of one box (most boxes are one unit).  acc[0..M): Z~^T r over its
+// own rows, acc[M..2M): W~^T r over its coupled rows, acc[2M]: ||r||^2;
 // returns (in thread 0) the unit's ||r||^2 after one block reduction.
 template <int M>
 __device__ __forceinline__ float restrict_update_unit(const RowBoxDev &B, int unit, float *u,
                                                       const float *r_cur, float *r_next,
                                                       const float *p, const float *q, int mode,
                                                       float alpha, double *g, double *zr) {
-    const int s = B.unitBox[unit], kind = B.unitKind[unit];
-    const int rb = B.unitBegin[unit], re = B.unitEnd[unit];
-    float acc[M + 1];
+    const int s = B.unitBox[unit];
+    float acc[2 * M + 1];
 #pragma unroll
-    for (int c = 0; c <= M; ++c) acc[c] = 0.0f;
+    for (int c = 0; c <= 2 * M; ++c) acc[c] = 0.0f;
     const uint64_t keep = l2_keep_policy();
-    if (kind == 0) {
+    {
         const int r0 = B.ownRowPtr[s], R = B.ownRowPtr[s + 1] - r0;
         const float *Z = B.Z + B.zBase[s];
+        const int re = B.unitOwnEnd[unit];
 #pragma unroll 4
-        for (int r = rb + threadIdx.x; r < re; r += blockDim.x) {
-            const int d = r;
-            float rn = r_cur[d];
+        for (int r = B.unitOwnBegin[unit] + threadIdx.x; r < re; r += blockDim.x) {
+            float rn = r_cur[r];
             if (mode == 0) {
-                rn = fmaf(-alpha, q[d], rn);
-                r_next[d] = rn;
-                u[d] = fmaf(alpha, p[d], u[d]);
+                rn = fmaf(-alpha, q[r], rn);
+                r_next[r] = rn;
+                u[r] = fmaf(alpha, p[r], u[r]);
             }
-            acc[M] = fmaf(rn, rn, acc[M]);
+            acc[2 * M] = fmaf(rn, rn, acc[2 * M]);
             const int rl = r - r0;
 #pragma unroll
-            for (int c = 0; c < M; ++c) acc[c] = fmaf(ld_keep(Z + (size_t)c * R + rl, keep), rn, acc[c]);
+            for (int c = 0; c < M; ++c)
+                acc[c] = fmaf(ld_keep(Z + (size_t)c * R + rl, keep), rn, acc[c]);
         }
-    } else if (mode != 2) {
+    }
+    if (mode != 2) {
         const int r0 = B.extRowPtr[s], R = B.extRowPtr[s + 1] - r0;
         const float *W = B.W + B.wBase[s];
+        const int re = B.unitExtEnd[unit];
 #pragma unroll 4
-        for (int r = rb + threadIdx.x; r < re; r += blockDim.x) {
+        for (int r = B.unitExtBegin[unit] + threadIdx.x; r < re; r += blockDim.x) {
             const int d = ld_keep(B.extRowDof + r, keep);
             const float rn = (mode == 0) ? fmaf(-alpha, q[d], r_cur[d]) : r_cur[d];
             const int rl = r - r0;
 #pragma unroll
-            for (int c = 0; c < M; ++c) acc[c] = fmaf(ld_keep(W + (size_t)c * R + rl, keep), rn, acc[c]);
+            for (int c = 0; c < M; ++c)
+                acc[M + c] = fmaf(ld_keep(W + (size_t)c * R + rl, keep), rn, acc[M + c]);
         }
     }
-    block_sum<float, M + 1>(acc);
+    block_sum<float, 2 * M + 1>(acc);
+    const int u0 = B.boxUnit[s], nu = B.boxUnit[s + 1] - u0;
+    const int c0 = B.col0[s];
+    __shared__ float red[2 * 12];
+    if (nu == 1) {
+        // the whole box in this block: no cross-block combination
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int c = 0; c < 2 * M; ++c) red[c] = acc[c];
+        }
+        __syncthreads();
+        if (threadIdx.x < M) {
+            const int c = threadIdx.x;
+            const double zs = red[c], ws = red[M + c];
+            g[c0 + c] = zs - ws;
+            B.g32[c0 + c] = (float)(zs - ws);
+            if (zr) zr[c0 + c] = zs;
+        }
+        return acc[2 * M];
+    }
     __shared__ bool lastUnit;
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int c = 0; c < M; ++c) B.unitPart[(size_t)unit * 12 + c] = (double)acc[c];
+        for (int c = 0; c < 2 * M; ++c) B.unitPart[(size_t)unit * 24 + c] = (double)acc[c];
         __threadfence();
-        const unsigned int nu = (unsigned int)(B.boxUnit[s + 1] - B.boxUnit[s]);
-        lastUnit = atomicAdd(&B.boxTicket[s], 1u) == nu - 1;
+        lastUnit = atomicAdd(&B.boxTicket[s], 1u) == (unsigned int)nu - 1;
     }
     __syncthreads();
     if (lastUnit) {
@@ -324,18 +347,17 @@ __device__ __forceinline__ float restrict_update_unit(const RowBoxDev &B, int un
         if (threadIdx.x < M) {
             const int c = threadIdx.x;
             double zs = 0.0, ws = 0.0;
-            for (int v = B.boxUnit[s]; v < B.boxUnit[s + 1]; ++v) {
-                const double x = __ldcg(B.unitPart + (size_t)v * 12 + c);
-                if (B.unitKind[v] == 0) zs += x; else ws += x;
+            for (int v = u0; v < u0 + nu; ++v) {
+                zs += __ldcg(B.unitPart + (size_t)v * 24 + c);
+                ws += __ldcg(B.unitPart + (size_t)v * 24 + M + c);
             }
-            const int c0 = B.col0[s];
             g[c0 + c] = zs - ws;
             B.g32[c0 + c] = (float)(zs - ws);
             if (zr) zr[c0 + c] = zs;
         }
         if (threadIdx.x == 0) B.boxTicket[s] = 0u;
     }
-    return acc[M];
+    return acc[2 * M];
 }
 
 __global__ void __launch_bounds__(kRowThreads)

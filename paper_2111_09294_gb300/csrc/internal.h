@@ -129,13 +129,14 @@ void launch_update(const NodeDev<T> &N, T *u, T *r, const T *p, const T *q, T *y
                    double *partials, Scalars *sc, cudaStream_t st);
 
 // Row-parallel form of the block-scaled FP32 path: per box, the rows of its
-// own nodes (Z~, column-major: column c of box s at Z + zBase[s] + c * R_s)
-// and the rows of the nodes coupled to it (W~, column-major likewise), each
-// row mapped to its dof.
-// Work is split into balanced units of at most kUnitRows rows (a box near
-// the crack front holds several times the rows of an average box): units of
-// a box are contiguous, its own-row units first; the last unit of a box to
-// finish (per-box ticket) adds the units' partial sums in unit order.
+// own nodes (Z~, column-major: column c of box s at Z + zBase[s] + c * R_s;
+// own row r is dof r of the box-major numbering) and the rows of the nodes
+// coupled to it (W~, column-major likewise, each row mapped to its dof).
+// The restriction splits each box's own rows followed by its coupled rows
+// into balanced units of at most kUnitRows rows (a box near the crack front
+// holds several times the rows of an average box; most boxes are one unit).
+// When a box has several units, the last to finish (per-box ticket) adds
+// their partial sums in unit order.
 struct RowBoxDev {
     int nBox;
     const int *col0, *menr;
@@ -146,16 +147,16 @@ struct RowBoxDev {
     float *g32;                         // [k] FP32 copy of g for the FP32 coarse solve
     const long long *wBase;             // [nBox]
     const float *W;
-    int nUnits, nOwnUnits;
-    const int *unitBox, *unitKind, *unitBegin, *unitEnd;   // [nUnits]; kind 0: own, 1: coupled
+    int nUnits;
+    const int *unitBox;                 // [nUnits]
+    const int *unitOwnBegin, *unitOwnEnd, *unitExtBegin, *unitExtEnd;   // [nUnits] row ranges
     const int *boxUnit;                 // [nBox + 1] first unit of each box
-    const int *ownUnit;                 // [nOwnUnits] the own-row units, in order
     int nPUnits;                        // prolongation units (own rows, <= kProlongRows)
     const int *pUnitBox, *pUnitBegin, *pUnitEnd;
-    double *unitPart;                   // [nUnits * 12] partial sums (scratch)
+    double *unitPart;                   // [nUnits * 24] partial sums (scratch)
     unsigned int *boxTicket;            // [nBox] (scratch, kept at zero between launches)
 };
-constexpr int kUnitRows = 2048;
+constexpr int kUnitRows = 3072;     // own + coupled rows per restriction unit
 constexpr int kProlongRows = 512;
 
 void launch_restrict(const BoxDev<double> &B, const double *a, const double *b, int withW,
