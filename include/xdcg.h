@@ -56,6 +56,7 @@ typedef enum {
 
 enum { XDCG_HOST = 0, XDCG_DEVICE = 1 };       /* memory space of input arrays */
 enum { XDCG_FP64 = 0, XDCG_MIXED = 1 };        /* solve precision */
+enum { XDCG_BLOCK_JACOBI = 0, XDCG_POINT_JACOBI = 1 };   /* M of Algorithm 3 */
 
 /* Stiffness matrix K in node-blocked CSR, full symmetric storage, FP64.
  * Row I lists the nodes J coupled to I (sharing an element), sorted, with
@@ -103,6 +104,13 @@ typedef struct {
                                 default 30 */
     int32_t time_spmv;       /* 1: bracket every SpMV launch of the iteration by CUDA events;
                                 2: bracket every kernel of the iteration (t_phase_ms) */
+    int32_t jacobi;          /* XDCG_BLOCK_JACOBI (default): one block per node (3/6/15 dofs,
+                                Eqs. block_jacobi, block_jacobi_enr); XDCG_POINT_JACOBI: the
+                                diagonal of K, the paper's comparison preconditioner
+                                (Section 4.1).  MIXED scales K~ by the same factors; with point
+                                Jacobi its FP32 run can break down (XDCG_BREAKDOWN) */
+    int32_t record_history;  /* 1: keep ||r_i|| / ||f|| of every iteration of FP64 solves
+                                (xdcg_get_history); default 0 */
 } xdcg_options;
 
 typedef struct {
@@ -158,12 +166,29 @@ xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflatio
  * res may be NULL.  On NO_CONVERGENCE u holds the last iterate. */
 xdcg_status xdcg_solve(xdcg_ctx *ctx, const double *f, double *u, double tol, xdcg_result *res);
 
+/* As xdcg_solve, started from the caller's guess: on entry u holds u_-1, and
+ * Algorithm 2 gives u_0 = u_-1 + Z E^-1 Z^T (f - K u_-1) (the paper's start
+ * with a nonzero u_-1; reusing the previous solution is the paper's stated
+ * future work).  The mixed path starts its FP64 solution at u_-1 and its
+ * FP32 run on the scaled residual f - K u_-1.  A guess that already meets
+ * tol returns it unchanged with 0 iterations.  Iteration counts and the
+ * stopping test are as for xdcg_solve. */
+xdcg_status xdcg_solve_x0(xdcg_ctx *ctx, const double *f, double *u, double tol,
+                          xdcg_result *res);
+
 /* As xdcg_solve with host arrays: copies f to the device, solves, copies u
  * back, all on the context stream; returns after u is on the host. */
 xdcg_status xdcg_solve_host(xdcg_ctx *ctx, const double *f_host, double *u_host, double tol,
                             xdcg_result *res);
 
 xdcg_status xdcg_get_info(const xdcg_ctx *ctx, xdcg_info_t *info);
+
+/* Recursive relative residuals ||r_i|| / ||f||, i = 0 .. iterations, of the
+ * last FP64 solve (the curves of the paper's Section 4.1 residual figure).
+ * Needs opt.record_history at set-up (else XDCG_INVALID_ARG).  Writes
+ * min(cap, *count) values to out (host) and the number recorded to *count.
+ * MIXED solves record nothing (their FP32 recursion lives in a scaled norm). */
+xdcg_status xdcg_get_history(xdcg_ctx *ctx, double *out, int32_t cap, int32_t *count);
 
 /* The operator of one solve path applied to x.  XDCG_FP64: y = K x with
  * double arrays.  XDCG_MIXED: y = K~ x with float arrays, where

@@ -13,14 +13,15 @@ LIB_PATH = os.path.join(HERE, "libxdcg.so")
 
 XDCG_HOST, XDCG_DEVICE = 0, 1
 XDCG_FP64, XDCG_MIXED = 0, 1
+XDCG_BLOCK_JACOBI, XDCG_POINT_JACOBI = 0, 1
 
 STATUS = {0: "XDCG_OK", 1: "XDCG_INVALID_ARG", 2: "XDCG_NOT_SPD_BLOCK",
           3: "XDCG_COARSE_NOT_SPD", 4: "XDCG_BREAKDOWN", 5: "XDCG_NO_CONVERGENCE",
           6: "XDCG_CUDA_ERROR", 7: "XDCG_OOM", 8: "XDCG_TOO_LARGE", 9: "XDCG_TIMEOUT"}
 
 # every function the header declares
-EXPORTS = ["xdcg_default_options", "xdcg_setup", "xdcg_solve", "xdcg_solve_host",
-           "xdcg_get_info", "xdcg_spmv", "xdcg_spmv_noalloc", "xdcg_precond", "xdcg_coarse_matrix",
+EXPORTS = ["xdcg_default_options", "xdcg_setup", "xdcg_solve", "xdcg_solve_x0", "xdcg_solve_host",
+           "xdcg_get_info", "xdcg_get_history", "xdcg_spmv", "xdcg_spmv_noalloc", "xdcg_precond", "xdcg_coarse_matrix",
            "xdcg_destroy", "xdcg_status_string"]
 
 
@@ -37,7 +38,8 @@ class Deflation(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("tol", c_double), ("max_iter", c_int32), ("precision", c_int32),
-                ("inner_tol", c_double), ("max_outer", c_int32), ("time_spmv", c_int32)]
+                ("inner_tol", c_double), ("max_outer", c_int32), ("time_spmv", c_int32),
+                ("jacobi", c_int32), ("record_history", c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -80,8 +82,10 @@ def load():
     lib.xdcg_setup.argtypes = [POINTER(c_void_p), POINTER(Matrix), POINTER(Deflation), c_void_p,
                                POINTER(Options), c_void_p, POINTER(c_int32)]
     lib.xdcg_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_double, POINTER(Result)]
+    lib.xdcg_solve_x0.argtypes = [c_void_p, c_void_p, c_void_p, c_double, POINTER(Result)]
     lib.xdcg_solve_host.argtypes = [c_void_p, c_void_p, c_void_p, c_double, POINTER(Result)]
     lib.xdcg_get_info.argtypes = [c_void_p, POINTER(Info)]
+    lib.xdcg_get_history.argtypes = [c_void_p, c_void_p, c_int32, POINTER(c_int32)]
     lib.xdcg_spmv.argtypes = [c_void_p, c_int32, c_void_p, c_void_p, POINTER(c_double)]
     lib.xdcg_spmv_noalloc.argtypes = [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]
     lib.xdcg_precond.argtypes = [c_void_p, c_void_p, c_void_p]

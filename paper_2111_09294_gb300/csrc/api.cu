@@ -51,6 +51,9 @@ struct xdcg_ctx {
     double *Einv = nullptr;
     float *Einv32 = nullptr;       // FP32 copy for the mixed path's FP32 iteration
     float *g32 = nullptr;          // FP32 copy of the coarse right-hand side g
+    double *hist = nullptr;        // record_history: ||r_i||^2 of the last FP64 solve
+    int histLen = 0;
+    double histFF = 0.0;
     long long extRows32 = 0, zEnt32 = 0, wEnt32 = 0;   // sizes of the FP32 box layouts
     double *E = nullptr;                      // E = Z^T K Z as assembled (diagnostics)
     std::vector<void *> temps;                // set-up temporaries
@@ -156,17 +159,21 @@ bool points_collinear(const std::vector<double> &x) {
     return true;
 }
 
-__global__ void k_init_scalars(Scalars *sc, double tol2, const double *ffsrc, int max_it) {
+__global__ void k_init_scalars(Scalars *sc, double tol2, const double *ffsrc, int max_it,
+                               double *hist, int histCap) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         Scalars z{};
         z.tol2ff = ffsrc ? tol2 * (*ffsrc) : tol2;
         z.max_it = max_it;
+        z.hist = hist;
+        z.histCap = histCap;
         *sc = z;
     }
 }
 
-void init_scalars(xdcg_ctx *c, Scalars *sc, double tol2, const double *ffsrc, int max_it) {
-    k_init_scalars<<<1, 32, 0, c->st>>>(sc, tol2, ffsrc, max_it);
+void init_scalars(xdcg_ctx *c, Scalars *sc, double tol2, const double *ffsrc, int max_it,
+                  double *hist = nullptr, int histCap = 0) {
+    k_init_scalars<<<1, 32, 0, c->st>>>(sc, tol2, ffsrc, max_it, hist, histCap);
     c->launches++;
 }
 
@@ -243,20 +250,31 @@ struct PlainPath {
 
 template <typename T, typename Path>
 xdcg_status run_pcg(xdcg_ctx *c, Path path, const T *f, T *u, T *r, T *p, T *q, T *y,
-                    Scalars *sc, int max_it, int *its_out, int *done_out, xdcg_result *res) {
+                    Scalars *sc, int max_it, bool guess, int *its_out, int *done_out,
+                    xdcg_result *res) {
     cudaStream_t st = c->st;
     const bool timeSpmv = c->opt.time_spmv == 1, timeKernels = c->opt.time_spmv == 2;
-    // Algorithm 2 with u_-1 = 0: u_0 = Z E^-1 Z^T f
-    path.restrict_(f, nullptr, 0, nullptr, sc);
-    path.coarse(nullptr, 0, sc);
-    path.prolong(nullptr, u, 1, sc);
+    if (guess) {
+        // Algorithm 2 with the caller's u_-1 (in u): u_0 = u_-1 + Z E^-1 Z^T (f - K u_-1)
+        path.spmv(u, r, f, 1, kFinStore, sc);
+        path.restrict_(r, nullptr, 0, nullptr, sc);
+        path.coarse(nullptr, 0, sc);
+        path.prolong(u, u, 2, sc);
+        c->launches += 4;
+    } else {
+        // Algorithm 2 with u_-1 = 0: u_0 = Z E^-1 Z^T f
+        path.restrict_(f, nullptr, 0, nullptr, sc);
+        path.coarse(nullptr, 0, sc);
+        path.prolong(nullptr, u, 1, sc);
+        c->launches += 3;
+    }
     // r_0 = f - K u_0, z_0 by Algorithm 3, p_0 = z_0
     path.spmv(u, r, f, 1, kFinRR, sc);
     path.update(u, r, nullptr, nullptr, y, 1, sc);
     path.restrict_(r, y, 1, c->zr, sc);
     path.coarse(c->zr, 1, sc);
     path.prolong(y, p, 2, sc);
-    c->launches += 8;
+    c->launches += 5;
 
     int launched = 0;
     const int max_batches = max_it / kBatch + 2;
@@ -433,15 +451,17 @@ xdcg_status read_aux(xdcg_ctx *c, double *vals, int count) {
     return c->h_sc->done == kFault ? XDCG_TIMEOUT : XDCG_OK;
 }
 
-xdcg_status solve_fp64(xdcg_ctx *c, const double *f, double *u, double tol, xdcg_result *res) {
+xdcg_status solve_fp64(xdcg_ctx *c, const double *f, double *u, double tol, bool guess,
+                       xdcg_result *res) {
     cudaStream_t st = c->st;
     init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
     launch_dot<double>(f, f, c->n, c->partials, c->aux, kFinStore, 0, st);
-    init_scalars(c, c->sc, tol * tol, &c->aux->scratch[0], c->opt.max_iter);
+    init_scalars(c, c->sc, tol * tol, &c->aux->scratch[0], c->opt.max_iter, c->hist,
+                 c->hist ? c->opt.max_iter + 1 : 0);
     c->launches += 1;
     int its = 0, done = 0;
     xdcg_status s = run_pcg<double>(c, PlainPath{c, c->L64}, f, u, c->r64, c->p64, c->q64,
-                                    c->y64, c->sc, c->opt.max_iter, &its, &done, res);
+                                    c->y64, c->sc, c->opt.max_iter, guess, &its, &done, res);
     if (s != XDCG_OK) return s;
     const double rr = c->h_sc->rr;
     // true residual f - K u in FP64
@@ -450,6 +470,8 @@ xdcg_status solve_fp64(xdcg_ctx *c, const double *f, double *u, double tol, xdcg
     double v[2];
     if ((s = read_aux(c, v, 2)) != XDCG_OK) return s;
     const double ff = v[0];
+    c->histLen = c->hist ? std::min(its, c->opt.max_iter) + 1 : 0;
+    c->histFF = ff;
     res->iterations = its;
     res->outer_cycles = 1;
     res->rel_res_recursive = ff > 0 ? std::sqrt(rr / ff) : 0.0;
@@ -464,7 +486,8 @@ xdcg_status solve_fp64(xdcg_ctx *c, const double *f, double *u, double tol, xdcg
 // residual f - K u is recomputed in FP64, and its scaled image replaces the
 // recursive residual while the search direction and rho carry on, so the
 // Krylov space is not restarted.
-xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, xdcg_result *res) {
+xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, bool guess,
+                        xdcg_result *res) {
     cudaStream_t st = c->st;
     Level32 &L = c->L32;
     init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
@@ -474,24 +497,40 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, xdc
     xdcg_status s;
     if ((s = read_aux(c, v, 1)) != XDCG_OK) return s;
     const double ff = v[0];
-    CK(cudaMemsetAsync(u, 0, c->n * sizeof(double), st));
+    if (!guess || ff == 0.0) CK(cudaMemsetAsync(u, 0, c->n * sizeof(double), st));
     res->iterations = 0;
     res->outer_cycles = 0;
     res->rel_res_recursive = 0.0;
     res->rel_res_true = 0.0;
     if (ff == 0.0) return XDCG_OK;
     if (!std::isfinite(ff)) return XDCG_BREAKDOWN;
+    double rn2 = ff;
+    const double *rhs = f;
+    if (guess) {
+        // start from the caller's u: the FP32 run solves for the correction of
+        // r = f - K u (Algorithm 2 with u_-1 = u, applied to the correction)
+        init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
+        launch_spmv<double>(c->L64.A, u, c->r64, f, 1, c->partials, c->aux, kFinStore, 0, st);
+        c->launches += 1;
+        if ((s = read_aux(c, v, 1)) != XDCG_OK) return s;
+        rn2 = v[0];
+        res->rel_res_true = std::sqrt(rn2 / ff);
+        if (!std::isfinite(rn2)) return XDCG_BREAKDOWN;
+        if (rn2 <= tol * tol * ff) return XDCG_OK;
+        rhs = c->r64;
+    }
     const double s0 = 1.0 / std::sqrt(ff);
     const double delta2 = c->opt.inner_tol * c->opt.inner_tol;
     float *rA = c->r32, *rB = c->y32;
-    // f~ = s0 L^-1 f, and the FP32 run from Algorithm 2
-    launch_fwd_scale(c->nNodes, L.dofStart64, L.dofStart64, L.dofStart32, L.F, f, s0, c->f32, st);
+    // f~ = s0 L^-1 f (or of the starting residual), and the FP32 run from Algorithm 2
+    launch_fwd_scale(c->nNodes, L.dofStart64, L.dofStart64, L.dofStart32, L.F, rhs, s0, c->f32,
+                     st);
     CK(cudaMemsetAsync(c->u32, 0, c->n * sizeof(float), st));
     init_scalars(c, c->sc32, -1.0, nullptr, c->opt.max_iter);
     scaled_init(c, c->f32, c->u32, rA, c->p32, c->sc32);
     k_set_trigger<<<1, 32, 0, st>>>(c->sc32, 1, delta2, 0.0);
     c->launches += 2;
-    double rn2 = ff, last_rec = 1.0;
+    double last_rec = 1.0;
     int cycles = 0, its = 0, done = 0, breakdowns = 0;
     xdcg_status status = XDCG_NO_CONVERGENCE;
     while (true) {
@@ -550,14 +589,15 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, xdc
     return status;
 }
 
-xdcg_status do_solve(xdcg_ctx *c, const double *f, double *u, double tol, xdcg_result *out) {
+xdcg_status do_solve(xdcg_ctx *c, const double *f, double *u, double tol, bool guess,
+                     xdcg_result *out) {
     xdcg_result res{};
     res.bad_index = -1;
     if (tol <= 0) tol = c->opt.tol;
     const long long l0 = c->launches;
     CK(cudaEventRecord(c->ev0, c->st));
-    xdcg_status s = (c->opt.precision == XDCG_MIXED) ? solve_mixed(c, f, u, tol, &res)
-                                                    : solve_fp64(c, f, u, tol, &res);
+    xdcg_status s = (c->opt.precision == XDCG_MIXED) ? solve_mixed(c, f, u, tol, guess, &res)
+                                                    : solve_fp64(c, f, u, tol, guess, &res);
     if (s == XDCG_CUDA_ERROR) return s;
     CK(cudaEventRecord(c->ev1, c->st));
     CK(cudaEventSynchronize(c->ev1));
@@ -781,6 +821,8 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     for (int I = 0; I < N; ++I) lists[kindb[I] == 3 ? 0 : (kindb[I] == 6 ? 1 : 2)].push_back(I);
     const int Bsz[3] = {3, 6, 15};
     std::vector<double> Dsoa[3];
+    // block Jacobi factors the node blocks; point Jacobi only their diagonals
+    const bool pointJacobi = c->opt.jacobi == XDCG_POINT_JACOBI;
     for (int t = 0; t < 3; ++t) {
         const int B = Bsz[t], cnt = (int)lists[t].size();
         Dsoa[t].assign((size_t)B * B * std::max(cnt, 1), 0.0);
@@ -789,7 +831,9 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
             long long pd = -1;
             for (long long p = rowp[I]; p < rowp[I + 1]; ++p)
                 if (col[p] == I) pd = p;
-            for (int e = 0; e < B * B; ++e) Dsoa[t][(size_t)e * cnt + i] = val[vptr[pd] + e];
+            for (int e = 0; e < B * B; ++e)
+                Dsoa[t][(size_t)e * cnt + i] =
+                    (pointJacobi && e / B != e % B) ? 0.0 : val[vptr[pd] + e];
         }
     }
 
@@ -1230,6 +1274,10 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     c->nu32 = dalloc<float>(c, k);
     c->partials = dalloc<double>(c, 4 * (size_t)kMaxGrid);
     c->sc = dalloc<Scalars>(c, 1); c->sc32 = dalloc<Scalars>(c, 1); c->aux = dalloc<Scalars>(c, 1);
+    if (c->opt.record_history) {
+        c->hist = dalloc<double>(c, (size_t)c->opt.max_iter + 1);
+        if (!c->hist) return XDCG_OOM;
+    }
     if (!c->u64 || !c->r64 || !c->p64 || !c->q64 || !c->y64 || !c->f64 || !c->uh64 || !c->g ||
         !c->zr || !c->nu || !c->nu32 || !c->partials || !c->sc || !c->sc32 || !c->aux)
         return XDCG_OOM;
@@ -1297,6 +1345,8 @@ xdcg_status xdcg_default_options(xdcg_options *opt) {
     opt->inner_tol = 1e-3;
     opt->max_outer = 30;
     opt->time_spmv = 0;
+    opt->jacobi = XDCG_BLOCK_JACOBI;
+    opt->record_history = 0;
     return XDCG_OK;
 }
 
@@ -1316,6 +1366,7 @@ xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflatio
     if (!(c->opt.tol > 0) || c->opt.max_iter < 0 || c->opt.max_outer < 1 ||
         (c->opt.precision != XDCG_FP64 && c->opt.precision != XDCG_MIXED) ||
         c->opt.time_spmv < 0 || c->opt.time_spmv > 2 ||
+        (c->opt.jacobi != XDCG_BLOCK_JACOBI && c->opt.jacobi != XDCG_POINT_JACOBI) ||
         !(c->opt.inner_tol > 0 && c->opt.inner_tol < 1)) {
         delete c;
         return XDCG_INVALID_ARG;
@@ -1339,18 +1390,36 @@ xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflatio
 
 xdcg_status xdcg_solve(xdcg_ctx *c, const double *f, double *u, double tol, xdcg_result *res) {
     if (!c || !f || !u || f == u) return XDCG_INVALID_ARG;
-    return do_solve(c, f, u, tol, res);
+    return do_solve(c, f, u, tol, false, res);
+}
+
+xdcg_status xdcg_solve_x0(xdcg_ctx *c, const double *f, double *u, double tol, xdcg_result *res) {
+    if (!c || !f || !u || f == u) return XDCG_INVALID_ARG;
+    return do_solve(c, f, u, tol, true, res);
 }
 
 xdcg_status xdcg_solve_host(xdcg_ctx *c, const double *f_host, double *u_host, double tol,
                             xdcg_result *res) {
     if (!c || !f_host || !u_host) return XDCG_INVALID_ARG;
     CK(cudaMemcpyAsync(c->f64, f_host, c->n * sizeof(double), cudaMemcpyHostToDevice, c->st));
-    xdcg_status s = do_solve(c, c->f64, c->uh64, tol, res);
+    xdcg_status s = do_solve(c, c->f64, c->uh64, tol, false, res);
     if (s == XDCG_CUDA_ERROR) return s;
     CK(cudaMemcpyAsync(u_host, c->uh64, c->n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     return s;
+}
+
+xdcg_status xdcg_get_history(xdcg_ctx *c, double *out, int32_t cap, int32_t *count) {
+    if (!c || !count || cap < 0 || (cap > 0 && !out)) return XDCG_INVALID_ARG;
+    if (!c->hist) return XDCG_INVALID_ARG;
+    const int m = std::min(cap, c->histLen);
+    *count = c->histLen;
+    if (m == 0) return XDCG_OK;
+    std::vector<double> rr(m);
+    CK(cudaMemcpyAsync(rr.data(), c->hist, m * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    for (int i = 0; i < m; ++i) out[i] = c->histFF > 0 ? std::sqrt(rr[i] / c->histFF) : 0.0;
+    return XDCG_OK;
 }
 
 xdcg_status xdcg_get_info(const xdcg_ctx *c, xdcg_info_t *info) {

@@ -39,6 +39,9 @@ struct Scalars {
     int max_it;
     int fault;        // set by a kernel whose bounded wait ran out
     unsigned int ticket[4];   // last-block tickets, reset by the last block
+    double *hist;     // if not null: ||r_i||^2 of iteration i, i < histCap
+    int histCap;
+    int pad2;
 };
 
 // Chunked 3x3 BSR over the chunk rows (3 consecutive dofs) in sliced-ELL

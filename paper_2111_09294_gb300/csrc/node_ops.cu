@@ -124,6 +124,7 @@ k_update(NodeDev<T> N, T *u, T *r, const T *p, const T *q, T *y, int mode, int n
     if (grid_sum<double, 2>(v, partials, &sc->ticket[2], tot) && threadIdx.x == 0) {
         sc->ry = tot[1];
         sc->rr = tot[0];
+        if (sc->hist && sc->its < sc->histCap) sc->hist[sc->its] = tot[0];
         if (tot[0] <= sc->tol2ff)
             sc->done = kConverged;
         else if (sc->its >= sc->max_it)

@@ -111,6 +111,7 @@ __device__ __forceinline__ void finalize(Scalars *sc, int fin, int slot, double 
         }
     } else if (fin == kFinRR) {
         sc->rr = val;
+        if (sc->hist && sc->histCap > 0) sc->hist[0] = val;
         if (val <= sc->tol2ff) sc->done = kConverged;
     } else {
         sc->scratch[slot] = val;

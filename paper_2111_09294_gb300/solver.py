@@ -21,11 +21,15 @@ class Solver:
     K: node-blocked CSR arrays (dof_ptr, row_ptr, col, val_ptr, val) in host memory;
     Z: box subdomains (sub_of_node, coords, hsign, centres).
     precision: "fp64" or "mixed" (FP32 PCG on the block-scaled system with FP64 residual replacement).
+    jacobi: "block" (one block per node, the method's M) or "point" (diag K, the
+    paper's comparison preconditioner).  record_history: keep ||r_i|| / ||f||
+    per iteration of FP64 solves (history()).
     """
 
     def __init__(self, dof_ptr, row_ptr, col, val_ptr, val, sub_of_node, coords, hsign, centres,
                  precision="fp64", tol=1e-8, max_iter=10000, inner_tol=1e-3, max_outer=30,
-                 time_spmv=False, enriched_modes=True, stream=None):
+                 time_spmv=False, enriched_modes=True, stream=None, jacobi="block",
+                 record_history=False):
         lib = L.load()
         self._lib = lib
         self.ctx = ctypes.c_void_p()
@@ -47,6 +51,10 @@ class Solver:
         opt.inner_tol = inner_tol
         opt.max_outer = max_outer
         opt.time_spmv = 2 if time_spmv == "kernels" else int(bool(time_spmv))
+        if jacobi not in ("block", "point"):
+            raise ValueError("jacobi must be 'block' or 'point'")
+        opt.jacobi = L.XDCG_POINT_JACOBI if jacobi == "point" else L.XDCG_BLOCK_JACOBI
+        opt.record_history = int(bool(record_history))
         self.precision = precision
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -73,17 +81,36 @@ class Solver:
             raise ValueError(f"expected a contiguous CUDA {dtype} tensor of {self.n} entries")
         return ctypes.c_void_p(t.data_ptr())
 
-    def solve(self, f, tol=0.0, out=None, raise_on_error=True):
-        """u with K u = f; f: CUDA float64 tensor.  Returns (u, info dict)."""
+    def solve(self, f, tol=0.0, out=None, raise_on_error=True, x0=None):
+        """u with K u = f; f: CUDA float64 tensor.  x0: optional starting guess
+        u_-1 (Algorithm 2 with a nonzero u_-1).  Returns (u, info dict)."""
         u = out if out is not None else torch.empty_like(f)
         res = L.Result()
-        s = self._lib.xdcg_solve(self.ctx, self._dev(f, torch.float64),
-                                 self._dev(u, torch.float64), float(tol), ctypes.byref(res))
+        if x0 is not None:
+            if x0.data_ptr() != u.data_ptr():
+                u.copy_(x0)
+            s = self._lib.xdcg_solve_x0(self.ctx, self._dev(f, torch.float64),
+                                        self._dev(u, torch.float64), float(tol), ctypes.byref(res))
+        else:
+            s = self._lib.xdcg_solve(self.ctx, self._dev(f, torch.float64),
+                                     self._dev(u, torch.float64), float(tol), ctypes.byref(res))
         info = res.as_dict()
         info["status"] = L.STATUS.get(s, s)
         if raise_on_error:
             L.check(s, "xdcg_solve", res.bad_index)
         return u, info
+
+    def history(self):
+        """||r_i|| / ||f||, i = 0 .. iterations, of the last FP64 solve."""
+        count = ctypes.c_int32(0)
+        L.check(self._lib.xdcg_get_history(self.ctx, None, 0, ctypes.byref(count)),
+                "xdcg_get_history")
+        out = np.empty(count.value)
+        if count.value:
+            L.check(self._lib.xdcg_get_history(self.ctx, ctypes.c_void_p(out.ctypes.data),
+                                               count.value, ctypes.byref(count)),
+                    "xdcg_get_history")
+        return out
 
     def solve_host(self, f_host, u_host, tol=0.0):
         """Host-memory solve (copies inside the call); f_host, u_host: float64 arrays

@@ -146,3 +146,23 @@ def test_indefinite_block_is_rejected():
     with pytest.raises(O.NotSPD) as ei:
         O.BlockJacobi(K.tocsr(), P.dof_ptr)
     assert ei.value.args[0] == 5
+
+
+def test_algorithm2_with_nonzero_start(cube8):
+    # Algorithm 2 with any u_-1 makes Z^T r_0 vanish (the start lies in the
+    # deflated affine space), and the run from it reaches the same solution
+    P, K, M, C = cube8
+    rng = np.random.default_rng(21)
+    u_m1 = rng.standard_normal(P.n) * np.linalg.norm(P.f) / np.sqrt(P.n)
+    u0 = O.adef2_initial(K, C, P.f, u_m1)
+    r0 = P.f - K @ u0
+    zn = sp.linalg.norm(C.Z)
+    assert np.linalg.norm(C.Z.T @ r0) <= 1e-10 * zn * np.linalg.norm(P.f)
+    cold = O.adef2_pcg(K, P.f, M, C, tol=1e-12)
+    warm = O.adef2_pcg(K, P.f, M, C, tol=1e-12, u_m1=u_m1)
+    assert np.linalg.norm(warm.u - cold.u) <= 1e-8 * np.linalg.norm(cold.u)
+    # a start that already meets the tolerance is returned after Algorithm 2
+    # with no iteration
+    again = O.adef2_pcg(K, P.f, M, C, tol=1e-8, u_m1=cold.u)
+    assert again.iterations == 0
+    assert np.linalg.norm(again.u - cold.u) <= 1e-12 * np.linalg.norm(cold.u)
