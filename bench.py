@@ -290,6 +290,45 @@ def run_ours(args):
             phases["mixed_gbs"] = {nm: round(nbytes[nm] / (phases[prec][nm] * 1e-6) / 1e9)
                                    for nm in names}
         diag.close()
+    # several load cases of the same crack configuration: one batched FP32 run
+    # against the same columns solved one after another (outside the value)
+    batch = None
+    if args.batch > 0:
+        m = args.batch
+        Fb = torch.tensor(X.load_cases(P, m, seed=0), device=dev)
+        Ub = torch.empty_like(Fb)
+        bsol = Solver.from_problem(P, precision="mixed", inner_tol=args.inner_tol, max_batch=m)
+        for _ in range(max(1, args.warmup)):
+            bsol.solve_batch(Fb, tol=TOL, out=Ub)
+        tb, t1, binfs = [], [], None
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, binfs = bsol.solve_batch(Fb, tol=TOL, out=Ub)
+            e1.record(stream)
+            e1.synchronize()
+            tb.append(e0.elapsed_time(e1))
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for j in range(m):
+                mixed.solve(Fb[j], tol=TOL, out=u)
+            e1.record(stream)
+            e1.synchronize()
+            t1.append(e0.elapsed_time(e1))
+        rmax = max(i["rel_res_true"] for i in binfs)
+        assert rmax <= TOL, rmax
+        tb_ms, t1_ms = float(np.mean(tb)), float(np.mean(t1))
+        batch = {"rhs": m, "ms": tb_ms, "rhs_per_s": m / tb_ms * 1e3,
+                 "ms_one_by_one": t1_ms, "speedup_vs_one_by_one": t1_ms / tb_ms,
+                 "iterations_max": max(i["iterations"] for i in binfs),
+                 "rel_res_true_max": rmax,
+                 "loads": "seeded tractions on z = 1: shear and tension, |t_i| ~ U[0.5, 1.5]"}
+        bsol.close()
     info = mixed.info
     n_sp = sum(i["n_spmv_timed"] for i in inf_mixed_t)
     t_sp = sum(i["t_spmv_ms"] for i in inf_mixed_t)
@@ -320,6 +359,7 @@ def run_ours(args):
         "setup_ms": info["t_setup_ms"],
         "spmv_fp32_gbs": achieved, "spmv_fp64_gbs": achieved64,
         "kernel_us_per_iteration": phases,
+        "batched_load_cases": batch,
         "roofline": {"bound": "hbm", "kernel": "k_spmv<float> (inner FP32 SpMV)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind,
@@ -364,6 +404,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--inner-tol", type=float, default=1e-3)
+    ap.add_argument("--batch", type=int, default=8,
+                    help="load cases of the batched-solve measurement (0: skip)")
     ap.add_argument("--sample-iters", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", choices=["mixed", "fp64"], default=None,

@@ -111,6 +111,8 @@ typedef struct {
                                 Jacobi its FP32 run can break down (XDCG_BREAKDOWN) */
     int32_t record_history;  /* 1: keep ||r_i|| / ||f|| of every iteration of FP64 solves
                                 (xdcg_get_history); default 0 */
+    int32_t max_batch;       /* MIXED: right-hand sides one xdcg_solve_batch call may take
+                                together (0..8; 0 = no batched buffers), default 0 */
 } xdcg_options;
 
 typedef struct {
@@ -175,6 +177,19 @@ xdcg_status xdcg_solve(xdcg_ctx *ctx, const double *f, double *u, double tol, xd
  * stopping test are as for xdcg_solve. */
 xdcg_status xdcg_solve_x0(xdcg_ctx *ctx, const double *f, double *u, double tol,
                           xdcg_result *res);
+
+/* Solve K U_j = F_j for m right-hand sides of the set-up system (several load
+ * cases of one crack configuration).  F, U: device arrays of m * n doubles,
+ * column j at offset j * n (may not alias).  With MIXED and opt.max_batch >= m
+ * the columns run as one batched FP32 iteration: each iteration reads K~, Z~,
+ * W~ and E^-1 once for all columns; each column stops once its FP64 true
+ * residual meets tol, and FP64 residual replacements happen for all active
+ * columns together.  Otherwise (FP64, or max_batch = 0) the columns are solved
+ * one after another.  res: NULL or m results; iterations are counted per
+ * column (the shared counter when the column converged).  Returns the worst
+ * status over the columns. */
+xdcg_status xdcg_solve_batch(xdcg_ctx *ctx, const double *F, double *U, int32_t m, double tol,
+                             xdcg_result *res);
 
 /* As xdcg_solve with host arrays: copies f to the device, solves, copies u
  * back, all on the context stream; returns after u is on the host. */

@@ -20,7 +20,8 @@ STATUS = {0: "XDCG_OK", 1: "XDCG_INVALID_ARG", 2: "XDCG_NOT_SPD_BLOCK",
           6: "XDCG_CUDA_ERROR", 7: "XDCG_OOM", 8: "XDCG_TOO_LARGE", 9: "XDCG_TIMEOUT"}
 
 # every function the header declares
-EXPORTS = ["xdcg_default_options", "xdcg_setup", "xdcg_solve", "xdcg_solve_x0", "xdcg_solve_host",
+EXPORTS = ["xdcg_default_options", "xdcg_setup", "xdcg_solve", "xdcg_solve_x0", "xdcg_solve_batch",
+           "xdcg_solve_host",
            "xdcg_get_info", "xdcg_get_history", "xdcg_spmv", "xdcg_spmv_noalloc", "xdcg_precond", "xdcg_coarse_matrix",
            "xdcg_destroy", "xdcg_status_string"]
 
@@ -39,7 +40,7 @@ class Deflation(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("tol", c_double), ("max_iter", c_int32), ("precision", c_int32),
                 ("inner_tol", c_double), ("max_outer", c_int32), ("time_spmv", c_int32),
-                ("jacobi", c_int32), ("record_history", c_int32)]
+                ("jacobi", c_int32), ("record_history", c_int32), ("max_batch", c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -83,6 +84,7 @@ def load():
                                POINTER(Options), c_void_p, POINTER(c_int32)]
     lib.xdcg_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_double, POINTER(Result)]
     lib.xdcg_solve_x0.argtypes = [c_void_p, c_void_p, c_void_p, c_double, POINTER(Result)]
+    lib.xdcg_solve_batch.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_double, c_void_p]
     lib.xdcg_solve_host.argtypes = [c_void_p, c_void_p, c_void_p, c_double, POINTER(Result)]
     lib.xdcg_get_info.argtypes = [c_void_p, POINTER(Info)]
     lib.xdcg_get_history.argtypes = [c_void_p, c_void_p, c_int32, POINTER(c_int32)]

@@ -51,6 +51,12 @@ struct xdcg_ctx {
     double *Einv = nullptr;
     float *Einv32 = nullptr;       // FP32 copy for the mixed path's FP32 iteration
     float *g32 = nullptr;          // FP32 copy of the coarse right-hand side g
+    // batched FP32 run (opt.max_batch > 0): vectors n x bMB interleaved by column
+    int bMB = 0;
+    float *bF32 = nullptr, *bU32 = nullptr, *bRA = nullptr, *bRB = nullptr, *bP = nullptr,
+          *bQ = nullptr, *bG32 = nullptr, *bNU32 = nullptr;
+    double *bG = nullptr, *bZR = nullptr, *bNU = nullptr, *bUnitPart = nullptr, *bR64 = nullptr;
+    BatchScalars *bs = nullptr, *h_bs = nullptr;
     double *hist = nullptr;        // record_history: ||r_i||^2 of the last FP64 solve
     int histLen = 0;
     double histFF = 0.0;
@@ -589,6 +595,175 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, boo
     return status;
 }
 
+// ---- batched mixed solve: m right-hand sides of one system --------------------
+
+template <int MB>
+xdcg_status batch_iterate(xdcg_ctx *c, int m, int max_it) {
+    cudaStream_t st = c->st;
+    Level32 &L = c->L32;
+    CK(cudaMemcpyAsync(c->h_bs, c->bs, sizeof(BatchScalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int i = c->h_bs->its;
+    const int max_batches = (max_it - i) / kBatch + 2;
+    for (int b = 0; b < max_batches; ++b) {
+        for (int j = 0; j < kBatch; ++j, ++i) {
+            float *rc = (i & 1) ? c->bRB : c->bRA;
+            float *rn = (i & 1) ? c->bRA : c->bRB;
+            launch_spmm<MB>(L.A, m, c->bP, c->bQ, nullptr, 0, c->partials, c->bs, 0, st);
+            launch_restrict_b<MB>(L.R, m, c->bU32, rc, rn, c->bP, c->bQ, 0, c->bG, c->bG32,
+                                  c->bZR, c->bUnitPart, c->partials, c->bs, st);
+            launch_coarse_b<MB>(c->Einv32, c->k, m, c->bG32, c->bZR, c->bNU, c->bNU32, 2,
+                                c->partials, c->bs, st);
+            launch_prolong_b<MB>(L.R, m, c->bNU32, rn, c->bP, 0, c->bs, st);
+            c->launches += 4;
+        }
+        CK(cudaMemcpyAsync(&c->h_done[b & 1], &c->bs->done, sizeof(int), cudaMemcpyDeviceToHost,
+                           st));
+        CK(cudaEventRecord(c->evb[b & 1], st));
+        if (b >= 1) {
+            CK(cudaEventSynchronize(c->evb[(b - 1) & 1]));
+            if (c->h_done[(b - 1) & 1] != kRunning) break;
+        }
+    }
+    CK(cudaMemcpyAsync(c->h_bs, c->bs, sizeof(BatchScalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    return XDCG_OK;
+}
+
+template <int MB>
+xdcg_status solve_batch_mixed(xdcg_ctx *c, const double *F, double *U, int m, double tol,
+                              xdcg_result *res) {
+    cudaStream_t st = c->st;
+    Level32 &L = c->L32;
+    const long long n = c->n;
+    double ff[kMaxBatch] = {0}, rn2[kMaxBatch] = {0};
+    int itsAt[kMaxBatch] = {0};
+    xdcg_status s;
+    for (int j = 0; j < m; ++j) {
+        init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
+        launch_dot<double>(F + j * n, F + j * n, n, c->partials, c->aux, kFinStore, 0, st);
+        c->launches += 1;
+        double v[1];
+        if ((s = read_aux(c, v, 1)) != XDCG_OK) return s;
+        ff[j] = rn2[j] = v[0];
+        if (!std::isfinite(ff[j])) return XDCG_BREAKDOWN;
+    }
+    CK(cudaMemsetAsync(U, 0, (size_t)m * n * sizeof(double), st));
+    BatchScalars &hb = *c->h_bs;
+    hb = BatchScalars{};
+    hb.max_it = c->opt.max_iter;
+    int nActive = 0;
+    for (int j = 0; j < m; ++j) {
+        hb.active[j] = ff[j] > 0.0;
+        hb.scale[j] = ff[j] > 0.0 ? 1.0 / std::sqrt(ff[j]) : 0.0;
+        hb.trig[j] = -1.0;
+        nActive += hb.active[j];
+    }
+    for (int j = 0; j < m; ++j) {
+        res[j] = xdcg_result{};
+        res[j].bad_index = -1;
+    }
+    if (nActive == 0) return XDCG_OK;
+    CK(cudaMemcpyAsync(c->bs, c->h_bs, sizeof(BatchScalars), cudaMemcpyHostToDevice, st));
+    // F~ = s_j L^-1 f_j, then Algorithm 2 and the first directions for every column
+    launch_fwd_scale_b<MB>(c->nNodes, m, L.dofStart64, L.dofStart32, L.F, F, n, c->bs, c->bF32,
+                           st);
+    CK(cudaMemsetAsync(c->bU32, 0, (size_t)n * MB * sizeof(float), st));
+    launch_restrict_b<MB>(L.R, m, nullptr, c->bF32, nullptr, nullptr, nullptr, 2, c->bG, c->bG32,
+                          nullptr, c->bUnitPart, c->partials, c->bs, st);
+    launch_coarse_b<MB>(c->Einv32, c->k, m, c->bG32, nullptr, c->bNU, c->bNU32, 0, c->partials,
+                        c->bs, st);
+    launch_prolong_b<MB>(L.R, m, c->bNU32, nullptr, c->bU32, 1, c->bs, st);
+    launch_spmm<MB>(L.A, m, c->bU32, c->bRA, c->bF32, 1, c->partials, c->bs, 1, st);
+    launch_restrict_b<MB>(L.R, m, nullptr, c->bRA, nullptr, nullptr, nullptr, 1, c->bG, c->bG32,
+                          c->bZR, c->bUnitPart, c->partials, c->bs, st);
+    launch_coarse_b<MB>(c->Einv32, c->k, m, c->bG32, c->bZR, c->bNU, c->bNU32, 1, c->partials,
+                        c->bs, st);
+    launch_prolong_b<MB>(L.R, m, c->bNU32, c->bRA, c->bP, 2, c->bs, st);
+    c->launches += 9;
+    CK(cudaMemcpyAsync(c->h_bs, c->bs, sizeof(BatchScalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double delta2 = c->opt.inner_tol * c->opt.inner_tol;
+    for (int j = 0; j < m; ++j) hb.trig[j] = hb.active[j] ? delta2 * hb.rr[j] : -1.0;
+    CK(cudaMemcpyAsync(c->bs, c->h_bs, sizeof(BatchScalars), cudaMemcpyHostToDevice, st));
+    int cycles = 0;
+    xdcg_status status = XDCG_NO_CONVERGENCE;
+    while (true) {
+        if ((s = batch_iterate<MB>(c, m, c->opt.max_iter)) != XDCG_OK) return s;
+        if (hb.done == kFault) return XDCG_TIMEOUT;
+        const int done = hb.done;
+        // fold the FP32 corrections into U and evaluate the true residuals
+        launch_bwd_accum_b<MB>(c->nNodes, m, L.dofStart64, L.dofStart32, L.F, c->bU32, c->bs, U, n,
+                               st);
+        CK(cudaMemsetAsync(c->bU32, 0, (size_t)n * MB * sizeof(float), st));
+        c->launches += 1;
+        cycles++;
+        bool anyBad = false;
+        nActive = 0;
+        for (int j = 0; j < m; ++j) {
+            if (!hb.active[j]) continue;
+            init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
+            launch_spmv<double>(c->L64.A, U + j * n, c->bR64 + j * n, F + j * n, 1, c->partials,
+                                c->aux, kFinStore, 0, st);
+            c->launches += 1;
+            double v[1];
+            if ((s = read_aux(c, v, 1)) != XDCG_OK) return s;
+            rn2[j] = v[0];
+            if (!std::isfinite(rn2[j])) {
+                anyBad = true;
+                hb.active[j] = 0;
+                itsAt[j] = hb.its;
+                res[j].bad_index = j;
+            } else if (rn2[j] <= tol * tol * ff[j]) {
+                hb.active[j] = 0;
+                itsAt[j] = hb.its;
+            } else {
+                nActive++;
+            }
+        }
+        if (nActive == 0) {
+            status = anyBad ? XDCG_BREAKDOWN : XDCG_OK;
+            break;
+        }
+        if (done == kMaxIter || cycles >= c->opt.max_outer) break;
+        // replace the recursive residuals by the scaled true ones and re-arm
+        for (int j = 0; j < m; ++j) {
+            hb.rrRep[j] = hb.rr[j];
+            hb.trig[j] = -1.0;
+        }
+        hb.done = kRunning;
+        CK(cudaMemcpyAsync(c->bs, c->h_bs, sizeof(BatchScalars), cudaMemcpyHostToDevice, st));
+        float *rbuf = (hb.its & 1) ? c->bRB : c->bRA;
+        launch_fwd_scale_b<MB>(c->nNodes, m, L.dofStart64, L.dofStart32, L.F, c->bR64, n, c->bs,
+                               rbuf, st);
+        launch_restrict_b<MB>(L.R, m, nullptr, rbuf, nullptr, nullptr, nullptr, 1, c->bG,
+                              c->bG32, c->bZR, c->bUnitPart, c->partials, c->bs, st);
+        launch_coarse_b<MB>(c->Einv32, c->k, m, c->bG32, c->bZR, c->bNU, c->bNU32, 3, c->partials,
+                            c->bs, st);
+        launch_prolong_b<MB>(L.R, m, c->bNU32, rbuf, c->bP, 0, c->bs, st);
+        c->launches += 4;
+        CK(cudaMemcpyAsync(c->h_bs, c->bs, sizeof(BatchScalars), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int j = 0; j < m; ++j) {
+            if (!hb.active[j]) continue;
+            const double sj = hb.scale[j];
+            const double gamma2 = hb.rr[j] / (sj * sj * rn2[j]);
+            const double floor2 = std::min(0.25 * tol * tol * ff[j] * sj * sj * gamma2,
+                                           kMinGroupDrop2 * hb.rr[j]);
+            hb.trig[j] = std::max(delta2 * hb.rr[j], floor2);
+        }
+        CK(cudaMemcpyAsync(c->bs, c->h_bs, sizeof(BatchScalars), cudaMemcpyHostToDevice, st));
+    }
+    for (int j = 0; j < m; ++j) {
+        res[j].iterations = hb.active[j] ? hb.its : itsAt[j];
+        res[j].outer_cycles = cycles;
+        res[j].rel_res_recursive = std::sqrt(hb.rr[j]);
+        res[j].rel_res_true = ff[j] > 0 ? std::sqrt(rn2[j] / ff[j]) : 0.0;
+    }
+    return status;
+}
+
 xdcg_status do_solve(xdcg_ctx *c, const double *f, double *u, double tol, bool guess,
                      xdcg_result *out) {
     xdcg_result res{};
@@ -614,6 +789,7 @@ void free_ctx(xdcg_ctx *c) {
     for (void *p : c->allocs) cudaFree(p);
     for (void *p : c->temps) cudaFree(p);
     if (c->h_sc) cudaFreeHost(c->h_sc);
+    if (c->h_bs) cudaFreeHost(c->h_bs);
     if (c->h_done) cudaFreeHost(c->h_done);
     for (auto e : c->evS) cudaEventDestroy(e);
     for (auto e : c->evE) cudaEventDestroy(e);
@@ -1278,6 +1454,24 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         c->hist = dalloc<double>(c, (size_t)c->opt.max_iter + 1);
         if (!c->hist) return XDCG_OOM;
     }
+    if (mixed && c->opt.max_batch > 0) {
+        const int MB = c->opt.max_batch <= 4 ? 4 : 8;
+        c->bMB = MB;
+        const size_t nv = (size_t)n * MB, kv = (size_t)std::max(k, 1) * MB;
+        c->bF32 = dalloc<float>(c, nv); c->bU32 = dalloc<float>(c, nv);
+        c->bRA = dalloc<float>(c, nv); c->bRB = dalloc<float>(c, nv);
+        c->bP = dalloc<float>(c, nv); c->bQ = dalloc<float>(c, nv);
+        c->bG32 = dalloc<float>(c, kv); c->bNU32 = dalloc<float>(c, kv);
+        c->bG = dalloc<double>(c, kv); c->bZR = dalloc<double>(c, kv); c->bNU = dalloc<double>(c, kv);
+        c->bUnitPart = dalloc<double>(c, (size_t)c->L32.R.nUnits * MB * 24);
+        c->bR64 = dalloc<double>(c, (size_t)n * MB);
+        c->bs = dalloc<BatchScalars>(c, 1);
+        if (!c->bF32 || !c->bU32 || !c->bRA || !c->bRB || !c->bP || !c->bQ || !c->bG32 ||
+            !c->bNU32 || !c->bG || !c->bZR || !c->bNU || !c->bUnitPart || !c->bR64 || !c->bs)
+            return XDCG_OOM;
+        if (cudaMallocHost(&c->h_bs, sizeof(BatchScalars)) != cudaSuccess) return XDCG_OOM;
+        if (!spmm_prepare()) return XDCG_CUDA_ERROR;
+    }
     if (!c->u64 || !c->r64 || !c->p64 || !c->q64 || !c->y64 || !c->f64 || !c->uh64 || !c->g ||
         !c->zr || !c->nu || !c->nu32 || !c->partials || !c->sc || !c->sc32 || !c->aux)
         return XDCG_OOM;
@@ -1347,6 +1541,7 @@ xdcg_status xdcg_default_options(xdcg_options *opt) {
     opt->time_spmv = 0;
     opt->jacobi = XDCG_BLOCK_JACOBI;
     opt->record_history = 0;
+    opt->max_batch = 0;
     return XDCG_OK;
 }
 
@@ -1367,6 +1562,7 @@ xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflatio
         (c->opt.precision != XDCG_FP64 && c->opt.precision != XDCG_MIXED) ||
         c->opt.time_spmv < 0 || c->opt.time_spmv > 2 ||
         (c->opt.jacobi != XDCG_BLOCK_JACOBI && c->opt.jacobi != XDCG_POINT_JACOBI) ||
+        c->opt.max_batch < 0 || c->opt.max_batch > kMaxBatch ||
         !(c->opt.inner_tol > 0 && c->opt.inner_tol < 1)) {
         delete c;
         return XDCG_INVALID_ARG;
@@ -1396,6 +1592,41 @@ xdcg_status xdcg_solve(xdcg_ctx *c, const double *f, double *u, double tol, xdcg
 xdcg_status xdcg_solve_x0(xdcg_ctx *c, const double *f, double *u, double tol, xdcg_result *res) {
     if (!c || !f || !u || f == u) return XDCG_INVALID_ARG;
     return do_solve(c, f, u, tol, true, res);
+}
+
+xdcg_status xdcg_solve_batch(xdcg_ctx *c, const double *F, double *U, int32_t m, double tol,
+                             xdcg_result *res) {
+    if (!c || !F || !U || F == U || m < 1) return XDCG_INVALID_ARG;
+    if (tol <= 0) tol = c->opt.tol;
+    xdcg_result local[kMaxBatch];
+    if (c->bMB == 0) {
+        // no batched run on this context: the columns one after another
+        xdcg_status worst = XDCG_OK;
+        for (int j = 0; j < m; ++j) {
+            xdcg_result r1{};
+            xdcg_status s = do_solve(c, F + (size_t)j * c->n, U + (size_t)j * c->n, tol, false, &r1);
+            if (s == XDCG_CUDA_ERROR || s == XDCG_TIMEOUT) return s;
+            if (s != XDCG_OK) worst = s;
+            if (res) res[j] = r1;
+        }
+        return worst;
+    }
+    if (m > c->opt.max_batch) return XDCG_INVALID_ARG;
+    const long long l0 = c->launches;
+    CK(cudaEventRecord(c->ev0, c->st));
+    xdcg_status s = c->bMB == 4 ? solve_batch_mixed<4>(c, F, U, m, tol, local)
+                                : solve_batch_mixed<8>(c, F, U, m, tol, local);
+    if (s == XDCG_CUDA_ERROR) return s;
+    CK(cudaEventRecord(c->ev1, c->st));
+    CK(cudaEventSynchronize(c->ev1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    for (int j = 0; j < m; ++j) {
+        local[j].t_solve_ms = ms;
+        local[j].n_launches = c->launches - l0;
+        if (res) res[j] = local[j];
+    }
+    return s;
 }
 
 xdcg_status xdcg_solve_host(xdcg_ctx *c, const double *f_host, double *u_host, double tol,

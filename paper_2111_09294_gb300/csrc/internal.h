@@ -70,6 +70,23 @@ constexpr int kTprS = 2;
 constexpr int kTprX = 16;
 constexpr int kXBucket = 8;     // X rows are grouped by len / kXBucket
 
+// ---- batched FP32 iteration (several right-hand sides of one system) ------
+
+constexpr int kMaxBatch = 8;   // right-hand sides per batched solve
+
+// Scalars of a batched FP32 run; column j of every vector is right-hand side j
+// (vectors interleaved: entry (dof d, column j) at d * MB + j).
+struct BatchScalars {
+    double rho[kMaxBatch], pq[kMaxBatch], alpha[kMaxBatch], beta[kMaxBatch], rr[kMaxBatch];
+    double trig[kMaxBatch];     // a replacement is requested once rr_j <= trig_j
+    double rrRep[kMaxBatch];    // rr_j before the last replacement (restart test)
+    double scale[kMaxBatch];    // per-column scale of the FP64 <-> FP32 transforms
+    int active[kMaxBatch];      // 1 while column j iterates
+    int broken[kMaxBatch];      // p_j^T K p_j <= 0 seen (restart at the replacement)
+    int its, done, max_it, fault;
+    unsigned int ticket[4];
+};
+
 template <typename T>
 struct SpmvDev {
     SellDev<T> S, X;
@@ -250,5 +267,31 @@ void launch_scale_blocks(const KinDev &K, const int *blockRow, long long nnzb, c
 void launch_scale_W(int nExt, const int *extBox, const int *extNode, const long long *wOff,
                     const int *menr, const int *dofStart, const FacDev &F, const double *W,
                     float *Wt, cudaStream_t st);
+
+// batched FP32 iteration (batch.cu); MB = 4 or 8
+template <int MB>
+void launch_spmm(const SpmvDev<float> &A, int m, const float *x, float *y, const float *b,
+                 int residual_mode, double *partials, BatchScalars *bs, int fin, cudaStream_t st);
+bool spmm_prepare();
+template <int MB>
+void launch_restrict_b(const RowBoxDev &B, int m, float *u, const float *r_cur, float *r_next,
+                       const float *p, const float *q, int mode, double *G, float *G32,
+                       double *ZR, double *unitPart, double *partials, BatchScalars *bs,
+                       cudaStream_t st);
+template <int MB>
+void launch_coarse_b(const float *Einv, int k, int m, const float *G32, const double *ZR,
+                     double *NU, float *NU32, int mode, double *partials, BatchScalars *bs,
+                     cudaStream_t st);
+template <int MB>
+void launch_prolong_b(const RowBoxDev &B, int m, const float *NU32, const float *y, float *p,
+                      int mode, const BatchScalars *bs, cudaStream_t st);
+template <int MB>
+void launch_fwd_scale_b(int nNodes, int m, const int *nat, const int *ot, const FacDev &F,
+                        const double *r, long long ldr, const BatchScalars *bs, float *out,
+                        cudaStream_t st);
+template <int MB>
+void launch_bwd_accum_b(int nNodes, int m, const int *nat, const int *in, const FacDev &F,
+                        const float *ut, const BatchScalars *bs, double *u, long long ldu,
+                        cudaStream_t st);
 
 }  // namespace xdcg

@@ -29,7 +29,7 @@ class Solver:
     def __init__(self, dof_ptr, row_ptr, col, val_ptr, val, sub_of_node, coords, hsign, centres,
                  precision="fp64", tol=1e-8, max_iter=10000, inner_tol=1e-3, max_outer=30,
                  time_spmv=False, enriched_modes=True, stream=None, jacobi="block",
-                 record_history=False):
+                 record_history=False, max_batch=0):
         lib = L.load()
         self._lib = lib
         self.ctx = ctypes.c_void_p()
@@ -55,6 +55,7 @@ class Solver:
             raise ValueError("jacobi must be 'block' or 'point'")
         opt.jacobi = L.XDCG_POINT_JACOBI if jacobi == "point" else L.XDCG_BLOCK_JACOBI
         opt.record_history = int(bool(record_history))
+        opt.max_batch = int(max_batch)
         self.precision = precision
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -99,6 +100,26 @@ class Solver:
         if raise_on_error:
             L.check(s, "xdcg_solve", res.bad_index)
         return u, info
+
+    def solve_batch(self, F, tol=0.0, out=None, raise_on_error=True):
+        """U with K U_j = F_j for the rows F_j of F ((m, n) contiguous CUDA float64);
+        mixed contexts with max_batch >= m run them as one batched FP32 iteration.
+        Returns (U, list of per-column info dicts)."""
+        if not (F.is_cuda and F.dtype == torch.float64 and F.is_contiguous() and F.dim() == 2
+                and F.shape[1] == self.n):
+            raise ValueError(f"expected a contiguous (m, {self.n}) CUDA float64 tensor")
+        m = F.shape[0]
+        U = out if out is not None else torch.empty_like(F)
+        res = (L.Result * m)()
+        s = self._lib.xdcg_solve_batch(self.ctx, ctypes.c_void_p(F.data_ptr()),
+                                       ctypes.c_void_p(U.data_ptr()), m, float(tol),
+                                       ctypes.cast(res, ctypes.c_void_p))
+        infos = [r.as_dict() for r in res]
+        for i in infos:
+            i["status"] = L.STATUS.get(s, s)
+        if raise_on_error:
+            L.check(s, "xdcg_solve_batch")
+        return U, infos
 
     def history(self):
         """||r_i|| / ||f||, i = 0 .. iterations, of the last FP64 solve."""

@@ -179,3 +179,52 @@ def test_adjoint_gradient_matches_oracle_and_differences():
     an = float(np.dot(lam, v.cpu().numpy()))
     assert abs(fd - an) <= 1e-6 * abs(an)
     s.close()
+
+
+# ---- several load cases of one crack configuration in one batched run
+
+
+@pytest.mark.parametrize("name,m", [("cube8_edge", 3), ("cube24_ellipse", 8)])
+def test_batched_mixed_solve_matches_oracle(name, m):
+    # each column of the batched FP32 run (shared reads of K~, Z~, W~, E^-1)
+    # must meet the tolerance on the FP64 true residual and agree with the
+    # oracle's solve of the same load case as the single mixed solve does
+    dev = _cuda()
+    P, K, M, C = problem(name)
+    F = X.load_cases(P, m, seed=5)
+    s = _solver(P, precision="mixed", max_batch=m)
+    U, infos = s.solve_batch(torch.tensor(F, device=dev), tol=1e-12)
+    Un = U.cpu().numpy()
+    for j in range(m):
+        ref = O.adef2_pcg(K, F[j], M, C, tol=1e-12)
+        rel = np.linalg.norm(F[j] - K @ Un[j]) / np.linalg.norm(F[j])
+        assert rel <= 1.05e-12, (j, rel)
+        assert infos[j]["rel_res_true"] <= 1e-12
+        err = np.linalg.norm(Un[j] - ref.u) / np.linalg.norm(ref.u)
+        assert err <= 1e-7, (j, err)
+    s.close()
+
+
+def test_batched_columns_converge_independently():
+    # a zero column and a column that is the first one scaled: the zero column
+    # returns 0 without iterating; the scaled one returns the scaled solution
+    dev = _cuda()
+    P, K, M, C = problem("cube8_edge")
+    F = X.load_cases(P, 3, seed=7)
+    F[1] = 0.0
+    F[2] = 1e3 * F[0]
+    s = _solver(P, precision="mixed", max_batch=4)
+    U, infos = s.solve_batch(torch.tensor(F, device=dev), tol=1e-10)
+    Un = U.cpu().numpy()
+    assert np.all(Un[1] == 0.0) and infos[1]["iterations"] == 0
+    assert np.linalg.norm(Un[2] - 1e3 * Un[0]) <= 1e-8 * np.linalg.norm(Un[2])
+    for j in (0, 2):
+        assert infos[j]["rel_res_true"] <= 1e-10
+    # the FP64 path solves the columns one after another, same answers
+    s64 = _solver(P)
+    U64, infos64 = s64.solve_batch(torch.tensor(F, device=dev), tol=1e-10)
+    for j in (0, 2):
+        err = np.linalg.norm(U64.cpu().numpy()[j] - Un[j]) / np.linalg.norm(Un[j])
+        assert err <= 1e-7
+    s.close()
+    s64.close()

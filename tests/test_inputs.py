@@ -166,3 +166,20 @@ def test_stiffness_is_symmetric_and_definite():
     K = X.to_dense(P)
     assert np.max(np.abs(K - K.T)) <= 1e-14 * np.max(np.abs(K))
     np.linalg.cholesky(K)
+
+
+def test_load_cases_are_linear_in_the_traction():
+    # the unit-tension case reproduces the workload's own load, and the loads
+    # add up as the tractions do (consistent nodal forces are linear in t)
+    P = X.make("cube8_edge")
+    F = X.load_cases(P, 4, seed=3)
+    t = X.tractions(4, seed=3)
+    assert F.shape == (4, P.n)
+    w = X.face_weights(P)
+    assert np.isclose(w.sum(), 1.0)            # the loaded face has unit area
+    for c in range(4):
+        total = F[c].reshape(-1)
+        dof = np.asarray(P.dof_ptr)
+        for d in range(3):
+            assert np.isclose(total[dof[:-1] + d].sum(), t[c, d])
+    assert np.all((0.5 <= np.abs(t)) & (np.abs(t) <= 1.5)) and np.all(t[:, 2] > 0)

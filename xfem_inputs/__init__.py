@@ -1,3 +1,4 @@
 """Seeded synthetic XFEM crack systems: the inputs shared by the oracle and the GPU harness."""
 from .assemble import (KIND_HEAVISIDE, KIND_STD, KIND_TIP, Problem, build_problem, to_dense)
 from .configs import CONFIGS, make
+from .loads import face_weights, load_cases, tractions
