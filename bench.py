@@ -381,16 +381,32 @@ def run_profile(args):
     import xfem_inputs as X
     from paper_2111_09294_gb300 import Solver
     P = X.make(args.workload)
-    s = Solver.from_problem(P, precision=args.profile, inner_tol=args.inner_tol)
-    f = torch.tensor(P.f, device="cuda")
-    u = torch.empty_like(f)
-    for _ in range(max(args.warmup, 1)):
-        s.solve(f, tol=TOL, out=u)
-    torch.cuda.synchronize()
-    torch.cuda.profiler.start()
-    _, info = s.solve(f, tol=TOL, out=u)
-    torch.cuda.synchronize()
-    torch.cuda.profiler.stop()
+    if args.profile == "batch":
+        # the batched solve of args.batch seeded load cases
+        s = Solver.from_problem(P, precision="mixed", inner_tol=args.inner_tol,
+                                max_batch=args.batch)
+        F = torch.tensor(X.load_cases(P, args.batch, seed=0), device="cuda")
+        U = torch.empty_like(F)
+        for _ in range(max(args.warmup, 1)):
+            s.solve_batch(F, tol=TOL, out=U)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        _, infos = s.solve_batch(F, tol=TOL, out=U)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        info = infos[0]
+        info["iterations"] = max(i["iterations"] for i in infos)
+    else:
+        s = Solver.from_problem(P, precision=args.profile, inner_tol=args.inner_tol)
+        f = torch.tensor(P.f, device="cuda")
+        u = torch.empty_like(f)
+        for _ in range(max(args.warmup, 1)):
+            s.solve(f, tol=TOL, out=u)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        _, info = s.solve(f, tol=TOL, out=u)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     print(json.dumps({"profile": args.profile, "iterations": info["iterations"],
                       "outer_cycles": info["outer_cycles"], "launches": info["n_launches"],
                       "t_solve_ms": info["t_solve_ms"], "info": s.info}))
@@ -408,7 +424,7 @@ def main():
                     help="load cases of the batched-solve measurement (0: skip)")
     ap.add_argument("--sample-iters", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", choices=["mixed", "fp64"], default=None,
+    ap.add_argument("--profile", choices=["mixed", "fp64", "batch"], default=None,
                     help="profiler capture: one solve of the given path between "
                          "cudaProfilerStart/Stop after warm-up, nothing else timed")
     args = ap.parse_args()

@@ -28,6 +28,7 @@ struct Level64 {
 struct Level32 {          // block-scaled system K~ = L^-1 K L^-T in FP32
     SpmvDev<float> A;
     RowBoxDev R;
+    RowBoxDev Rb;            // the same boxes with the batched kernels' unit tables
     FacDev F;
     const int *dofStart64;    // [nNodes + 1] node dofs in the FP64 (caller's) numbering
     const int *dofStart32;    // [nNodes + 1] node dofs in the box-major FP32 numbering
@@ -610,11 +611,11 @@ xdcg_status batch_iterate(xdcg_ctx *c, int m, int max_it) {
             float *rc = (i & 1) ? c->bRB : c->bRA;
             float *rn = (i & 1) ? c->bRA : c->bRB;
             launch_spmm<MB>(L.A, m, c->bP, c->bQ, nullptr, 0, c->partials, c->bs, 0, st);
-            launch_restrict_b<MB>(L.R, m, c->bU32, rc, rn, c->bP, c->bQ, 0, c->bG, c->bG32,
+            launch_restrict_b<MB>(L.Rb, m, c->bU32, rc, rn, c->bP, c->bQ, 0, c->bG, c->bG32,
                                   c->bZR, c->bUnitPart, c->partials, c->bs, st);
             launch_coarse_b<MB>(c->Einv32, c->k, m, c->bG32, c->bZR, c->bNU, c->bNU32, 2,
                                 c->partials, c->bs, st);
-            launch_prolong_b<MB>(L.R, m, c->bNU32, rn, c->bP, 0, c->bs, st);
+            launch_prolong_b<MB>(L.Rb, m, c->bNU32, rn, c->bP, 0, c->bs, st);
             c->launches += 4;
         }
         CK(cudaMemcpyAsync(&c->h_done[b & 1], &c->bs->done, sizeof(int), cudaMemcpyDeviceToHost,
@@ -656,6 +657,7 @@ xdcg_status solve_batch_mixed(xdcg_ctx *c, const double *F, double *U, int m, do
     int nActive = 0;
     for (int j = 0; j < m; ++j) {
         hb.active[j] = ff[j] > 0.0;
+        hb.repl[j] = 1;
         hb.scale[j] = ff[j] > 0.0 ? 1.0 / std::sqrt(ff[j]) : 0.0;
         hb.trig[j] = -1.0;
         nActive += hb.active[j];
@@ -670,39 +672,54 @@ xdcg_status solve_batch_mixed(xdcg_ctx *c, const double *F, double *U, int m, do
     launch_fwd_scale_b<MB>(c->nNodes, m, L.dofStart64, L.dofStart32, L.F, F, n, c->bs, c->bF32,
                            st);
     CK(cudaMemsetAsync(c->bU32, 0, (size_t)n * MB * sizeof(float), st));
-    launch_restrict_b<MB>(L.R, m, nullptr, c->bF32, nullptr, nullptr, nullptr, 2, c->bG, c->bG32,
-                          nullptr, c->bUnitPart, c->partials, c->bs, st);
+    launch_restrict_b<MB>(L.Rb, m, nullptr, c->bF32, nullptr, nullptr, nullptr, 2, c->bG,
+                          c->bG32, nullptr, c->bUnitPart, c->partials, c->bs, st);
     launch_coarse_b<MB>(c->Einv32, c->k, m, c->bG32, nullptr, c->bNU, c->bNU32, 0, c->partials,
                         c->bs, st);
-    launch_prolong_b<MB>(L.R, m, c->bNU32, nullptr, c->bU32, 1, c->bs, st);
+    launch_prolong_b<MB>(L.Rb, m, c->bNU32, nullptr, c->bU32, 1, c->bs, st);
     launch_spmm<MB>(L.A, m, c->bU32, c->bRA, c->bF32, 1, c->partials, c->bs, 1, st);
-    launch_restrict_b<MB>(L.R, m, nullptr, c->bRA, nullptr, nullptr, nullptr, 1, c->bG, c->bG32,
-                          c->bZR, c->bUnitPart, c->partials, c->bs, st);
+    launch_restrict_b<MB>(L.Rb, m, nullptr, c->bRA, nullptr, nullptr, nullptr, 1, c->bG,
+                          c->bG32, c->bZR, c->bUnitPart, c->partials, c->bs, st);
     launch_coarse_b<MB>(c->Einv32, c->k, m, c->bG32, c->bZR, c->bNU, c->bNU32, 1, c->partials,
                         c->bs, st);
-    launch_prolong_b<MB>(L.R, m, c->bNU32, c->bRA, c->bP, 2, c->bs, st);
+    launch_prolong_b<MB>(L.Rb, m, c->bNU32, c->bRA, c->bP, 2, c->bs, st);
     c->launches += 9;
     CK(cudaMemcpyAsync(c->h_bs, c->bs, sizeof(BatchScalars), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     const double delta2 = c->opt.inner_tol * c->opt.inner_tol;
     for (int j = 0; j < m; ++j) hb.trig[j] = hb.active[j] ? delta2 * hb.rr[j] : -1.0;
     CK(cudaMemcpyAsync(c->bs, c->h_bs, sizeof(BatchScalars), cudaMemcpyHostToDevice, st));
-    int cycles = 0;
+    int passes = 0, cycles[kMaxBatch] = {0};
     xdcg_status status = XDCG_NO_CONVERGENCE;
+    bool anyBad = false;
     while (true) {
         if ((s = batch_iterate<MB>(c, m, c->opt.max_iter)) != XDCG_OK) return s;
         if (hb.done == kFault) return XDCG_TIMEOUT;
-        const int done = hb.done;
-        // fold the FP32 corrections into U and evaluate the true residuals
+        const bool last = hb.done == kMaxIter || passes + 1 >= c->opt.max_outer;
+        // which columns are replaced now: those at their trigger or not finite
+        // (all of them at the end, or after a breakdown, which stops the
+        // iteration before its residual update); the others finish the
+        // interrupted iteration and keep going
+        bool anyBroken = false;
+        for (int j = 0; j < m; ++j) anyBroken |= hb.active[j] && hb.broken[j];
+        for (int j = 0; j < m; ++j)
+            hb.repl[j] = hb.active[j] && (last || anyBroken || hb.rr[j] <= hb.trig[j] ||
+                                          !std::isfinite(hb.rr[j]));
+        // fold the FP32 corrections of every active column into U (exact for the
+        // columns that continue too: their recursion now refers to the new U)
         launch_bwd_accum_b<MB>(c->nNodes, m, L.dofStart64, L.dofStart32, L.F, c->bU32, c->bs, U, n,
                                st);
         CK(cudaMemsetAsync(c->bU32, 0, (size_t)n * MB * sizeof(float), st));
         c->launches += 1;
-        cycles++;
-        bool anyBad = false;
+        passes++;
         nActive = 0;
         for (int j = 0; j < m; ++j) {
             if (!hb.active[j]) continue;
+            if (!hb.repl[j]) {
+                nActive++;
+                continue;
+            }
+            cycles[j]++;
             init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
             launch_spmv<double>(c->L64.A, U + j * n, c->bR64 + j * n, F + j * n, 1, c->partials,
                                 c->aux, kFinStore, 0, st);
@@ -726,27 +743,29 @@ xdcg_status solve_batch_mixed(xdcg_ctx *c, const double *F, double *U, int m, do
             status = anyBad ? XDCG_BREAKDOWN : XDCG_OK;
             break;
         }
-        if (done == kMaxIter || cycles >= c->opt.max_outer) break;
-        // replace the recursive residuals by the scaled true ones and re-arm
-        for (int j = 0; j < m; ++j) {
-            hb.rrRep[j] = hb.rr[j];
-            hb.trig[j] = -1.0;
-        }
+        if (last) break;
+        // replace the recursive residuals of the replaced columns by their scaled
+        // true ones (zero for the columns that just left) and re-arm
+        for (int j = 0; j < m; ++j)
+            if (hb.repl[j]) {
+                hb.rrRep[j] = hb.rr[j];
+                hb.trig[j] = -1.0;
+            }
         hb.done = kRunning;
         CK(cudaMemcpyAsync(c->bs, c->h_bs, sizeof(BatchScalars), cudaMemcpyHostToDevice, st));
         float *rbuf = (hb.its & 1) ? c->bRB : c->bRA;
         launch_fwd_scale_b<MB>(c->nNodes, m, L.dofStart64, L.dofStart32, L.F, c->bR64, n, c->bs,
                                rbuf, st);
-        launch_restrict_b<MB>(L.R, m, nullptr, rbuf, nullptr, nullptr, nullptr, 1, c->bG,
+        launch_restrict_b<MB>(L.Rb, m, nullptr, rbuf, nullptr, nullptr, nullptr, 1, c->bG,
                               c->bG32, c->bZR, c->bUnitPart, c->partials, c->bs, st);
         launch_coarse_b<MB>(c->Einv32, c->k, m, c->bG32, c->bZR, c->bNU, c->bNU32, 3, c->partials,
                             c->bs, st);
-        launch_prolong_b<MB>(L.R, m, c->bNU32, rbuf, c->bP, 0, c->bs, st);
+        launch_prolong_b<MB>(L.Rb, m, c->bNU32, rbuf, c->bP, 0, c->bs, st);
         c->launches += 4;
         CK(cudaMemcpyAsync(c->h_bs, c->bs, sizeof(BatchScalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         for (int j = 0; j < m; ++j) {
-            if (!hb.active[j]) continue;
+            if (!hb.active[j] || !hb.repl[j]) continue;
             const double sj = hb.scale[j];
             const double gamma2 = hb.rr[j] / (sj * sj * rn2[j]);
             const double floor2 = std::min(0.25 * tol * tol * ff[j] * sj * sj * gamma2,
@@ -757,7 +776,7 @@ xdcg_status solve_batch_mixed(xdcg_ctx *c, const double *F, double *U, int m, do
     }
     for (int j = 0; j < m; ++j) {
         res[j].iterations = hb.active[j] ? hb.its : itsAt[j];
-        res[j].outer_cycles = cycles;
+        res[j].outer_cycles = cycles[j];
         res[j].rel_res_recursive = std::sqrt(hb.rr[j]);
         res[j].rel_res_true = ff[j] > 0 ? std::sqrt(rn2[j] / ff[j]) : 0.0;
     }
@@ -1376,48 +1395,52 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
             !R.wBase || !Zcm || !Wcm || !d_ownSub || !d_ors || !d_ers)
             return XDCG_OOM;
         // balanced restriction units: each box's own rows followed by its coupled
-        // rows, cut into ceil(total / kUnitRows) nearly equal pieces
-        std::vector<int> unitBox, uOb, uOe, uEb, uEe, boxUnit(S + 1, 0);
-        for (int sb2 = 0; sb2 < S; ++sb2) {
-            boxUnit[sb2] = (int)unitBox.size();
-            const long long nOwn = ownRowPtr[sb2 + 1] - ownRowPtr[sb2];
-            const long long nCpl = extRowPtr[sb2 + 1] - extRowPtr[sb2];
-            const long long T = nOwn + nCpl;
-            const long long nu = std::max<long long>(1, (T + kUnitRows - 1) / kUnitRows);
-            for (long long j = 0; j < nu; ++j) {
-                const long long a0 = T * j / nu, a1 = T * (j + 1) / nu;   // [a0, a1) of own|coupled
-                unitBox.push_back(sb2);
-                uOb.push_back(ownRowPtr[sb2] + (int)std::min(a0, nOwn));
-                uOe.push_back(ownRowPtr[sb2] + (int)std::min(a1, nOwn));
-                uEb.push_back(extRowPtr[sb2] + (int)(std::max(a0, nOwn) - nOwn));
-                uEe.push_back(extRowPtr[sb2] + (int)(std::max(a1, nOwn) - nOwn));
+        // rows, cut into ceil(total / unitRows) nearly equal pieces; prolongation
+        // units: each box's own rows in pieces of at most pRows
+        auto build_units = [&](RowBoxDev &T, int unitRows, int pRows) -> bool {
+            std::vector<int> unitBox, uOb, uOe, uEb, uEe, boxUnit(S + 1, 0);
+            for (int sb2 = 0; sb2 < S; ++sb2) {
+                boxUnit[sb2] = (int)unitBox.size();
+                const long long nOwn = ownRowPtr[sb2 + 1] - ownRowPtr[sb2];
+                const long long nCpl = extRowPtr[sb2 + 1] - extRowPtr[sb2];
+                const long long Tr = nOwn + nCpl;
+                const long long nu = std::max<long long>(1, (Tr + unitRows - 1) / unitRows);
+                for (long long j = 0; j < nu; ++j) {
+                    const long long a0 = Tr * j / nu, a1 = Tr * (j + 1) / nu;   // [a0, a1)
+                    unitBox.push_back(sb2);
+                    uOb.push_back(ownRowPtr[sb2] + (int)std::min(a0, nOwn));
+                    uOe.push_back(ownRowPtr[sb2] + (int)std::min(a1, nOwn));
+                    uEb.push_back(extRowPtr[sb2] + (int)(std::max(a0, nOwn) - nOwn));
+                    uEe.push_back(extRowPtr[sb2] + (int)(std::max(a1, nOwn) - nOwn));
+                }
             }
-        }
-        boxUnit[S] = (int)unitBox.size();
-        R.nUnits = (int)unitBox.size();
-        R.unitBox = upload(c, unitBox);
-        R.unitOwnBegin = upload(c, uOb);
-        R.unitOwnEnd = upload(c, uOe);
-        R.unitExtBegin = upload(c, uEb);
-        R.unitExtEnd = upload(c, uEe);
-        R.boxUnit = upload(c, boxUnit);
-        std::vector<int> pBox, pBegin, pEnd;
-        for (int sb2 = 0; sb2 < S; ++sb2)
-            for (int rb = ownRowPtr[sb2]; rb < ownRowPtr[sb2 + 1]; rb += kProlongRows) {
-                pBox.push_back(sb2);
-                pBegin.push_back(rb);
-                pEnd.push_back(std::min(ownRowPtr[sb2 + 1], rb + kProlongRows));
-            }
-        R.nPUnits = (int)pBox.size();
-        R.pUnitBox = upload(c, pBox);
-        R.pUnitBegin = upload(c, pBegin);
-        R.pUnitEnd = upload(c, pEnd);
-        if (!R.pUnitBox || !R.pUnitBegin || !R.pUnitEnd || R.nPUnits == 0) return XDCG_OOM;
+            boxUnit[S] = (int)unitBox.size();
+            T.nUnits = (int)unitBox.size();
+            T.unitBox = upload(c, unitBox);
+            T.unitOwnBegin = upload(c, uOb);
+            T.unitOwnEnd = upload(c, uOe);
+            T.unitExtBegin = upload(c, uEb);
+            T.unitExtEnd = upload(c, uEe);
+            T.boxUnit = upload(c, boxUnit);
+            std::vector<int> pBox, pBegin, pEnd;
+            for (int sb2 = 0; sb2 < S; ++sb2)
+                for (int rb = ownRowPtr[sb2]; rb < ownRowPtr[sb2 + 1]; rb += pRows) {
+                    pBox.push_back(sb2);
+                    pBegin.push_back(rb);
+                    pEnd.push_back(std::min(ownRowPtr[sb2 + 1], rb + pRows));
+                }
+            T.nPUnits = (int)pBox.size();
+            T.pUnitBox = upload(c, pBox);
+            T.pUnitBegin = upload(c, pBegin);
+            T.pUnitEnd = upload(c, pEnd);
+            return T.unitBox && T.unitOwnBegin && T.unitOwnEnd && T.unitExtBegin &&
+                   T.unitExtEnd && T.boxUnit && T.pUnitBox && T.pUnitBegin && T.pUnitEnd &&
+                   T.nPUnits > 0 && T.nUnits <= kMaxGrid;
+        };
+        if (!build_units(R, kUnitRows, kProlongRows)) return XDCG_OOM;
         R.unitPart = dalloc<double>(c, 24 * (size_t)R.nUnits);
         R.boxTicket = dalloc<unsigned int>(c, S);
-        if (!R.unitBox || !R.unitOwnBegin || !R.unitOwnEnd || !R.unitExtBegin || !R.unitExtEnd ||
-            !R.boxUnit || !R.unitPart || !R.boxTicket || R.nUnits > kMaxGrid)
-            return XDCG_OOM;
+        if (!R.unitPart || !R.boxTicket) return XDCG_OOM;
         CK(cudaMemsetAsync(R.boxTicket, 0, S * sizeof(unsigned int), st));
         launch_to_colmajor(N, d_ownSub, d_ors, d_ownB, d_zOff, R.ownRowPtr, R.zBase, d_menr, d_Zt,
                            Zcm, st);
@@ -1425,6 +1448,12 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
                            d_Wt, Wcm, st);
         R.Z = Zcm;
         R.W = Wcm;
+        if (c->opt.max_batch > 0) {
+            // the batched kernels give each row MB threads: smaller units keep as
+            // many rows in flight per block as the single-column kernels have
+            c->L32.Rb = R;
+            if (!build_units(c->L32.Rb, kUnitRowsBatch, kProlongRowsBatch)) return XDCG_OOM;
+        }
         c->L32.dofStart64 = d_dof;
         c->L32.dofStart32 = d_dof32;
     }
@@ -1463,7 +1492,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         c->bP = dalloc<float>(c, nv); c->bQ = dalloc<float>(c, nv);
         c->bG32 = dalloc<float>(c, kv); c->bNU32 = dalloc<float>(c, kv);
         c->bG = dalloc<double>(c, kv); c->bZR = dalloc<double>(c, kv); c->bNU = dalloc<double>(c, kv);
-        c->bUnitPart = dalloc<double>(c, (size_t)c->L32.R.nUnits * MB * 24);
+        c->bUnitPart = dalloc<double>(c, (size_t)c->L32.Rb.nUnits * MB * 24);
         c->bR64 = dalloc<double>(c, (size_t)n * MB);
         c->bs = dalloc<BatchScalars>(c, 1);
         if (!c->bF32 || !c->bU32 || !c->bRA || !c->bRB || !c->bP || !c->bQ || !c->bG32 ||

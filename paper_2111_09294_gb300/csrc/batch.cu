@@ -425,13 +425,17 @@ void launch_restrict_b(const RowBoxDev &B, int m, float *u, const float *r_cur, 
 
 // ---- batched coarse solve NU = E^-1 G -----------------------------------------
 
-constexpr int kCoarseChunkB = 256;
+constexpr int kCoarseChunkB = 1024;
 
 // mode 0: nothing else; mode 1: rho_j = rr_j + nu_j^T zr_j, beta_j = 0; mode 2:
-// the same rho_new, beta_j = rho_new / rho_j; mode 3: as 2 after a replacement,
-// beta_j = 0 where the replacement lengthened the residual by more than 2x or
-// the column broke down.  Inactive columns get beta = 0.
-template <int MB>
+// the same rho_new, beta_j = rho_new / rho_j; mode 3 (after a replacement): as
+// 2, with beta_j = 0 for a replaced column whose residual the replacement
+// lengthened by more than 2x or that broke down (the other columns finish the
+// iteration the trigger interrupted, as in mode 2).  Inactive columns get
+// beta = 0.  One warp per row of
+// E^-1 (16-byte loads when k is a multiple of 4); G staged in shared memory
+// chunk by chunk.
+template <int MB, int V>
 __global__ void __launch_bounds__(kThreads)
 k_coarse_b(const float *__restrict__ Einv, int k, int m, const float *__restrict__ G32,
            const double *__restrict__ ZR, double *NU, float *NU32, int mode, double *partials,
@@ -451,7 +455,27 @@ k_coarse_b(const float *__restrict__ Einv, int k, int m, const float *__restrict
         __syncthreads();
         for (int e = threadIdx.x; e < len * MB; e += blockDim.x) gs[e] = G32[(size_t)l0 * MB + e];
         __syncthreads();
-        if (i < k) {
+        if (i >= k) continue;
+        if (V == 4) {
+            const float4 *r4 = reinterpret_cast<const float4 *>(row + l0);
+#pragma unroll 4
+            for (int l4 = lane; 4 * l4 < len; l4 += 32) {
+                const float4 ev = ld_keep(r4 + l4, keep);
+                const float e4[4] = {ev.x, ev.y, ev.z, ev.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const float4 *g4 = reinterpret_cast<const float4 *>(gs + (4 * l4 + t) * MB);
+#pragma unroll
+                    for (int q = 0; q < MB / 4; ++q) {
+                        const float4 g = g4[q];
+                        acc[4 * q] = fmaf(e4[t], g.x, acc[4 * q]);
+                        acc[4 * q + 1] = fmaf(e4[t], g.y, acc[4 * q + 1]);
+                        acc[4 * q + 2] = fmaf(e4[t], g.z, acc[4 * q + 2]);
+                        acc[4 * q + 3] = fmaf(e4[t], g.w, acc[4 * q + 3]);
+                    }
+                }
+            }
+        } else {
 #pragma unroll 4
             for (int l = lane; l < len; l += 32) {
                 const float ev = ld_keep(row + l0 + l, keep);
@@ -483,17 +507,18 @@ k_coarse_b(const float *__restrict__ Einv, int k, int m, const float *__restrict
     if (grid_sum<double, MB>(part, partials, &bs->ticket[3], tot) && threadIdx.x == 0 &&
         mode != 0) {
         for (int j = 0; j < m; ++j) {
+            // a column not being replaced finishes its interrupted iteration as in mode 2
+            const bool rep = mode == 1 || (mode == 3 && bs->repl[j]);
             const double rho_new = bs->rr[j] + tot[j];
             if (!bs->active[j]) {
                 bs->beta[j] = 0.0;
-            } else if (mode == 1 || bs->broken[j] ||
-                       (mode == 3 && bs->rr[j] > 4.0 * bs->rrRep[j])) {
+            } else if (mode == 1 || (rep && (bs->broken[j] || bs->rr[j] > 4.0 * bs->rrRep[j]))) {
                 bs->beta[j] = 0.0;
             } else {
                 bs->beta[j] = rho_new / bs->rho[j];
             }
             bs->rho[j] = rho_new;
-            if (mode != 2) bs->broken[j] = 0;
+            if (rep) bs->broken[j] = 0;
         }
     }
 }
@@ -503,8 +528,8 @@ void launch_coarse_b(const float *Einv, int k, int m, const float *G32, const do
                      double *NU, float *NU32, int mode, double *partials, BatchScalars *bs,
                      cudaStream_t st) {
     const int grid = (k + kWarps - 1) / kWarps;
-    launch_pdl(k_coarse_b<MB>, grid > 0 ? grid : 1, kThreads, 0, st, Einv, k, m, G32, ZR, NU,
-               NU32, mode, partials, bs);
+    launch_pdl(k % 4 == 0 ? k_coarse_b<MB, 4> : k_coarse_b<MB, 1>, grid > 0 ? grid : 1, kThreads,
+               0, st, Einv, k, m, G32, ZR, NU, NU32, mode, partials, bs);
 }
 
 // ---- batched prolongation -----------------------------------------------------
@@ -563,8 +588,9 @@ void launch_prolong_b(const RowBoxDev &B, int m, const float *NU32, const float 
 
 // ---- FP64 <-> FP32 transforms of several columns --------------------------------
 
-// out[(ot[I] + i) * MB + j] = scale_j (L^-1 r_j)_i for active columns j < m;
-// r_j = r + j * ldr in the caller's numbering (nat).  Other columns: 0.
+// out[(ot[I] + i) * MB + j] = scale_j (L^-1 r_j)_i for the active columns being
+// replaced (repl_j); r_j = r + j * ldr in the caller's numbering (nat).
+// Inactive columns get 0; active columns not being replaced are left as they are.
 template <int MB>
 __global__ void k_fwd_scale_b(int nNodes, int m, const int *nat, const int *ot, FacDev F,
                               const double *r, long long ldr, const BatchScalars *bs,
@@ -575,6 +601,7 @@ __global__ void k_fwd_scale_b(int nNodes, int m, const int *nat, const int *ot, 
     for (int j = 0; j < MB; ++j) {
         double x[15];
         const bool on = j < m && bs->active[j];
+        if (on && !bs->repl[j]) continue;
         for (int i = 0; i < b; ++i) x[i] = on ? r[j * ldr + d0 + i] : 0.0;
         if (on) fwd_solve_node(F, I, b, x);
         const double sj = on ? bs->scale[j] : 0.0;

@@ -83,6 +83,7 @@ struct BatchScalars {
     double scale[kMaxBatch];    // per-column scale of the FP64 <-> FP32 transforms
     int active[kMaxBatch];      // 1 while column j iterates
     int broken[kMaxBatch];      // p_j^T K p_j <= 0 seen (restart at the replacement)
+    int repl[kMaxBatch];        // column j is replaced (or leaves) at this replacement
     int its, done, max_it, fault;
     unsigned int ticket[4];
 };
@@ -178,6 +179,8 @@ struct RowBoxDev {
 };
 constexpr int kUnitRows = 3072;     // own + coupled rows per restriction unit
 constexpr int kProlongRows = 512;
+constexpr int kUnitRowsBatch = 384;      // the same for the batched kernels (MB threads per row)
+constexpr int kProlongRowsBatch = 64;
 
 void launch_restrict(const BoxDev<double> &B, const double *a, const double *b, int withW,
                      double *g, double *zr, const Scalars *sc, cudaStream_t st);
