@@ -426,15 +426,17 @@ void launch_restrict_b(const RowBoxDev &B, int m, float *u, const float *r_cur, 
 // ---- batched coarse solve NU = E^-1 G -----------------------------------------
 
 constexpr int kCoarseChunkB = 1024;
+constexpr int kCoarsePadB = kCoarseChunkB + 4;   // row pitch of the transposed G chunk
 
 // mode 0: nothing else; mode 1: rho_j = rr_j + nu_j^T zr_j, beta_j = 0; mode 2:
 // the same rho_new, beta_j = rho_new / rho_j; mode 3 (after a replacement): as
 // 2, with beta_j = 0 for a replaced column whose residual the replacement
 // lengthened by more than 2x or that broke down (the other columns finish the
 // iteration the trigger interrupted, as in mode 2).  Inactive columns get
-// beta = 0.  One warp per row of
-// E^-1 (16-byte loads when k is a multiple of 4); G staged in shared memory
-// chunk by chunk.
+// beta = 0.  One warp per row of E^-1 (16-byte loads when k is a multiple of
+// 4); G staged in shared memory chunk by chunk, transposed (one padded row
+// per column), so a lane's four consecutive entries of a column are one
+// conflict-free 16-byte load.
 template <int MB, int V>
 __global__ void __launch_bounds__(kThreads)
 k_coarse_b(const float *__restrict__ Einv, int k, int m, const float *__restrict__ G32,
@@ -442,7 +444,7 @@ k_coarse_b(const float *__restrict__ Einv, int k, int m, const float *__restrict
            BatchScalars *bs) {
     pdl_wait();
     if (bs->done != kRunning) return;
-    __shared__ __align__(16) float gs[kCoarseChunkB * MB];
+    __shared__ __align__(16) float gs[MB * kCoarsePadB];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kWarps + warp;
     const float *row = Einv + (size_t)(i < k ? i : 0) * k;
@@ -453,7 +455,8 @@ k_coarse_b(const float *__restrict__ Einv, int k, int m, const float *__restrict
     for (int l0 = 0; l0 < k; l0 += kCoarseChunkB) {
         const int len = min(kCoarseChunkB, k - l0);
         __syncthreads();
-        for (int e = threadIdx.x; e < len * MB; e += blockDim.x) gs[e] = G32[(size_t)l0 * MB + e];
+        for (int e = threadIdx.x; e < len * MB; e += blockDim.x)
+            gs[(e % MB) * kCoarsePadB + e / MB] = G32[(size_t)l0 * MB + e];
         __syncthreads();
         if (i >= k) continue;
         if (V == 4) {
@@ -461,33 +464,21 @@ k_coarse_b(const float *__restrict__ Einv, int k, int m, const float *__restrict
 #pragma unroll 4
             for (int l4 = lane; 4 * l4 < len; l4 += 32) {
                 const float4 ev = ld_keep(r4 + l4, keep);
-                const float e4[4] = {ev.x, ev.y, ev.z, ev.w};
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const float4 *g4 = reinterpret_cast<const float4 *>(gs + (4 * l4 + t) * MB);
-#pragma unroll
-                    for (int q = 0; q < MB / 4; ++q) {
-                        const float4 g = g4[q];
-                        acc[4 * q] = fmaf(e4[t], g.x, acc[4 * q]);
-                        acc[4 * q + 1] = fmaf(e4[t], g.y, acc[4 * q + 1]);
-                        acc[4 * q + 2] = fmaf(e4[t], g.z, acc[4 * q + 2]);
-                        acc[4 * q + 3] = fmaf(e4[t], g.w, acc[4 * q + 3]);
-                    }
+                for (int j = 0; j < MB; ++j) {
+                    const float4 g = *reinterpret_cast<const float4 *>(gs + j * kCoarsePadB + 4 * l4);
+                    float a = fmaf(ev.x, g.x, acc[j]);
+                    a = fmaf(ev.y, g.y, a);
+                    a = fmaf(ev.z, g.z, a);
+                    acc[j] = fmaf(ev.w, g.w, a);
                 }
             }
         } else {
 #pragma unroll 4
             for (int l = lane; l < len; l += 32) {
                 const float ev = ld_keep(row + l0 + l, keep);
-                const float4 *g4 = reinterpret_cast<const float4 *>(gs + l * MB);
 #pragma unroll
-                for (int q = 0; q < MB / 4; ++q) {
-                    const float4 g = g4[q];
-                    acc[4 * q] = fmaf(ev, g.x, acc[4 * q]);
-                    acc[4 * q + 1] = fmaf(ev, g.y, acc[4 * q + 1]);
-                    acc[4 * q + 2] = fmaf(ev, g.z, acc[4 * q + 2]);
-                    acc[4 * q + 3] = fmaf(ev, g.w, acc[4 * q + 3]);
-                }
+                for (int j = 0; j < MB; ++j) acc[j] = fmaf(ev, gs[j * kCoarsePadB + l], acc[j]);
             }
         }
     }
@@ -590,56 +581,58 @@ void launch_prolong_b(const RowBoxDev &B, int m, const float *NU32, const float 
 
 // out[(ot[I] + i) * MB + j] = scale_j (L^-1 r_j)_i for the active columns being
 // replaced (repl_j); r_j = r + j * ldr in the caller's numbering (nat).
-// Inactive columns get 0; active columns not being replaced are left as they are.
+// Inactive columns get 0; active columns not being replaced are left as they
+// are.  One thread per (node, column).
 template <int MB>
 __global__ void k_fwd_scale_b(int nNodes, int m, const int *nat, const int *ot, FacDev F,
                               const double *r, long long ldr, const BatchScalars *bs,
                               float *out) {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= nNodes) return;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)nNodes * MB) return;
+    const int I = (int)(t / MB), j = (int)(t % MB);
     const int b = nat[I + 1] - nat[I], d0 = nat[I], o0 = ot[I];
-    for (int j = 0; j < MB; ++j) {
-        double x[15];
-        const bool on = j < m && bs->active[j];
-        if (on && !bs->repl[j]) continue;
-        for (int i = 0; i < b; ++i) x[i] = on ? r[j * ldr + d0 + i] : 0.0;
-        if (on) fwd_solve_node(F, I, b, x);
-        const double sj = on ? bs->scale[j] : 0.0;
-        for (int i = 0; i < b; ++i) out[(size_t)(o0 + i) * MB + j] = (float)(sj * x[i]);
-    }
+    const bool on = j < m && bs->active[j];
+    if (on && !bs->repl[j]) return;
+    double x[15];
+    for (int i = 0; i < b; ++i) x[i] = on ? r[j * ldr + d0 + i] : 0.0;
+    if (on) fwd_solve_node(F, I, b, x);
+    const double sj = on ? bs->scale[j] : 0.0;
+    for (int i = 0; i < b; ++i) out[(size_t)(o0 + i) * MB + j] = (float)(sj * x[i]);
 }
 
-// u_j += (L^-T ut_j)_i / scale_j for active columns j < m
+// u_j += (L^-T ut_j)_i / scale_j for active columns j < m; one thread per
+// (node, column)
 template <int MB>
 __global__ void k_bwd_accum_b(int nNodes, int m, const int *nat, const int *in, FacDev F,
                               const float *ut, const BatchScalars *bs, double *u, long long ldu) {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= nNodes) return;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)nNodes * MB) return;
+    const int I = (int)(t / MB), j = (int)(t % MB);
+    if (j >= m || !bs->active[j]) return;
     const int b = nat[I + 1] - nat[I], d0 = in[I], o0 = nat[I];
-    for (int j = 0; j < m; ++j) {
-        if (!bs->active[j]) continue;
-        double x[15];
-        for (int i = 0; i < b; ++i) x[i] = (double)ut[(size_t)(d0 + i) * MB + j];
-        bwd_solve_node(F, I, b, x);
-        const double inv = 1.0 / bs->scale[j];
-        for (int i = 0; i < b; ++i) u[j * ldu + o0 + i] += inv * x[i];
-    }
+    double x[15];
+    for (int i = 0; i < b; ++i) x[i] = (double)ut[(size_t)(d0 + i) * MB + j];
+    bwd_solve_node(F, I, b, x);
+    const double inv = 1.0 / bs->scale[j];
+    for (int i = 0; i < b; ++i) u[j * ldu + o0 + i] += inv * x[i];
 }
 
 template <int MB>
 void launch_fwd_scale_b(int nNodes, int m, const int *nat, const int *ot, const FacDev &F,
                         const double *r, long long ldr, const BatchScalars *bs, float *out,
                         cudaStream_t st) {
-    k_fwd_scale_b<MB><<<(nNodes + 127) / 128, 128, 0, st>>>(nNodes, m, nat, ot, F, r, ldr, bs,
-                                                            out);
+    const long long nt = (long long)nNodes * MB;
+    k_fwd_scale_b<MB><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(nNodes, m, nat, ot, F, r, ldr,
+                                                                     bs, out);
 }
 
 template <int MB>
 void launch_bwd_accum_b(int nNodes, int m, const int *nat, const int *in, const FacDev &F,
                         const float *ut, const BatchScalars *bs, double *u, long long ldu,
                         cudaStream_t st) {
-    k_bwd_accum_b<MB><<<(nNodes + 127) / 128, 128, 0, st>>>(nNodes, m, nat, in, F, ut, bs, u,
-                                                            ldu);
+    const long long nt = (long long)nNodes * MB;
+    k_bwd_accum_b<MB><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(nNodes, m, nat, in, F, ut, bs,
+                                                                     u, ldu);
 }
 
 #define XDCG_BATCH_INST(MB)                                                                    \
