@@ -46,9 +46,20 @@ def peaks():
     return FALLBACK_HBM, "fallback"
 
 
-def profiled_traffic(kernel_file, summary):
+def kernel_source_sha(files):
+    """First 12 hex digits of the SHA-256 of the kernel's source files, in order."""
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_2111_09294_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+SPMV_SOURCES = ("spmv.cu", "spmv_cfg.cuh", "tma.cuh", "pdl.cuh", "cache.cuh")
+
+
+def profiled_traffic(kernel_files, summary):
     """Per-launch DRAM bytes of the FP32 SpMV from the committed ncu summary,
-    or None when the kernel source changed since the capture."""
+    or None when the kernel's sources changed since the capture."""
     path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
@@ -57,8 +68,7 @@ def profiled_traffic(kernel_file, summary):
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]{12})", txt)
     if not m or not h:
         return None
-    src = open(os.path.join(ROOT, "paper_2111_09294_gb300", "csrc", kernel_file), "rb").read()
-    if hashlib.sha256(src).hexdigest()[:12] != h.group(1):
+    if kernel_source_sha(kernel_files) != h.group(1):
         return None
     return float(m.group(1))
 
@@ -329,6 +339,28 @@ def run_ours(args):
                  "rel_res_true_max": rmax,
                  "loads": "seeded tractions on z = 1: shear and tension, |t_i| ~ U[0.5, 1.5]"}
         bsol.close()
+    # differentiable solve: forward u = K^-1 f and the adjoint backward
+    # (dJ/df = K^-1 w for J = w.u), mixed against FP64 (outside the value)
+    from paper_2111_09294_gb300.autograd import solve as dsolve
+    w = torch.tensor(np.random.default_rng(3).standard_normal(P.n), device=dev)
+    fwd_bwd = {}
+    for name, solver in (("mixed", mixed), ("fp64", fp64)):
+        ts = []
+        for it in range(args.warmup + args.steps):
+            fg = f.clone().requires_grad_(True)
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            J = (w * dsolve(solver, fg, TOL)).sum()
+            J.backward()
+            e1.record(stream)
+            e1.synchronize()
+            if it >= args.warmup:
+                ts.append(e0.elapsed_time(e1))
+        fwd_bwd[name + "_ms"] = float(np.mean(ts))
+    fwd_bwd["speedup_mixed_vs_fp64"] = fwd_bwd["fp64_ms"] / fwd_bwd["mixed_ms"]
+    fwd_bwd["loss"] = "J = w . u, w seeded N(0, 1); backward = adjoint solve to the same tol"
     info = mixed.info
     n_sp = sum(i["n_spmv_timed"] for i in inf_mixed_t)
     t_sp = sum(i["t_spmv_ms"] for i in inf_mixed_t)
@@ -338,7 +370,7 @@ def run_ours(args):
     spmv64_ms = sum(i["t_spmv_ms"] for i in inf_fp64_t) / max(n64, 1)
     achieved64 = info["spmv_bytes_fp64"] / (spmv64_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    traffic = profiled_traffic("spmv.cu", f"spmv_fp32_{WORKLOAD}.md")
+    traffic = profiled_traffic(SPMV_SOURCES, f"spmv_fp32_{WORKLOAD}.md")
     its_fp64 = inf_fp64[-1]["iterations"]
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -360,6 +392,7 @@ def run_ours(args):
         "spmv_fp32_gbs": achieved, "spmv_fp64_gbs": achieved64,
         "kernel_us_per_iteration": phases,
         "batched_load_cases": batch,
+        "forward_backward": fwd_bwd,
         "roofline": {"bound": "hbm", "kernel": "k_spmv<float> (inner FP32 SpMV)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind,

@@ -99,7 +99,10 @@ k_spmm(SpmvDev<float> A, int m, const float *__restrict__ x, float *__restrict__
         pStep += n;
         ++issued;
     };
-    if (lane == 0)
+    // prologue copies before the wait unless the run has visibly stopped
+    // (an L2 read that may be stale; the read after the wait decides)
+    const bool early = __ldcg(&bs->done) == kRunning;
+    if (lane == 0 && early)
         while (more && issued < NS) issue();
     issued = __shfl_sync(0xffffffffu, issued, 0);
     pdl_wait();
@@ -108,6 +111,11 @@ k_spmm(SpmvDev<float> A, int m, const float *__restrict__ x, float *__restrict__
         for (int k = 0; k < issued; ++k) mbar_wait(bars + k % NS, (uint32_t)(k / NS) & 1u, drain);
         __syncwarp();
         return;
+    }
+    if (!early) {
+        if (lane == 0)
+            while (more && issued < NS) issue();
+        issued = __shfl_sync(0xffffffffu, issued, 0);
     }
 
     float part[MB];
@@ -593,11 +601,17 @@ __global__ void k_fwd_scale_b(int nNodes, int m, const int *nat, const int *ot, 
     const int b = nat[I + 1] - nat[I], d0 = nat[I], o0 = ot[I];
     const bool on = j < m && bs->active[j];
     if (on && !bs->repl[j]) return;
-    double x[15];
-    for (int i = 0; i < b; ++i) x[i] = on ? r[j * ldr + d0 + i] : 0.0;
-    if (on) fwd_solve_node(F, I, b, x);
     const double sj = on ? bs->scale[j] : 0.0;
-    for (int i = 0; i < b; ++i) out[(size_t)(o0 + i) * MB + j] = (float)(sj * x[i]);
+    const int q = F.nodeIdx[I];
+    with_node_size(b, [&](auto Bc) {
+        constexpr int B = decltype(Bc)::value;
+        double x[B];
+#pragma unroll
+        for (int i = 0; i < B; ++i) x[i] = on ? r[j * ldr + d0 + i] : 0.0;
+        if (on) fwd_solve_fixed<B>(F, q, x);
+#pragma unroll
+        for (int i = 0; i < B; ++i) out[(size_t)(o0 + i) * MB + j] = (float)(sj * x[i]);
+    });
 }
 
 // u_j += (L^-T ut_j)_i / scale_j for active columns j < m; one thread per
@@ -610,11 +624,17 @@ __global__ void k_bwd_accum_b(int nNodes, int m, const int *nat, const int *in, 
     const int I = (int)(t / MB), j = (int)(t % MB);
     if (j >= m || !bs->active[j]) return;
     const int b = nat[I + 1] - nat[I], d0 = in[I], o0 = nat[I];
-    double x[15];
-    for (int i = 0; i < b; ++i) x[i] = (double)ut[(size_t)(d0 + i) * MB + j];
-    bwd_solve_node(F, I, b, x);
     const double inv = 1.0 / bs->scale[j];
-    for (int i = 0; i < b; ++i) u[j * ldu + o0 + i] += inv * x[i];
+    const int q = F.nodeIdx[I];
+    with_node_size(b, [&](auto Bc) {
+        constexpr int B = decltype(Bc)::value;
+        double x[B];
+#pragma unroll
+        for (int i = 0; i < B; ++i) x[i] = (double)ut[(size_t)(d0 + i) * MB + j];
+        bwd_solve_fixed<B>(F, q, x);
+#pragma unroll
+        for (int i = 0; i < B; ++i) u[j * ldu + o0 + i] += inv * x[i];
+    });
 }
 
 template <int MB>

@@ -2,6 +2,8 @@
 // triangular solves, shared by the FP64 <-> FP32 transforms of the mixed path.
 #pragma once
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace xdcg {
@@ -33,13 +35,48 @@ __device__ __forceinline__ void bwd_solve(const FacDev &F, int l, int t, int b, 
     }
 }
 
-// the same for node I, unit stride
-__device__ __forceinline__ void fwd_solve_node(const FacDev &F, int I, int b, double *x) {
-    fwd_solve(F, F.nodeList[I], F.nodeIdx[I], b, x, 1);
+// The same with the block size B a compile-time constant, so that x stays in
+// registers (a runtime-sized x lives in local memory).  The factor list of a
+// B-dof node is fixed by B (3, 6, 15 -> 0, 1, 2), so it is not indexed at
+// run time either; t is the node's index within that list.
+template <int B>
+__device__ __forceinline__ void fwd_solve_fixed(const FacDev &F, int t, double (&x)[B]) {
+    constexpr int l = B == 3 ? 0 : (B == 6 ? 1 : 2);
+    const double *L = F.L[l];
+    const size_t cnt = (size_t)F.cnt[l];
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+        double s = x[i];
+#pragma unroll
+        for (int j = 0; j < i; ++j) s -= L[tri2(i, j) * cnt + t] * x[j];
+        x[i] = s * L[tri2(i, i) * cnt + t];
+    }
 }
 
-__device__ __forceinline__ void bwd_solve_node(const FacDev &F, int I, int b, double *x) {
-    bwd_solve(F, F.nodeList[I], F.nodeIdx[I], b, x, 1);
+template <int B>
+__device__ __forceinline__ void bwd_solve_fixed(const FacDev &F, int t, double (&x)[B]) {
+    constexpr int l = B == 3 ? 0 : (B == 6 ? 1 : 2);
+    const double *L = F.L[l];
+    const size_t cnt = (size_t)F.cnt[l];
+#pragma unroll
+    for (int i = B - 1; i >= 0; --i) {
+        double s = x[i];
+#pragma unroll
+        for (int j = i + 1; j < B; ++j) s -= L[tri2(j, i) * cnt + t] * x[j];
+        x[i] = s * L[tri2(i, i) * cnt + t];
+    }
+}
+
+// Calls f(std::integral_constant<int, b>) for a node of b dofs: 3, 6 or 15,
+// the only node sizes set-up accepts.
+template <typename Fn>
+__device__ __forceinline__ void with_node_size(int b, Fn &&f) {
+    if (b == 3)
+        f(std::integral_constant<int, 3>());
+    else if (b == 6)
+        f(std::integral_constant<int, 6>());
+    else
+        f(std::integral_constant<int, 15>());
 }
 
 }  // namespace xdcg

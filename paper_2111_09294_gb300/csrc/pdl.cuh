@@ -1,7 +1,8 @@
 // Programmatic dependent launch.  The kernels of the iteration loop are
 // launched with programmatic stream serialisation: a kernel's blocks may be
 // launched while its predecessor drains (each predecessor block counts as
-// triggered when it exits; an explicit early trigger measured slower), and
+// triggered when it exits; an explicit trigger, at kernel start or after a
+// block's main work, measured slower), and
 // they wait (griddepcontrol.wait) for the predecessor's completion and
 // memory before touching anything it wrote.  Work that reads only set-up
 // data (the SpMV's matrix stream) runs before the wait.  The wait is a no-op

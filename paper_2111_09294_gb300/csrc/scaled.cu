@@ -164,10 +164,16 @@ __global__ void k_fwd_scale(int nNodes, const int *nat, const int *in, const int
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nNodes) return;
     const int b = nat[I + 1] - nat[I], d0 = in[I], o0 = ot[I];
-    double x[15];
-    for (int i = 0; i < b; ++i) x[i] = r[d0 + i];
-    fwd_solve(F, F.nodeList[I], F.nodeIdx[I], b, x, 1);
-    for (int i = 0; i < b; ++i) out[o0 + i] = (float)(s * x[i]);
+    const int t = F.nodeIdx[I];
+    with_node_size(b, [&](auto Bc) {
+        constexpr int B = decltype(Bc)::value;
+        double x[B];
+#pragma unroll
+        for (int i = 0; i < B; ++i) x[i] = r[d0 + i];
+        fwd_solve_fixed<B>(F, t, x);
+#pragma unroll
+        for (int i = 0; i < B; ++i) out[o0 + i] = (float)(s * x[i]);
+    });
 }
 
 void launch_fwd_scale(int nNodes, const int *nat, const int *in, const int *ot, const FacDev &F,
@@ -181,10 +187,16 @@ __global__ void k_bwd_accum(int nNodes, const int *nat, const int *in, const int
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nNodes) return;
     const int b = nat[I + 1] - nat[I], d0 = in[I], o0 = ot[I];
-    double x[15];
-    for (int i = 0; i < b; ++i) x[i] = (double)ut[d0 + i];
-    bwd_solve(F, F.nodeList[I], F.nodeIdx[I], b, x, 1);
-    for (int i = 0; i < b; ++i) u[o0 + i] += scale * x[i];
+    const int t = F.nodeIdx[I];
+    with_node_size(b, [&](auto Bc) {
+        constexpr int B = decltype(Bc)::value;
+        double x[B];
+#pragma unroll
+        for (int i = 0; i < B; ++i) x[i] = (double)ut[d0 + i];
+        bwd_solve_fixed<B>(F, t, x);
+#pragma unroll
+        for (int i = 0; i < B; ++i) u[o0 + i] += scale * x[i];
+    });
 }
 
 void launch_bwd_accum(int nNodes, const int *nat, const int *in, const int *ot, const FacDev &F,

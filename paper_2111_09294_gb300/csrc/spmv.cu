@@ -83,8 +83,11 @@ k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__rest
         ++issued;
     };
     // the first stages stream set-up data only: issue them before waiting
-    // for the kernel that produced x
-    if (lane == 0)
+    // for the kernel that produced x, unless the run has visibly stopped
+    // already (launches queued past a stop).  That early read of the flag
+    // bypasses L1 and may be stale; the flag read after the wait decides.
+    const bool early = __ldcg(&sc->done) == kRunning;
+    if (lane == 0 && early)
         while (more && issued < NS) issue();
     issued = __shfl_sync(0xffffffffu, issued, 0);
     pdl_wait();
@@ -94,6 +97,11 @@ k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__rest
         for (int k = 0; k < issued; ++k) mbar_wait(bars + k % NS, (uint32_t)(k / NS) & 1u, drain);
         __syncwarp();
         return;
+    }
+    if (!early) {
+        if (lane == 0)
+            while (more && issued < NS) issue();
+        issued = __shfl_sync(0xffffffffu, issued, 0);
     }
 
     T part[1] = {T(0)};
