@@ -26,6 +26,11 @@ namespace xdcg {
 // be computed (unless GUARD).  The fused dot (x^T y, or y^T y in residual
 // mode) is summed per warp over a fixed slice range, then by the
 // deterministic grid reduction.
+//
+// No dependent global load sits on a warp's path from one slice to the
+// next: the first 32 slices' extents are read into shared memory at kernel
+// start (one slice per lane), and a slice's row indices are loaded when the
+// slice begins, its x (or b) entries one stage later, for use when it ends.
 template <typename T, bool RES>
 __global__ void __launch_bounds__(kSpmvThreads, SpmvCfg<T>::MINB)
 k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__restrict__ b,
@@ -38,7 +43,18 @@ k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__rest
     int *meta = reinterpret_cast<int *>(smem + (size_t)kSpmvWarps * NS * (SB + 8)) + warp * NS * 3;
     const int nS = A.S.nSlices;
     const int gw = blockIdx.x * kSpmvWarps + warp;
-    const int sEnd = A.warpSlice[gw + 1];
+    const int sFirst = A.warpSlice[gw], sEnd = A.warpSlice[gw + 1];
+    // extents of the warp's first 32 slices (set-up data)
+    __shared__ long long tBase[kSpmvWarps][32];
+    __shared__ int tSteps[kSpmvWarps][32];
+    if (sFirst + lane < sEnd) {
+        const int g = sFirst + lane;
+        const SellDev<T> &P = g < nS ? A.S : A.X;
+        const int sl = g < nS ? g : g - nS;
+        const long long b0 = P.slicePtr[sl];
+        tBase[warp][lane] = b0;
+        tSteps[warp][lane] = (int)((P.slicePtr[sl + 1] - b0) >> 5);
+    }
     if (lane == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(bars + s, 1);
         mbar_init_fence();
@@ -48,7 +64,7 @@ k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__rest
     const unsigned long long deadline = global_ns() + kWaitNs;
 
     // producer state, meaningful in lane 0
-    int issued = 0, more = 1, pSlice = A.warpSlice[gw] - 1, pStep = 0, pSteps = 0;
+    int issued = 0, more = 1, pSlice = sFirst - 1, pStep = 0, pSteps = 0;
     long long pBase = 0;
     const int *pCol = nullptr;
     const T *pVal = nullptr;
@@ -61,8 +77,13 @@ k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__rest
             const bool isS = pSlice < nS;
             const SellDev<T> &P = isS ? A.S : A.X;
             const int sl = isS ? pSlice : pSlice - nS;
-            pBase = P.slicePtr[sl];
-            pSteps = (int)((P.slicePtr[sl + 1] - pBase) >> 5);
+            if (pSlice - sFirst < 32) {
+                pBase = tBase[warp][pSlice - sFirst];
+                pSteps = tSteps[warp][pSlice - sFirst];
+            } else {
+                pBase = P.slicePtr[sl];
+                pSteps = (int)((P.slicePtr[sl + 1] - pBase) >> 5);
+            }
             pStep = 0;
             pCol = P.col;
             pVal = P.val;
@@ -106,23 +127,34 @@ k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__rest
 
     T part[1] = {T(0)};
     int cur = -1, rpw = 16, rl = 0, h = 0, tpr = 2, len = 0;
-    bool valid = false, isS = true;
+    bool valid = false, isS = true, own = false, pend = false;
+    long long r3 = 0;            // first dof of the lane's row (own lanes)
+    T e0 = T(0), e1 = T(0), e2 = T(0);   // its x (or b) entries
     T a0 = T(0), a1 = T(0), a2 = T(0);
+    const T *ev = RES ? b : x;
+    auto fetch_row_entries = [&]() {
+        pend = false;
+        if (own) {
+            e0 = ev[r3];
+            e1 = ev[r3 + 1];
+            e2 = ev[r3 + 2];
+        }
+    };
     auto finish = [&]() {
         for (int o = rpw; o < 32; o <<= 1) {
             a0 += __shfl_xor_sync(0xffffffffu, a0, o);
             a1 += __shfl_xor_sync(0xffffffffu, a1, o);
             a2 += __shfl_xor_sync(0xffffffffu, a2, o);
         }
-        if (valid && h == 0) {
-            const long long r3 = 3 * (long long)(isS ? A.S.row[rl] : A.X.row[rl]);
+        if (pend) fetch_row_entries();
+        if (own) {
             if (RES) {
-                a0 = b[r3] - a0;
-                a1 = b[r3 + 1] - a1;
-                a2 = b[r3 + 2] - a2;
+                a0 = e0 - a0;
+                a1 = e1 - a1;
+                a2 = e2 - a2;
                 part[0] += a0 * a0 + a1 * a1 + a2 * a2;
             } else {
-                part[0] += x[r3] * a0 + x[r3 + 1] * a1 + x[r3 + 2] * a2;
+                part[0] += e0 * a0 + e1 * a1 + e2 * a2;
             }
             y[r3] = a0;
             y[r3 + 1] = a1;
@@ -175,6 +207,11 @@ k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__rest
             h = lane / rpw;
             valid = rl < (isS ? A.S.nRows : A.X.nRows);
             if (SpmvCfg<T>::GUARD) len = valid ? (isS ? A.S.len[rl] : A.X.len[rl]) : 0;
+            own = valid && h == 0;
+            // consumed when the slice ends; the row's x (or b) entries are
+            // loaded after this stage, once the index has arrived
+            r3 = own ? 3 * (long long)(isS ? A.S.row[rl] : A.X.row[rl]) : 0;
+            pend = true;
             a0 = a1 = a2 = T(0);
         }
         const int s0 = meta[st * 3 + 1];
@@ -197,6 +234,7 @@ k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__rest
         __syncwarp();
         if (lane == 0 && more) issue();
         issued = __shfl_sync(0xffffffffu, issued, 0);
+        if (pend) fetch_row_entries();
 #pragma unroll
         for (int t = 0; t < C; ++t) {
             xa[t][0] = xb[t][0];
