@@ -340,27 +340,48 @@ def run_ours(args):
                  "loads": "seeded tractions on z = 1: shear and tension, |t_i| ~ U[0.5, 1.5]"}
         bsol.close()
     # differentiable solve: forward u = K^-1 f and the adjoint backward
-    # (dJ/df = K^-1 w for J = w.u), mixed against FP64 (outside the value)
+    # (dJ/df = K^-1 w for J = w.u, and dJ/dE_e for every element's modulus),
+    # mixed against FP64 (outside the value)
+    from paper_2111_09294_gb300 import Elements
     from paper_2111_09294_gb300.autograd import solve as dsolve
     w = torch.tensor(np.random.default_rng(3).standard_normal(P.n), device=dev)
+    elems = Elements.from_dict(X.element_data(P), dev)
+    young = torch.tensor(P.young, device=dev)
     fwd_bwd = {}
     for name, solver in (("mixed", mixed), ("fp64", fp64)):
         ts = []
         for it in range(args.warmup + args.steps):
             fg = f.clone().requires_grad_(True)
+            yg = young.clone().requires_grad_(True)
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            J = (w * dsolve(solver, fg, TOL)).sum()
+            J = (w * dsolve(solver, fg, TOL, young=yg, elements=elems)).sum()
             J.backward()
             e1.record(stream)
             e1.synchronize()
             if it >= args.warmup:
                 ts.append(e0.elapsed_time(e1))
         fwd_bwd[name + "_ms"] = float(np.mean(ts))
+    # the element kernel alone (all elements, one launch)
+    lam_t = torch.randn(P.n, dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        mixed.element_sensitivity(elems, u, lam_t)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        mixed.element_sensitivity(elems, u, lam_t)
+    e1.record(stream)
+    e1.synchronize()
+    # per call, including the call's status read (a stream synchronisation)
+    fwd_bwd["element_call_ms"] = e0.elapsed_time(e1) / max(args.steps, 1)
+    fwd_bwd["elements"] = elems.n_el
     fwd_bwd["speedup_mixed_vs_fp64"] = fwd_bwd["fp64_ms"] / fwd_bwd["mixed_ms"]
-    fwd_bwd["loss"] = "J = w . u, w seeded N(0, 1); backward = adjoint solve to the same tol"
+    fwd_bwd["loss"] = ("J = w . u, w seeded N(0, 1); backward = adjoint solve to the same tol, "
+                       "then dJ/df and dJ/dE_e for every element")
     info = mixed.info
     n_sp = sum(i["n_spmv_timed"] for i in inf_mixed_t)
     t_sp = sum(i["t_spmv_ms"] for i in inf_mixed_t)

@@ -248,6 +248,31 @@ xdcg_status xdcg_spmv_noalloc(xdcg_ctx *ctx, int32_t precision, const void *x, v
  * solve), FP64.  r, z: device, length n. */
 xdcg_status xdcg_precond(xdcg_ctx *ctx, const double *r, double *z);
 
+/* Sensitivity of a loss J(u), u = K^-1 f, to each element's Young's modulus
+ * (for differentiable use of the solver; not part of the paper's method).
+ * With K = sum_e E_e Khat_e, Khat_e the element stiffness for E = 1 at fixed
+ * Poisson ratio, the adjoint of the solve gives
+ *     out[e] = dJ/dE_e = -lam_e^T Khat_e u_e,   K lam = dJ/du
+ * (lam: a second solve on this context; K is symmetric).
+ *
+ * n_el elements.  Element e's local dofs are elem_dofs[elem_dof_ptr[e] ..
+ * elem_dof_ptr[e+1]) (at most 120: 8 nodes x 15 dofs), each the global dof
+ * (0 <= d < n) of that local dof or -1 for an eliminated one (its u and lam
+ * entries count as 0).  Its d_e x d_e row-major Khat_e starts at
+ * elem_mat[elem_mat_off[e]] and must lie within the mat_len doubles of
+ * elem_mat; elements may share a matrix.  u, lam: length n.  All arrays are
+ * device arrays owned by the caller; out (device, n_el doubles) is written
+ * in FP64, each element's sum in a fixed order.
+ *
+ * Synchronises the context stream.  XDCG_INVALID_ARG for a null pointer, a
+ * negative n_el, a global dof >= n, more than 120 local dofs or a matrix
+ * outside elem_mat; the offending elements' out entries are then NaN and the
+ * others are valid. */
+xdcg_status xdcg_element_sensitivity(xdcg_ctx *ctx, int64_t n_el, const int64_t *elem_dof_ptr,
+                                     const int32_t *elem_dofs, const int64_t *elem_mat_off,
+                                     const double *elem_mat, int64_t mat_len, const double *u,
+                                     const double *lam, double *out);
+
 /* Copy the coarse matrix E (k x k, row-major, FP64) to host memory E_host. */
 xdcg_status xdcg_coarse_matrix(xdcg_ctx *ctx, double *E_host);
 

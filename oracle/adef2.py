@@ -16,6 +16,11 @@ Plain, slow and literal:
 * loop   -- Algorithm 1, stopped when ||r_i||_2 <= tol ||f||_2, the test made
             after every residual update; the iteration count is the number of
             loop bodies run (products K p).
+* dJ/dE  -- sensitivity of J(u), u = K^-1 f, to each element's Young's
+            modulus (not in the paper; the adjoint of the solve): K depends on
+            E_e through E_e Khat_e, so dJ/dE_e = -lam_e^T Khat_e u_e with
+            K lam = dJ/du.  Pinned by central differences of J over rebuilt
+            systems and by sum_e E_e dJ/dE_e = -lam^T f.
 
 Readings of the paper that this file fixes:
 * the coordinates in the rigid-body block are taken relative to a per-box
@@ -314,3 +319,24 @@ def setup(P, enriched_modes=True):
 def solve(P, tol=1e-8, maxit=10000, record=False, enriched_modes=True):
     K, M, C = setup(P, enriched_modes)
     return adef2_pcg(K, P.f, M, C, tol=tol, maxit=maxit, record=record)
+
+
+def element_sensitivity(D, u, lam, elements=None):
+    """dJ/dE_e = -lam_e^T Khat_e u_e for the given elements (all by default).
+
+    D: element data (xfem_inputs.element_data): each element's global dofs
+    (-1 where eliminated) and its unit-modulus matrix Khat_e; u: the solution;
+    lam: the adjoint solution, K lam = dJ/du.  One element at a time, as
+    written."""
+    if elements is None:
+        elements = range(len(D["mat_off"]))
+    out = []
+    for e in elements:
+        d = D["dofs"][D["dof_ptr"][e]:D["dof_ptr"][e + 1]]
+        de = d.size
+        Kh = D["mats"][D["mat_off"][e]:D["mat_off"][e] + de * de].reshape(de, de)
+        live = d >= 0
+        ue = np.where(live, u[np.maximum(d, 0)], 0.0)
+        le = np.where(live, lam[np.maximum(d, 0)], 0.0)
+        out.append(-(le @ (Kh @ ue)))
+    return np.array(out)

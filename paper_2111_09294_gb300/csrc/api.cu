@@ -1719,6 +1719,26 @@ xdcg_status xdcg_spmv(xdcg_ctx *c, int32_t precision, const void *x, void *y, do
     return XDCG_OK;
 }
 
+xdcg_status xdcg_element_sensitivity(xdcg_ctx *c, int64_t n_el, const int64_t *elem_dof_ptr,
+                                     const int32_t *elem_dofs, const int64_t *elem_mat_off,
+                                     const double *elem_mat, int64_t mat_len, const double *u,
+                                     const double *lam, double *out) {
+    if (!c || n_el < 0) return XDCG_INVALID_ARG;
+    if (n_el == 0) return XDCG_OK;
+    if (!elem_dof_ptr || !elem_dofs || !elem_mat_off || !elem_mat || mat_len < 0 || !u || !lam ||
+        !out)
+        return XDCG_INVALID_ARG;
+    // the fault word of the scalar block flags bad element data
+    init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
+    launch_element_sensitivity(n_el, c->n, elem_dof_ptr, elem_dofs, elem_mat_off, mat_len,
+                               elem_mat, u, lam, out, &c->aux->fault, c->st);
+    c->launches++;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(c->h_sc, c->aux, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return c->h_sc->fault ? XDCG_INVALID_ARG : XDCG_OK;
+}
+
 // ---- no-allocation SpMV: reduction scratch in one static device array ------
 
 namespace {

@@ -297,4 +297,11 @@ void launch_bwd_accum_b(int nNodes, int m, const int *nat, const int *in, const 
                         const float *ut, const BatchScalars *bs, double *u, long long ldu,
                         cudaStream_t st);
 
+// element sensitivities -lam_e^T Khat_e u_e (sensitivity.cu)
+constexpr int kSensMaxDofs = 120;   // 8 nodes x 15 dofs
+void launch_element_sensitivity(long long nEl, long long n, const int64_t *dofPtr,
+                                const int32_t *dofs, const int64_t *matOff, long long matLen,
+                                const double *mats, const double *u, const double *lam,
+                                double *out, int *bad, cudaStream_t st);
+
 }  // namespace xdcg

@@ -15,6 +15,26 @@ def _host(a, dtype):
     return np.ascontiguousarray(np.asarray(a), dtype=dtype)
 
 
+class Elements:
+    """Per-element data on the device for Solver.element_sensitivity: element
+    e's local dofs dofs[dof_ptr[e]:dof_ptr[e+1]] (global dof, or -1 where
+    eliminated) and its row-major unit-modulus stiffness at mats[mat_off[e]:]
+    (layout of xdcg_element_sensitivity)."""
+
+    def __init__(self, dof_ptr, dofs, mat_off, mats, device="cuda"):
+        self.dof_ptr = torch.as_tensor(np.ascontiguousarray(dof_ptr, dtype=np.int64), device=device)
+        self.dofs = torch.as_tensor(np.ascontiguousarray(dofs, dtype=np.int32), device=device)
+        self.mat_off = torch.as_tensor(np.ascontiguousarray(mat_off, dtype=np.int64), device=device)
+        self.mats = torch.as_tensor(np.ascontiguousarray(mats, dtype=np.float64), device=device)
+        self.n_el = int(self.mat_off.numel())
+        if self.dof_ptr.numel() != self.n_el + 1:
+            raise ValueError("dof_ptr needs one entry more than mat_off")
+
+    @classmethod
+    def from_dict(cls, D, device="cuda"):
+        return cls(D["dof_ptr"], D["dofs"], D["mat_off"], D["mats"], device)
+
+
 class Solver:
     """Adapted deflated CG (A-DEF2 + node-block Jacobi) for one stiffness matrix.
 
@@ -156,6 +176,22 @@ class Solver:
                                     self._dev(x, dt), self._dev(y, dt), ctypes.byref(xty)),
                 "xdcg_spmv")
         return y, xty.value
+
+    def element_sensitivity(self, elements, u, lam, out=None):
+        """dJ/dE_e = -lam_e^T Khat_e u_e per element (K lam = dJ/du); u, lam:
+        CUDA float64 tensors of n entries; elements: an Elements on the same
+        device.  Returns a float64 tensor of one entry per element."""
+        out = out if out is not None else torch.empty(elements.n_el, dtype=torch.float64,
+                                                      device=u.device)
+        if out.numel() != elements.n_el or out.dtype != torch.float64 or not out.is_contiguous():
+            raise ValueError("out: a contiguous float64 tensor of one entry per element")
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+        L.check(self._lib.xdcg_element_sensitivity(
+            self.ctx, elements.n_el, ptr(elements.dof_ptr), ptr(elements.dofs),
+            ptr(elements.mat_off), ptr(elements.mats), elements.mats.numel(),
+            self._dev(u, torch.float64), self._dev(lam, torch.float64), ptr(out)),
+            "xdcg_element_sensitivity")
+        return out
 
     def precond(self, r):
         """z = A-DEF2 preconditioner applied to r (FP64)."""

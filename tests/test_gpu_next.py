@@ -228,3 +228,92 @@ def test_batched_columns_converge_independently():
         assert err <= 1e-7
     s.close()
     s64.close()
+
+
+# ---- dJ/dE: the elements' Young's moduli, through the same adjoint solve
+
+
+def _abs_scale(D, u, lam):
+    # per element |lam_e|^T |Khat_e| |u_e|, the size of the terms summed
+    Da = dict(D)
+    Da["mats"] = np.abs(D["mats"])
+    return -O.element_sensitivity(Da, np.abs(u), np.abs(lam))
+
+
+@pytest.mark.parametrize("name", ["cube8_edge", "cube24_ellipse"])
+def test_element_sensitivity_kernel_matches_oracle(name):
+    # the same seeded u and lam on both sides, so only the kernel's own
+    # arithmetic is compared: FP64 sums of at most 120 x 120 terms
+    dev = _cuda()
+    from paper_2111_09294_gb300 import Elements
+    P = problem(name)[0]
+    D = X.element_data(P)
+    rng = np.random.default_rng(61)
+    u, lam = rng.standard_normal(P.n), rng.standard_normal(P.n)
+    ref = O.element_sensitivity(D, u, lam)
+    s = _solver(P)
+    g = s.element_sensitivity(Elements.from_dict(D, dev), torch.tensor(u, device=dev),
+                              torch.tensor(lam, device=dev)).cpu().numpy()
+    assert g.shape == ref.shape
+    assert np.all(np.abs(g - ref) <= 1e-13 * _abs_scale(D, u, lam))
+    s.close()
+
+
+def test_element_sensitivity_flags_bad_element_data():
+    # a global dof past n and a matrix past the end of mats: those elements
+    # read nothing out of range, come back NaN and the call reports
+    # XDCG_INVALID_ARG; every other element is still computed
+    dev = _cuda()
+    from paper_2111_09294_gb300 import Elements, XdcgError
+    P = problem("cube8_edge")[0]
+    D = X.element_data(P)
+    rng = np.random.default_rng(62)
+    u, lam = rng.standard_normal(P.n), rng.standard_normal(P.n)
+    ref = O.element_sensitivity(D, u, lam)
+    bad = dict(D)
+    bad["dofs"] = D["dofs"].copy()
+    bad["mat_off"] = D["mat_off"].copy()
+    bad["dofs"][D["dof_ptr"][5] + 2] = P.n
+    bad["mat_off"][7] = D["mats"].size - 10
+    s = _solver(P)
+    out = torch.zeros(len(ref), dtype=torch.float64, device=dev)
+    with pytest.raises(XdcgError) as ei:
+        s.element_sensitivity(Elements.from_dict(bad, dev), torch.tensor(u, device=dev),
+                              torch.tensor(lam, device=dev), out=out)
+    assert ei.value.status == 1   # XDCG_INVALID_ARG
+    g = out.cpu().numpy()
+    assert np.isnan(g[5]) and np.isnan(g[7])
+    keep = np.ones(len(ref), dtype=bool)
+    keep[[5, 7]] = False
+    assert np.all(np.abs(g[keep] - ref[keep]) <= 1e-13 * _abs_scale(D, u, lam)[keep])
+    s.close()
+
+
+def test_modulus_gradient_through_autograd_matches_oracle():
+    # J = w.u: the backward's dJ/dE against the oracle's formula on the
+    # oracle's own u and lam (both solved to 1e-12), and the identity
+    # sum_e E_e dJ/dE_e = -lam^T K u = -J (up to the adjoint residual)
+    dev = _cuda()
+    from paper_2111_09294_gb300 import Elements
+    from paper_2111_09294_gb300.autograd import solve as dsolve
+    P, K, M, C = problem("cube8_edge")
+    D = X.element_data(P)
+    w = np.random.default_rng(63).standard_normal(P.n)
+    s = _solver(P)
+    young = torch.tensor(D["young"], device=dev, requires_grad=True)
+    f = torch.tensor(P.f, device=dev, requires_grad=True)
+    u = dsolve(s, f, 1e-12, young=young, elements=Elements.from_dict(D, dev))
+    J = (torch.tensor(w, device=dev) * u).sum()
+    J.backward()
+    g = young.grad.cpu().numpy()
+    uref = O.adef2_pcg(K, P.f, M, C, tol=1e-12).u
+    lref = O.adef2_pcg(K, w, M, C, tol=1e-12).u
+    ref = O.element_sensitivity(D, uref, lref)
+    assert np.max(np.abs(g - ref)) <= 1e-5 * np.max(np.abs(ref))
+    un = u.detach().cpu().numpy()
+    euler = D["young"] @ g + float(J.detach())
+    assert abs(euler) <= 1e-9 * (np.linalg.norm(w) * np.linalg.norm(un)
+                                 + np.abs(D["young"]) @ np.abs(g))
+    # dJ/df is still the adjoint solution
+    assert np.linalg.norm(f.grad.cpu().numpy() - lref) <= 1e-7 * np.linalg.norm(lref)
+    s.close()

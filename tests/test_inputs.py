@@ -183,3 +183,24 @@ def test_load_cases_are_linear_in_the_traction():
         for d in range(3):
             assert np.isclose(total[dof[:-1] + d].sum(), t[c, d])
     assert np.all((0.5 <= np.abs(t)) & (np.abs(t) <= 1.5)) and np.all(t[:, 2] > 0)
+
+
+def test_element_data_reassembles_K():
+    # K = sum_e E_e Khat_e scattered to each element's dofs (eliminated dofs
+    # dropped), with per-element moduli: a wrong local dof order, a missing
+    # enriched block or a matrix taken at the wrong modulus breaks it
+    from xfem_inputs.configs import CONFIGS
+    cfg = CONFIGS["cube8_edge"]
+    young = np.random.default_rng(9).lognormal(0.0, 0.3, cfg["m"] ** 3)
+    P = X.build_problem(cfg["m"], cfg["cracks"](), cfg["n_box"], young=young)
+    D = X.element_data(P)
+    K = X.to_dense(P)
+    Ks = np.zeros_like(K)
+    for e in range(len(D["mat_off"])):
+        d = D["dofs"][D["dof_ptr"][e]:D["dof_ptr"][e + 1]]
+        de = d.size
+        Kh = D["mats"][D["mat_off"][e]:D["mat_off"][e] + de * de].reshape(de, de)
+        live = d >= 0
+        Ks[np.ix_(d[live], d[live])] += D["young"][e] * Kh[np.ix_(live, live)]
+    assert np.max(np.abs(Ks - K)) <= 1e-14 * np.max(np.abs(K))
+    assert np.all(D["young"] == young)

@@ -1,4 +1,5 @@
 """Seeded synthetic XFEM crack systems: the inputs shared by the oracle and the GPU harness."""
 from .assemble import (KIND_HEAVISIDE, KIND_STD, KIND_TIP, Problem, build_problem, to_dense)
 from .configs import CONFIGS, make
+from .elements import element_data
 from .loads import face_weights, load_cases, tractions

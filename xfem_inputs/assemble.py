@@ -314,15 +314,17 @@ def build_problem(m, cracks, n_box, E=1.0, nu=0.3, traction=(0.0, 0.0, 1.0),
         r_, t_ = polar(phis[ci][sel], psis[ci][sel])
         rI_all[sel], thI_all[sel] = r_, t_
     n_enr_dofs_el = []
+    khat_enr = []                                    # element matrices for E = 1
     for e in enr_el:
         nodes = elem_nodes[e]
         kinds_e = kind[nodes]
         ci = int(ek_owner[e][ek_owner[e] >= 0][0])
         order = 4 if np.any(kinds_e == KIND_TIP) else 3
-        lam, mu = lame(young[e], nu)
         x0 = coords[nodes[0]]
-        Ke = _enriched_element_matrix(x0, h, lam, mu, kinds_e, phis[ci][nodes],
-                                      psis[ci][nodes], rI_all[nodes], thI_all[nodes], order)
+        Khat = _enriched_element_matrix(x0, h, lam1, mu1, kinds_e, phis[ci][nodes],
+                                        psis[ci][nodes], rI_all[nodes], thI_all[nodes], order)
+        khat_enr.append(Khat)
+        Ke = young[e] * Khat                         # K_e is linear in E at fixed nu
         loc = np.array([BLOCK_OF_KIND[k] for k in kinds_e])
         off = np.concatenate([[0], np.cumsum(loc)])
         n_enr_dofs_el.append(off[-1])
@@ -408,6 +410,14 @@ def build_problem(m, cracks, n_box, E=1.0, nu=0.3, traction=(0.0, 0.0, 1.0),
     P.young = young
     P.nu = nu
     P.n_enriched_elements = len(enr_el)
+    # per-element stiffness for unit Young's modulus (dK/dE_e), node-major
+    # with each node's dofs in its own block order
+    P.khat_std = Ke0
+    P.enr_elements = np.asarray(enr_el, dtype=np.int64)
+    P.khat_enr_ptr = np.zeros(len(enr_el) + 1, dtype=np.int64)
+    P.khat_enr_ptr[1:] = np.cumsum([K.size for K in khat_enr])
+    P.khat_enr = (np.concatenate([K.ravel() for K in khat_enr]) if khat_enr
+                  else np.zeros(0))
     P.n_heaviside_dofs = int(3 * np.sum(P.kind == KIND_HEAVISIDE))
     P.n_tip_dofs = int(12 * np.sum(P.kind == KIND_TIP))
     if bc == "roller":
