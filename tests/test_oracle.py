@@ -203,3 +203,32 @@ def test_element_sensitivity_matches_central_differences():
         u_m = np.linalg.solve(Ks[1], P.f)
         fd = -(w @ np.linalg.solve(Ks[0], (Ks[0] - Ks[1]) @ u_m)) / (2 * delta)
         assert abs(fd - g[e]) <= 1e-5 * abs(g[e]), (name, e, fd, g[e])
+
+
+def test_compliance_gradient_matches_differences_on_20_elements():
+    # the differentiable-solve objective (compliance J = f^T u, so lam = u)
+    # with log-normal element moduli, at the oracle's size: 20 seeded
+    # elements against exact product-form differences of J over
+    # K +- delta dK/dE_e (the element data themselves are pinned by their
+    # reassembly of K in test_inputs)
+    from xfem_inputs.configs import CONFIGS
+    cfg = CONFIGS["cube8_edge"]
+    young = np.random.default_rng(1).lognormal(0.0, 0.3, cfg["m"] ** 3)
+    P = X.build_problem(cfg["m"], cfg["cracks"](), cfg["n_box"], young=young)
+    D = X.element_data(P)
+    K = X.to_dense(P)
+    u = np.linalg.solve(K, P.f)
+    g = O.element_sensitivity(D, u, u)
+    assert np.all(g <= 1e-12 * np.max(np.abs(g)))     # -u_e^T Khat_e u_e, Khat_e PSD
+    assert abs(young @ g + P.f @ u) <= 1e-10 * (np.abs(young) @ np.abs(g))
+    for e in np.random.default_rng(2).choice(len(young), 20, replace=False):
+        d = D["dofs"][D["dof_ptr"][e]:D["dof_ptr"][e + 1]]
+        de = d.size
+        Kh = D["mats"][D["mat_off"][e]:D["mat_off"][e] + de * de].reshape(de, de)
+        live = d >= 0
+        dK = np.zeros_like(K)
+        dK[np.ix_(d[live], d[live])] = Kh[np.ix_(live, live)]
+        delta = 1e-4 * young[e]
+        u_m = np.linalg.solve(K - delta * dK, P.f)
+        fd = -(P.f @ np.linalg.solve(K + delta * dK, (2 * delta * dK) @ u_m)) / (2 * delta)
+        assert abs(fd - g[e]) <= 1e-5 * abs(g[e]) + 1e-12 * np.max(np.abs(g)), (e, fd, g[e])

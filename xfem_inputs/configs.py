@@ -9,8 +9,13 @@
                      (0.5, 0.5) at z = 0.3) and warped edge crack (z = 0.7,
                      depth 0.25 from x = 0), warp 0.02 sin(2 pi y) cos(2 pi x),
                      r_e = 0.05, 8^3 boxes.
+* cube64_penny_lognormal: 64^3 hexes, warped penny (radius 0.3 centred at
+                     (0.5, 0.5, 0.5), the same warp), r_e = 0.05, 8^3 boxes,
+                     per-element Young's modulus log-normal (mu 0, sigma 0.3,
+                     seed 0): the differentiable-solve workload.
 
-All use E = 1, nu = 0.3, z = 0 clamped and unit tension on z = 1.
+All use nu = 0.3, z = 0 clamped and unit tension on z = 1; E = 1 unless a
+per-element modulus is given.
 """
 import os
 import pickle
@@ -30,6 +35,11 @@ CONFIGS = {
     "cube48_two_cracks": dict(m=48, n_box=8,
                               cracks=lambda: [WarpedPennyCrack((0.5, 0.5, 0.3), 0.2, 0.02, 0.05),
                                               WarpedEdgeCrack(0.7, 0.25, 0.02, 0.05)]),
+    "cube64_penny_lognormal": dict(m=64, n_box=8,
+                                   cracks=lambda: [WarpedPennyCrack((0.5, 0.5, 0.5), 0.3, 0.02,
+                                                                    0.05)],
+                                   young=lambda m: np.random.default_rng(0).lognormal(
+                                       0.0, 0.3, m ** 3)),
 }
 
 
@@ -53,7 +63,8 @@ def make(name, cache=True):
     if cache and os.path.exists(path):
         with open(path, "rb") as fh:
             return pickle.load(fh)
-    P = build_problem(cfg["m"], cfg["cracks"](), cfg["n_box"])
+    young = cfg["young"](cfg["m"]) if "young" in cfg else None
+    P = build_problem(cfg["m"], cfg["cracks"](), cfg["n_box"], young=young)
     P.name = name
     if cache:
         tmp = path + f".{os.getpid()}"
