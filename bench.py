@@ -390,6 +390,44 @@ def run_ours(args):
     fwd_bwd["speedup_mixed_vs_fp64"] = fwd_bwd["fp64_ms"] / fwd_bwd["mixed_ms"]
     fwd_bwd["loss"] = ("compliance J = f . u; backward = adjoint solve to the same tol, then "
                        "dJ/df and dJ/dE_e for every element")
+    # a propagation sweep: --sweep systems of the 32^3 inclined-penny sweep,
+    # 8 load cases each, every system a batched mixed solve on its own stream;
+    # concurrent against one after another (outside the value)
+    sweep = None
+    if args.sweep > 0:
+        from paper_2111_09294_gb300 import sweep as S
+        Ps = X.make_many(X.SWEEP[:args.sweep])
+        ssol = S.make_solvers(Ps, max_batch=8)
+        Fs = [torch.tensor(X.load_cases(Pi, 8, seed=100 + i), device=dev)
+              for i, Pi in enumerate(Ps)]
+        Us = [torch.empty_like(Fi) for Fi in Fs]
+        for _ in range(max(1, args.warmup)):
+            S.solve_systems(ssol, Fs, TOL, outs=Us)
+        tc, ts_, res = [], [], None
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = S.solve_systems(ssol, Fs, TOL, outs=Us)
+            tc.append((time.perf_counter() - t0) * 1e3)
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            S.solve_systems(ssol, Fs, TOL, outs=Us, concurrent=False)
+            ts_.append((time.perf_counter() - t0) * 1e3)
+        infos = [i for _, inf in res for i in inf]
+        assert max(i["rel_res_true"] for i in infos) <= TOL
+        ms_c, ms_s = float(np.mean(tc)), float(np.mean(ts_))
+        sweep = {"systems": len(Ps), "rhs_per_system": 8,
+                 "n_dofs": [int(Pi.n) for Pi in Ps], "ms": ms_c, "ms_one_after_another": ms_s,
+                 "speedup_concurrent": ms_s / ms_c,
+                 "systems_rhs_per_s": len(Ps) * 8 / ms_c * 1e3,
+                 "iterations_max": max(i["iterations"] for i in infos),
+                 "rel_res_true_max": max(i["rel_res_true"] for i in infos),
+                 "timing": "host wall clock around the calls (each returns after its stream)"}
+        for s_ in ssol:
+            s_.close()
     info = mixed.info
     n_sp = sum(i["n_spmv_timed"] for i in inf_mixed_t)
     t_sp = sum(i["t_spmv_ms"] for i in inf_mixed_t)
@@ -422,6 +460,7 @@ def run_ours(args):
         "kernel_us_per_iteration": phases,
         "batched_load_cases": batch,
         "forward_backward": fwd_bwd,
+        "propagation_sweep": sweep,
         "roofline": {"bound": "hbm", "kernel": "k_spmv<float> (inner FP32 SpMV)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind,
@@ -485,6 +524,8 @@ def main():
     ap.add_argument("--batch", type=int, default=8,
                     help="load cases of the batched-solve measurement (0: skip)")
     ap.add_argument("--sample-iters", type=int, default=10)
+    ap.add_argument("--sweep", type=int, default=0,
+                    help="also solve this many systems of the 32^3 propagation sweep (<= 16)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", choices=["mixed", "fp64", "batch"], default=None,
                     help="profiler capture: one solve of the given path between "

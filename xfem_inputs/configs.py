@@ -13,6 +13,12 @@
                      (0.5, 0.5, 0.5), the same warp), r_e = 0.05, 8^3 boxes,
                      per-element Young's modulus log-normal (mu 0, sigma 0.3,
                      seed 0): the differentiable-solve workload.
+* cube32_sweep_00 .. cube32_sweep_15: 32^3 hexes, an inclined penny
+                     (centre (0.5, 0.5, 0.5), tilted 30 deg about x, no warp)
+                     whose radius grows linearly from 0.15 to 0.35 over the 16
+                     systems, r_e = 0.07, 8^3 boxes: successive crack-front
+                     positions of a propagation sweep (the radii are
+                     prescribed; no growth law is computed).
 
 All use nu = 0.3, z = 0 clamped and unit tension on z = 1; E = 1 unless a
 per-element modulus is given.
@@ -25,6 +31,9 @@ import numpy as np
 
 from .assemble import build_problem
 from .cracks import PlanarEdgeCrack, TiltedEllipticalCrack, WarpedEdgeCrack, WarpedPennyCrack
+
+SWEEP_RADII = np.linspace(0.15, 0.35, 16)
+SWEEP = [f"cube32_sweep_{i:02d}" for i in range(len(SWEEP_RADII))]
 
 CONFIGS = {
     "cube8_edge": dict(m=8, n_box=2,
@@ -41,6 +50,10 @@ CONFIGS = {
                                    young=lambda m: np.random.default_rng(0).lognormal(
                                        0.0, 0.3, m ** 3)),
 }
+for _name, _r in zip(SWEEP, SWEEP_RADII):
+    CONFIGS[_name] = dict(m=32, n_box=8,
+                          cracks=lambda r=float(_r): [TiltedEllipticalCrack(
+                              (0.5, 0.5, 0.5), r, r, np.deg2rad(30.0), 0.0, 0.07)])
 
 
 def _source_hash():
@@ -56,10 +69,14 @@ def _source_hash():
     return h.hexdigest()[:12]
 
 
+def _cache_path(name):
+    return os.path.join(tempfile.gettempdir(), f"xfem_inputs_{name}_{_source_hash()}.pkl")
+
+
 def make(name, cache=True):
     """Build (or load from a per-user temp cache) the named workload."""
     cfg = CONFIGS[name]
-    path = os.path.join(tempfile.gettempdir(), f"xfem_inputs_{name}_{_source_hash()}.pkl")
+    path = _cache_path(name)
     if cache and os.path.exists(path):
         with open(path, "rb") as fh:
             return pickle.load(fh)
@@ -72,3 +89,21 @@ def make(name, cache=True):
             pickle.dump(P, fh, protocol=pickle.HIGHEST_PROTOCOL)
         os.replace(tmp, path)
     return P
+
+
+def _make_cached(name):
+    make(name)
+    return name
+
+
+def make_many(names, workers=8):
+    """make() for several workloads, the missing ones built in parallel
+    worker processes (spawned, so a parent that already uses CUDA is safe)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    todo = [n for n in names if not os.path.exists(_cache_path(n))]
+    if len(todo) > 1 and workers > 1:
+        with cf.ProcessPoolExecutor(min(workers, len(todo)),
+                                    mp_context=mp.get_context("spawn")) as ex:
+            list(ex.map(_make_cached, todo))
+    return [make(n) for n in names]
