@@ -311,8 +311,7 @@ def run_ours(args):
         diag.close()
     # several load cases of the same crack configuration: one batched FP32 run
     # against the same columns solved one after another (outside the value)
-    batch = None
-    if args.batch > 0:
+    def measure_batch():
         m = args.batch
         Fb = torch.tensor(X.load_cases(P, m, seed=0), device=dev)
         Ub = torch.empty_like(Fb)
@@ -348,53 +347,55 @@ def run_ours(args):
                  "rel_res_true_max": rmax,
                  "loads": "seeded tractions on z = 1: shear and tension, |t_i| ~ U[0.5, 1.5]"}
         bsol.close()
+        return batch
     # differentiable solve: forward u = K^-1 f and the adjoint backward for
     # the compliance J = f.u (dJ/df and dJ/dE_e for every element's modulus),
     # mixed against FP64 (outside the value)
-    from paper_2111_09294_gb300 import Elements
-    from paper_2111_09294_gb300.autograd import solve as dsolve
-    elems = Elements.from_dict(X.element_data(P), dev)
-    young = torch.tensor(P.young, device=dev)
-    fwd_bwd = {}
-    for name, solver in (("mixed", mixed), ("fp64", fp64)):
-        ts = []
-        for it in range(args.warmup + args.steps):
-            fg = f.clone().requires_grad_(True)
-            yg = young.clone().requires_grad_(True)
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            J = (fg * dsolve(solver, fg, TOL, young=yg, elements=elems)).sum()
-            J.backward()
-            e1.record(stream)
-            e1.synchronize()
-            if it >= args.warmup:
-                ts.append(e0.elapsed_time(e1))
-        fwd_bwd[name + "_ms"] = float(np.mean(ts))
-    # the element kernel alone (all elements, one launch)
-    lam_t = torch.randn(P.n, dtype=torch.float64, device=dev)
-    for _ in range(args.warmup):
-        mixed.element_sensitivity(elems, u, lam_t)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        mixed.element_sensitivity(elems, u, lam_t)
-    e1.record(stream)
-    e1.synchronize()
-    # per call, including the call's status read (a stream synchronisation)
-    fwd_bwd["element_call_ms"] = e0.elapsed_time(e1) / max(args.steps, 1)
-    fwd_bwd["elements"] = elems.n_el
-    fwd_bwd["speedup_mixed_vs_fp64"] = fwd_bwd["fp64_ms"] / fwd_bwd["mixed_ms"]
-    fwd_bwd["loss"] = ("compliance J = f . u; backward = adjoint solve to the same tol, then "
-                       "dJ/df and dJ/dE_e for every element")
+    def measure_fwd_bwd():
+        from paper_2111_09294_gb300 import Elements
+        from paper_2111_09294_gb300.autograd import solve as dsolve
+        elems = Elements.from_dict(X.element_data(P), dev)
+        young = torch.tensor(P.young, device=dev)
+        fwd_bwd = {}
+        for name, solver in (("mixed", mixed), ("fp64", fp64)):
+            ts = []
+            for it in range(args.warmup + args.steps):
+                fg = f.clone().requires_grad_(True)
+                yg = young.clone().requires_grad_(True)
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                J = (fg * dsolve(solver, fg, TOL, young=yg, elements=elems)).sum()
+                J.backward()
+                e1.record(stream)
+                e1.synchronize()
+                if it >= args.warmup:
+                    ts.append(e0.elapsed_time(e1))
+            fwd_bwd[name + "_ms"] = float(np.mean(ts))
+        # the element kernel alone (all elements, one launch)
+        lam_t = torch.randn(P.n, dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            mixed.element_sensitivity(elems, u, lam_t)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            mixed.element_sensitivity(elems, u, lam_t)
+        e1.record(stream)
+        e1.synchronize()
+        # per call, including the call's status read (a stream synchronisation)
+        fwd_bwd["element_call_ms"] = e0.elapsed_time(e1) / max(args.steps, 1)
+        fwd_bwd["elements"] = elems.n_el
+        fwd_bwd["speedup_mixed_vs_fp64"] = fwd_bwd["fp64_ms"] / fwd_bwd["mixed_ms"]
+        fwd_bwd["loss"] = ("compliance J = f . u; backward = adjoint solve to the same tol, then "
+                           "dJ/df and dJ/dE_e for every element")
+        return fwd_bwd
     # a propagation sweep: --sweep systems of the 32^3 inclined-penny sweep,
     # 8 load cases each, every system a batched mixed solve on its own stream;
     # concurrent against one after another (outside the value)
-    sweep = None
-    if args.sweep > 0:
+    def measure_sweep():
         from paper_2111_09294_gb300 import sweep as S
         Ps = X.make_many(X.SWEEP[:args.sweep])
         ssol = S.make_solvers(Ps, max_batch=8)
@@ -428,6 +429,18 @@ def run_ours(args):
                  "timing": "host wall clock around the calls (each returns after its stream)"}
         for s_ in ssol:
             s_.close()
+        return sweep
+
+    def optional(fn):
+        # an extra measurement that fails is reported, not fatal to the line
+        try:
+            return fn()
+        except Exception as e:   # noqa: BLE001
+            return {"error": f"{type(e).__name__}: {e}"[:300]}
+
+    batch = optional(measure_batch) if args.batch > 0 else None
+    fwd_bwd = optional(measure_fwd_bwd)
+    sweep = optional(measure_sweep) if args.sweep > 0 else None
     info = mixed.info
     n_sp = sum(i["n_spmv_timed"] for i in inf_mixed_t)
     t_sp = sum(i["t_spmv_ms"] for i in inf_mixed_t)
