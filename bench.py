@@ -372,7 +372,10 @@ def run_ours(args):
                 e1.synchronize()
                 if it >= args.warmup:
                     ts.append(e0.elapsed_time(e1))
-            fwd_bwd[name + "_ms"] = float(np.mean(ts))
+            # median and mean of the timed steps (the median is robust to a
+            # one-off host stall inside autograd)
+            fwd_bwd[name + "_ms"] = float(np.median(ts))
+            fwd_bwd[name + "_ms_mean"] = float(np.mean(ts))
         # the element kernel alone (all elements, one launch)
         lam_t = torch.randn(P.n, dtype=torch.float64, device=dev)
         for _ in range(args.warmup):
