@@ -35,7 +35,8 @@ def solve_systems(solvers, loads, tol, outs=None, concurrent=True, raise_on_erro
     if len(solvers) != len(loads):
         raise ValueError("one load tensor per solver")
     outs = outs if outs is not None else [torch.empty_like(F) for F in loads]
-    torch.cuda.synchronize()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
 
     def run(i):
         return solvers[i].solve_batch(loads[i], tol=tol, out=outs[i],
