@@ -183,9 +183,11 @@ xdcg_status xdcg_solve_x0(xdcg_ctx *ctx, const double *f, double *u, double tol,
  * column j at offset j * n (may not alias).  With MIXED and opt.max_batch >= m
  * the columns run as one batched FP32 iteration: each iteration reads K~, Z~,
  * W~ and E^-1 once for all columns; each column stops once its FP64 true
- * residual meets tol, and FP64 residual replacements happen for all active
- * columns together.  Otherwise (FP64, or max_batch = 0) the columns are solved
- * one after another.  res: NULL or m results; iterations are counted per
+ * residual meets tol.  A column's FP64 residual replacement happens when its
+ * own FP32 residual has dropped far enough (the other columns finish the
+ * interrupted iteration); a breakdown in any column replaces every active
+ * column.  Otherwise (FP64, or max_batch = 0) the columns are solved one
+ * after another.  res: NULL or m results; iterations are counted per
  * column (the shared counter when the column converged).  Returns the worst
  * status over the columns. */
 xdcg_status xdcg_solve_batch(xdcg_ctx *ctx, const double *F, double *U, int32_t m, double tol,
