@@ -10,7 +10,9 @@ Plain, slow and literal:
             enriched modes (Section 3.3.2, Eqs. enriched_deflated_modes,
             dcg_deflation_space_enr_std, dcg_deflation_space_enr_enr).
 * M^-1   -- block Jacobi (Section 3.4, Eqs. block_jacobi, block_jacobi_enr):
-            dense Cholesky of each diagonal block, two triangular solves.
+            dense Cholesky of each diagonal block, two triangular solves;
+            blocks per node (the GPU path's choice) or per subdomain (the
+            paper's experiments).
 * u_0    -- Algorithm 2 (two coarse solves).
 * z      -- Algorithm 3 (two coarse solves, W^T K y evaluated as Z^T (K y)).
 * loop   -- Algorithm 1, stopped when ||r_i||_2 <= tol ||f||_2, the test made
@@ -175,6 +177,42 @@ class BlockJacobi:
             w = np.linalg.solve(L, rb)
             y[idx] = np.linalg.solve(np.swapaxes(L, 1, 2), w)[:, :, 0]
         return y
+
+
+class SubdomainJacobi:
+    """M^-1 with one block per subdomain, the block choice of the paper's
+    experiments (Section 3.4: all dofs of a subdomain, enriched ones
+    included, form one diagonal block of K), each block factored by dense
+    Cholesky at set-up.  groups: one array of global dofs per block."""
+
+    def __init__(self, K, groups):
+        Kc = K.tocsr()
+        self.groups = [np.asarray(g, dtype=np.int64) for g in groups]
+        self.cho = []
+        for i, g in enumerate(self.groups):
+            B = Kc[g][:, g].toarray()
+            try:
+                self.cho.append(sla.cho_factor(B, lower=True))
+            except np.linalg.LinAlgError:
+                raise NotSPD(i)
+
+    def apply(self, r):
+        y = np.zeros_like(r)
+        for g, c in zip(self.groups, self.cho):
+            y[g] = sla.cho_solve(c, r[g])
+        return y
+
+
+def subdomain_dofs(P):
+    """The dofs of each box subdomain (its nodes' dofs, node by node)."""
+    dof = np.asarray(P.dof_ptr, dtype=np.int64)
+    sub = np.asarray(P.sub_of_node)
+    out = []
+    for s in range(P.n_sub):
+        nodes = np.nonzero(sub == s)[0]
+        out.append(np.concatenate([np.arange(dof[I], dof[I + 1]) for I in nodes])
+                   if nodes.size else np.zeros(0, dtype=np.int64))
+    return out
 
 
 class Identity:
