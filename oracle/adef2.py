@@ -48,7 +48,8 @@ class Breakdown(Exception):
 
 
 def stiffness_csr(P):
-    """K as a scipy CSR matrix from the node-blocked storage of Problem P."""
+    """K of Eq. linear_system (Section 2.4) as a scipy CSR matrix, from the
+    node-blocked storage of Problem P."""
     dof = np.asarray(P.dof_ptr, dtype=np.int64)
     rowp = np.asarray(P.row_ptr, dtype=np.int64)
     col = np.asarray(P.col, dtype=np.int64)
@@ -98,7 +99,7 @@ def collinear(x):
 
 
 def deflation_basis(P, enriched=True):
-    """Z (n x k, scipy CSC) and the first column of each box.
+    """Z (n x k, scipy CSC) of Section 3.3 and the first column of each box.
 
     Box s owns columns [col0[s], col0[s] + 6) for the rigid modes and, when it
     holds a jump-enriched node (and `enriched`), [col0[s] + 6, col0[s] + 12)
@@ -204,7 +205,8 @@ class SubdomainJacobi:
 
 
 def subdomain_dofs(P):
-    """The dofs of each box subdomain (its nodes' dofs, node by node)."""
+    """The dofs of each box subdomain (its nodes' dofs, node by node): the
+    blocks of the subdomain-sized block Jacobi of Section 3.4."""
     dof = np.asarray(P.dof_ptr, dtype=np.int64)
     sub = np.asarray(P.sub_of_node)
     out = []
@@ -216,12 +218,15 @@ def subdomain_dofs(P):
 
 
 class Identity:
+    """M = I: Algorithm 3 without the block-Jacobi part (test cases)."""
+
     def apply(self, r):
         return r.copy()
 
 
 class Coarse:
-    """E = Z^T K Z, factored by dense Cholesky; k = 0 gives no deflation."""
+    """E = Z^T K Z, the coarse matrix of the deflation (Section 3.2), factored
+    by dense Cholesky; k = 0 gives no deflation."""
 
     def __init__(self, K, Z):
         self.Z = Z
@@ -355,6 +360,7 @@ def setup(P, enriched_modes=True):
 
 
 def solve(P, tol=1e-8, maxit=10000, record=False, enriched_modes=True):
+    """setup() and adef2_pcg() for Problem P's own load."""
     K, M, C = setup(P, enriched_modes)
     return adef2_pcg(K, P.f, M, C, tol=tol, maxit=maxit, record=record)
 
