@@ -11,6 +11,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 using namespace xdcg;
@@ -90,6 +92,16 @@ namespace {
         cudaError_t e_ = (call);                      \
         if (e_ != cudaSuccess) return XDCG_CUDA_ERROR; \
     } while (0)
+
+// A named range on the profiler timeline (NVTX) for the life of a scope, so
+// that a profiler can select the set-up or one solve; a no-op when no
+// profiler is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 template <typename T>
 T *dalloc(xdcg_ctx *c, size_t count) {
@@ -785,6 +797,7 @@ xdcg_status solve_batch_mixed(xdcg_ctx *c, const double *F, double *U, int m, do
 
 xdcg_status do_solve(xdcg_ctx *c, const double *f, double *u, double tol, bool guess,
                      xdcg_result *out) {
+    NvtxRange range(c->opt.precision == XDCG_MIXED ? "xdcg solve (mixed)" : "xdcg solve (fp64)");
     xdcg_result res{};
     res.bad_index = -1;
     if (tol <= 0) tol = c->opt.tol;
@@ -1577,6 +1590,7 @@ xdcg_status xdcg_default_options(xdcg_options *opt) {
 xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflation *Z,
                        const void *blocks, const xdcg_options *opt, void *stream,
                        int32_t *bad_index) {
+    NvtxRange range("xdcg setup");
     if (bad_index) *bad_index = -1;
     if (!out) return XDCG_INVALID_ARG;
     *out = nullptr;
@@ -1625,6 +1639,7 @@ xdcg_status xdcg_solve_x0(xdcg_ctx *c, const double *f, double *u, double tol, x
 
 xdcg_status xdcg_solve_batch(xdcg_ctx *c, const double *F, double *U, int32_t m, double tol,
                              xdcg_result *res) {
+    NvtxRange range("xdcg solve_batch");
     if (!c || !F || !U || F == U || m < 1) return XDCG_INVALID_ARG;
     if (tol <= 0) tol = c->opt.tol;
     xdcg_result local[kMaxBatch];
