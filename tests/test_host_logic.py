@@ -66,7 +66,7 @@ class _FakeSolver:
 
 def test_sweep_keeps_system_order_and_overlaps_calls():
     from paper_2111_09294_gb300 import sweep as S
-    solvers = [_FakeSolver(0.2), _FakeSolver(0.05), _FakeSolver(0.1)]
+    solvers = [_FakeSolver(0.6), _FakeSolver(0.15), _FakeSolver(0.3)]
     loads = [torch.full((2, 3), float(i)) for i in range(3)]
     t0 = time.perf_counter()
     res = S.solve_systems(solvers, loads, 1e-8)
@@ -75,7 +75,7 @@ def test_sweep_keeps_system_order_and_overlaps_calls():
         assert torch.equal(U, 2 * loads[i]) and len(infos) == 2 and infos[0]["tol"] == 1e-8
     # one host thread per system: the calls overlap
     assert len({s.threads[0] for s in solvers}) == 3
-    assert concurrent < 0.3
+    assert concurrent < 0.9           # one after another takes 1.05 s
     seq = S.solve_systems(solvers, loads, 1e-8, concurrent=False)
     assert all(torch.equal(a[0], b[0]) for a, b in zip(res, seq))
     assert len({s.threads[1] for s in solvers}) == 1
