@@ -35,6 +35,10 @@ def test_cube8_edge_counts_match_hand_derivation():
     assert P.n_heaviside_dofs == g["heaviside_dofs"]
     assert P.n_tip_dofs == g["tip_dofs"]
     assert P.n == g["n"]
+    # the coarse dimension of the hand derivation, from the oracle's own basis
+    from oracle import adef2 as O
+    Z, col0 = O.deflation_basis(P)
+    assert Z.shape[1] == col0[-1] == g["coarse_k"]
 
 
 def test_tet_rule_exact_for_degree_5():
