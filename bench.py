@@ -5,9 +5,12 @@ hot path: Algorithm 2 start, A-DEF2 PCG iterations, FP64 residual replacement
 for the mixed path) with the load vector already resident in HBM; L2 is flushed
 (a 256 MiB write) before every timed step, outside the step's events.
 Reported: mixed (FP32 PCG / FP64 residual replacement) solve time as the value, the
-plain FP64 solve time beside it, iterations, SpMV bandwidth against the
-measured HBM copy bandwidth, the FP64 CPU oracle on a bounded sample, and an
-end-to-end figure through the host-memory entry point.
+plain FP64 solve time and the mixed solve with an FP64 coarse solve beside it,
+iterations (the oracle's too), SpMV bandwidth against the measured HBM copy
+bandwidth, the FP64 SpMV against the measured FP64 rate, one full FP64 CPU
+oracle solve on 1 thread and on all host cores, an end-to-end figure through
+the host-memory entry point, and the batched, differentiable and
+propagation-sweep workloads.
 
 --impl reference: the CPU oracle as the reference arm (same metric and
 workload, each step a bounded sample of oracle iterations scaled to the
@@ -155,16 +158,63 @@ def max_over_ranks(pg, v, device=None):
     return float(t.item())
 
 
-def oracle_sample(P, iterations_full, sample_iters):
-    """Time the oracle's setup-free solve on a bounded number of iterations and
-    scale to the full iteration count."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_full_solve(workload):
+    """One full FP64 oracle solve to 1e-8 (set-up timed separately); runs in
+    the process whose BLAS thread count the caller fixed."""
+    import xfem_inputs as X
     from oracle import adef2 as O
-    K, M, C = O.setup(P)
+    P = X.make(workload)
     t0 = time.perf_counter()
-    r = O.adef2_pcg(K, P.f, M, C, tol=TOL, maxit=sample_iters)
-    dt = time.perf_counter() - t0
-    per_it = dt / max(r.iterations, 1)
-    return per_it * iterations_full * 1e3, per_it, r.iterations, (K, M, C)
+    K, M, C = O.setup(P)
+    t1 = time.perf_counter()
+    r = O.adef2_pcg(K, P.f, M, C, tol=TOL)
+    t2 = time.perf_counter()
+    return {"ms": (t2 - t1) * 1e3, "setup_ms": (t1 - t0) * 1e3, "iterations": r.iterations,
+            "rel_res_true": float(np.linalg.norm(P.f - K @ r.u) / np.linalg.norm(P.f))}
+
+
+def oracle_timing(workload, threads):
+    """oracle_full_solve in a fresh Python process with `threads` BLAS/OpenMP
+    threads (the thread count is fixed when numpy loads, so each count needs a
+    process of its own; no CUDA is touched there)."""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = str(threads)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-solve",
+                        "--workload", workload], env=env, capture_output=True, text=True,
+                       timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle run failed: {r.stderr[-300:]}")
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    out["threads"] = threads
+    return out
+
+
+def fp64_peak_tflops(dev):
+    """Measured FP64 rate of this GPU: a cuBLAS DGEMM (4096^3, 2 n^3 flops),
+    best of 5 after a warm-up, CUDA events."""
+    import torch
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    torch.matmul(a, b)
+    best = float("inf")
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
 
 
 def run_reference(args):
@@ -216,6 +266,14 @@ def config_dict(P, k, workload):
             "l2": "flushed (256 MiB write) before every timed step"}
 
 
+def optional(fn):
+    """An extra measurement that fails is reported in the line, not fatal to it."""
+    try:
+        return fn()
+    except Exception as e:   # noqa: BLE001
+        return {"error": f"{type(e).__name__}: {e}"[:300]}
+
+
 def run_ours(args):
     import torch
     world, rank, local, pg = dist_setup(args)
@@ -230,6 +288,8 @@ def run_ours(args):
     # solvers with CUDA events around every SpMV give the SpMV's own time
     mixed = Solver.from_problem(P, precision="mixed", inner_tol=args.inner_tol)
     fp64 = Solver.from_problem(P, precision="fp64")
+    mixed_c64 = Solver.from_problem(P, precision="mixed", inner_tol=args.inner_tol,
+                                    coarse_fp64=True)
     mixed_t = Solver.from_problem(P, precision="mixed", time_spmv=True, inner_tol=args.inner_tol)
     fp64_t = Solver.from_problem(P, precision="fp64", time_spmv=True)
     f = torch.tensor(P.f, device=dev)
@@ -260,6 +320,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier(pg)
     ms_fp64, inf_fp64 = timed(fp64, args.steps, args.warmup, True)
+    torch.cuda.synchronize()
+    barrier(pg)
+    ms_c64, inf_c64 = timed(mixed_c64, args.steps, args.warmup, True)
     torch.cuda.synchronize()
     barrier(pg)
     # SpMV kernel time: a timed pass of the same solves with events around each SpMV
@@ -434,13 +497,6 @@ def run_ours(args):
             s_.close()
         return sweep
 
-    def optional(fn):
-        # an extra measurement that fails is reported, not fatal to the line
-        try:
-            return fn()
-        except Exception as e:   # noqa: BLE001
-            return {"error": f"{type(e).__name__}: {e}"[:300]}
-
     batch = optional(measure_batch) if args.batch > 0 else None
     fwd_bwd = optional(measure_fwd_bwd)
     sweep = optional(measure_sweep) if args.sweep > 0 else None
@@ -448,19 +504,27 @@ def run_ours(args):
     n_sp = sum(i["n_spmv_timed"] for i in inf_mixed_t)
     t_sp = sum(i["t_spmv_ms"] for i in inf_mixed_t)
     spmv_ms = t_sp / max(n_sp, 1)
-    achieved = info["spmv_bytes_fp32"] / (spmv_ms * 1e-3) / 1e9
+    # algorithmic bytes on the node-blocked matrix (one index per node block);
+    # the kernel's own chunked layout moves spmv_bytes_fp32 (one index per 3x3)
+    achieved = info["spmv_alg_bytes_fp32"] / (spmv_ms * 1e-3) / 1e9
+    achieved_fmt = info["spmv_bytes_fp32"] / (spmv_ms * 1e-3) / 1e9
     n64 = sum(i["n_spmv_timed"] for i in inf_fp64_t)
     spmv64_ms = sum(i["t_spmv_ms"] for i in inf_fp64_t) / max(n64, 1)
-    achieved64 = info["spmv_bytes_fp64"] / (spmv64_ms * 1e-3) / 1e9
+    achieved64 = info["spmv_alg_bytes_fp64"] / (spmv64_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
     traffic = profiled_traffic(SPMV_SOURCES, f"spmv_fp32_{args.workload}.md")
     its_fp64 = inf_fp64[-1]["iterations"]
-    cpu = None
+    fp64_tf = optional(lambda: fp64_peak_tflops(dev))
+    cpu, oracle_all, one = None, None, None
     if not args.no_cpu_baseline and world == 1:
-        est_ms, per_it, n_s, _ = oracle_sample(P, its_fp64, args.sample_iters)
-        cpu = {"value": est_ms, "unit": "ms", "cores": 1, "kind": "oracle",
-               "sample": f"{n_s} FP64 oracle iterations ({per_it * 1e3:.1f} ms each, 1 thread) "
-                         f"scaled to {its_fp64} iterations to 1e-8, setup excluded"}
+        one = oracle_timing(args.workload, 1)
+        cpu = {"value": one["ms"], "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": f"one full FP64 oracle solve to 1e-8 ({one['iterations']} iterations, "
+                         f"1 thread), set-up ({one['setup_ms']:.0f} ms) excluded"}
+        nc = host_cores()
+        oracle_all = optional(lambda: oracle_timing(args.workload, nc))
+        if isinstance(oracle_all, dict) and "ms" in oracle_all:
+            oracle_all["cores"] = nc
     out = {
         "metric": METRIC, "value": t_mixed, "unit": "ms", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_mixed,
@@ -470,6 +534,12 @@ def run_ours(args):
         "fp64_ms": t_fp64, "speedup_mixed_vs_fp64": t_fp64 / t_mixed,
         "iterations_mixed": inf_mixed[-1]["iterations"],
         "outer_cycles_mixed": inf_mixed[-1]["outer_cycles"], "iterations_fp64": its_fp64,
+        "iterations_oracle": one["iterations"] if one else None,
+        "mixed_coarse_fp64": {"ms": max_over_ranks(pg, float(np.mean(ms_c64)), dev),
+                              "iterations": inf_c64[-1]["iterations"],
+                              "outer_cycles": inf_c64[-1]["outer_cycles"],
+                              "rel_res_true": max(i["rel_res_true"] for i in inf_c64),
+                              "note": "E^-1 applied in FP64 inside the FP32 iteration"},
         "rel_res_true_mixed": res_true, "rel_res_true_fp64": inf_fp64[-1]["rel_res_true"],
         "setup_ms": info["t_setup_ms"],
         "spmv_fp32_gbs": achieved, "spmv_fp64_gbs": achieved64,
@@ -480,8 +550,16 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": "k_spmv<float> (inner FP32 SpMV)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind,
-                     "traffic": traffic, "algorithmic_bytes": info["spmv_bytes_fp32"],
+                     "traffic": traffic, "algorithmic_bytes": info["spmv_alg_bytes_fp32"],
+                     "format_bytes": info["spmv_bytes_fp32"], "achieved_format": achieved_fmt,
                      "avg_launch_ms": spmv_ms},
+        "roofline_fp64_spmv": {"bound": "alu", "kernel": "k_spmv<double> (FP64 SpMV)",
+                               "flops": 2 * info["nnz"], "avg_launch_ms": spmv64_ms,
+                               "achieved_tflops": 2 * info["nnz"] / (spmv64_ms * 1e-3) / 1e12,
+                               "peak_tflops": fp64_tf if isinstance(fp64_tf, float) else None,
+                               "peak_source": "measured: cuBLAS DGEMM 4096^3 in this run",
+                               "gbs": achieved64},
+        "oracle_all_cores": oracle_all,
         "e2e": {"value": t_e2e, "unit": "ms", "h2d_bytes_per_step": 8 * P.n,
                 "d2h_bytes_per_step": 8 * P.n},
         "gpu_launches": int(sum(i["n_launches"] for i in inf_mixed)),
@@ -540,13 +618,20 @@ def main():
     ap.add_argument("--batch", type=int, default=8,
                     help="load cases of the batched-solve measurement (0: skip)")
     ap.add_argument("--sample-iters", type=int, default=10)
-    ap.add_argument("--sweep", type=int, default=0,
-                    help="also solve this many systems of the 32^3 propagation sweep (<= 16)")
+    ap.add_argument("--sweep", type=int, default=16,
+                    help="also solve this many systems of the 32^3 propagation sweep "
+                         "(<= 16; 0: skip)")
+    ap.add_argument("--oracle-solve", action="store_true",
+                    help="internal: one timed FP64 oracle solve of --workload, printed as JSON "
+                         "(run in a child process with a fixed BLAS thread count)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", choices=["mixed", "fp64", "batch"], default=None,
                     help="profiler capture: one solve of the given path between "
                          "cudaProfilerStart/Stop after warm-up, nothing else timed")
     args = ap.parse_args()
+    if args.oracle_solve:
+        print(json.dumps(oracle_full_solve(args.workload)))
+        return
     if args.profile:
         run_profile(args)
     elif args.impl == "reference":

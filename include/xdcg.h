@@ -113,6 +113,18 @@ typedef struct {
                                 (xdcg_get_history); default 0 */
     int32_t max_batch;       /* MIXED: right-hand sides one xdcg_solve_batch call may take
                                 together (0..8; 0 = no batched buffers), default 0 */
+    int32_t coarse_fp64;     /* MIXED: 1 applies E^-1 in FP64 inside the FP32 iteration (an FP64
+                                GEMV whose result is rounded to FP32); default 0: an FP32 copy
+                                of E^-1 (half the bytes; A-DEF2 tolerates the inexact coarse
+                                solve).  Single right-hand-side solves; the batched FP32
+                                iteration of xdcg_solve_batch uses the FP32 copy.  The FP64
+                                path always applies E^-1 in FP64 */
+    double wait_s;           /* limit of every bounded device wait on the SpMV's own bulk copies,
+                                in seconds, default 2.  A wait that runs out ends the call with
+                                XDCG_TIMEOUT after the copies in flight have landed (their own
+                                limit, 0.1 s, is fixed).  0 gives up at the first check that
+                                finds a copy still in flight: it exists to exercise that
+                                status, not for use */
 } xdcg_options;
 
 typedef struct {
@@ -138,14 +150,22 @@ typedef struct {
     int32_t k;                   /* coarse dimension */
     int64_t nnz;                 /* scalar nonzeros of K */
     int64_t nnzb3;               /* 3x3 blocks of the chunked SpMV layout */
-    int64_t spmv_bytes_fp64;     /* algorithmic bytes of one FP64 SpMV */
-    int64_t spmv_bytes_fp32;     /* algorithmic bytes of one FP32 SpMV */
+    int64_t spmv_bytes_fp64;     /* bytes one FP64 SpMV reads and writes in the library's
+                                    chunked layout (one index per 3x3 chunk block, row data,
+                                    p read once, q written once; slot padding excluded) */
+    int64_t spmv_bytes_fp32;     /* the same for the FP32 SpMV */
     int64_t iter_bytes_fp64;     /* algorithmic bytes of one FP64 iteration */
     int64_t iter_bytes_fp32;     /* algorithmic bytes of one FP32 inner iteration (MIXED) */
     double t_setup_ms;           /* wall time of xdcg_setup */
     int64_t restrict_bytes_fp32; /* ... of its restriction + update kernel (MIXED) */
     int64_t coarse_bytes_fp32;   /* ... of its coarse solve kernel (MIXED) */
     int64_t prolong_bytes_fp32;  /* ... of its prolongation kernel (MIXED) */
+    int64_t nnzb;                /* node blocks of K (entries of the caller's block CSR) */
+    int64_t spmv_alg_bytes_fp64; /* bytes one product q = K p must move at least, counted on
+                                    the node-blocked matrix: 8 nnz + 4 nnzb + 4 (n_nodes + 1)
+                                    + 2 * 8 n (values, block indices, row pointers, p read
+                                    once, q written once) */
+    int64_t spmv_alg_bytes_fp32; /* the same with 4-byte values and vectors */
 } xdcg_info_t;
 
 /* Fill *opt with the defaults listed above. */
@@ -217,11 +237,13 @@ xdcg_status xdcg_get_history(xdcg_ctx *ctx, double *out, int32_t cap, int32_t *c
  * the host. */
 xdcg_status xdcg_spmv(xdcg_ctx *ctx, int32_t precision, const void *x, void *y, double *xty);
 
-/* Same result as xdcg_spmv, for callers that must not allocate device
- * memory: code that records into a CUDA stream capture (an allocation there
- * would break the capture), or that runs where another allocator owns the
- * whole device memory budget.  The paper has no counterpart; this is a
- * property of the library, not of the method.
+/* Same result as xdcg_spmv, for callers that cannot allocate device memory
+ * at the point of the call: code that runs while another allocator (a
+ * framework's caching allocator, or a memory pool sized to the whole device)
+ * holds the device memory budget, so that a cudaMalloc would fail; and code
+ * on a latency-critical path, where cudaMalloc and cudaFree can synchronise
+ * the device and stall its other streams.  The paper has no counterpart;
+ * this is a property of the library, not of the method.
  *
  * It allocates nothing.  The SpMV's reduction scratch (block partial sums
  * and its scalar block) lives in one file-scope device array of
@@ -229,16 +251,21 @@ xdcg_status xdcg_spmv(xdcg_ctx *ctx, int32_t precision, const void *x, void *y, 
  * every GPU that loads the library keeps until the process exits.  The
  * first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current, so make that first call
- * before any stream capture.  All calls share the array, which keeps the
- * last call's contents; each call clears what must start at zero, but calls
- * that overlap on the GPU (other streams, other contexts) race on it.  The
- * XDCG_MIXED product also uses the context's own FP32 work vectors (it
- * renumbers x and y, see xdcg_spmv), so it must not overlap another call on
- * the same context.
+ * before any stream capture.  The device current at the call must be the
+ * context's (the one current at xdcg_setup), else XDCG_INVALID_ARG.  All
+ * calls share the array, which keeps the last call's contents; each call
+ * clears what must start at zero, but calls that overlap on the GPU (other
+ * streams, other contexts) race on it.  The XDCG_MIXED product also uses the
+ * context's own FP32 work vectors (it renumbers x and y, see xdcg_spmv), so
+ * it must not overlap another call on the same context.
  *
  * x, y: device arrays of n values (double for XDCG_FP64, float for
  * XDCG_MIXED, as in xdcg_spmv).  xty_dev: NULL or a device double that
- * receives x^T y.  Asynchronous on the context stream.  Returns
+ * receives x^T y.  Asynchronous on the context stream, so the call returns
+ * before the product is done and reports no device-side failure itself: if
+ * a bounded wait of the product on its own copies ran out (the condition
+ * xdcg_spmv reports as XDCG_TIMEOUT), *xty_dev is set to NaN and y is not
+ * valid; a caller that must detect this passes xty_dev.  Returns
  * XDCG_TOO_LARGE when the context's SpMV grid exceeds
  * XDCG_NOALLOC_MAX_BLOCKS blocks (the SpMV runs a persistent grid of at
  * most a few blocks per SM, so this does not happen on current GPUs). */

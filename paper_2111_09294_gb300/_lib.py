@@ -40,7 +40,8 @@ class Deflation(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("tol", c_double), ("max_iter", c_int32), ("precision", c_int32),
                 ("inner_tol", c_double), ("max_outer", c_int32), ("time_spmv", c_int32),
-                ("jacobi", c_int32), ("record_history", c_int32), ("max_batch", c_int32)]
+                ("jacobi", c_int32), ("record_history", c_int32), ("max_batch", c_int32),
+                ("coarse_fp64", c_int32), ("wait_s", c_double)]
 
 
 class Result(ctypes.Structure):
@@ -61,7 +62,9 @@ class Info(ctypes.Structure):
                 ("nnzb3", c_int64), ("spmv_bytes_fp64", c_int64), ("spmv_bytes_fp32", c_int64),
                 ("iter_bytes_fp64", c_int64), ("iter_bytes_fp32", c_int64),
                 ("t_setup_ms", c_double), ("restrict_bytes_fp32", c_int64),
-                ("coarse_bytes_fp32", c_int64), ("prolong_bytes_fp32", c_int64)]
+                ("coarse_bytes_fp32", c_int64), ("prolong_bytes_fp32", c_int64),
+                ("nnzb", c_int64), ("spmv_alg_bytes_fp64", c_int64),
+                ("spmv_alg_bytes_fp32", c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -375,6 +375,15 @@ __global__ void k_set_trigger(Scalars *sc, int mode, double delta2, double floor
     }
 }
 
+// nu = E^-1 g inside the FP32 iteration: the FP32 copy of E^-1 (default) or
+// the FP64 one (opt.coarse_fp64), both writing nu and its FP32 copy nu32
+void coarse_inner(xdcg_ctx *c, const double *zr, int mode, Scalars *sc) {
+    if (c->opt.coarse_fp64)
+        launch_coarse(c->Einv, c->k, c->g, zr, c->nu, c->nu32, mode, c->partials, sc, c->st);
+    else
+        launch_coarse32(c->Einv32, c->k, c->g32, zr, c->nu, c->nu32, mode, c->partials, sc, c->st);
+}
+
 // Algorithm 2 and the first direction: u~ = Z~ E^-1 Z~^T f~, r = f~ - K~ u~ (rA),
 // z = r + Z~ nu, p = z.
 void scaled_init(xdcg_ctx *c, const float *f, float *u, float *rA, float *p, Scalars *sc) {
@@ -382,12 +391,12 @@ void scaled_init(xdcg_ctx *c, const float *f, float *u, float *rA, float *p, Sca
     Level32 &L = c->L32;
     launch_restrict_update(L.R, nullptr, f, nullptr, nullptr, nullptr, 2, c->g, nullptr,
                            c->partials, sc, st);
-    launch_coarse32(c->Einv32, c->k, c->g32, nullptr, c->nu, c->nu32, 0, c->partials, sc, st);
+    coarse_inner(c, nullptr, 0, sc);
     launch_prolong_rows(L.R, c->nu32, nullptr, u, 1, sc, st);
     launch_spmv<float>(L.A, u, rA, f, 1, c->partials, sc, kFinRR, 0, st);
     launch_restrict_update(L.R, nullptr, rA, nullptr, nullptr, nullptr, 1, c->g, c->zr,
                            c->partials, sc, st);
-    launch_coarse32(c->Einv32, c->k, c->g32, c->zr, c->nu, c->nu32, 1, c->partials, sc, st);
+    coarse_inner(c, c->zr, 1, sc);
     launch_prolong_rows(L.R, c->nu32, rA, p, 2, sc, st);
     c->launches += 7;
 }
@@ -425,7 +434,7 @@ xdcg_status scaled_iterate(xdcg_ctx *c, float *u, float *rA, float *rB, float *p
             MARK(launched, 1);
             launch_restrict_update(L.R, u, rc, rn, p, q, 0, c->g, c->zr, c->partials, sc, st);
             MARK(launched, 2);
-            launch_coarse32(c->Einv32, c->k, c->g32, c->zr, c->nu, c->nu32, 2, c->partials, sc, st);
+            coarse_inner(c, c->zr, 2, sc);
             MARK(launched, 3);
             launch_prolong_rows(L.R, c->nu32, rn, p, 0, sc, st);
             MARK(launched, 4);
@@ -584,8 +593,7 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, boo
         k_set_trigger<<<1, 32, 0, st>>>(c->sc32, 0, 0.0, 0.0);
         launch_restrict_update(L.R, nullptr, rbuf, nullptr, nullptr, nullptr, 1, c->g, c->zr,
                                c->partials, c->sc32, st);
-        launch_coarse32(c->Einv32, c->k, c->g32, c->zr, c->nu, c->nu32, done == kBreakdown ? 1 : 3,
-                      c->partials, c->sc32, st);
+        coarse_inner(c, c->zr, done == kBreakdown ? 1 : 3, c->sc32);
         launch_prolong_rows(L.R, c->nu32, rbuf, c->p32, done == kBreakdown ? 2 : 0, c->sc32, st);
         c->launches += 5;
         CK(cudaMemcpyAsync(c->h_sc, c->sc32, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
@@ -1176,6 +1184,8 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         ws[nW] = nT;
         return upload(c, ws);
     };
+    const unsigned long long waitNs = (unsigned long long)(c->opt.wait_s * 1e9);
+    A.waitNs = waitNs;
     A.grid = spmv_persistent_grid<double>(HS.nSlices + HX.nSlices);
     if (A.grid < 1) return XDCG_CUDA_ERROR;
     A.warpSlice = partition(HS, HX, A.grid);
@@ -1359,6 +1369,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         launch_scale_blocks(kin, d_brow, nnzb, F, d_Kt, st);
         launch_gather(d_src32S, (long long)HS32.src.size(), d_Kt, nullptr, v32S, st);
         launch_gather(d_src32X, (long long)HX32.src.size(), d_Kt, nullptr, v32X, st);
+        A2.waitNs = waitNs;
         A2.grid = spmv_persistent_grid<float>(HS32.nSlices + HX32.nSlices);
         if (A2.grid < 1) return XDCG_CUDA_ERROR;
         A2.warpSlice = partition(HS32, HX32, A2.grid);
@@ -1551,7 +1562,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     const long long restrict32 = mixed ? 28LL * n + 4LL * c->zEnt32 + 12LL * c->extRows32 +
                                              4LL * c->wEnt32 + 16LL * k
                                        : 0;
-    const long long coarse32 = mixed ? 4LL * k * k + 28LL * k : 0;
+    const long long coarse32 = mixed ? (c->opt.coarse_fp64 ? 8LL : 4LL) * k * k + 28LL * k : 0;
     const long long prolong32 = mixed ? 16LL * n + 4LL * c->zEnt32 + 4LL * k : 0;
     const long long iter32 = mixed ? spmv_bytes(4) + restrict32 + coarse32 + prolong32 : 0;
     c->info.n = n;
@@ -1566,6 +1577,12 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     c->info.restrict_bytes_fp32 = restrict32;
     c->info.coarse_bytes_fp32 = coarse32;
     c->info.prolong_bytes_fp32 = prolong32;
+    c->info.nnzb = nnzb;
+    auto spmv_alg = [&](int s) {
+        return (long long)s * 9LL * nnzb3 + 4LL * nnzb + 4LL * (N + 1) + 2LL * s * n;
+    };
+    c->info.spmv_alg_bytes_fp64 = spmv_alg(8);
+    c->info.spmv_alg_bytes_fp32 = spmv_alg(4);
     return XDCG_OK;
 }
 
@@ -1584,6 +1601,8 @@ xdcg_status xdcg_default_options(xdcg_options *opt) {
     opt->jacobi = XDCG_BLOCK_JACOBI;
     opt->record_history = 0;
     opt->max_batch = 0;
+    opt->coarse_fp64 = 0;
+    opt->wait_s = 2.0;
     return XDCG_OK;
 }
 
@@ -1606,6 +1625,8 @@ xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflatio
         c->opt.time_spmv < 0 || c->opt.time_spmv > 2 ||
         (c->opt.jacobi != XDCG_BLOCK_JACOBI && c->opt.jacobi != XDCG_POINT_JACOBI) ||
         c->opt.max_batch < 0 || c->opt.max_batch > kMaxBatch ||
+        (c->opt.coarse_fp64 != 0 && c->opt.coarse_fp64 != 1) ||
+        !(c->opt.wait_s >= 0.0 && c->opt.wait_s <= 60.0) ||
         !(c->opt.inner_tol > 0 && c->opt.inner_tol < 1)) {
         delete c;
         return XDCG_INVALID_ARG;
@@ -1781,9 +1802,11 @@ xdcg_status xdcg_spmv_noalloc(xdcg_ctx *c, int32_t precision, const void *x, voi
     if (precision == XDCG_MIXED && !c->mixed) return XDCG_INVALID_ARG;
     const int grid = precision == XDCG_FP64 ? c->L64.A.grid : c->L32.A.grid;
     if (grid > XDCG_NOALLOC_MAX_BLOCKS) return XDCG_TOO_LARGE;
+    // the context's stream and buffers belong to the device that was current
+    // at set-up; the scratch must be that device's copy of the array
     int dev = 0;
     CK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return XDCG_INVALID_ARG;
+    if (dev != c->device || dev < 0 || dev >= kMaxDevices) return XDCG_INVALID_ARG;
     double *base = nullptr;
     {
         // first call on this device: resolve the array's device address

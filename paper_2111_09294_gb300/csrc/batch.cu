@@ -64,7 +64,7 @@ k_spmm(SpmvDev<float> A, int m, const float *__restrict__ x, float *__restrict__
     }
     __syncwarp();
     const uint64_t stream = l2_stream_policy();
-    const unsigned long long deadline = global_ns() + kWaitNs;
+    const unsigned long long deadline = global_ns() + A.waitNs;
     int issued = 0, more = 1, pSlice = A.warpSlice[gw] - 1, pStep = 0, pSteps = 0;
     long long pBase = 0;
     const int *pCol = nullptr;

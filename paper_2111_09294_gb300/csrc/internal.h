@@ -94,6 +94,7 @@ struct SpmvDev {
     int grid;                  // persistent blocks (kSpmvThreads each)
     const int *warpSlice;      // [grid * kSpmvWarps + 1] slice range of each warp
                                // (S slices, then X slices offset by S.nSlices)
+    unsigned long long waitNs; // limit of each launch's bounded waits on its bulk copies
 };
 
 // Node-level data: node lists per block size, packed Cholesky factors of
@@ -138,6 +139,10 @@ struct BoxDev {
 };
 
 // ---- launchers (defined in the .cu files) --------------------------------
+
+// Multiprocessors of the current device (queried once per device, then
+// cached); grids of the streaming kernels are sized from it.
+int device_sm_count();
 
 template <typename T>
 void launch_spmv(const SpmvDev<T> &A, const T *x, T *y, const T *b, int residual_mode,

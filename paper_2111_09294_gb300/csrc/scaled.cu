@@ -35,8 +35,8 @@ __global__ void k_gather_f32(const int *__restrict__ src, long long n, const dou
 }
 
 static int grid_of(long long n, int th) {
-    long long g = (n + th - 1) / th;
-    return (int)(g < 8 * 152 ? (g > 0 ? g : 1) : 8 * 152);
+    const long long g = (n + th - 1) / th, cap = 8LL * device_sm_count();
+    return (int)(g < cap ? (g > 0 ? g : 1) : cap);
 }
 
 void launch_gather(const int *src, long long n, const double *v, double *out64, float *out32,

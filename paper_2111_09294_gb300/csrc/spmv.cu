@@ -61,7 +61,7 @@ k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__rest
     }
     __syncwarp();
     const uint64_t stream = l2_stream_policy();
-    const unsigned long long deadline = global_ns() + kWaitNs;
+    const unsigned long long deadline = global_ns() + A.waitNs;
 
     // producer state, meaningful in lane 0
     int issued = 0, more = 1, pSlice = sFirst - 1, pStep = 0, pSteps = 0;
@@ -297,7 +297,18 @@ template void launch_spmv<float>(const SpmvDev<float> &, const float *, float *,
 
 // ---- dot products and mixed-precision conversions -------------------------
 
-constexpr int kDotBlocks = 304;   // 2 x 152 SMs
+int device_sm_count() {
+    constexpr int kMaxDev = 64;
+    static int cache[kMaxDev] = {0};   // 0 = not queried yet; every writer stores the same value
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+    if (dev < kMaxDev && cache[dev] > 0) return cache[dev];
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        return 1;
+    if (dev < kMaxDev) cache[dev] = sms;
+    return sms;
+}
+
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
@@ -315,7 +326,7 @@ k_dot(const T *__restrict__ a, const T *__restrict__ b, long long n, double *par
 template <typename T>
 void launch_dot(const T *a, const T *b, long long n, double *partials, Scalars *sc, int fin,
                 int slot, cudaStream_t st) {
-    k_dot<T><<<kDotBlocks, kThreads, 0, st>>>(a, b, n, partials, sc, fin, slot);
+    k_dot<T><<<2 * device_sm_count(), kThreads, 0, st>>>(a, b, n, partials, sc, fin, slot);
 }
 template void launch_dot<double>(const double *, const double *, long long, double *, Scalars *,
                                  int, int, cudaStream_t);
@@ -323,8 +334,8 @@ template void launch_dot<float>(const float *, const float *, long long, double 
                                 int, cudaStream_t);
 
 static int grid_for(long long n) {
-    long long g = (n + kThreads - 1) / kThreads;
-    return (int)(g < 4 * 152 ? (g > 0 ? g : 1) : 4 * 152);
+    const long long g = (n + kThreads - 1) / kThreads, cap = 4LL * device_sm_count();
+    return (int)(g < cap ? (g > 0 ? g : 1) : cap);
 }
 
 __global__ void k_cast_f32(const double *__restrict__ a, float *__restrict__ b, long long n) {

@@ -8,7 +8,7 @@
 
 namespace xdcg {
 
-constexpr unsigned long long kWaitNs = 2000000000ull;    // 2 s per kernel
+constexpr unsigned long long kWaitNs = 2000000000ull;    // default wait limit: 2 s per kernel
 constexpr unsigned long long kDrainNs = 100000000ull;    // 0.1 s to let copies land
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {

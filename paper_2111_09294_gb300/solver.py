@@ -43,13 +43,15 @@ class Solver:
     precision: "fp64" or "mixed" (FP32 PCG on the block-scaled system with FP64 residual replacement).
     jacobi: "block" (one block per node, the method's M) or "point" (diag K, the
     paper's comparison preconditioner).  record_history: keep ||r_i|| / ||f||
-    per iteration of FP64 solves (history()).
+    per iteration of FP64 solves (history()).  coarse_fp64: mixed solves apply
+    E^-1 in FP64 instead of its FP32 copy.  wait_s: limit of the SpMV's bounded
+    waits on its own copies (xdcg_options.wait_s).
     """
 
     def __init__(self, dof_ptr, row_ptr, col, val_ptr, val, sub_of_node, coords, hsign, centres,
                  precision="fp64", tol=1e-8, max_iter=10000, inner_tol=1e-3, max_outer=30,
                  time_spmv=False, enriched_modes=True, stream=None, jacobi="block",
-                 record_history=False, max_batch=0):
+                 record_history=False, max_batch=0, coarse_fp64=False, wait_s=2.0):
         lib = L.load()
         self._lib = lib
         self.ctx = ctypes.c_void_p()
@@ -76,6 +78,8 @@ class Solver:
         opt.jacobi = L.XDCG_POINT_JACOBI if jacobi == "point" else L.XDCG_BLOCK_JACOBI
         opt.record_history = int(bool(record_history))
         opt.max_batch = int(max_batch)
+        opt.coarse_fp64 = int(bool(coarse_fp64))
+        opt.wait_s = float(wait_s)
         self.precision = precision
         if stream is None:
             stream = torch.cuda.current_stream()

@@ -142,3 +142,42 @@ def test_kernel_timing_mode_times_every_iteration(prec, nphase):
     t = i1["t_phase_ms"]
     assert all(x > 0 for x in t[:nphase]) and all(x == 0 for x in t[nphase:])
     assert abs(t[0] - i1["t_spmv_ms"]) <= 1e-9
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_bounded_copy_wait_that_runs_out_reports_timeout(prec):
+    # The SpMV waits for its own bulk copies with a limit (xdcg_options.wait_s);
+    # with no time allowed, the waits give up while copies are still in
+    # flight.  The kernel flags the failure, lets every issued copy land
+    # (that drain keeps its own fixed limit) and returns; the call reports
+    # XDCG_TIMEOUT.  The context is then destroyed cleanly, and a fresh one on
+    # the same device solves correctly.
+    dev = _cuda()
+    P = X.make("cube24_ellipse")
+    f = torch.tensor(P.f, device=dev)
+    s = _solver(P, precision=prec, wait_s=0.0)
+    u, info = s.solve(f, tol=1e-8, raise_on_error=False)
+    assert info["status"] == "XDCG_TIMEOUT", info
+    s.close()
+    torch.cuda.synchronize()
+    s2 = _solver(P, precision=prec)
+    u, info = s2.solve(f, tol=1e-8)
+    assert info["rel_res_true"] <= 1e-8 * 1.01
+    s2.close()
+
+
+def test_mixed_solve_with_fp64_coarse_matches_oracle():
+    # the mixed path with E^-1 applied in FP64 inside the FP32 iteration: the
+    # same answer as the oracle's at 1e-12, as with the FP32 copy
+    dev = _cuda()
+    P = X.make("cube24_ellipse")
+    K, M, C = O.setup(P)
+    ref = O.adef2_pcg(K, P.f, M, C, tol=1e-12)
+    f = torch.tensor(P.f, device=dev)
+    for fp64 in (False, True):
+        s = _solver(P, precision="mixed", coarse_fp64=fp64)
+        u, info = s.solve(f, tol=1e-12)
+        un = u.cpu().numpy()
+        assert np.linalg.norm(P.f - K @ un) <= 1.05e-12 * np.linalg.norm(P.f)
+        assert np.linalg.norm(un - ref.u) <= 1e-7 * np.linalg.norm(ref.u), fp64
+        s.close()

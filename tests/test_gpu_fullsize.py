@@ -3,9 +3,11 @@ boxes: n = 373,254, k = 3,240), in the configuration bench.py times.
 
 The oracle computes everything here at this size within about a minute:
 full products K x, the coarse matrix E, one application of Algorithm 3 and
-the FP64 A-DEF2 solve to 1e-8.  Tolerances are those of the smaller parity
-tests (test_gpu_parity.py), except for Algorithm 3, whose sensitivity to
-rounding at this size is measured in the test itself."""
+the FP64 A-DEF2 solve to 1e-8 and to 1e-12.  Tolerances are those of the
+smaller parity tests (test_gpu_parity.py): iterations within +-2 at 1e-8 and
+||u - u_ref|| <= 1e-7 ||u_ref|| with both run to 1e-12, for the FP64 and the
+mixed path; Algorithm 3's sensitivity to rounding at this size is measured
+in the test itself."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -97,6 +99,8 @@ def _perturbed_apply(K, M, C, r):
 
 
 def test_fp64_and_mixed_solves_full_size():
+    # at the benchmark's tolerance: the FP64 iteration count within +-2 of
+    # the oracle's, both paths' true residuals, and Z^T r = 0 (Section 3.2)
     P, K, M, C = _need()
     ref = O.adef2_pcg(K, P.f, M, C, tol=1e-8)
     f = torch.tensor(P.f, device="cuda:0")
@@ -109,17 +113,41 @@ def test_fp64_and_mixed_solves_full_size():
     rt = P.f - K @ un
     assert np.linalg.norm(rt) <= 1.05e-8 * fn
     assert np.linalg.norm(C.Z.T @ rt) <= 1e-10 * zn * fn
-    # at tol 1e-8 the oracle's own error against its 1e-11 solution is 4.3e-8
-    # on this case; two solutions stopped at 1e-8 agree well inside 1e-6
-    assert np.linalg.norm(un - ref.u) <= 1e-6 * np.linalg.norm(ref.u)
     s.close()
     sm = _solver(precision="mixed")
     um, infom = sm.solve(f, tol=1e-8)
     rtm = P.f - K @ um.cpu().numpy()
     assert np.linalg.norm(rtm) <= 1.0e-8 * fn * 1.001
     assert infom["rel_res_true"] <= 1e-8
-    assert np.linalg.norm(um.cpu().numpy() - ref.u) <= 1e-6 * np.linalg.norm(ref.u)
+    # the mixed path's inner FP32 iterations against the oracle's FP64 count:
+    # a stated figure per result (its own recurrence, replaced residuals), not
+    # bound to +-2; print it for the record and keep it within 25 %
+    print(f"\n48^3 iterations to 1e-8: oracle {ref.iterations}, GPU FP64 {info['iterations']}, "
+          f"mixed {infom['iterations']} inner / {infom['outer_cycles']} FP64 residuals")
+    assert infom["iterations"] <= 1.25 * ref.iterations
     sm.close()
+
+
+def test_solutions_full_size_at_tight_tolerance():
+    # u against the oracle's u with both run to 1e-12 (two runs stopped at
+    # 1e-8 one iteration apart can differ by more than 1e-7):
+    # ||u - u_ref|| <= 1e-7 ||u_ref|| for the FP64 and the mixed path
+    P, K, M, C = _need()
+    ref = O.adef2_pcg(K, P.f, M, C, tol=1e-12)
+    assert ref.converged
+    f = torch.tensor(P.f, device="cuda:0")
+    fn = np.linalg.norm(P.f)
+    un_ref = np.linalg.norm(ref.u)
+    for prec in ("fp64", "mixed"):
+        s = _solver(precision=prec)
+        u, info = s.solve(f, tol=1e-12)
+        un = u.cpu().numpy()
+        assert np.linalg.norm(P.f - K @ un) <= 1.05e-12 * fn, (prec, info)
+        err = np.linalg.norm(un - ref.u) / un_ref
+        print(f"\n48^3 at 1e-12, {prec}: ||u - u_ref|| / ||u_ref|| = {err:.2e}, "
+              f"iterations {info['iterations']} (oracle {ref.iterations})")
+        assert err <= 1e-7, (prec, err)
+        s.close()
 
 
 def test_element_sensitivity_full_size():
