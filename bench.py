@@ -497,6 +497,42 @@ def run_ours(args):
             s_.close()
         return sweep
 
+    # the paper's own block choice, one block-Jacobi block per subdomain
+    # (enriched dofs included), on the same system numbered box by box:
+    # FP64 and mixed solves against node blocks in that numbering (outside
+    # the value)
+    def measure_subdomain_blocks():
+        P2, bp = X.by_subdomain(P)
+        f2 = torch.tensor(P2.f, device=dev)
+        u2 = torch.empty_like(f2)
+        out = {"blocks": len(bp) - 1, "block_dofs_max": int(np.max(np.diff(bp))),
+               "block_dofs_mean": float(np.mean(np.diff(bp)))}
+        for prec in ("mixed", "fp64"):
+            for kind, kw in (("subdomain", {"blocks": bp}), ("node", {})):
+                sol = Solver.from_problem(P2, precision=prec, inner_tol=args.inner_tol, **kw)
+                for _ in range(max(1, args.warmup)):
+                    sol.solve(f2, tol=TOL, out=u2)
+                ts, inf = [], None
+                for _ in range(args.steps):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    _, inf = sol.solve(f2, tol=TOL, out=u2)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                assert inf["rel_res_true"] <= TOL * 1.05, inf
+                out[f"{prec}_{kind}"] = {"ms": float(np.mean(ts)), "iterations": inf["iterations"],
+                                         "setup_ms": sol.info["t_setup_ms"],
+                                         "iter_bytes": sol.info["iter_bytes_fp32" if prec == "mixed"
+                                                                else "iter_bytes_fp64"]}
+                if kind == "subdomain":
+                    out["block_entries"] = sol.info["block_entries"]
+                sol.close()
+        return out
+
+    blocks_row = optional(measure_subdomain_blocks) if args.subdomain_blocks else None
     batch = optional(measure_batch) if args.batch > 0 else None
     fwd_bwd = optional(measure_fwd_bwd)
     sweep = optional(measure_sweep) if args.sweep > 0 else None
@@ -547,6 +583,7 @@ def run_ours(args):
         "batched_load_cases": batch,
         "forward_backward": fwd_bwd,
         "propagation_sweep": sweep,
+        "subdomain_blocks": blocks_row,
         "roofline": {"bound": "hbm", "kernel": "k_spmv<float> (inner FP32 SpMV)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind,
@@ -625,6 +662,8 @@ def main():
                     help="internal: one timed FP64 oracle solve of --workload, printed as JSON "
                          "(run in a child process with a fixed BLAS thread count)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--subdomain-blocks", type=int, default=1,
+                    help="also time block Jacobi with one block per subdomain (0: skip)")
     ap.add_argument("--profile", choices=["mixed", "fp64", "batch"], default=None,
                     help="profiler capture: one solve of the given path between "
                          "cudaProfilerStart/Stop after warm-up, nothing else timed")

@@ -74,7 +74,17 @@ typedef struct {
     int32_t mem;               /* XDCG_HOST or XDCG_DEVICE, for all six arrays */
 } xdcg_matrix;
 
-/* Geometric description of the deflation space Z (Section 3.3).  The
+/* The deflation space Z (Section 3.3), one box subdomain s = sub_of_node[I]
+ * per node, in one of two forms.
+ *
+ * Valued form (values != NULL): Z itself.  Box s owns sub_cols[s] (6 or 12)
+ * consecutive coarse columns, boxes in order; node I's block of Z is b_I x
+ * sub_cols[sub[I]] doubles, row-major (rows: I's dofs, columns: its box's
+ * columns), and the blocks of nodes 0, 1, ... follow one another in values.
+ * Z is zero outside each node's own box columns.  coords, hsign, centre and
+ * enriched_modes are then ignored and may be NULL.
+ *
+ * Geometric form (values == NULL): the
  * library builds Z on the device from it: for node I in box s = sub[I] and
  * x = coords[I] - centre[s], the rigid block R(x) of Eq. dcg_deflation_space
  * on I's standard dofs (columns 6 s' .. 6 s' + 5 of box s); if
@@ -91,8 +101,32 @@ typedef struct {
     const int8_t *hsign;         /* [n_nodes], +1 or -1 */
     const double *centre;        /* [3 n_sub] */
     int32_t enriched_modes;      /* 0: rigid modes only; 1: add enriched modes */
-    int32_t mem;                 /* XDCG_HOST or XDCG_DEVICE, for all four arrays */
+    int32_t mem;                 /* XDCG_HOST or XDCG_DEVICE, for all the arrays */
+    const int32_t *sub_cols;     /* valued form: [n_sub] columns of each box, 6 or 12 */
+    const double *values;        /* valued form: the node blocks of Z; NULL: geometric form */
 } xdcg_deflation;
+
+/* Block-Jacobi blocks chosen by the caller (Section 3.4, Eqs. block_jacobi,
+ * block_jacobi_enr): M is the block diagonal of K over these blocks.  The
+ * paper's own choice is one block per subdomain, enriched dofs included;
+ * number the dofs subdomain by subdomain and give each subdomain's range.
+ * Block b is the contiguous dof range [dof_ptr[b], dof_ptr[b+1]) of K's
+ * numbering; every boundary must fall between two nodes, and no block may
+ * hold more than XDCG_MAX_BLOCK_DOFS dofs (else XDCG_INVALID_ARG).  At set-up
+ * each block's part of K is gathered as a dense matrix and inverted in FP64;
+ * every iteration applies the inverses as dense products (in FP64, or for
+ * MIXED in FP32 on the block-scaled system).  A block whose inversion meets a
+ * pivot <= 1e-14 times its largest diagonal entry gives XDCG_NOT_SPD_BLOCK
+ * with bad_index = the block.  Passing NULL selects one block per node
+ * (3, 6 or 15 dofs, factored by Cholesky), the library's default.  Not
+ * combinable with XDCG_POINT_JACOBI or with a batched context (max_batch >
+ * 0).  Copied at set-up. */
+#define XDCG_MAX_BLOCK_DOFS 4096
+typedef struct {
+    int32_t n_blocks;
+    const int32_t *dof_ptr;    /* [n_blocks + 1], dof_ptr[0] = 0, dof_ptr[n_blocks] = n */
+    int32_t mem;               /* XDCG_HOST or XDCG_DEVICE */
+} xdcg_blocks;
 
 typedef struct {
     double tol;              /* relative residual target, default 1e-8 */
@@ -101,7 +135,11 @@ typedef struct {
     double inner_tol;        /* MIXED: residual replacement each time the FP32 recursive
                                 residual has dropped by this factor, default 1e-3 */
     int32_t max_outer;       /* MIXED: residual replacements (FP64 residual evaluations),
-                                default 30 */
+                                default 30.  When two replacements in a row shorten the FP64
+                                residual by less than 2x (the FP32 recurrence's rounding floor,
+                                near 1e-11 relative on large systems), or max_outer is reached,
+                                the solve finishes with the FP64 iteration from its current u
+                                (Algorithm 2 with u_-1 = u) */
     int32_t time_spmv;       /* 1: bracket every SpMV launch of the iteration by CUDA events;
                                 2: bracket every kernel of the iteration (t_phase_ms) */
     int32_t jacobi;          /* XDCG_BLOCK_JACOBI (default): one block per node (3/6/15 dofs,
@@ -122,9 +160,8 @@ typedef struct {
     double wait_s;           /* limit of every bounded device wait on the SpMV's own bulk copies,
                                 in seconds, default 2.  A wait that runs out ends the call with
                                 XDCG_TIMEOUT after the copies in flight have landed (their own
-                                limit, 0.1 s, is fixed).  0 gives up at the first check that
-                                finds a copy still in flight: it exists to exercise that
-                                status, not for use */
+                                limit, 0.1 s, is fixed).  0 gives up at the first wait: it
+                                exists to exercise that status, not for use */
 } xdcg_options;
 
 typedef struct {
@@ -142,6 +179,8 @@ typedef struct {
     double t_phase_ms[5];        /* their summed CUDA-event time per kernel of the iteration:
                                     FP64: SpMV, update, restriction, coarse solve, prolongation;
                                     MIXED: SpMV, restriction+update, coarse solve, prolongation */
+    int32_t n_fp64_iterations;   /* MIXED: iterations of the FP64 finish (included in
+                                    iterations), 0 when the FP32 cycles alone met tol */
 } xdcg_result;
 
 typedef struct {
@@ -166,6 +205,8 @@ typedef struct {
                                     + 2 * 8 n (values, block indices, row pointers, p read
                                     once, q written once) */
     int64_t spmv_alg_bytes_fp32; /* the same with 4-byte values and vectors */
+    int64_t block_entries;       /* caller blocks: sum of their squared sizes (entries of the
+                                    dense inverses applied per iteration); 0 for node blocks */
 } xdcg_info_t;
 
 /* Fill *opt with the defaults listed above. */
@@ -174,13 +215,13 @@ xdcg_status xdcg_default_options(xdcg_options *opt);
 /* Validate K and the deflation description, copy them to the device, lay K
  * out for the SpMV (FP64 and, for MIXED, FP32 copies), factor the node
  * blocks (FP64 Cholesky), build Z, W = K Z and E = Z^T K Z, and invert E in
- * FP64 (MIXED also keeps an FP32 copy of E^-1).  stream: a cudaStream_t
- * (NULL = legacy default stream).  blocks must be NULL (one block per node).
- * On error *out is NULL and, if bad_index is
- * not NULL, *bad_index names the failing node (XDCG_NOT_SPD_BLOCK) or coarse
- * pivot (XDCG_COARSE_NOT_SPD), else -1. */
+ * FP64 (MIXED also keeps an FP32 copy of E^-1).  blocks: NULL (one block per
+ * node) or the caller's blocks (xdcg_blocks), inverted in FP64.  stream: a
+ * cudaStream_t (NULL = legacy default stream).  On error *out is NULL and,
+ * if bad_index is not NULL, *bad_index names the failing node or caller
+ * block (XDCG_NOT_SPD_BLOCK) or coarse pivot (XDCG_COARSE_NOT_SPD), else -1. */
 xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflation *Z,
-                       const void *blocks, const xdcg_options *opt, void *stream,
+                       const xdcg_blocks *blocks, const xdcg_options *opt, void *stream,
                        int32_t *bad_index);
 
 /* Solve K u = f with the options given at set-up, tol overriding opt.tol

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "libxdcg.so")
 XDCG_HOST, XDCG_DEVICE = 0, 1
 XDCG_FP64, XDCG_MIXED = 0, 1
 XDCG_BLOCK_JACOBI, XDCG_POINT_JACOBI = 0, 1
+XDCG_MAX_BLOCK_DOFS = 4096
 
 STATUS = {0: "XDCG_OK", 1: "XDCG_INVALID_ARG", 2: "XDCG_NOT_SPD_BLOCK",
           3: "XDCG_COARSE_NOT_SPD", 4: "XDCG_BREAKDOWN", 5: "XDCG_NO_CONVERGENCE",
@@ -34,7 +35,11 @@ class Matrix(ctypes.Structure):
 class Deflation(ctypes.Structure):
     _fields_ = [("n_sub", c_int32), ("sub_of_node", c_void_p), ("coords", c_void_p),
                 ("hsign", c_void_p), ("centre", c_void_p), ("enriched_modes", c_int32),
-                ("mem", c_int32)]
+                ("mem", c_int32), ("sub_cols", c_void_p), ("values", c_void_p)]
+
+
+class Blocks(ctypes.Structure):
+    _fields_ = [("n_blocks", c_int32), ("dof_ptr", c_void_p), ("mem", c_int32)]
 
 
 class Options(ctypes.Structure):
@@ -49,7 +54,8 @@ class Result(ctypes.Structure):
                 ("rel_res_recursive", c_double), ("rel_res_true", c_double),
                 ("t_solve_ms", c_double), ("bad_index", c_int32), ("n_spmv_timed", c_int32),
                 ("t_spmv_ms", c_double), ("n_launches", c_int64),
-                ("n_phase_timed", c_int32), ("t_phase_ms", c_double * 5)]
+                ("n_phase_timed", c_int32), ("t_phase_ms", c_double * 5),
+                ("n_fp64_iterations", c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -64,7 +70,7 @@ class Info(ctypes.Structure):
                 ("t_setup_ms", c_double), ("restrict_bytes_fp32", c_int64),
                 ("coarse_bytes_fp32", c_int64), ("prolong_bytes_fp32", c_int64),
                 ("nnzb", c_int64), ("spmv_alg_bytes_fp64", c_int64),
-                ("spmv_alg_bytes_fp32", c_int64)]
+                ("spmv_alg_bytes_fp32", c_int64), ("block_entries", c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -83,8 +89,8 @@ def load():
                            "`python -c 'import __graft_entry__ as g; g.build()'`")
     lib = ctypes.CDLL(LIB_PATH)
     lib.xdcg_default_options.argtypes = [POINTER(Options)]
-    lib.xdcg_setup.argtypes = [POINTER(c_void_p), POINTER(Matrix), POINTER(Deflation), c_void_p,
-                               POINTER(Options), c_void_p, POINTER(c_int32)]
+    lib.xdcg_setup.argtypes = [POINTER(c_void_p), POINTER(Matrix), POINTER(Deflation),
+                               POINTER(Blocks), POINTER(Options), c_void_p, POINTER(c_int32)]
     lib.xdcg_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_double, POINTER(Result)]
     lib.xdcg_solve_x0.argtypes = [c_void_p, c_void_p, c_void_p, c_double, POINTER(Result)]
     lib.xdcg_solve_batch.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_double, c_void_p]

@@ -26,6 +26,7 @@ struct Level64 {
     SpmvDev<double> A;
     NodeDev<double> N;
     BoxDev<double> B;
+    BlkDev<double> J;         // caller blocks (when given): dense FP64 inverses
 };
 struct Level32 {          // block-scaled system K~ = L^-1 K L^-T in FP32
     SpmvDev<float> A;
@@ -34,6 +35,7 @@ struct Level32 {          // block-scaled system K~ = L^-1 K L^-T in FP32
     FacDev F;
     const int *dofStart64;    // [nNodes + 1] node dofs in the FP64 (caller's) numbering
     const int *dofStart32;    // [nNodes + 1] node dofs in the box-major FP32 numbering
+    BlkDev<float> J;          // caller blocks: FP32 inverses of the block-scaled blocks
 };
 
 }  // namespace
@@ -44,6 +46,8 @@ struct xdcg_ctx {
     xdcg_options opt{};
     xdcg_info_t info{};
     bool mixed = false;
+    bool userBlocks = false;       // M from the caller's blocks (dense inverses)
+    long long blkEntries = 0;      // sum of the caller blocks' squared sizes
 
     int nNodes = 0, nBox = 0, k = 0;
     long long n = 0;
@@ -254,7 +258,14 @@ struct PlainPath {
     }
     void update(double *u, double *r, const double *p, const double *q, double *y, int mode,
                 Scalars *sc) {
-        launch_update<double>(L.N, u, r, p, q, y, mode, c->partials, sc, c->st);
+        if (c->userBlocks) {
+            // caller blocks: the update, then y = M^-1 r by the blocks' dense inverses
+            launch_update_plain<double>(u, r, p, q, c->n, mode, c->partials, sc, c->st);
+            launch_block_apply<double>(L.J, r, y, c->partials, sc, c->st);
+            c->launches++;
+        } else {
+            launch_update<double>(L.N, u, r, p, q, y, mode, c->partials, sc, c->st);
+        }
     }
     void restrict_(const double *a, const double *b, int withW, double *zr, Scalars *sc) {
         launch_restrict(L.B, a, b, withW, c->g, zr, sc, c->st);
@@ -394,6 +405,16 @@ void scaled_init(xdcg_ctx *c, const float *f, float *u, float *rA, float *p, Sca
     coarse_inner(c, nullptr, 0, sc);
     launch_prolong_rows(L.R, c->nu32, nullptr, u, 1, sc, st);
     launch_spmv<float>(L.A, u, rA, f, 1, c->partials, sc, kFinRR, 0, st);
+    if (c->userBlocks) {
+        // y = M~^-1 r by the caller blocks, then g = Z~^T r - W~^T y
+        launch_block_apply<float>(L.J, rA, c->y32, c->partials, sc, st);
+        launch_restrict_update(L.R, nullptr, rA, nullptr, nullptr, nullptr, 3, c->g, c->zr,
+                               c->partials, sc, st, c->y32);
+        coarse_inner(c, c->zr, 1, sc);
+        launch_prolong_rows(L.R, c->nu32, c->y32, p, 2, sc, st);
+        c->launches += 8;
+        return;
+    }
     launch_restrict_update(L.R, nullptr, rA, nullptr, nullptr, nullptr, 1, c->g, c->zr,
                            c->partials, sc, st);
     coarse_inner(c, c->zr, 1, sc);
@@ -432,11 +453,21 @@ xdcg_status scaled_iterate(xdcg_ctx *c, float *u, float *rA, float *rB, float *p
             launch_spmv<float>(L.A, p, q, nullptr, 0, c->partials, sc, kFinAlpha, 0, st);
             if (timeSpmv) CK(cudaEventRecord(c->evE[launched], st));
             MARK(launched, 1);
-            launch_restrict_update(L.R, u, rc, rn, p, q, 0, c->g, c->zr, c->partials, sc, st);
+            if (c->userBlocks) {
+                // residual in place (no neighbour reads before the apply), y
+                // = M~^-1 r by the caller blocks, then the restriction
+                launch_update_plain<float>(u, rA, p, q, c->n, 0, c->partials, sc, st);
+                launch_block_apply<float>(L.J, rA, c->y32, c->partials, sc, st);
+                launch_restrict_update(L.R, nullptr, rA, nullptr, nullptr, nullptr, 3, c->g, c->zr,
+                                       c->partials, sc, st, c->y32);
+                c->launches += 2;
+            } else {
+                launch_restrict_update(L.R, u, rc, rn, p, q, 0, c->g, c->zr, c->partials, sc, st);
+            }
             MARK(launched, 2);
             coarse_inner(c, c->zr, 2, sc);
             MARK(launched, 3);
-            launch_prolong_rows(L.R, c->nu32, rn, p, 0, sc, st);
+            launch_prolong_rows(L.R, c->nu32, c->userBlocks ? c->y32 : rn, p, 0, sc, st);
             MARK(launched, 4);
             c->launches += 4;
         }
@@ -559,7 +590,8 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, boo
     k_set_trigger<<<1, 32, 0, st>>>(c->sc32, 1, delta2, 0.0);
     c->launches += 2;
     double last_rec = 1.0;
-    int cycles = 0, its = 0, done = 0, breakdowns = 0;
+    int cycles = 0, its = 0, done = 0, breakdowns = 0, slow = 0;
+    bool finishFp64 = false;
     xdcg_status status = XDCG_NO_CONVERGENCE;
     while (true) {
         s = scaled_iterate(c, c->u32, rA, rB, c->p32, c->q32, c->sc32, c->opt.max_iter, &its,
@@ -580,21 +612,36 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, boo
         cycles++;
         if (!std::isfinite(rn2)) { status = XDCG_BREAKDOWN; break; }
         if (rn2 <= tol * tol * ff) { status = XDCG_OK; break; }
-        if (done == kMaxIter || cycles >= c->opt.max_outer) { status = XDCG_NO_CONVERGENCE; break; }
+        if (done == kMaxIter) { status = XDCG_NO_CONVERGENCE; break; }
+        // two replacements in a row that shortened the FP64 residual by less
+        // than 2x (or the replacement budget spent): the FP32 recurrence has
+        // reached its rounding floor; the FP64 iteration finishes from u
+        slow = rn2 > 0.25 * prev ? slow + 1 : 0;
+        if (slow >= 2 || cycles >= c->opt.max_outer) { finishFp64 = true; break; }
         if (done == kBreakdown) {
             if (rn2 >= prev || ++breakdowns > 2) { status = XDCG_BREAKDOWN; break; }
         }
         // replace the recursive residual by the scaled true residual and finish
         // the interrupted iteration: z = r + Z~ nu, beta, p = z + beta p (beta =
         // 0 if the replacement moved the residual far: see k_coarse mode 3)
-        float *rbuf = (its & 1) ? rB : rA;
+        float *rbuf = (c->userBlocks || !(its & 1)) ? rA : rB;
         launch_fwd_scale(c->nNodes, L.dofStart64, L.dofStart64, L.dofStart32, L.F, c->r64, s0, rbuf,
                          st);
         k_set_trigger<<<1, 32, 0, st>>>(c->sc32, 0, 0.0, 0.0);
-        launch_restrict_update(L.R, nullptr, rbuf, nullptr, nullptr, nullptr, 1, c->g, c->zr,
-                               c->partials, c->sc32, st);
+        if (c->userBlocks) {
+            launch_update_plain<float>(nullptr, rbuf, nullptr, nullptr, c->n, 1, c->partials,
+                                       c->sc32, st);
+            launch_block_apply<float>(L.J, rbuf, c->y32, c->partials, c->sc32, st);
+            launch_restrict_update(L.R, nullptr, rbuf, nullptr, nullptr, nullptr, 3, c->g, c->zr,
+                                   c->partials, c->sc32, st, c->y32);
+            c->launches += 2;
+        } else {
+            launch_restrict_update(L.R, nullptr, rbuf, nullptr, nullptr, nullptr, 1, c->g, c->zr,
+                                   c->partials, c->sc32, st);
+        }
         coarse_inner(c, c->zr, done == kBreakdown ? 1 : 3, c->sc32);
-        launch_prolong_rows(L.R, c->nu32, rbuf, c->p32, done == kBreakdown ? 2 : 0, c->sc32, st);
+        launch_prolong_rows(L.R, c->nu32, c->userBlocks ? c->y32 : rbuf, c->p32,
+                            done == kBreakdown ? 2 : 0, c->sc32, st);
         c->launches += 5;
         CK(cudaMemcpyAsync(c->h_sc, c->sc32, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -613,6 +660,19 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, boo
     res->outer_cycles = cycles;
     res->rel_res_recursive = last_rec;
     res->rel_res_true = std::sqrt(rn2 / ff);
+    if (finishFp64) {
+        // Algorithm 2 with u_-1 = u, then FP64 A-DEF2 PCG to tol; its iterations
+        // and its one FP64 residual evaluation are added to the counts
+        xdcg_result r64{};
+        r64.bad_index = -1;
+        s = solve_fp64(c, f, u, tol, true, &r64);
+        res->iterations = its + r64.iterations;
+        res->outer_cycles = cycles + 1;
+        res->rel_res_recursive = r64.rel_res_recursive;
+        res->rel_res_true = r64.rel_res_true;
+        res->n_fp64_iterations = r64.iterations;
+        return s;
+    }
     return status;
 }
 
@@ -843,7 +903,51 @@ void free_ctx(xdcg_ctx *c) {
 
 // ---- set-up -----------------------------------------------------------------
 
-xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *Zd, int *bad) {
+// In-place FP64 inversion of the SPD matrices dims[m] x dims[m] at A + offs[m]
+// (blocked symmetric sweeps, dense_inv.cu); a failing pivot sets *d_bad to
+// the matrix index (badByMatrix) or the pivot index.  Tables and scratch are
+// set-up temporaries.
+xdcg_status dense_inverse(xdcg_ctx *c, double *A, const std::vector<int> &dims,
+                          const std::vector<long long> &offs, int *d_bad, int badByMatrix) {
+    const int nMat = (int)dims.size();
+    if (nMat == 0) return XDCG_OK;
+    std::vector<int> tileOff(nMat + 1, 0), rowTileOff(nMat + 1, 0);
+    std::vector<long long> cOff(nMat, 0);
+    long long cTot = 0, nEnt = 0;
+    int maxDim = 0;
+    for (int m = 0; m < nMat; ++m) {
+        const int T = dense_inv_tiles(dims[m]);
+        if ((long long)tileOff[m] + (long long)T * (T + 1) / 2 > INT_MAX) return XDCG_INVALID_ARG;
+        tileOff[m + 1] = tileOff[m] + T * (T + 1) / 2;
+        rowTileOff[m + 1] = rowTileOff[m] + T;
+        cOff[m] = cTot;
+        cTot += (long long)dense_inv_panel_doubles(dims[m]);
+        nEnt = std::max(nEnt, offs[m] + (long long)dims[m] * dims[m]);
+        maxDim = std::max(maxDim, dims[m]);
+    }
+    DenseBatch B;
+    B.nMat = nMat;
+    B.nTiles = tileOff[nMat];
+    B.nRowTiles = rowTileOff[nMat];
+    B.dim = upload_tmp(c, dims);
+    B.off = upload_tmp(c, offs);
+    B.tileOff = upload_tmp(c, tileOff);
+    B.rowTileOff = upload_tmp(c, rowTileOff);
+    B.cOff = upload_tmp(c, cOff);
+    B.A = A;
+    B.D = dalloc_tmp<double>(c, (size_t)nMat * dense_inv_pivot_doubles());
+    B.C = dalloc_tmp<double>(c, (size_t)cTot);
+    B.thr = dalloc_tmp<double>(c, nMat);
+    B.bad = d_bad;
+    B.badByMatrix = badByMatrix;
+    if (!B.dim || !B.off || !B.tileOff || !B.rowTileOff || !B.cOff || !B.D || !B.C || !B.thr)
+        return XDCG_OOM;
+    CK(launch_dense_inverse(B, maxDim, nEnt, 1e-14, c->st));
+    return XDCG_OK;
+}
+
+xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *Zd,
+                       const xdcg_blocks *blocks, int *bad) {
     const int N = K->n_nodes;
     if (N <= 0 || !K->dof_ptr || !K->row_ptr) return XDCG_INVALID_ARG;
     if ((K->mem != XDCG_HOST && K->mem != XDCG_DEVICE) ||
@@ -908,20 +1012,67 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     std::vector<int> sub;
     std::vector<double> coords, centre;
     std::vector<int8_t> hs;
-    if (!fetch(sub, Zd->sub_of_node, N, Zd->mem) || !fetch(coords, Zd->coords, 3 * (size_t)N, Zd->mem) ||
-        !fetch(hs, Zd->hsign, N, Zd->mem) || !fetch(centre, Zd->centre, 3 * (size_t)S, Zd->mem))
-        return XDCG_INVALID_ARG;
-    for (int I = 0; I < N; ++I) {
+    // valued form: the caller's Z blocks per node (6 or 12 columns per box);
+    // geometric form: coordinates, H signs and box centres
+    const bool valued = Zd->values != nullptr;
+    std::vector<int> subCols;
+    std::vector<double> zval;
+    std::vector<long long> zvOff(N + 1, 0);
+    if (!fetch(sub, Zd->sub_of_node, N, Zd->mem)) return XDCG_INVALID_ARG;
+    for (int I = 0; I < N; ++I)
         if (sub[I] < 0 || sub[I] >= S) return XDCG_INVALID_ARG;
-        if (hs[I] != 1 && hs[I] != -1) return XDCG_INVALID_ARG;
-        for (int e = 0; e < 3; ++e)
-            if (!std::isfinite(coords[3 * I + e])) return XDCG_INVALID_ARG;
+    if (valued) {
+        if (!fetch(subCols, Zd->sub_cols, S, Zd->mem)) return XDCG_INVALID_ARG;
+        for (int s2 = 0; s2 < S; ++s2)
+            if (subCols[s2] != 6 && subCols[s2] != 12) return XDCG_INVALID_ARG;
+        for (int I = 0; I < N; ++I)
+            zvOff[I + 1] = zvOff[I] + (long long)(dof[I + 1] - dof[I]) * subCols[sub[I]];
+        if (!fetch(zval, Zd->values, (size_t)zvOff[N], Zd->mem)) return XDCG_INVALID_ARG;
+        for (double v : zval)
+            if (!std::isfinite(v)) return XDCG_INVALID_ARG;
+        coords.assign(3 * (size_t)N, 0.0);
+        hs.assign(N, 1);
+        centre.assign(3 * (size_t)S, 0.0);
+    } else {
+        if (!fetch(coords, Zd->coords, 3 * (size_t)N, Zd->mem) || !fetch(hs, Zd->hsign, N, Zd->mem) ||
+            !fetch(centre, Zd->centre, 3 * (size_t)S, Zd->mem))
+            return XDCG_INVALID_ARG;
+        for (int I = 0; I < N; ++I) {
+            if (hs[I] != 1 && hs[I] != -1) return XDCG_INVALID_ARG;
+            for (int e = 0; e < 3; ++e)
+                if (!std::isfinite(coords[3 * I + e])) return XDCG_INVALID_ARG;
+        }
     }
 
     c->nNodes = N;
     c->n = dof[N];
     c->nBox = S;
     const long long n = c->n;
+
+    // caller blocks: contiguous dof ranges of whole nodes, each at most
+    // XDCG_MAX_BLOCK_DOFS dofs
+    std::vector<int> bptr, bNode0, bNode1, blockOfNode;
+    if (blocks) {
+        const int nb = blocks->n_blocks;
+        if (nb < 1 || nb > N || (blocks->mem != XDCG_HOST && blocks->mem != XDCG_DEVICE) ||
+            !fetch(bptr, blocks->dof_ptr, (size_t)nb + 1, blocks->mem))
+            return XDCG_INVALID_ARG;
+        if (bptr[0] != 0 || bptr[nb] != n) return XDCG_INVALID_ARG;
+        bNode0.resize(nb);
+        bNode1.resize(nb);
+        blockOfNode.resize(N);
+        for (int b = 0; b < nb; ++b) {
+            const int d0 = bptr[b], d1 = bptr[b + 1];
+            if (d1 <= d0 || d1 - d0 > XDCG_MAX_BLOCK_DOFS) return XDCG_INVALID_ARG;
+            const auto i0 = std::lower_bound(dof.begin(), dof.end(), d0);
+            const auto i1 = std::lower_bound(dof.begin(), dof.end(), d1);
+            if (i0 == dof.end() || *i0 != d0 || i1 == dof.end() || *i1 != d1)
+                return XDCG_INVALID_ARG;   // a boundary inside a node
+            bNode0[b] = (int)(i0 - dof.begin());
+            bNode1[b] = (int)(i1 - dof.begin());
+            for (int I = bNode0[b]; I < bNode1[b]; ++I) blockOfNode[I] = b;
+        }
+    }
 
     // ---- chunk rows: S (pure standard) and X (the rest)
     std::vector<int> kindb(N);
@@ -1063,7 +1214,9 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     }
     std::vector<int> menr(S, 0), col0(S + 1, 0);
     for (int s = 0; s < S; ++s) {
-        if (Zd->enriched_modes) {
+        if (valued) {
+            menr[s] = subCols[s] == 12;
+        } else if (Zd->enriched_modes) {
             std::vector<double> pts;
             for (int t = ownPtr[s]; t < ownPtr[s + 1]; ++t) {
                 const int I = ownNodes[t];
@@ -1192,11 +1345,12 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     if (!A.warpSlice) return XDCG_OOM;
 
     // node data and block factors (FP64)
-    int *d_bad = dalloc<int>(c, 2);
+    // failure slots: [0] node block (node), [1] coarse pivot, [2] caller block
+    int *d_bad = dalloc<int>(c, 3);
     if (!d_bad) return XDCG_OOM;
     {
-        std::vector<int> init = {INT_MAX, INT_MAX};
-        CK(cudaMemcpyAsync(d_bad, init.data(), 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+        std::vector<int> init = {INT_MAX, INT_MAX, INT_MAX};
+        CK(cudaMemcpyAsync(d_bad, init.data(), 3 * sizeof(int), cudaMemcpyHostToDevice, st));
         CK(cudaStreamSynchronize(st));
     }
     auto &N64 = c->L64.N;
@@ -1230,7 +1384,28 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     double *d_W = dalloc<double>(c, nW);
     if (!d_extBox || !d_extNode || !d_extPtr || !d_ownPtr || !d_own || !d_wOff || !d_W)
         return XDCG_OOM;
-    launch_build_W(kin, nExt, d_extBox, d_extNode, d_wOff, d_sub, d_x64, d_hs, d_menr, d_W, st);
+    // Z by value: the caller's blocks for the set-up kernels (node order) and,
+    // in box order, for the FP64 restriction and prolongation
+    ZvalDev zv{nullptr, nullptr};
+    double *d_zslot = nullptr;
+    long long *d_zslotOff = nullptr;
+    if (valued) {
+        zv.v = upload_tmp(c, zval);
+        zv.off = upload_tmp(c, zvOff);
+        std::vector<double> zslot;
+        std::vector<long long> zslotOff(N);
+        zslot.reserve(zval.size());
+        for (int t = 0; t < N; ++t) {
+            const int I = ownNodes[t];
+            zslotOff[t] = (long long)zslot.size();
+            zslot.insert(zslot.end(), zval.begin() + zvOff[I], zval.begin() + zvOff[I + 1]);
+        }
+        d_zslot = upload(c, zslot);
+        d_zslotOff = upload(c, zslotOff);
+        if (!zv.v || !zv.off || !d_zslot || !d_zslotOff) return XDCG_OOM;
+    }
+    launch_build_W(kin, nExt, d_extBox, d_extNode, d_wOff, d_sub, d_x64, d_hs, d_menr, zv, d_W,
+                   st);
     // node data in box order (slots) and per-entry dof data for the box kernels
     std::vector<int> ownDof(N), extDof(nExt);
     std::vector<unsigned char> ownB(N), extB(nExt);
@@ -1269,8 +1444,8 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     B64.ownB = d_ownB;
     B64.ownH = d_ownH;
     B64.ownX = d_ownX;
-    B64.ownZ = nullptr;
-    B64.Zt = nullptr;
+    B64.ownZ = d_zslotOff;
+    B64.Zt = d_zslot;
     B64.extPtr = d_extPtr;
     B64.extDof = d_extDof;
     B64.extB = d_extB;
@@ -1278,25 +1453,19 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     B64.W = d_W;
     c->Einv = dalloc<double>(c, (size_t)k * k);
     c->E = dalloc<double>(c, (size_t)k * k);
-    double *colbuf = dalloc_tmp<double>(c, k);
     int *sb = upload_tmp(c, segBox), *so = upload_tmp(c, segOwner),
         *sbg = upload_tmp(c, segBegin), *se = upload_tmp(c, segEnd);
-    if (!c->Einv || !c->E || !colbuf || !sb || !so || !sbg || !se) return XDCG_OOM;
+    if (!c->Einv || !c->E || !sb || !so || !sbg || !se) return XDCG_OOM;
     CK(cudaMemsetAsync(c->Einv, 0, (size_t)k * k * sizeof(double), st));
     launch_build_E((int)segBox.size(), sb, so, sbg, se, d_extNode, d_wOff, d_W, d_dof, d_x64,
-                   d_hs, d_col0, d_menr, k, c->Einv, st);
+                   d_hs, d_col0, d_menr, zv, k, c->Einv, st);
     launch_symmetrize(c->Einv, k, st);
     CK(cudaMemcpyAsync(c->E, c->Einv, (size_t)k * k * sizeof(double), cudaMemcpyDeviceToDevice,
                        st));
-    // pivot threshold relative to the largest diagonal entry of E
+    // E^-1 in place (pivots relative to E's largest diagonal entry)
     {
-        std::vector<double> diag(k);
-        CK(cudaMemcpy2DAsync(diag.data(), sizeof(double), c->Einv, (k + 1) * sizeof(double),
-                             sizeof(double), k, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        double dm = 0;
-        for (double d : diag) dm = std::max(dm, d);
-        launch_sweep_inverse(c->Einv, k, colbuf, d_bad + 1, 1e-14 * dm, st);
+        xdcg_status es = dense_inverse(c, c->Einv, {k}, {0LL}, d_bad + 1, 0);
+        if (es != XDCG_OK) return es;
     }
 
     // block-scaled FP32 level of the mixed path: K~ = L^-1 K L^-T, Z~ = L^T Z, W~ = L^-1 W
@@ -1374,7 +1543,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         if (A2.grid < 1) return XDCG_CUDA_ERROR;
         A2.warpSlice = partition(HS32, HX32, A2.grid);
         if (!A2.warpSlice) return XDCG_OOM;
-        launch_build_Zt(N, d_own, d_dof, d_sub, d_x64, d_hs, d_menr, F, d_zOff, d_Zt, st);
+        launch_build_Zt(N, d_own, d_dof, d_sub, d_x64, d_hs, d_menr, zv, F, d_zOff, d_Zt, st);
         launch_scale_W(nExt, d_extBox, d_extNode, d_wOff, d_menr, d_dof, F, d_W, d_Wt, st);
         // row-parallel layouts: own rows (Z~) and coupled rows (W~) of each box,
         // column-major per box
@@ -1481,13 +1650,100 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         c->L32.dofStart64 = d_dof;
         c->L32.dofStart32 = d_dof32;
     }
-    int hbad[2];
-    CK(cudaMemcpyAsync(hbad, d_bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    // ---- caller blocks: K's diagonal blocks gathered densely and inverted in
+    // FP64; for MIXED also L_b^T (K_bb)^-1 L_b in FP32 (the blocks of the
+    // block-scaled system's M~^-1)
+    if (blocks) {
+        const int nb = blocks->n_blocks;
+        std::vector<int> bStart(nb), bDim(nb), rowBlock(n), blockRow(nnzb);
+        std::vector<long long> aOff(nb);
+        long long tot = 0;
+        for (int b = 0; b < nb; ++b) {
+            bStart[b] = bptr[b];
+            bDim[b] = bptr[b + 1] - bptr[b];
+            aOff[b] = tot;
+            tot += (long long)bDim[b] * bDim[b];
+            for (int d = bptr[b]; d < bptr[b + 1]; ++d) rowBlock[d] = b;
+        }
+        c->blkEntries = tot;
+        for (int I = 0; I < N; ++I)
+            for (long long p = rowp[I]; p < rowp[I + 1]; ++p) blockRow[p] = I;
+        std::vector<int> unitBlk, unitR0, unitR1;
+        for (int b = 0; b < nb; ++b)
+            for (int r = 0; r < bDim[b]; r += kBlkUnitRows) {
+                unitBlk.push_back(b);
+                unitR0.push_back(r);
+                unitR1.push_back(std::min(bDim[b], r + kBlkUnitRows));
+            }
+        if (unitBlk.size() > (size_t)kMaxGrid) return XDCG_INVALID_ARG;
+        std::vector<int> idx64(n);
+        for (long long d = 0; d < n; ++d) idx64[d] = (int)d;
+        double *A64 = dalloc<double>(c, (size_t)tot);
+        int *d_bStart = upload_tmp(c, bStart), *d_bDim = upload_tmp(c, bDim);
+        int *d_bon = upload_tmp(c, blockOfNode), *d_brow = upload_tmp(c, blockRow);
+        long long *d_aOff = upload(c, aOff);
+        int *d_bPos = upload(c, bptr), *d_idx64 = upload(c, idx64);
+        int *d_ub = upload(c, unitBlk), *d_u0 = upload(c, unitR0), *d_u1 = upload(c, unitR1);
+        if (!A64 || !d_bStart || !d_bDim || !d_bon || !d_brow || !d_aOff || !d_bPos || !d_idx64 ||
+            !d_ub || !d_u0 || !d_u1)
+            return XDCG_OOM;
+        CK(cudaMemsetAsync(A64, 0, (size_t)tot * sizeof(double), st));
+        launch_gather_blocks(kin, nnzb, d_brow, d_bon, d_bStart, d_bDim, d_aOff, A64, st);
+        xdcg_status es = dense_inverse(c, A64, bDim, aOff, d_bad + 2, 1);
+        if (es != XDCG_OK) return es;
+        BlkDev<double> &J = c->L64.J;
+        J.nBlk = nb;
+        J.nUnits = (int)unitBlk.size();
+        J.aOff = d_aOff;
+        J.bPos = d_bPos;
+        J.idx = d_idx64;
+        J.A = A64;
+        J.unitBlk = d_ub;
+        J.unitRow0 = d_u0;
+        J.unitRow1 = d_u1;
+        if (mixed) {
+            // positions in the box-major FP32 numbering
+            std::vector<int> dof32(N + 1, 0);
+            {
+                int off = 0;
+                for (int t = 0; t < N; ++t) {
+                    dof32[ownNodes[t]] = off;
+                    off += kindb[ownNodes[t]];
+                }
+            }
+            std::vector<int> idx32(n);
+            for (int I = 0; I < N; ++I)
+                for (int i = 0; i < kindb[I]; ++i) idx32[dof[I] + i] = dof32[I] + i;
+            float *A32 = dalloc<float>(c, (size_t)tot);
+            double *Y = dalloc_tmp<double>(c, (size_t)tot);
+            int *d_rowBlock = upload_tmp(c, rowBlock), *d_n0 = upload_tmp(c, bNode0),
+                *d_n1 = upload_tmp(c, bNode1);
+            int *d_idx32 = upload(c, idx32);
+            if (!A32 || !Y || !d_rowBlock || !d_n0 || !d_n1 || !d_idx32) return XDCG_OOM;
+            launch_scale_block_inverse((int)n, d_rowBlock, d_bStart, d_bDim, d_n0, d_n1, d_aOff,
+                                       d_dof, c->L32.F, A64, Y, A32, st);
+            BlkDev<float> &J32 = c->L32.J;
+            J32.nBlk = nb;
+            J32.nUnits = J.nUnits;
+            J32.aOff = d_aOff;
+            J32.bPos = d_bPos;
+            J32.idx = d_idx32;
+            J32.A = A32;
+            J32.unitBlk = d_ub;
+            J32.unitRow0 = d_u0;
+            J32.unitRow1 = d_u1;
+        }
+        c->userBlocks = true;
+    }
+
+    int hbad[3];
+    CK(cudaMemcpyAsync(hbad, d_bad, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
     for (void *p : c->temps) cudaFree(p);
     c->temps.clear();
     if (hbad[0] != INT_MAX) { *bad = hbad[0]; return XDCG_NOT_SPD_BLOCK; }
+    if (hbad[2] != INT_MAX) { *bad = hbad[2]; return XDCG_NOT_SPD_BLOCK; }
     if (hbad[1] != INT_MAX) { *bad = hbad[1]; return XDCG_COARSE_NOT_SPD; }
 
     // ---- work vectors and scalar blocks
@@ -1564,7 +1820,10 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
                                        : 0;
     const long long coarse32 = mixed ? (c->opt.coarse_fp64 ? 8LL : 4LL) * k * k + 28LL * k : 0;
     const long long prolong32 = mixed ? 16LL * n + 4LL * c->zEnt32 + 4LL * k : 0;
-    const long long iter32 = mixed ? spmv_bytes(4) + restrict32 + coarse32 + prolong32 : 0;
+    // caller blocks: the inverses, r gathered and y written once (per precision)
+    const long long blk64 = c->userBlocks ? 8LL * c->blkEntries + 20LL * n : 0;
+    const long long blk32 = c->userBlocks ? 4LL * c->blkEntries + 12LL * n : 0;
+    const long long iter32 = mixed ? spmv_bytes(4) + restrict32 + coarse32 + prolong32 + blk32 : 0;
     c->info.n = n;
     c->info.n_nodes = N;
     c->info.k = k;
@@ -1572,7 +1831,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     c->info.nnzb3 = nnzb3;
     c->info.spmv_bytes_fp64 = spmv_bytes(8);
     c->info.spmv_bytes_fp32 = spmv_bytes(4);
-    c->info.iter_bytes_fp64 = iter64;
+    c->info.iter_bytes_fp64 = iter64 + blk64;
     c->info.iter_bytes_fp32 = iter32;
     c->info.restrict_bytes_fp32 = restrict32;
     c->info.coarse_bytes_fp32 = coarse32;
@@ -1583,6 +1842,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     };
     c->info.spmv_alg_bytes_fp64 = spmv_alg(8);
     c->info.spmv_alg_bytes_fp32 = spmv_alg(4);
+    c->info.block_entries = c->blkEntries;
     return XDCG_OK;
 }
 
@@ -1607,13 +1867,13 @@ xdcg_status xdcg_default_options(xdcg_options *opt) {
 }
 
 xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflation *Z,
-                       const void *blocks, const xdcg_options *opt, void *stream,
+                       const xdcg_blocks *blocks, const xdcg_options *opt, void *stream,
                        int32_t *bad_index) {
     NvtxRange range("xdcg setup");
     if (bad_index) *bad_index = -1;
     if (!out) return XDCG_INVALID_ARG;
     *out = nullptr;
-    if (!K || !Z || blocks) return XDCG_INVALID_ARG;
+    if (!K || !Z) return XDCG_INVALID_ARG;
     xdcg_ctx *c = new (std::nothrow) xdcg_ctx();
     if (!c) return XDCG_OOM;
     if (opt)
@@ -1627,7 +1887,8 @@ xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflatio
         c->opt.max_batch < 0 || c->opt.max_batch > kMaxBatch ||
         (c->opt.coarse_fp64 != 0 && c->opt.coarse_fp64 != 1) ||
         !(c->opt.wait_s >= 0.0 && c->opt.wait_s <= 60.0) ||
-        !(c->opt.inner_tol > 0 && c->opt.inner_tol < 1)) {
+        !(c->opt.inner_tol > 0 && c->opt.inner_tol < 1) ||
+        (blocks && (c->opt.jacobi != XDCG_BLOCK_JACOBI || c->opt.max_batch > 0))) {
         delete c;
         return XDCG_INVALID_ARG;
     }
@@ -1635,7 +1896,7 @@ xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflatio
     if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return XDCG_CUDA_ERROR; }
     const auto t0 = std::chrono::steady_clock::now();
     int bad = -1;
-    xdcg_status s = setup_impl(c, K, Z, &bad);
+    xdcg_status s = setup_impl(c, K, Z, blocks, &bad);
     if (bad_index) *bad_index = bad;
     if (s != XDCG_OK) {
         cudaStreamSynchronize(c->st);
@@ -1843,8 +2104,7 @@ xdcg_status xdcg_precond(xdcg_ctx *c, const double *r, double *z) {
     cudaStream_t st = c->st;
     init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
     CK(cudaMemcpyAsync(c->r64, r, c->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    launch_update<double>(c->L64.N, nullptr, c->r64, nullptr, nullptr, c->y64, 1, c->partials,
-                          c->aux, st);
+    PlainPath{c, c->L64}.update(nullptr, c->r64, nullptr, nullptr, c->y64, 1, c->aux);
     launch_restrict(c->L64.B, c->r64, c->y64, 1, c->g, c->zr, c->aux, st);
     launch_coarse(c->Einv, c->k, c->g, c->zr, c->nu, nullptr, 0, c->partials, c->aux, st);
     launch_prolong(c->L64.B, c->nu, c->y64, z, 2, c->aux, st);

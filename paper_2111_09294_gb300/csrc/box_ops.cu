@@ -159,8 +159,9 @@ k_restrict(BoxDev<T> B, const T *a, const T *b, int withW, double *g, double *zr
 
 void launch_restrict(const BoxDev<double> &B, const double *a, const double *b, int withW,
                      double *g, double *zr, const Scalars *sc, cudaStream_t st) {
-    launch_pdl(k_restrict<double, double, false>, B.nBox, kBoxThreads, 0, st, B, a, b, withW, g, zr,
-               sc);
+    // Z by value (B.Zt) or from the geometry
+    launch_pdl(B.Zt ? k_restrict<double, double, true> : k_restrict<double, double, false>, B.nBox,
+               kBoxThreads, 0, st, B, a, b, withW, g, zr, sc);
 }
 
 
@@ -259,7 +260,8 @@ k_prolong(BoxDev<T> B, const T *nu, const T *y, T *p, int mode, Scalars *sc) {
 
 void launch_prolong(const BoxDev<double> &B, const double *nu, const double *y, double *p,
                     int mode, Scalars *sc, cudaStream_t st) {
-    launch_pdl(k_prolong<double, false>, B.nBox, kBoxThreads, 0, st, B, nu, y, p, mode, sc);
+    launch_pdl(B.Zt ? k_prolong<double, true> : k_prolong<double, false>, B.nBox, kBoxThreads, 0,
+               st, B, nu, y, p, mode, sc);
 }
 
 
@@ -274,8 +276,9 @@ constexpr int kRowThreads = 256;
 template <int M>
 __device__ __forceinline__ float restrict_update_unit(const RowBoxDev &B, int unit, float *u,
                                                       const float *r_cur, float *r_next,
-                                                      const float *p, const float *q, int mode,
-                                                      float alpha, double *g, double *zr) {
+                                                      const float *p, const float *q,
+                                                      const float *yv, int mode, float alpha,
+                                                      double *g, double *zr) {
     const int s = B.unitBox[unit];
     float acc[2 * M + 1];
 #pragma unroll
@@ -304,10 +307,12 @@ __device__ __forceinline__ float restrict_update_unit(const RowBoxDev &B, int un
         const int r0 = B.extRowPtr[s], R = B.extRowPtr[s + 1] - r0;
         const float *W = B.W + B.wBase[s];
         const int re = B.unitExtEnd[unit];
+        // coupled rows take W~^T of y = M~^-1 r (mode 3) or of r itself
+        const float *rv = (mode == 3) ? yv : r_cur;
 #pragma unroll 4
         for (int r = B.unitExtBegin[unit] + threadIdx.x; r < re; r += blockDim.x) {
             const int d = ld_keep(B.extRowDof + r, keep);
-            const float rn = (mode == 0) ? fmaf(-alpha, q[d], r_cur[d]) : r_cur[d];
+            const float rn = (mode == 0) ? fmaf(-alpha, q[d], rv[d]) : rv[d];
             const int rl = r - r0;
 #pragma unroll
             for (int c = 0; c < M; ++c)
@@ -362,18 +367,18 @@ __device__ __forceinline__ float restrict_update_unit(const RowBoxDev &B, int un
 
 __global__ void __launch_bounds__(kRowThreads)
 k_restrict_update(RowBoxDev B, float *u, const float *r_cur, float *r_next, const float *p,
-                  const float *q, int mode, double *g, double *zr, double *partials,
-                  Scalars *sc) {
+                  const float *q, const float *yv, int mode, double *g, double *zr,
+                  double *partials, Scalars *sc) {
     pdl_wait();
     if (sc->done != kRunning) return;
     const int unit = blockIdx.x;
     const float alpha = (mode == 0) ? (float)sc->alpha : 0.0f;
     float rr;
     if (B.menr[B.unitBox[unit]])
-        rr = restrict_update_unit<12>(B, unit, u, r_cur, r_next, p, q, mode, alpha, g, zr);
+        rr = restrict_update_unit<12>(B, unit, u, r_cur, r_next, p, q, yv, mode, alpha, g, zr);
     else
-        rr = restrict_update_unit<6>(B, unit, u, r_cur, r_next, p, q, mode, alpha, g, zr);
-    if (mode == 2) return;
+        rr = restrict_update_unit<6>(B, unit, u, r_cur, r_next, p, q, yv, mode, alpha, g, zr);
+    if (mode >= 2) return;
     double tot;
     if (grid_sum_t0((double)rr, partials, &sc->ticket[2], tot) && threadIdx.x == 0) {
         sc->rr = tot;
@@ -389,9 +394,9 @@ k_restrict_update(RowBoxDev B, float *u, const float *r_cur, float *r_next, cons
 
 void launch_restrict_update(const RowBoxDev &B, float *u, const float *r_cur, float *r_next,
                             const float *p, const float *q, int mode, double *g, double *zr,
-                            double *partials, Scalars *sc, cudaStream_t st) {
-    launch_pdl(k_restrict_update, B.nUnits, kRowThreads, 0, st, B, u, r_cur, r_next, p, q, mode, g,
-               zr, partials, sc);
+                            double *partials, Scalars *sc, cudaStream_t st, const float *y) {
+    launch_pdl(k_restrict_update, B.nUnits, kRowThreads, 0, st, B, u, r_cur, r_next, p, q, y, mode,
+               g, zr, partials, sc);
 }
 
 template <int M>

@@ -36,10 +36,24 @@ __device__ __forceinline__ void z_row(int j, int b, int menr, double X, double Y
     }
 }
 
+// Row j of node I's deflation block (M columns of box s): the caller's values
+// in the valued form, else from the geometry.
+__device__ __forceinline__ void z_row_of(const ZvalDev &Zv, int I, int j, int b, int M, int menr,
+                                         double X, double Y, double Z, double H,
+                                         double (&o)[12]) {
+    if (Zv.v) {
+        const double *r = Zv.v + Zv.off[I] + (long long)j * M;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) o[c] = c < M ? r[c] : 0.0;
+    } else {
+        z_row(j, b, menr, X, Y, Z, H, o);
+    }
+}
+
 // W block of entry e (node I coupled to box s): W_Is = sum_{J in s} K_IJ Z_J.
 __global__ void k_build_W(KinDev K, int nExt, const int *extBox, const int *extNode,
                           const long long *wOff, const int *sub, const double *xrel,
-                          const signed char *hsign, const int *menr, double *W) {
+                          const signed char *hsign, const int *menr, ZvalDev Zv, double *W) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nExt) return;
     const int s = extBox[e], I = extNode[e];
@@ -56,7 +70,7 @@ __global__ void k_build_W(KinDev K, int nExt, const int *extBox, const int *extN
         const double H = (double)hsign[J];
         for (int j = 0; j < bJ; ++j) {
             double zr[12];
-            z_row(j, bJ, menr[s], X, Y, Z, H, zr);
+            z_row_of(Zv, J, j, bJ, M, menr[s], X, Y, Z, H, zr);
             for (int i = 0; i < bI; ++i) {
                 const double kij = Kb[i * bJ + j];
                 if (kij == 0.0) continue;
@@ -70,10 +84,11 @@ __global__ void k_build_W(KinDev K, int nExt, const int *extBox, const int *extN
 
 void launch_build_W(const KinDev &K, int nExt, const int *extBox, const int *extNode,
                     const long long *wOff, const int *sub, const double *xrel,
-                    const signed char *hsign, const int *menr, double *W, cudaStream_t st) {
+                    const signed char *hsign, const int *menr, const ZvalDev &Zv, double *W,
+                    cudaStream_t st) {
     if (nExt == 0) return;
     k_build_W<<<(nExt + 127) / 128, 128, 0, st>>>(K, nExt, extBox, extNode, wOff, sub, xrel,
-                                                   hsign, menr, W);
+                                                   hsign, menr, Zv, W);
 }
 
 // E block (owner box t rows, box s columns) from one segment of box s's
@@ -81,8 +96,8 @@ void launch_build_W(const KinDev &K, int nExt, const int *extBox, const int *ext
 __global__ void k_build_E(const int *segBox, const int *segOwner, const int *segBegin,
                           const int *segEnd, const int *extNode, const long long *wOff,
                           const double *W, const int *dofStart, const double *xrel,
-                          const signed char *hsign, const int *col0, const int *menr, int k,
-                          double *E) {
+                          const signed char *hsign, const int *col0, const int *menr,
+                          ZvalDev Zv, int k, double *E) {
     const int g = blockIdx.x;
     const int s = segBox[g], t = segOwner[g];
     const int Ms = menr[s] ? 12 : 6, Mt = menr[t] ? 12 : 6;
@@ -97,7 +112,7 @@ __global__ void k_build_E(const int *segBox, const int *segOwner, const int *seg
         const double H = (double)hsign[I];
         for (int i = 0; i < bI; ++i) {
             double zr[12];
-            z_row(i, bI, menr[t], X, Y, Z, H, zr);
+            z_row_of(Zv, I, i, bI, Mt, menr[t], X, Y, Z, H, zr);
             sum += zr[a] * Wb[i * Ms + b];
         }
     }
@@ -107,11 +122,11 @@ __global__ void k_build_E(const int *segBox, const int *segOwner, const int *seg
 void launch_build_E(int nSeg, const int *segBox, const int *segOwner, const int *segBegin,
                     const int *segEnd, const int *extNode, const long long *wOff,
                     const double *W, const int *dofStart, const double *xrel,
-                    const signed char *hsign, const int *col0, const int *menr, int k,
-                    double *E, cudaStream_t st) {
+                    const signed char *hsign, const int *col0, const int *menr,
+                    const ZvalDev &Zv, int k, double *E, cudaStream_t st) {
     if (nSeg == 0) return;
     k_build_E<<<nSeg, 144, 0, st>>>(segBox, segOwner, segBegin, segEnd, extNode, wOff, W,
-                                     dofStart, xrel, hsign, col0, menr, k, E);
+                                     dofStart, xrel, hsign, col0, menr, Zv, k, E);
 }
 
 __global__ void k_symmetrize(double *E, int k) {
@@ -127,48 +142,6 @@ __global__ void k_symmetrize(double *E, int k) {
 void launch_symmetrize(double *E, int k, cudaStream_t st) {
     const long long n = (long long)k * k;
     k_symmetrize<<<(int)((n + 255) / 256), 256, 0, st>>>(E, k);
-}
-
-// In-place inversion of an SPD matrix by successive symmetric sweeps: after
-// sweeping every pivot the array holds -E^-1.  A pivot that is not larger
-// than thr (or not finite) marks the matrix as not SPD.
-__global__ void k_sweep_col(const double *A, int k, int j, double *c, int *bad, double thr) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= k) return;
-    const double v = A[(size_t)i * k + j];
-    c[i] = v;
-    if (i == j && (!(v > thr) || !isfinite(v))) atomicMin(bad, j);
-}
-
-__global__ void k_sweep_update(double *A, int k, int j, const double *__restrict__ c) {
-    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (idx >= (long long)k * k) return;
-    const int i = (int)(idx / k), l = (int)(idx % k);
-    const double inv = 1.0 / c[j];
-    if (i == j && l == j)
-        A[idx] = -inv;
-    else if (i == j)
-        A[idx] = c[l] * inv;
-    else if (l == j)
-        A[idx] = c[i] * inv;
-    else
-        A[idx] -= (c[i] * c[l]) * inv;
-}
-
-__global__ void k_negate(double *A, long long n) {
-    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (idx < n) A[idx] = -A[idx];
-}
-
-void launch_sweep_inverse(double *A, int k, double *colbuf, int *bad, double thr,
-                          cudaStream_t st) {
-    const long long n = (long long)k * k;
-    const int gridN = (int)((n + 255) / 256), gridK = (k + 255) / 256;
-    for (int j = 0; j < k; ++j) {
-        k_sweep_col<<<gridK, 256, 0, st>>>(A, k, j, colbuf, bad, thr);
-        k_sweep_update<<<gridN, 256, 0, st>>>(A, k, j, colbuf);
-    }
-    k_negate<<<gridN, 256, 0, st>>>(A, n);
 }
 
 // ---- per-iteration coarse solve -------------------------------------------

@@ -195,10 +195,12 @@ void launch_prolong(const BoxDev<double> &B, const double *nu, const double *y, 
 // to r_next), g = Z~^T r' - W~^T r', zr = Z~^T r', ||r'||^2 with the
 // convergence and iteration-cap tests; mode 1 (start): the same without the
 // update (alpha = 0, nothing written but g, zr, ||r||^2); mode 2 (Algorithm
-// 2): g = Z~^T r only.
+// 2): g = Z~^T r only; mode 3 (caller blocks, y = M~^-1 r given): g = Z~^T r
+// - W~^T y and zr = Z~^T r, nothing else.
 void launch_restrict_update(const RowBoxDev &B, float *u, const float *r_cur, float *r_next,
                             const float *p, const float *q, int mode, double *g, double *zr,
-                            double *partials, Scalars *sc, cudaStream_t st);
+                            double *partials, Scalars *sc, cudaStream_t st,
+                            const float *y = nullptr);
 void launch_prolong_rows(const RowBoxDev &B, const float *nu32, const float *y, float *p,
                          int mode, Scalars *sc, cudaStream_t st);
 void launch_to_colmajor(int nItems, const int *itemBox, const int *rowStart,
@@ -226,11 +228,21 @@ struct FacDev {
     const int *nodeList, *nodeIdx;
 };
 
+// Z given by value (the valued deflation form): node I's b_I x M_s block
+// (M_s = 12 if menr[s] else 6), row-major, at v + off[I].  v == nullptr: Z is
+// built from the geometry (Eqs. dcg_deflation_space, dcg_deflation_space_enr_std,
+// dcg_deflation_space_enr_enr).
+struct ZvalDev {
+    const double *v;
+    const long long *off;
+};
+
 void launch_gather(const int *src, long long n, const double *v, double *out64, float *out32,
                    cudaStream_t st);
 void launch_build_Zt(int nSlots, const int *slotNode, const int *dofStart, const int *sub,
                      const double *xrel, const signed char *hsign, const int *menr,
-                     const FacDev &F, const long long *zOff, float *Zt, cudaStream_t st);
+                     const ZvalDev &Zv, const FacDev &F, const long long *zOff, float *Zt,
+                     cudaStream_t st);
 // node-wise transforms between the caller's dof numbering (nat, which also
 // gives the node sizes) and the box-major FP32 numbering: in / ot are the
 // numberings of the input / output vector
@@ -240,10 +252,34 @@ void launch_bwd_accum(int nNodes, const int *nat, const int *in, const int *ot, 
                       const float *ut, double scale, double *u, cudaStream_t st);
 void launch_renumber(int nNodes, const int *nat, const int *in, const int *ot, const float *x,
                      float *out, cudaStream_t st);
-void launch_update_id(float *u, float *r, const float *p, const float *q, long long n, int mode,
-                      double *partials, Scalars *sc, cudaStream_t st);
+
+// ---- batched dense SPD inversion (set-up; dense_inv.cu) ---------------------
+
+// nMat row-major matrices, matrix m (dim[m] x dim[m]) at A + off[m], inverted
+// in place.  Tile tables: rowTileOff = prefix of T_m, tileOff = prefix of
+// T_m (T_m + 1) / 2 (upper 64 x 64 tiles), T_m = ceil(dim[m] / 64).  Scratch:
+// D (nMat x 64 x 64), C (panel rows of matrix m at cOff[m], dim[m] x 64),
+// thr (nMat).  A pivot that is not above rel times the matrix's largest
+// diagonal entry sets *bad (atomic min) to the matrix index (badByMatrix) or
+// to the pivot's index within its matrix.
+struct DenseBatch {
+    int nMat, nTiles, nRowTiles;
+    const int *dim;
+    const long long *off;
+    const int *tileOff, *rowTileOff;
+    double *A, *D, *C, *thr;
+    const long long *cOff;
+    int *bad;
+    int badByMatrix;
+};
+size_t dense_inv_panel_doubles(int dim);
+size_t dense_inv_pivot_doubles();
+int dense_inv_tiles(int dim);
+cudaError_t launch_dense_inverse(const DenseBatch &B, int maxDim, long long nEntries, double rel,
+                                 cudaStream_t st);
 
 // ---- set-up kernels -------------------------------------------------------
+
 
 struct KinDev {   // node-blocked input matrix on the device (FP64)
     int nNodes;
@@ -252,21 +288,51 @@ struct KinDev {   // node-blocked input matrix on the device (FP64)
     const double *val;
 };
 
+// ---- caller-given block-Jacobi blocks (blocks.cu) ----------------------------
+
+// Dense inverses of the caller's blocks, block b (positions bPos[b] ..
+// bPos[b+1]-1, row-major, at A + aOff[b]); position p is entry idx[p] of this
+// path's vectors.  Apply units: rows [unitRow0[u], unitRow1[u]) of block
+// unitBlk[u].
+template <typename T>
+struct BlkDev {
+    int nBlk, nUnits;
+    const long long *aOff;
+    const int *bPos, *idx;
+    const T *A;
+    const int *unitBlk, *unitRow0, *unitRow1;
+};
+constexpr int kBlkUnitRows = 64;
+
+void launch_gather_blocks(const KinDev &K, long long nnzb, const int *blockRow,
+                          const int *blockOfNode, const int *bStart, const int *bDim,
+                          const long long *aOff, double *A, cudaStream_t st);
+void launch_scale_block_inverse(int n, const int *rowBlock, const int *bStart, const int *bDim,
+                                const int *bNode0, const int *bNode1, const long long *aOff,
+                                const int *dofStart, const FacDev &F, const double *X, double *Y,
+                                float *Z, cudaStream_t st);
+template <typename T>
+void launch_block_apply(const BlkDev<T> &B, const T *r, T *y, double *partials, Scalars *sc,
+                        cudaStream_t st);
+template <typename T>
+void launch_update_plain(T *u, T *r, const T *p, const T *q, long long n, int mode,
+                         double *partials, Scalars *sc, cudaStream_t st);
+
+
 int launch_block_cholesky(int B, int count, const int *nodes, const double *Dsoa, double *L64,
                           float *L32, int *bad, cudaStream_t st);
 void launch_xrel(int nNodes, const double *coords, const double *centre, const int *sub,
                  double *x64, float *x32, cudaStream_t st);
 void launch_build_W(const KinDev &K, int nExt, const int *extBox, const int *extNode,
                     const long long *wOff, const int *sub, const double *xrel,
-                    const signed char *hsign, const int *menr, double *W, cudaStream_t st);
+                    const signed char *hsign, const int *menr, const ZvalDev &Zv, double *W,
+                    cudaStream_t st);
 void launch_build_E(int nSeg, const int *segBox, const int *segOwner, const int *segBegin,
                     const int *segEnd, const int *extNode, const long long *wOff,
                     const double *W, const int *dofStart, const double *xrel,
-                    const signed char *hsign, const int *col0, const int *menr, int k,
-                    double *E, cudaStream_t st);
+                    const signed char *hsign, const int *col0, const int *menr,
+                    const ZvalDev &Zv, int k, double *E, cudaStream_t st);
 void launch_symmetrize(double *E, int k, cudaStream_t st);
-void launch_sweep_inverse(double *A, int k, double *colbuf, int *bad, double thr,
-                          cudaStream_t st);
 void launch_coarse32(const float *Einv, int k, const float *g32, const double *zr, double *nu,
                      float *nu32, int mode, double *partials, Scalars *sc, cudaStream_t st);
 void launch_cast_f32(const double *a, float *b, long long n, cudaStream_t st);

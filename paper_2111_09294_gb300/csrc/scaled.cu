@@ -93,7 +93,7 @@ __device__ __forceinline__ void zrow(int j, int b, int menr, double X, double Y,
 // Z~_I = L_I^T Z_I (b_I x M, row-major at zOff[t] for slot t holding node I), FP32.
 __global__ void k_build_Zt(int nSlots, const int *slotNode, const int *dofStart, const int *sub,
                            const double *xrel, const signed char *hsign, const int *menr,
-                           FacDev F, const long long *zOff, float *Zt) {
+                           ZvalDev Zv, FacDev F, const long long *zOff, float *Zt) {
     const int ts = blockIdx.x * blockDim.x + threadIdx.x;
     if (ts >= nSlots) return;
     const int I = slotNode[ts];
@@ -105,7 +105,12 @@ __global__ void k_build_Zt(int nSlots, const int *slotNode, const int *dofStart,
     for (int e = 0; e < b * M; ++e) acc[e] = 0.0;
     for (int j = 0; j < b; ++j) {
         double zr[12];
-        zrow(j, b, me, X, Y, Z, H, zr);
+        if (Zv.v) {
+            const double *r = Zv.v + Zv.off[I] + (long long)j * M;
+            for (int c = 0; c < 12; ++c) zr[c] = c < M ? r[c] : 0.0;
+        } else {
+            zrow(j, b, me, X, Y, Z, H, zr);
+        }
         bool any = false;
         for (int c = 0; c < M; ++c) any |= zr[c] != 0.0;
         if (!any) continue;
@@ -120,9 +125,10 @@ __global__ void k_build_Zt(int nSlots, const int *slotNode, const int *dofStart,
 
 void launch_build_Zt(int nSlots, const int *slotNode, const int *dofStart, const int *sub,
                      const double *xrel, const signed char *hsign, const int *menr,
-                     const FacDev &F, const long long *zOff, float *Zt, cudaStream_t st) {
+                     const ZvalDev &Zv, const FacDev &F, const long long *zOff, float *Zt,
+                     cudaStream_t st) {
     k_build_Zt<<<(nSlots + 127) / 128, 128, 0, st>>>(nSlots, slotNode, dofStart, sub, xrel, hsign,
-                                                     menr, F, zOff, Zt);
+                                                     menr, Zv, F, zOff, Zt);
 }
 
 // W~ = L^-1 W per W entry (b_I x M), FP32.
@@ -216,44 +222,6 @@ __global__ void k_renumber(int nNodes, const int *nat, const int *in, const int 
 void launch_renumber(int nNodes, const int *nat, const int *in, const int *ot, const float *x,
                      float *out, cudaStream_t st) {
     k_renumber<<<(nNodes + 127) / 128, 128, 0, st>>>(nNodes, nat, in, ot, x, out);
-}
-
-// ---- inner FP32 iteration kernels ------------------------------------------
-
-// u += alpha p, r -= alpha q, ||r||^2 (the preconditioner is the identity:
-// y = r, so r^T y = ||r||^2).  mode 1: only the norm.
-__global__ void __launch_bounds__(kThreads)
-k_update_id(float *u, float *r, const float *p, const float *q, long long n, int mode,
-            double *partials, Scalars *sc) {
-    if (sc->done != kRunning) return;
-    const float alpha = (float)sc->alpha;
-    float v[1] = {0.0f};
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        float ri = r[i];
-        if (mode == 0) {
-            u[i] = fmaf(alpha, p[i], u[i]);
-            ri = fmaf(-alpha, q[i], ri);
-            r[i] = ri;
-        }
-        v[0] = fmaf(ri, ri, v[0]);
-    }
-    double tot[1];
-    if (grid_sum<float, 1>(v, partials, &sc->ticket[2], tot) && threadIdx.x == 0) {
-        sc->rr = tot[0];
-        sc->ry = tot[0];
-        if (tot[0] <= sc->tol2ff)
-            sc->done = kConverged;
-        else if (sc->its >= sc->max_it)
-            sc->done = kMaxIter;
-        else if (!isfinite(tot[0]))
-            sc->done = kBreakdown;
-    }
-}
-
-void launch_update_id(float *u, float *r, const float *p, const float *q, long long n, int mode,
-                      double *partials, Scalars *sc, cudaStream_t st) {
-    k_update_id<<<grid_of(n, kThreads), kThreads, 0, st>>>(u, r, p, q, n, mode, partials, sc);
 }
 
 }  // namespace xdcg

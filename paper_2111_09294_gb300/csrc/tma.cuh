@@ -8,7 +8,6 @@
 
 namespace xdcg {
 
-constexpr unsigned long long kWaitNs = 2000000000ull;    // default wait limit: 2 s per kernel
 constexpr unsigned long long kDrainNs = 100000000ull;    // 0.1 s to let copies land
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -50,12 +49,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// true once the phase with this parity has completed; false at the deadline
+// true once the phase with this parity has completed; false at the deadline.
+// The deadline is checked before every try (a try itself may block for a
+// while), so a deadline already passed gives up at once, whatever the copy.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
                                           unsigned long long deadline) {
-    while (!mbar_try_wait(bar, parity))
-        if (global_ns() > deadline) return false;
-    return true;
+    while (global_ns() < deadline)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
 }
 
 // orders this thread's earlier generic accesses to shared memory before

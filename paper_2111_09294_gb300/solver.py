@@ -45,13 +45,19 @@ class Solver:
     paper's comparison preconditioner).  record_history: keep ||r_i|| / ||f||
     per iteration of FP64 solves (history()).  coarse_fp64: mixed solves apply
     E^-1 in FP64 instead of its FP32 copy.  wait_s: limit of the SpMV's bounded
-    waits on its own copies (xdcg_options.wait_s).
+    waits on its own copies (xdcg_options.wait_s).  blocks: None (one block per
+    node) or the block-Jacobi blocks as dof ranges, blocks[b] .. blocks[b+1]
+    (whole nodes each; xdcg_blocks), e.g. one per subdomain of a problem
+    numbered subdomain by subdomain.  z_cols, z_values: Z by value instead of
+    from the geometry (xdcg_deflation's valued form: 6 or 12 columns per box,
+    node I's b_I x z_cols[sub[I]] block row-major, nodes in order).
     """
 
     def __init__(self, dof_ptr, row_ptr, col, val_ptr, val, sub_of_node, coords, hsign, centres,
                  precision="fp64", tol=1e-8, max_iter=10000, inner_tol=1e-3, max_outer=30,
                  time_spmv=False, enriched_modes=True, stream=None, jacobi="block",
-                 record_history=False, max_batch=0, coarse_fp64=False, wait_s=2.0):
+                 record_history=False, max_batch=0, coarse_fp64=False, wait_s=2.0,
+                 blocks=None, z_cols=None, z_values=None):
         lib = L.load()
         self._lib = lib
         self.ctx = ctypes.c_void_p()
@@ -64,7 +70,11 @@ class Solver:
         m = L.Matrix(n_nodes, keep[0].ctypes.data, keep[1].ctypes.data, keep[2].ctypes.data,
                      keep[3].ctypes.data, keep[4].ctypes.data, L.XDCG_HOST)
         z = L.Deflation(n_sub, keep[5].ctypes.data, keep[6].ctypes.data, keep[7].ctypes.data,
-                        keep[8].ctypes.data, int(bool(enriched_modes)), L.XDCG_HOST)
+                        keep[8].ctypes.data, int(bool(enriched_modes)), L.XDCG_HOST, None, None)
+        if z_values is not None:
+            zc, zv = _host(z_cols, np.int32), _host(z_values, np.float64)
+            keep += [zc, zv]
+            z.sub_cols, z.values = zc.ctypes.data, zv.ctypes.data
         opt = L.Options()
         lib.xdcg_default_options(ctypes.byref(opt))
         opt.tol = tol
@@ -84,8 +94,13 @@ class Solver:
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
+        blk = None
+        if blocks is not None:
+            bp = _host(blocks, np.int32)
+            keep.append(bp)
+            blk = ctypes.byref(L.Blocks(bp.size - 1, bp.ctypes.data, L.XDCG_HOST))
         bad = ctypes.c_int32(-1)
-        st = lib.xdcg_setup(ctypes.byref(self.ctx), ctypes.byref(m), ctypes.byref(z), None,
+        st = lib.xdcg_setup(ctypes.byref(self.ctx), ctypes.byref(m), ctypes.byref(z), blk,
                             ctypes.byref(opt), ctypes.c_void_p(stream.cuda_stream),
                             ctypes.byref(bad))
         L.check(st, "xdcg_setup", bad.value)

@@ -208,3 +208,22 @@ def test_element_data_reassembles_K():
         Ks[np.ix_(d[live], d[live])] += D["young"][e] * Kh[np.ix_(live, live)]
     assert np.max(np.abs(Ks - K)) <= 1e-14 * np.max(np.abs(K))
     assert np.all(D["young"] == young)
+
+
+def test_subdomain_renumbering_moves_entries_only():
+    # by_subdomain relabels nodes box by box: K, f and the element dof maps
+    # are the same up to that permutation, and each box's dofs are one range
+    P = X.make("cube8_edge")
+    P2, bp = X.by_subdomain(P)
+    d = P2.dof_map_from
+    assert np.array_equal(np.sort(d), np.arange(P.n))
+    assert np.array_equal(X.to_dense(P2)[np.ix_(d, d)], X.to_dense(P))
+    assert np.array_equal(P2.f[d], P.f)
+    sub2 = np.asarray(P2.sub_of_node)
+    assert np.all(np.diff(sub2) >= 0)
+    dof2 = np.asarray(P2.dof_ptr)
+    for s in range(P.n_sub):
+        nodes = np.nonzero(sub2 == s)[0]
+        assert bp[s] == dof2[nodes[0]] and bp[s + 1] == dof2[nodes[-1] + 1]
+    D1, D2 = X.element_data(P), X.element_data(P2)
+    assert np.array_equal(np.where(D1["dofs"] >= 0, d[np.maximum(D1["dofs"], 0)], -1), D2["dofs"])

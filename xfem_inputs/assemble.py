@@ -456,3 +456,65 @@ def to_dense(P):
             c0, c1 = P.dof_ptr[J], P.dof_ptr[J + 1]
             K[r0:r1, c0:c1] = P.val[P.val_ptr[p]:P.val_ptr[p + 1]].reshape(r1 - r0, c1 - c0)
     return K
+
+
+def by_subdomain(P):
+    """The same system with its free nodes renumbered subdomain by
+    subdomain (nodes of box 0 first, each box's nodes in their original
+    order), so that every box's dofs form one contiguous range.  Returns
+    (P2, block_ptr): block_ptr[s] .. block_ptr[s + 1] is box s's dof range,
+    the blocks of the subdomain-sized block Jacobi of Section 3.4.  Only
+    integer relabelling: every matrix entry, load and coordinate is moved,
+    none is computed."""
+    import copy
+    sub = np.asarray(P.sub_of_node)
+    perm = np.argsort(sub, kind="stable")            # new node i = old node perm[i]
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(perm.size)
+    dof = np.asarray(P.dof_ptr, dtype=np.int64)
+    bsz = np.diff(dof)
+    nbsz = bsz[perm]
+    ndof = np.zeros(P.n_nodes + 1, dtype=np.int64)
+    ndof[1:] = np.cumsum(nbsz)
+    # dof map old -> new (within-node order kept)
+    dmap = np.empty(P.n, dtype=np.int64)
+    for I in range(P.n_nodes):
+        dmap[dof[I]:dof[I + 1]] = ndof[inv[I]] + np.arange(bsz[I])
+    rowp = np.asarray(P.row_ptr, dtype=np.int64)
+    col = np.asarray(P.col, dtype=np.int64)
+    vptr = np.asarray(P.val_ptr, dtype=np.int64)
+    nrowp = np.zeros(P.n_nodes + 1, dtype=np.int64)
+    ncol, nvals, nvptr = [], [], [0]
+    for i in range(P.n_nodes):
+        I = perm[i]
+        ps = np.arange(rowp[I], rowp[I + 1])
+        ps = ps[np.argsort(inv[col[ps]], kind="stable")]
+        for p in ps:
+            ncol.append(inv[col[p]])
+            nvals.append(P.val[vptr[p]:vptr[p + 1]])
+            nvptr.append(nvptr[-1] + vptr[p + 1] - vptr[p])
+        nrowp[i + 1] = nrowp[i] + ps.size
+    P2 = copy.copy(P)
+    P2.dof_ptr = ndof.astype(np.int32)
+    P2.row_ptr = nrowp.astype(np.int32)
+    P2.col = np.asarray(ncol, dtype=np.int32)
+    P2.val_ptr = np.asarray(nvptr, dtype=np.int64)
+    P2.val = np.concatenate(nvals)
+    f = np.empty(P.n)
+    f[dmap] = P.f
+    P2.f = f
+    fixed = np.zeros(P.n, dtype=bool)
+    fixed[dmap] = np.asarray(P.fixed_dofs)
+    P2.fixed_dofs = fixed
+    P2.coords = P.coords[perm].copy()
+    P2.kind = np.asarray(P.kind)[perm].copy()
+    P2.sub_of_node = sub[perm].copy()
+    P2.hsign = np.asarray(P.hsign)[perm].copy()
+    P2.node_ids = np.asarray(P.node_ids)[perm].copy()
+    en = np.asarray(P.elem_nodes_free)
+    P2.elem_nodes_free = np.where(en >= 0, inv[np.maximum(en, 0)], -1)
+    counts = np.bincount(P2.sub_of_node, minlength=P.n_sub)
+    node_ptr = np.concatenate([[0], np.cumsum(counts)])
+    block_ptr = ndof[node_ptr].astype(np.int32)
+    P2.dof_map_from = dmap
+    return P2, block_ptr
