@@ -369,8 +369,9 @@ def run_ours(args):
             di = diag.info
             nbytes = {"spmv": di["spmv_bytes_fp32"], "restrict_update": di["restrict_bytes_fp32"],
                       "coarse": di["coarse_bytes_fp32"], "prolong": di["prolong_bytes_fp32"]}
+            # the fused iteration has no separate prolongation (0 us, 0 bytes)
             phases["mixed_gbs"] = {nm: round(nbytes[nm] / (phases[prec][nm] * 1e-6) / 1e9)
-                                   for nm in names}
+                                   for nm in names if phases[prec][nm] > 0 and nbytes[nm] > 0}
         diag.close()
     # several load cases of the same crack configuration: one batched FP32 run
     # against the same columns solved one after another (outside the value)
@@ -533,6 +534,27 @@ def run_ours(args):
         return out
 
     blocks_row = optional(measure_subdomain_blocks) if args.subdomain_blocks else None
+
+    # iterations against n at a fixed subdomain size (boxes of 6^3 hexes, the
+    # 24^3 case's crack at 12^3 .. 48^3 hexes): GPU counts and times
+    def measure_trend():
+        rows = []
+        for name in X.TREND:
+            Pt = X.make(name)
+            ft = torch.tensor(Pt.f, device=dev)
+            row = {"workload": name, "n": int(Pt.n), "n_sub": int(Pt.n_sub),
+                   "n_per_sub": int(Pt.n // Pt.n_sub)}
+            for prec in ("fp64", "mixed"):
+                sol = Solver.from_problem(Pt, precision=prec)
+                sol.solve(ft, tol=TOL)
+                _, inf = sol.solve(ft, tol=TOL)
+                row[f"iterations_{prec}"] = inf["iterations"]
+                row[f"ms_{prec}"] = inf["t_solve_ms"]
+                sol.close()
+            rows.append(row)
+        return rows
+
+    trend = optional(measure_trend) if args.trend else None
     batch = optional(measure_batch) if args.batch > 0 else None
     fwd_bwd = optional(measure_fwd_bwd)
     sweep = optional(measure_sweep) if args.sweep > 0 else None
@@ -584,6 +606,7 @@ def run_ours(args):
         "forward_backward": fwd_bwd,
         "propagation_sweep": sweep,
         "subdomain_blocks": blocks_row,
+        "iterations_vs_n": trend,
         "roofline": {"bound": "hbm", "kernel": "k_spmv<float> (inner FP32 SpMV)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind,
@@ -662,6 +685,8 @@ def main():
                     help="internal: one timed FP64 oracle solve of --workload, printed as JSON "
                          "(run in a child process with a fixed BLAS thread count)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--trend", type=int, default=1,
+                    help="also report iterations against n at a fixed subdomain size (0: skip)")
     ap.add_argument("--subdomain-blocks", type=int, default=1,
                     help="also time block Jacobi with one block per subdomain (0: skip)")
     ap.add_argument("--profile", choices=["mixed", "fp64", "batch"], default=None,

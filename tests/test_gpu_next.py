@@ -317,3 +317,25 @@ def test_modulus_gradient_through_autograd_matches_oracle():
     # dJ/df is still the adjoint solution
     assert np.linalg.norm(f.grad.cpu().numpy() - lref) <= 1e-7 * np.linalg.norm(lref)
     s.close()
+
+
+def test_iterations_flat_in_n_at_fixed_subdomain_size():
+    # Section 4.1's scalability study: the same crack at 12^3, 24^3 and 36^3
+    # hexes with boxes of 6^3 hexes (dofs per subdomain roughly fixed).  Each
+    # GPU FP64 count is within +-2 of the oracle's, and the counts stay within
+    # 25 % of each other while n grows 18-fold (the paper's figure shows
+    # fluctuations but no growth).
+    dev = torch.device("cuda:0") if torch.cuda.is_available() else pytest.skip("no CUDA device")
+    from paper_2111_09294_gb300 import Solver
+    counts = []
+    for name in X.TREND[:3]:
+        P = X.make(name)
+        K, M, C = O.setup(P)
+        ref = O.adef2_pcg(K, P.f, M, C, tol=1e-8)
+        s = Solver.from_problem(P)
+        u, info = s.solve(torch.tensor(P.f, device=dev), tol=1e-8)
+        assert abs(info["iterations"] - ref.iterations) <= 2, (name, info["iterations"], ref.iterations)
+        assert info["rel_res_true"] <= 1.05e-8
+        counts.append(info["iterations"])
+        s.close()
+    assert max(counts) <= 1.25 * min(counts), counts

@@ -13,6 +13,9 @@
                      (0.5, 0.5, 0.5), the same warp), r_e = 0.05, 8^3 boxes,
                      per-element Young's modulus log-normal (mu 0, sigma 0.3,
                      seed 0): the differentiable-solve workload.
+* trend12 .. trend48: the cube24_ellipse crack at 12^3 .. 48^3 hexes, boxes
+                     of 6^3 hexes, r_e = 2 h: iterations against n at a
+                     fixed subdomain size.
 * cube32_sweep_00 .. cube32_sweep_15: 32^3 hexes, an inclined penny
                      (centre (0.5, 0.5, 0.5), tilted 30 deg about x, no warp)
                      whose radius grows linearly from 0.15 to 0.35 over the 16
@@ -50,6 +53,16 @@ CONFIGS = {
                                    young=lambda m: np.random.default_rng(0).lognormal(
                                        0.0, 0.3, m ** 3)),
 }
+# iterations against system size at a fixed subdomain size (Section 4.1's
+# scalability study): the 24^3 case's crack at m = 12 .. 48 hexes per axis,
+# boxes of 6^3 hexes (n / n_sd about 650-730), tip radius 2 h
+TREND_M = (12, 24, 36, 48)
+TREND = [f"trend{m}" for m in TREND_M]
+for _m in TREND_M:
+    CONFIGS[f"trend{_m}"] = dict(m=_m, n_box=_m // 6,
+                                 cracks=lambda m=_m: [TiltedEllipticalCrack(
+                                     (0.5, 0.5, 0.5), 0.30, 0.20, np.deg2rad(30.0), 0.03,
+                                     2.0 / m)])
 for _name, _r in zip(SWEEP, SWEEP_RADII):
     CONFIGS[_name] = dict(m=32, n_box=8,
                           cracks=lambda r=float(_r): [TiltedEllipticalCrack(
