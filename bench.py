@@ -455,10 +455,46 @@ def run_ours(args):
         # per call, including the call's status read (a stream synchronisation)
         fwd_bwd["element_call_ms"] = e0.elapsed_time(e1) / max(args.steps, 1)
         fwd_bwd["elements"] = elems.n_el
+        if args.chain_steps > 1 and args.workload == X.STEPS64[0]:
+            fwd_bwd["propagation_steps"] = optional(lambda: chain(args.chain_steps))
         fwd_bwd["speedup_mixed_vs_fp64"] = fwd_bwd["fp64_ms"] / fwd_bwd["mixed_ms"]
         fwd_bwd["loss"] = ("compliance J = f . u; backward = adjoint solve to the same tol, then "
                            "dJ/df and dJ/dE_e for every element")
         return fwd_bwd
+    # total compliance over successive crack-front positions of the 64^3
+    # log-normal workload, u recomputed in the backward instead of stored
+    def chain(nsteps):
+        from paper_2111_09294_gb300 import Elements
+        from paper_2111_09294_gb300.autograd import compliance_steps
+        Ps = X.make_many(X.STEPS64[:nsteps])
+        elems = [Elements.from_dict(X.element_data(Pi), dev) for Pi in Ps]
+        young = torch.tensor(Ps[0].young, device=dev)
+        out = {"steps": nsteps, "n_dofs": [int(Pi.n) for Pi in Ps],
+               "loss": "sum over steps of f_s . u_s; u_s recomputed in the backward"}
+        for name in ("mixed", "fp64"):
+            sols = [Solver.from_problem(Pi, precision=name, inner_tol=args.inner_tol)
+                    for Pi in Ps]
+            loads = [torch.tensor(Pi.f, device=dev) for Pi in Ps]
+            ts = []
+            for it in range(max(1, args.warmup) + args.steps):
+                fs = [l.clone().requires_grad_(True) for l in loads]
+                yg = young.clone().requires_grad_(True)
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                J = compliance_steps(sols, fs, TOL, young=yg, elements=elems)
+                J.backward()
+                e1.record(stream)
+                e1.synchronize()
+                if it >= max(1, args.warmup):
+                    ts.append(e0.elapsed_time(e1))
+            out[name + "_ms"] = float(np.median(ts))
+            for sl in sols:
+                sl.close()
+        out["speedup_mixed_vs_fp64"] = out["fp64_ms"] / out["mixed_ms"]
+        return out
+
     # a propagation sweep: --sweep systems of the 32^3 inclined-penny sweep,
     # 8 load cases each, every system a batched mixed solve on its own stream;
     # concurrent against one after another (outside the value)
@@ -685,6 +721,9 @@ def main():
                     help="internal: one timed FP64 oracle solve of --workload, printed as JSON "
                          "(run in a child process with a fixed BLAS thread count)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--chain-steps", type=int, default=0,
+                    help="with --workload cube64_penny_lognormal: also time the compliance "
+                         "over this many crack-front steps (u recomputed, not stored)")
     ap.add_argument("--trend", type=int, default=1,
                     help="also report iterations against n at a fixed subdomain size (0: skip)")
     ap.add_argument("--subdomain-blocks", type=int, default=1,

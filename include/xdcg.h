@@ -137,9 +137,12 @@ typedef struct {
     int32_t max_outer;       /* MIXED: residual replacements (FP64 residual evaluations),
                                 default 30.  When two replacements in a row shorten the FP64
                                 residual by less than 2x (the FP32 recurrence's rounding floor,
-                                near 1e-11 relative on large systems), or max_outer is reached,
-                                the solve finishes with the FP64 iteration from its current u
-                                (Algorithm 2 with u_-1 = u) */
+                                near 1e-11 relative on large systems), when the FP32 run stalls
+                                (200 iterations without its residual dropping by 10 %: the
+                                FP32 rounding of K~ hides what is left to resolve), or when
+                                max_outer is reached, the solve folds in the FP32 correction and
+                                finishes with the FP64 iteration from its current u (Algorithm
+                                2 with u_-1 = u) */
     int32_t time_spmv;       /* 1: bracket every SpMV launch of the iteration by CUDA events;
                                 2: bracket every kernel of the iteration (t_phase_ms) */
     int32_t jacobi;          /* XDCG_BLOCK_JACOBI (default): one block per node (3/6/15 dofs,
@@ -342,6 +345,25 @@ xdcg_status xdcg_element_sensitivity(xdcg_ctx *ctx, int64_t n_el, const int64_t 
                                      const int32_t *elem_dofs, const int64_t *elem_mat_off,
                                      const double *elem_mat, int64_t mat_len, const double *u,
                                      const double *lam, double *out);
+
+/* Gradient of a loss J(u), u = K^-1 f, with respect to K's stored entries
+ * (for differentiable use of the solver; not part of the paper's method):
+ *     dJ/dK_ij = -lam_i u_j,   K lam = dJ/du
+ * (lam: a second solve on this context, K being symmetric), sampled at the
+ * positions K stores: out[val_ptr[p] + a * b_J + b] receives -lam[dof_ptr[I]
+ * + a] * u[dof_ptr[J] + b] for the stored block p = (I, J).  The per-element
+ * modulus sensitivities of xdcg_element_sensitivity are the contractions
+ * <dJ/dK, Khat_e>.
+ *
+ * K: the context's matrix structure as device arrays (mem = XDCG_DEVICE,
+ * n_nodes as at set-up; val is not read).  lam, u: device, length n.  out:
+ * device, val_ptr[nnzb] doubles, written in FP64 (each entry one product).
+ * Synchronises the context stream.  XDCG_INVALID_ARG for a null pointer, a
+ * host-memory structure or a node count other than the context's, and for
+ * a stored block whose column, dofs or value range are out of bounds (that
+ * block's entries are left unwritten). */
+xdcg_status xdcg_stiffness_gradient(xdcg_ctx *ctx, const xdcg_matrix *K, const double *lam,
+                                    const double *u, double *out);
 
 /* Copy the coarse matrix E (k x k, row-major, FP64) to host memory E_host. */
 xdcg_status xdcg_coarse_matrix(xdcg_ctx *ctx, double *E_host);

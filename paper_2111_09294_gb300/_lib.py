@@ -23,8 +23,8 @@ STATUS = {0: "XDCG_OK", 1: "XDCG_INVALID_ARG", 2: "XDCG_NOT_SPD_BLOCK",
 # every function the header declares
 EXPORTS = ["xdcg_default_options", "xdcg_setup", "xdcg_solve", "xdcg_solve_x0", "xdcg_solve_batch",
            "xdcg_solve_host", "xdcg_get_info", "xdcg_get_history", "xdcg_spmv", "xdcg_spmv_noalloc",
-           "xdcg_precond", "xdcg_element_sensitivity", "xdcg_coarse_matrix", "xdcg_destroy",
-           "xdcg_status_string"]
+           "xdcg_precond", "xdcg_element_sensitivity", "xdcg_stiffness_gradient",
+           "xdcg_coarse_matrix", "xdcg_destroy", "xdcg_status_string"]
 
 
 class Matrix(ctypes.Structure):
@@ -102,6 +102,8 @@ def load():
     lib.xdcg_precond.argtypes = [c_void_p, c_void_p, c_void_p]
     lib.xdcg_element_sensitivity.argtypes = [c_void_p, c_int64, c_void_p, c_void_p, c_void_p,
                                              c_void_p, c_int64, c_void_p, c_void_p, c_void_p]
+    lib.xdcg_stiffness_gradient.argtypes = [c_void_p, POINTER(Matrix), c_void_p, c_void_p,
+                                            c_void_p]
     lib.xdcg_coarse_matrix.argtypes = [c_void_p, c_void_p]
     lib.xdcg_destroy.argtypes = [c_void_p]
     lib.xdcg_status_string.argtypes = [c_int]

@@ -83,6 +83,7 @@ struct xdcg_ctx {
     Scalars *sc = nullptr, *sc32 = nullptr, *aux = nullptr;
     Scalars *h_sc = nullptr;   // pinned
     int *h_done = nullptr;     // pinned, 2 slots
+    double *h_rr = nullptr;    // pinned, 2 slots: ||r||^2 at each poll of the FP32 run
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evb[2] = {nullptr, nullptr};
     std::vector<cudaEvent_t> evS, evE;
     std::vector<cudaEvent_t> evP;      // per-kernel marks of timed iterations (time_spmv = 2)
@@ -422,11 +423,18 @@ void scaled_init(xdcg_ctx *c, const float *f, float *u, float *rA, float *p, Sca
     c->launches += 7;
 }
 
+// A stall of the FP32 run: kStallIts iterations without the recursive
+// ||r|| dropping by 10 % (||r||^2 by 19 %) below its best.  A healthy run
+// drops it by 1e-3 in some tens of iterations; a stall means that the FP32
+// rounding of K~ hides the components still to be resolved.
+constexpr int kStallIts = 200;
+
 // Run iterations (in batches, polling the device flag) until a kernel stops
-// the run: the replacement trigger, breakdown, or the iteration cap.
+// the run (the replacement trigger, breakdown, the iteration cap) or the run
+// stalls (*stalled, the device flag still running).
 xdcg_status scaled_iterate(xdcg_ctx *c, float *u, float *rA, float *rB, float *p, float *q,
                            Scalars *sc, int max_it, int *its_out, int *done_out,
-                           xdcg_result *res) {
+                           xdcg_result *res, bool *stalled) {
     cudaStream_t st = c->st;
     Level32 &L = c->L32;
     const bool timeSpmv = c->opt.time_spmv == 1, timeKernels = c->opt.time_spmv == 2;
@@ -435,6 +443,9 @@ xdcg_status scaled_iterate(xdcg_ctx *c, float *u, float *rA, float *rB, float *p
     const int it0 = c->h_sc->its;
     int i = it0, launched = 0;
     const int max_batches = (max_it - it0) / kBatch + 2;
+    double bestRR = c->h_sc->rr;
+    int lastGain = it0;
+    *stalled = false;
     for (int b = 0; b < max_batches; ++b) {
         for (int j = 0; j < kBatch; ++j, ++i, ++launched) {
             float *rc = (i & 1) ? rB : rA;
@@ -472,10 +483,20 @@ xdcg_status scaled_iterate(xdcg_ctx *c, float *u, float *rA, float *rB, float *p
             c->launches += 4;
         }
         CK(cudaMemcpyAsync(&c->h_done[b & 1], &sc->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&c->h_rr[b & 1], &sc->rr, sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaEventRecord(c->evb[b & 1], st));
         if (b >= 1) {
             CK(cudaEventSynchronize(c->evb[(b - 1) & 1]));
             if (c->h_done[(b - 1) & 1] != kRunning) break;
+            const double rrNow = c->h_rr[(b - 1) & 1];
+            const int itNow = it0 + b * kBatch;
+            if (rrNow < 0.81 * bestRR) {
+                bestRR = rrNow;
+                lastGain = itNow;
+            } else if (itNow - lastGain >= kStallIts) {
+                *stalled = true;
+                break;
+            }
         }
     }
     CK(cudaMemcpyAsync(c->h_sc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
@@ -483,6 +504,7 @@ xdcg_status scaled_iterate(xdcg_ctx *c, float *u, float *rA, float *rB, float *p
     CK(cudaGetLastError());
     *its_out = c->h_sc->its;
     *done_out = c->h_sc->done;
+    if (*done_out != kRunning) *stalled = false;
     const int nt = std::min(launched, c->h_sc->its - it0);
     if (timeSpmv) {
         for (int e = 0; e < nt; ++e) {
@@ -591,11 +613,11 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, boo
     c->launches += 2;
     double last_rec = 1.0;
     int cycles = 0, its = 0, done = 0, breakdowns = 0, slow = 0;
-    bool finishFp64 = false;
+    bool finishFp64 = false, stalled = false;
     xdcg_status status = XDCG_NO_CONVERGENCE;
     while (true) {
         s = scaled_iterate(c, c->u32, rA, rB, c->p32, c->q32, c->sc32, c->opt.max_iter, &its,
-                           &done, res);
+                           &done, res, &stalled);
         if (s != XDCG_OK) return s;
         if (done == kFault) return XDCG_TIMEOUT;
         last_rec = std::sqrt(c->h_sc->rr);
@@ -617,7 +639,7 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, boo
         // than 2x (or the replacement budget spent): the FP32 recurrence has
         // reached its rounding floor; the FP64 iteration finishes from u
         slow = rn2 > 0.25 * prev ? slow + 1 : 0;
-        if (slow >= 2 || cycles >= c->opt.max_outer) { finishFp64 = true; break; }
+        if (stalled || slow >= 2 || cycles >= c->opt.max_outer) { finishFp64 = true; break; }
         if (done == kBreakdown) {
             if (rn2 >= prev || ++breakdowns > 2) { status = XDCG_BREAKDOWN; break; }
         }
@@ -891,6 +913,7 @@ void free_ctx(xdcg_ctx *c) {
     if (c->h_sc) cudaFreeHost(c->h_sc);
     if (c->h_bs) cudaFreeHost(c->h_bs);
     if (c->h_done) cudaFreeHost(c->h_done);
+    if (c->h_rr) cudaFreeHost(c->h_rr);
     for (auto e : c->evS) cudaEventDestroy(e);
     for (auto e : c->evE) cudaEventDestroy(e);
     for (auto e : c->evP) cudaEventDestroy(e);
@@ -1789,6 +1812,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     CK(cudaMemsetAsync(c->aux, 0, sizeof(Scalars), st));
     if (cudaMallocHost(&c->h_sc, sizeof(Scalars)) != cudaSuccess) return XDCG_OOM;
     if (cudaMallocHost(&c->h_done, 2 * sizeof(int)) != cudaSuccess) return XDCG_OOM;
+    if (cudaMallocHost(&c->h_rr, 2 * sizeof(double)) != cudaSuccess) return XDCG_OOM;
     CK(cudaEventCreate(&c->ev0));
     CK(cudaEventCreate(&c->ev1));
     CK(cudaEventCreateWithFlags(&c->evb[0], cudaEventDisableTiming));
@@ -2029,6 +2053,32 @@ xdcg_status xdcg_element_sensitivity(xdcg_ctx *c, int64_t n_el, const int64_t *e
     init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
     launch_element_sensitivity(n_el, c->n, elem_dof_ptr, elem_dofs, elem_mat_off, mat_len,
                                elem_mat, u, lam, out, &c->aux->fault, c->st);
+    c->launches++;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(c->h_sc, c->aux, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return c->h_sc->fault ? XDCG_INVALID_ARG : XDCG_OK;
+}
+
+xdcg_status xdcg_stiffness_gradient(xdcg_ctx *c, const xdcg_matrix *K, const double *lam,
+                                    const double *u, double *out) {
+    if (!c || !K || !lam || !u || !out || K->mem != XDCG_DEVICE || !K->dof_ptr ||
+        !K->row_ptr || !K->col || !K->val_ptr || K->n_nodes != c->nNodes)
+        return XDCG_INVALID_ARG;
+    // the pattern's sizes (two entries each, read back)
+    int32_t nnzb32 = 0;
+    int64_t nval = 0;
+    CK(cudaMemcpyAsync(&nnzb32, K->row_ptr + K->n_nodes, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                       c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (nnzb32 < 0) return XDCG_INVALID_ARG;
+    CK(cudaMemcpyAsync(&nval, K->val_ptr + nnzb32, sizeof(int64_t), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (nval < 0) return XDCG_INVALID_ARG;
+    // the fault word of the scalar block flags bad structure
+    init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
+    launch_stiffness_gradient(c->nNodes, nnzb32, c->n, nval, K->dof_ptr, K->row_ptr, K->col,
+                              K->val_ptr, lam, u, out, &c->aux->fault, c->st);
     c->launches++;
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c->h_sc, c->aux, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st));

@@ -374,5 +374,9 @@ void launch_element_sensitivity(long long nEl, long long n, const int64_t *dofPt
                                 const int32_t *dofs, const int64_t *matOff, long long matLen,
                                 const double *mats, const double *u, const double *lam,
                                 double *out, int *bad, cudaStream_t st);
+void launch_stiffness_gradient(int nNodes, long long nnzb, long long n, long long nval,
+                               const int32_t *dofStart, const int32_t *rowPtr, const int32_t *col,
+                               const int64_t *valPtr, const double *lam, const double *u,
+                               double *out, int *bad, cudaStream_t st);
 
 }  // namespace xdcg

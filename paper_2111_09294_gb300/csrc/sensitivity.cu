@@ -78,4 +78,57 @@ void launch_element_sensitivity(long long nEl, long long n, const int64_t *dofPt
         nEl, n, dofPtr, dofs, matOff, matLen, mats, u, lam, out, bad);
 }
 
+// dJ/dK sampled on K's stored pattern: for the stored block p = (I, J),
+// entry (a, b) of the block receives -lam[dofStart[I] + a] * u[dofStart[J] + b],
+// the outer product -lam u^T (the gradient of J(u), u = K^-1 f, with respect
+// to K's entries, K lam = dJ/du) at the positions K stores.  One thread per
+// stored block; its row I by binary search in rowPtr.  A structural entry out
+// of range (column, value range, dof) sets *bad and leaves that block
+// unwritten.
+__global__ void k_stiffness_gradient(int nNodes, long long nnzb, long long n, long long nval,
+                                     const int32_t *__restrict__ dofStart,
+                                     const int32_t *__restrict__ rowPtr,
+                                     const int32_t *__restrict__ col,
+                                     const int64_t *__restrict__ valPtr,
+                                     const double *__restrict__ lam,
+                                     const double *__restrict__ u, double *__restrict__ out,
+                                     int *bad) {
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= nnzb) return;
+    int lo = 0, hi = nNodes - 1;   // last row I with rowPtr[I] <= p
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (rowPtr[mid] <= p)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const int I = lo, J = col[p];
+    if (J < 0 || J >= nNodes) {
+        atomicExch(bad, 1);
+        return;
+    }
+    const long long dI = dofStart[I], dJ = dofStart[J];
+    const int bI = dofStart[I + 1] - dofStart[I], bJ = dofStart[J + 1] - dofStart[J];
+    const long long v0 = valPtr[p];
+    if (bI < 1 || bJ < 1 || dI + bI > n || dJ + bJ > n || v0 < 0 || valPtr[p + 1] != v0 + bI * bJ ||
+        v0 + bI * bJ > nval) {
+        atomicExch(bad, 1);
+        return;
+    }
+    for (int a = 0; a < bI; ++a) {
+        const double la = -lam[dI + a];
+        for (int b = 0; b < bJ; ++b) out[v0 + a * bJ + b] = la * u[dJ + b];
+    }
+}
+
+void launch_stiffness_gradient(int nNodes, long long nnzb, long long n, long long nval,
+                               const int32_t *dofStart, const int32_t *rowPtr, const int32_t *col,
+                               const int64_t *valPtr, const double *lam, const double *u,
+                               double *out, int *bad, cudaStream_t st) {
+    if (nnzb <= 0) return;
+    k_stiffness_gradient<<<(unsigned)((nnzb + 255) / 256), 256, 0, st>>>(
+        nNodes, nnzb, n, nval, dofStart, rowPtr, col, valPtr, lam, u, out, bad);
+}
+
 }  // namespace xdcg

@@ -35,6 +35,24 @@ class Elements:
         return cls(D["dof_ptr"], D["dofs"], D["mat_off"], D["mats"], device)
 
 
+class Pattern:
+    """The stored block pattern of a node-blocked K on the device (dof_ptr,
+    row_ptr, col, val_ptr), for Solver.stiffness_gradient."""
+
+    def __init__(self, dof_ptr, row_ptr, col, val_ptr, device="cuda"):
+        as_dev = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a, dtype=dt), device=device)
+        self.dof_ptr = as_dev(dof_ptr, np.int32)
+        self.row_ptr = as_dev(row_ptr, np.int32)
+        self.col = as_dev(col, np.int32)
+        self.val_ptr = as_dev(val_ptr, np.int64)
+        self.n_nodes = int(self.dof_ptr.numel()) - 1
+        self.nval = int(self.val_ptr[-1].item())
+
+    @classmethod
+    def from_problem(cls, P, device="cuda"):
+        return cls(P.dof_ptr, P.row_ptr, P.col, P.val_ptr, device)
+
+
 class Solver:
     """Adapted deflated CG (A-DEF2 + node-block Jacobi) for one stiffness matrix.
 
@@ -210,6 +228,21 @@ class Solver:
             ptr(elements.mat_off), ptr(elements.mats), elements.mats.numel(),
             self._dev(u, torch.float64), self._dev(lam, torch.float64), ptr(out)),
             "xdcg_element_sensitivity")
+        return out
+
+    def stiffness_gradient(self, pattern, lam, u, out=None):
+        """dJ/dK = -lam u^T at K's stored entries (K lam = dJ/du), in K's
+        value layout: one float64 entry per stored value."""
+        out = out if out is not None else torch.empty(pattern.nval, dtype=torch.float64,
+                                                      device=u.device)
+        if out.numel() != pattern.nval or out.dtype != torch.float64 or not out.is_contiguous():
+            raise ValueError("out: a contiguous float64 tensor of one entry per stored value")
+        ptr = lambda t: t.data_ptr()
+        m = L.Matrix(pattern.n_nodes, ptr(pattern.dof_ptr), ptr(pattern.row_ptr),
+                     ptr(pattern.col), ptr(pattern.val_ptr), None, L.XDCG_DEVICE)
+        L.check(self._lib.xdcg_stiffness_gradient(
+            self.ctx, ctypes.byref(m), self._dev(lam, torch.float64), self._dev(u, torch.float64),
+            ctypes.c_void_p(out.data_ptr())), "xdcg_stiffness_gradient")
         return out
 
     def precond(self, r):

@@ -13,6 +13,9 @@
                      (0.5, 0.5, 0.5), the same warp), r_e = 0.05, 8^3 boxes,
                      per-element Young's modulus log-normal (mu 0, sigma 0.3,
                      seed 0): the differentiable-solve workload.
+* cube64_penny_lognormal_step1 .. _step3: the same with the penny's radius
+                     0.32, 0.34, 0.36: four crack-front positions for a
+                     differentiable solve over propagation steps.
 * trend12 .. trend48: the cube24_ellipse crack at 12^3 .. 48^3 hexes, boxes
                      of 6^3 hexes, r_e = 2 h: iterations against n at a
                      fixed subdomain size.
@@ -63,6 +66,14 @@ for _m in TREND_M:
                                  cracks=lambda m=_m: [TiltedEllipticalCrack(
                                      (0.5, 0.5, 0.5), 0.30, 0.20, np.deg2rad(30.0), 0.03,
                                      2.0 / m)])
+# four successive crack-front positions of the 64^3 log-normal workload (the
+# penny grows by 0.02 a step; prescribed, no growth law), same moduli
+STEPS64 = ["cube64_penny_lognormal"] + [f"cube64_penny_lognormal_step{s}" for s in (1, 2, 3)]
+for _s in (1, 2, 3):
+    CONFIGS[f"cube64_penny_lognormal_step{_s}"] = dict(
+        m=64, n_box=8,
+        cracks=lambda s=_s: [WarpedPennyCrack((0.5, 0.5, 0.5), 0.3 + 0.02 * s, 0.02, 0.05)],
+        young=CONFIGS["cube64_penny_lognormal"]["young"])
 for _name, _r in zip(SWEEP, SWEEP_RADII):
     CONFIGS[_name] = dict(m=32, n_box=8,
                           cracks=lambda r=float(_r): [TiltedEllipticalCrack(
