@@ -591,6 +591,44 @@ def run_ours(args):
         return rows
 
     trend = optional(measure_trend) if args.trend else None
+    # the sweep's crack fronts one after another, as a propagation runs them:
+    # each front's set-up fresh and as an update of the previous front's
+    # context (unchanged node factors and E^-1 carried over), and its
+    # unit-tension solve from zero and warm-started from the previous front's
+    # solution (outside the value)
+    def measure_sequence():
+        from paper_2111_09294_gb300.sweep import transfer_guess, transfer_index
+        Ps = X.make_many(X.SWEEP[:args.sweep])
+        rows, prev, uprev, Pprev = [], None, None, None
+        for Pi in Ps:
+            fresh = Solver.from_problem(Pi, precision="mixed", inner_tol=args.inner_tol)
+            t_fresh = fresh.info["t_setup_ms"]
+            fresh.close()
+            sol = Solver.from_problem(Pi, precision="mixed", inner_tol=args.inner_tol, prev=prev)
+            fi = torch.tensor(Pi.f, device=dev)
+            ucold, icold = sol.solve(fi, tol=TOL)
+            row = {"n": int(Pi.n), "setup_fresh_ms": t_fresh, "setup_update_ms":
+                   sol.info["t_setup_ms"] if prev is not None else None,
+                   "reused_node_factors": sol.info["reused_node_factors"],
+                   "iterations_cold": icold["iterations"], "ms_cold": icold["t_solve_ms"]}
+            if prev is not None:
+                guess = transfer_guess(uprev, transfer_index(Pprev.dof_ptr, Pprev.kind,
+                                                             Pi.dof_ptr, Pi.kind), Pi.n)
+                _, iw = sol.solve(fi, tol=TOL, x0=guess)
+                assert iw["rel_res_true"] <= TOL * 1.05, iw
+                row.update(iterations_warm=iw["iterations"], ms_warm=iw["t_solve_ms"])
+                prev.close()
+            rows.append(row)
+            prev, uprev, Pprev = sol, ucold.clone(), Pi
+        prev.close()
+        upd = [r["setup_update_ms"] for r in rows[1:]]
+        return {"fronts": rows, "setup_fresh_ms_total": sum(r["setup_fresh_ms"] for r in rows),
+                "setup_update_ms_total": rows[0]["setup_fresh_ms"] + sum(upd),
+                "solve_cold_ms_total": sum(r["ms_cold"] for r in rows[1:]),
+                "solve_warm_ms_total": sum(r["ms_warm"] for r in rows[1:]),
+                "note": "mixed, unit tension, tol 1e-8; totals over fronts 1..15 for the solves"}
+
+    sequence = optional(measure_sequence) if args.sweep > 1 else None
     batch = optional(measure_batch) if args.batch > 0 else None
     fwd_bwd = optional(measure_fwd_bwd)
     sweep = optional(measure_sweep) if args.sweep > 0 else None
@@ -641,6 +679,7 @@ def run_ours(args):
         "batched_load_cases": batch,
         "forward_backward": fwd_bwd,
         "propagation_sweep": sweep,
+        "propagation_sequence": sequence,
         "subdomain_blocks": blocks_row,
         "iterations_vs_n": trend,
         "roofline": {"bound": "hbm", "kernel": "k_spmv<float> (inner FP32 SpMV)",

@@ -210,6 +210,12 @@ typedef struct {
     int64_t spmv_alg_bytes_fp32; /* the same with 4-byte values and vectors */
     int64_t block_entries;       /* caller blocks: sum of their squared sizes (entries of the
                                     dense inverses applied per iteration); 0 for node blocks */
+    double t_setup_phase_ms[8];  /* wall time of xdcg_setup's phases: validation; host layout
+                                    (integer maps); uploads and SpMV value gathers; node-block
+                                    factors, W and E; E^-1; the FP32 level (MIXED); caller
+                                    blocks; work vectors */
+    int32_t reused_node_factors; /* xdcg_setup_update: node-block factors carried over */
+    int32_t reused_coarse_inverse; /* xdcg_setup_update: 1 if E^-1 was carried over */
 } xdcg_info_t;
 
 /* Fill *opt with the defaults listed above. */
@@ -226,6 +232,23 @@ xdcg_status xdcg_default_options(xdcg_options *opt);
 xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflation *Z,
                        const xdcg_blocks *blocks, const xdcg_options *opt, void *stream,
                        int32_t *bad_index);
+
+/* Set-up for the next crack-front position of a propagation (the paper's
+ * crack propagation studies, Section 4: the preconditioner is updated rather
+ * than rebuilt from nothing).  Same arguments and result as xdcg_setup, plus
+ * prev, a context of the same mesh (the same nodes, in the same order) for
+ * the previous front.  The new context is built as by xdcg_setup, except
+ * that every node whose dofs and diagonal block of K are unchanged (bitwise)
+ * takes its block-Jacobi factor from prev instead of refactoring it (so only
+ * the blocks the front changed are factored), and that an unchanged E
+ * (bitwise, same k) takes prev's E^-1 instead of inverting it.  The results
+ * are bit for bit those of xdcg_setup on the same input.  prev is only read
+ * (its stream is synchronised first) and stays valid; destroy it when it is
+ * no longer needed.  info.reused_node_factors and info.reused_coarse_inverse
+ * say what was carried over. */
+xdcg_status xdcg_setup_update(xdcg_ctx **out, const xdcg_ctx *prev, const xdcg_matrix *K,
+                              const xdcg_deflation *Z, const xdcg_blocks *blocks,
+                              const xdcg_options *opt, void *stream, int32_t *bad_index);
 
 /* Solve K u = f with the options given at set-up, tol overriding opt.tol
  * when > 0.  f, u: caller-owned device arrays of n doubles (may not alias).

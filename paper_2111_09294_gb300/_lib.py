@@ -21,7 +21,7 @@ STATUS = {0: "XDCG_OK", 1: "XDCG_INVALID_ARG", 2: "XDCG_NOT_SPD_BLOCK",
           6: "XDCG_CUDA_ERROR", 7: "XDCG_OOM", 8: "XDCG_TOO_LARGE", 9: "XDCG_TIMEOUT"}
 
 # every function the header declares
-EXPORTS = ["xdcg_default_options", "xdcg_setup", "xdcg_solve", "xdcg_solve_x0", "xdcg_solve_batch",
+EXPORTS = ["xdcg_default_options", "xdcg_setup", "xdcg_setup_update", "xdcg_solve", "xdcg_solve_x0", "xdcg_solve_batch",
            "xdcg_solve_host", "xdcg_get_info", "xdcg_get_history", "xdcg_spmv", "xdcg_spmv_noalloc",
            "xdcg_precond", "xdcg_element_sensitivity", "xdcg_stiffness_gradient",
            "xdcg_coarse_matrix", "xdcg_destroy", "xdcg_status_string"]
@@ -70,10 +70,17 @@ class Info(ctypes.Structure):
                 ("t_setup_ms", c_double), ("restrict_bytes_fp32", c_int64),
                 ("coarse_bytes_fp32", c_int64), ("prolong_bytes_fp32", c_int64),
                 ("nnzb", c_int64), ("spmv_alg_bytes_fp64", c_int64),
-                ("spmv_alg_bytes_fp32", c_int64), ("block_entries", c_int64)]
+                ("spmv_alg_bytes_fp32", c_int64), ("block_entries", c_int64),
+                ("t_setup_phase_ms", c_double * 8), ("reused_node_factors", c_int32),
+                ("reused_coarse_inverse", c_int32)]
+
+    PHASES = ("validate", "host_layout", "upload", "factors_W_E", "E_inverse", "fp32_level",
+              "blocks", "work_vectors")
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["t_setup_phase_ms"] = dict(zip(self.PHASES, list(self.t_setup_phase_ms)))
+        return d
 
 
 _lib = None
@@ -91,6 +98,9 @@ def load():
     lib.xdcg_default_options.argtypes = [POINTER(Options)]
     lib.xdcg_setup.argtypes = [POINTER(c_void_p), POINTER(Matrix), POINTER(Deflation),
                                POINTER(Blocks), POINTER(Options), c_void_p, POINTER(c_int32)]
+    lib.xdcg_setup_update.argtypes = [POINTER(c_void_p), c_void_p, POINTER(Matrix),
+                                      POINTER(Deflation), POINTER(Blocks), POINTER(Options),
+                                      c_void_p, POINTER(c_int32)]
     lib.xdcg_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_double, POINTER(Result)]
     lib.xdcg_solve_x0.argtypes = [c_void_p, c_void_p, c_void_p, c_double, POINTER(Result)]
     lib.xdcg_solve_batch.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_double, c_void_p]

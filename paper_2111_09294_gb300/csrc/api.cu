@@ -3,12 +3,14 @@
 // kernels, and the solve drivers for the FP64 and the FP32-inner / FP64-
 // refinement paths.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <climits>
 #include <cmath>
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -64,6 +66,12 @@ struct xdcg_ctx {
           *bQ = nullptr, *bG32 = nullptr, *bNU32 = nullptr;
     double *bG = nullptr, *bZR = nullptr, *bNU = nullptr, *bUnitPart = nullptr, *bR64 = nullptr;
     BatchScalars *bs = nullptr, *h_bs = nullptr;
+    // kept for xdcg_setup_update: each node's dofs, its (Jacobi-filtered)
+    // diagonal block (host) and its position in its factor list
+    std::vector<int> hostKind, hostListPos;
+    std::vector<long long> hostDiagOff;
+    std::vector<double> hostDiag;
+    int reusedFactors = 0, reusedCoarse = 0;
     double *hist = nullptr;        // record_history: ||r_i||^2 of the last FP64 solve
     int histLen = 0;
     double histFF = 0.0;
@@ -83,7 +91,7 @@ struct xdcg_ctx {
     Scalars *sc = nullptr, *sc32 = nullptr, *aux = nullptr;
     Scalars *h_sc = nullptr;   // pinned
     int *h_done = nullptr;     // pinned, 2 slots
-    double *h_rr = nullptr;    // pinned, 2 slots: ||r||^2 at each poll of the FP32 run
+    Scalars *h_poll = nullptr; // pinned, 2 slots: the FP32 run's scalars at each poll
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evb[2] = {nullptr, nullptr};
     std::vector<cudaEvent_t> evS, evE;
     std::vector<cudaEvent_t> evP;      // per-kernel marks of timed iterations (time_spmv = 2)
@@ -155,6 +163,23 @@ bool fetch(std::vector<T> &dst, const T *src, size_t count, int mem) {
         return cudaMemcpy(dst.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost) == cudaSuccess;
     std::memcpy(dst.data(), src, count * sizeof(T));
     return true;
+}
+
+// f(begin, end) over [0, n) split into contiguous pieces, one host thread
+// each (at most 16, and none for small n): the set-up's validation and
+// layout loops, whose pieces write disjoint outputs.
+template <typename F>
+void parallel_for(long long n, F &&f) {
+    static const int hw = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const int T = (int)std::min<long long>(hw, (n + 8191) / 8192);
+    if (T <= 1) {
+        f(0LL, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(T);
+    for (int t = 0; t < T; ++t) th.emplace_back([&f, n, t, T] { f(n * t / T, n * (t + 1) / T); });
+    for (auto &x : th) x.join();
 }
 
 // Every point of x (p x 3) on one line?  (true for fewer than 3 points)
@@ -482,13 +507,13 @@ xdcg_status scaled_iterate(xdcg_ctx *c, float *u, float *rA, float *rB, float *p
             MARK(launched, 4);
             c->launches += 4;
         }
-        CK(cudaMemcpyAsync(&c->h_done[b & 1], &sc->done, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(&c->h_rr[b & 1], &sc->rr, sizeof(double), cudaMemcpyDeviceToHost, st));
+        // one copy per poll: the stop flag and ||r||^2 for the stall test
+        CK(cudaMemcpyAsync(&c->h_poll[b & 1], sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
         CK(cudaEventRecord(c->evb[b & 1], st));
         if (b >= 1) {
             CK(cudaEventSynchronize(c->evb[(b - 1) & 1]));
-            if (c->h_done[(b - 1) & 1] != kRunning) break;
-            const double rrNow = c->h_rr[(b - 1) & 1];
+            if (c->h_poll[(b - 1) & 1].done != kRunning) break;
+            const double rrNow = c->h_poll[(b - 1) & 1].rr;
             const int itNow = it0 + b * kBatch;
             if (rrNow < 0.81 * bestRR) {
                 bestRR = rrNow;
@@ -913,7 +938,7 @@ void free_ctx(xdcg_ctx *c) {
     if (c->h_sc) cudaFreeHost(c->h_sc);
     if (c->h_bs) cudaFreeHost(c->h_bs);
     if (c->h_done) cudaFreeHost(c->h_done);
-    if (c->h_rr) cudaFreeHost(c->h_rr);
+    if (c->h_poll) cudaFreeHost(c->h_poll);
     for (auto e : c->evS) cudaEventDestroy(e);
     for (auto e : c->evE) cudaEventDestroy(e);
     for (auto e : c->evP) cudaEventDestroy(e);
@@ -970,7 +995,17 @@ xdcg_status dense_inverse(xdcg_ctx *c, double *A, const std::vector<int> &dims,
 }
 
 xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *Zd,
-                       const xdcg_blocks *blocks, int *bad) {
+                       const xdcg_blocks *blocks, int *bad, const xdcg_ctx *prev) {
+    // wall time of each set-up phase (device work waited for at each mark)
+    auto tPrev = std::chrono::steady_clock::now();
+    auto mark = [&](int phase) -> bool {
+        if (cudaStreamSynchronize(c->st) != cudaSuccess) return false;
+        const auto now = std::chrono::steady_clock::now();
+        c->info.t_setup_phase_ms[phase] +=
+            std::chrono::duration<double, std::milli>(now - tPrev).count();
+        tPrev = now;
+        return true;
+    };
     const int N = K->n_nodes;
     if (N <= 0 || !K->dof_ptr || !K->row_ptr) return XDCG_INVALID_ARG;
     if ((K->mem != XDCG_HOST && K->mem != XDCG_DEVICE) ||
@@ -993,42 +1028,76 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     if (!fetch(vp64, K->val_ptr, nnzb + 1, K->mem)) return XDCG_INVALID_ARG;
     vptr.assign(vp64.begin(), vp64.end());
     if (vptr[0] != 0) return XDCG_INVALID_ARG;
-    for (int I = 0; I < N; ++I) {
-        bool diag = false;
-        for (long long p = rowp[I]; p < rowp[I + 1]; ++p) {
-            const int J = col[p];
-            if (J < 0 || J >= N) return XDCG_INVALID_ARG;
-            if (p > rowp[I] && col[p - 1] >= J) return XDCG_INVALID_ARG;
-            if (J == I) diag = true;
-            if (vptr[p + 1] - vptr[p] != (long long)(dof[I + 1] - dof[I]) * (dof[J + 1] - dof[J]))
-                return XDCG_INVALID_ARG;
+    std::atomic<bool> badInput{false};
+    parallel_for(N, [&](long long i0, long long i1) {
+        for (long long I = i0; I < i1 && !badInput; ++I) {
+            bool diag = false;
+            for (long long p = rowp[I]; p < rowp[I + 1]; ++p) {
+                const int J = col[p];
+                if (J < 0 || J >= N || (p > rowp[I] && col[p - 1] >= J) ||
+                    vptr[p + 1] - vptr[p] !=
+                        (long long)(dof[I + 1] - dof[I]) * (dof[J + 1] - dof[J])) {
+                    badInput = true;
+                    break;
+                }
+                if (J == I) diag = true;
+            }
+            if (!diag) badInput = true;
         }
-        if (!diag) return XDCG_INVALID_ARG;
+    });
+    if (badInput) return XDCG_INVALID_ARG;
+    // values: read in place from host memory, fetched from device memory
+    const long long nval = vptr[nnzb];
+    const double *valp = nullptr;
+    if (K->mem == XDCG_DEVICE) {
+        if (!fetch(val, K->val, nval, K->mem)) return XDCG_INVALID_ARG;
+        valp = val.data();
+    } else {
+        if (nval > 0 && !K->val) return XDCG_INVALID_ARG;
+        valp = K->val;
     }
-    if (!fetch(val, K->val, vptr[nnzb], K->mem)) return XDCG_INVALID_ARG;
-    double vmax = 0.0;
-    for (double v : val) {
-        if (!std::isfinite(v)) return XDCG_INVALID_ARG;
-        vmax = std::max(vmax, std::fabs(v));
-    }
+    std::vector<double> vmaxPart(16, 0.0);
+    std::atomic<int> piece{0};
+    parallel_for(nval, [&](long long i0, long long i1) {
+        double m = 0.0;
+        for (long long i = i0; i < i1; ++i) {
+            const double v = valp[i];
+            if (!std::isfinite(v)) {
+                badInput = true;
+                return;
+            }
+            m = std::max(m, std::fabs(v));
+        }
+        vmaxPart[piece++] = m;
+    });
+    if (badInput) return XDCG_INVALID_ARG;
+    const double vmax = *std::max_element(vmaxPart.begin(), vmaxPart.end());
     // symmetry of pattern and values
-    for (int I = 0; I < N; ++I) {
-        const int bI = dof[I + 1] - dof[I];
-        for (long long p = rowp[I]; p < rowp[I + 1]; ++p) {
-            const int J = col[p];
-            if (J < I) continue;
-            const int bJ = dof[J + 1] - dof[J];
-            const int *beg = &col[rowp[J]], *end = &col[0] + rowp[J + 1];
-            const int *it = std::lower_bound(beg, end, I);
-            if (it == end || *it != I) return XDCG_INVALID_ARG;
-            const long long q = rowp[J] + (it - beg);
-            for (int a = 0; a < bI; ++a)
-                for (int b2 = 0; b2 < bJ; ++b2)
-                    if (std::fabs(val[vptr[p] + a * bJ + b2] - val[vptr[q] + b2 * bI + a]) >
-                        1e-12 * vmax)
-                        return XDCG_INVALID_ARG;
+    parallel_for(N, [&](long long i0, long long i1) {
+        for (long long I = i0; I < i1 && !badInput; ++I) {
+            const int bI = dof[I + 1] - dof[I];
+            for (long long p = rowp[I]; p < rowp[I + 1]; ++p) {
+                const int J = col[p];
+                if (J < I) continue;
+                const int bJ = dof[J + 1] - dof[J];
+                const int *beg = &col[rowp[J]], *end = &col[0] + rowp[J + 1];
+                const int *it = std::lower_bound(beg, end, (int)I);
+                if (it == end || *it != I) {
+                    badInput = true;
+                    return;
+                }
+                const long long q = rowp[J] + (it - beg);
+                for (int a = 0; a < bI; ++a)
+                    for (int b2 = 0; b2 < bJ; ++b2)
+                        if (std::fabs(valp[vptr[p] + a * bJ + b2] - valp[vptr[q] + b2 * bI + a]) >
+                            1e-12 * vmax) {
+                            badInput = true;
+                            return;
+                        }
+            }
         }
-    }
+    });
+    if (badInput) return XDCG_INVALID_ARG;
     // deflation description
     const int S = Zd->n_sub;
     if (S <= 0) return XDCG_INVALID_ARG;
@@ -1097,6 +1166,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         }
     }
 
+    if (!mark(0)) return XDCG_CUDA_ERROR;   // validation
     // ---- chunk rows: S (pure standard) and X (the rest)
     std::vector<int> kindb(N);
     for (int I = 0; I < N; ++I) kindb[I] = dof[I + 1] - dof[I];
@@ -1117,11 +1187,16 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         pure[I] = ok;
     }
     std::vector<int> rowLen(nChunks, 0);
+    parallel_for(nChunks, [&](long long r0, long long r1) {
+        for (long long r = r0; r < r1; ++r) {
+            const int I = rowNode[r];
+            int len = 0;
+            for (long long p = rowp[I]; p < rowp[I + 1]; ++p) len += kindb[col[p]] / 3;
+            rowLen[r] = len;
+        }
+    });
     for (long long r = 0; r < nChunks; ++r) {
         const int I = rowNode[r];
-        int len = 0;
-        for (long long p = rowp[I]; p < rowp[I + 1]; ++p) len += kindb[col[p]] / 3;
-        rowLen[r] = len;
         if (pure[I] && rowPart[r] == 0)
             sRows.push_back((int)r);
         else
@@ -1175,10 +1250,14 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
             H.slicePtr[sl + 1] = H.slicePtr[sl] + 32LL * std::max(1, (mx + tpr - 1) / tpr);
         }
         const long long slots = std::max<long long>(H.slicePtr[H.nSlices], 1);
-        H.col.assign(slots, 0);
-        H.src.assign(9 * (size_t)slots, -1);
-        for (int sl = 0; sl < H.nSlices; ++sl) {
+        H.col.resize(slots);
+        H.src.resize(9 * (size_t)slots);
+        // slices write disjoint ranges of col, src and len
+        parallel_for(H.nSlices, [&](long long sl0, long long sl1) {
+          for (long long sl = sl0; sl < sl1; ++sl) {
             const long long base = H.slicePtr[sl];
+            std::fill(H.col.begin() + base, H.col.begin() + H.slicePtr[sl + 1], 0);
+            std::fill(H.src.begin() + 9 * base, H.src.begin() + 9 * H.slicePtr[sl + 1], -1);
             const long long steps = (H.slicePtr[sl + 1] - base) / 32;
             auto cidx = [&](long long st2, int lane) { return base + st2 * 32 + lane; };
             auto vidx = [&](long long st2, int e, int lane) {
@@ -1197,6 +1276,11 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
                     for (int e = 0; e < 9; ++e) H.src[vidx(st2, e, lane)] = blk[e];
                 });
             }
+          }
+        });
+        if (H.nSlices == 0) {
+            H.col[0] = 0;
+            std::fill(H.src.begin(), H.src.end(), -1);
         }
     };
     SellHost HS, HX;
@@ -1223,8 +1307,46 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
                 if (col[p] == I) pd = p;
             for (int e = 0; e < B * B; ++e)
                 Dsoa[t][(size_t)e * cnt + i] =
-                    (pointJacobi && e / B != e % B) ? 0.0 : val[vptr[pd] + e];
+                    (pointJacobi && e / B != e % B) ? 0.0 : valp[vptr[pd] + e];
         }
+    }
+    // each node's block as factored, for a later update of this context
+    c->hostKind.assign(kindb.begin(), kindb.end());
+    c->hostListPos.assign(N, 0);
+    c->hostDiagOff.assign(N + 1, 0);
+    for (int I = 0; I < N; ++I) c->hostDiagOff[I + 1] = c->hostDiagOff[I] + (long long)kindb[I] * kindb[I];
+    c->hostDiag.resize((size_t)c->hostDiagOff[N]);
+    for (int t = 0; t < 3; ++t) {
+        const int B = Bsz[t], cnt = (int)lists[t].size();
+        for (int i = 0; i < cnt; ++i) {
+            const int I = lists[t][i];
+            c->hostListPos[I] = i;
+            for (int e = 0; e < B * B; ++e)
+                c->hostDiag[c->hostDiagOff[I] + e] = Dsoa[t][(size_t)e * cnt + i];
+        }
+    }
+    // an update reuses the factor of every node whose kind and block are
+    // unchanged (bitwise) since the previous context
+    const bool reuse = prev && prev->nNodes == N && prev->opt.jacobi == c->opt.jacobi &&
+                       (int)prev->hostKind.size() == N;
+    std::vector<int> fresh[3], freshPos[3], keepSrc[3], keepDst[3];
+    for (int t = 0; t < 3; ++t) {
+        const int B = Bsz[t];
+        for (int i = 0; i < (int)lists[t].size(); ++i) {
+            const int I = lists[t][i];
+            const bool same =
+                reuse && prev->hostKind[I] == B &&
+                std::memcmp(&prev->hostDiag[prev->hostDiagOff[I]], &c->hostDiag[c->hostDiagOff[I]],
+                            sizeof(double) * B * B) == 0;
+            if (same) {
+                keepSrc[t].push_back(prev->hostListPos[I]);
+                keepDst[t].push_back(i);
+            } else {
+                fresh[t].push_back(I);
+                freshPos[t].push_back(i);
+            }
+        }
+        c->reusedFactors += (int)keepSrc[t].size();
     }
 
     // ---- boxes: own nodes, enriched-mode decision, coarse columns, W entries
@@ -1291,6 +1413,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     const long long nW = wOff.back();
     wOff.pop_back();
 
+    if (!mark(1)) return XDCG_CUDA_ERROR;   // host layout
     // ---- upload and set-up kernels
     cudaStream_t st = c->st;
     c->mixed = c->opt.precision == XDCG_MIXED;
@@ -1314,7 +1437,9 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     kin.rowPtr = upload_tmp(c, rowp);
     kin.col = upload_tmp(c, col);
     kin.valPtr = upload_tmp(c, vptr);
-    double *d_val = upload_tmp(c, val);
+    double *d_val = dalloc_tmp<double>(c, (size_t)nval);
+    if (d_val && nval > 0)
+        CK(cudaMemcpyAsync(d_val, valp, (size_t)nval * sizeof(double), cudaMemcpyHostToDevice, st));
     kin.val = d_val;
     if (!kin.rowPtr || !kin.col || !kin.valPtr || !kin.val) return XDCG_OOM;
     // SpMV layouts: values gathered on the device through the index maps
@@ -1367,6 +1492,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     A.warpSlice = partition(HS, HX, A.grid);
     if (!A.warpSlice) return XDCG_OOM;
 
+    if (!mark(2)) return XDCG_CUDA_ERROR;   // uploads, SpMV values
     // node data and block factors (FP64)
     // failure slots: [0] node block (node), [1] coarse pivot, [2] caller block
     int *d_bad = dalloc<int>(c, 3);
@@ -1393,8 +1519,32 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         const int B = Bsz[t], cnt = (int)lists[t].size();
         dl[t] = upload(c, lists[t]);
         L64[t] = dalloc<double>(c, (size_t)B * (B + 1) / 2 * std::max(cnt, 1));
+        if (!dl[t] || !L64[t]) return XDCG_OOM;
+        if (reuse) {
+            // carried-over factors, then only the changed nodes factored
+            const int nf = (int)fresh[t].size(), nk = (int)keepSrc[t].size();
+            const double *Lprev = t == 0 ? prev->L64.N.Lstd : (t == 1 ? prev->L64.N.Lh : prev->L64.N.Lt);
+            const int prevCnt = t == 0 ? prev->L64.N.nStd : (t == 1 ? prev->L64.N.nH : prev->L64.N.nT);
+            if (nk > 0) {
+                int *d_src = upload_tmp(c, keepSrc[t]), *d_dst = upload_tmp(c, keepDst[t]);
+                if (!d_src || !d_dst) return XDCG_OOM;
+                launch_copy_factors(nk, B * (B + 1) / 2, d_src, d_dst, Lprev, prevCnt, L64[t], cnt,
+                                    st);
+            }
+            if (nf > 0) {
+                std::vector<double> Df((size_t)B * B * nf);
+                for (int j = 0; j < nf; ++j)
+                    for (int e = 0; e < B * B; ++e)
+                        Df[(size_t)e * nf + j] = Dsoa[t][(size_t)e * cnt + freshPos[t][j]];
+                int *d_nodes = upload_tmp(c, fresh[t]), *d_pos = upload_tmp(c, freshPos[t]);
+                double *d_D = upload_tmp(c, Df);
+                if (!d_nodes || !d_pos || !d_D) return XDCG_OOM;
+                launch_block_cholesky(B, nf, d_nodes, d_D, L64[t], nullptr, d_bad, st, d_pos, cnt);
+            }
+            continue;
+        }
         double *d_D = upload_tmp(c, Dsoa[t]);
-        if (!dl[t] || !L64[t] || !d_D) return XDCG_OOM;
+        if (!d_D) return XDCG_OOM;
         launch_block_cholesky(B, cnt, dl[t], d_D, L64[t], nullptr, d_bad, st);
     }
     N64.stdNodes = dl[0]; N64.hNodes = dl[1]; N64.tNodes = dl[2];
@@ -1485,11 +1635,31 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     launch_symmetrize(c->Einv, k, st);
     CK(cudaMemcpyAsync(c->E, c->Einv, (size_t)k * k * sizeof(double), cudaMemcpyDeviceToDevice,
                        st));
-    // E^-1 in place (pivots relative to E's largest diagonal entry)
+    if (!mark(3)) return XDCG_CUDA_ERROR;   // node factors, W, E
+    // E^-1 in place (pivots relative to E's largest diagonal entry); an update
+    // whose E is unchanged (bitwise) takes the previous context's inverse
     {
-        xdcg_status es = dense_inverse(c, c->Einv, {k}, {0LL}, d_bad + 1, 0);
-        if (es != XDCG_OK) return es;
+        bool same = false;
+        if (prev && prev->k == k && prev->E) {
+            int *d_differ = dalloc_tmp<int>(c, 1);
+            if (!d_differ) return XDCG_OOM;
+            CK(cudaMemsetAsync(d_differ, 0, sizeof(int), st));
+            launch_differ(c->E, prev->E, (long long)k * k, d_differ, st);
+            int h = 1;
+            CK(cudaMemcpyAsync(&h, d_differ, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            same = h == 0;
+        }
+        if (same) {
+            CK(cudaMemcpyAsync(c->Einv, prev->Einv, (size_t)k * k * sizeof(double),
+                               cudaMemcpyDeviceToDevice, st));
+            c->reusedCoarse = 1;
+        } else {
+            xdcg_status es = dense_inverse(c, c->Einv, {k}, {0LL}, d_bad + 1, 0);
+            if (es != XDCG_OK) return es;
+        }
     }
+    if (!mark(4)) return XDCG_CUDA_ERROR;   // E^-1
 
     // block-scaled FP32 level of the mixed path: K~ = L^-1 K L^-T, Z~ = L^T Z, W~ = L^-1 W
     if (mixed) {
@@ -1513,7 +1683,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         for (int I = 0; I < N; ++I)
             for (long long p = rowp[I]; p < rowp[I + 1]; ++p) blockRow[p] = I;
         int *d_brow = upload_tmp(c, blockRow);
-        double *d_Kt = dalloc_tmp<double>(c, val.size());
+        double *d_Kt = dalloc_tmp<double>(c, (size_t)nval);
         std::vector<long long> zOff(N + 1, 0);   // explicit Z~ blocks in slot order
         for (int t = 0; t < N; ++t)
             zOff[t + 1] = zOff[t] + (long long)ownB[t] * (menr[ownSub[t]] ? 12 : 6);
@@ -1557,7 +1727,8 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         A2.S.val = v32S;
         A2.X.val = v32X;
         c->L32.F = F;
-        CK(cudaMemcpyAsync(d_Kt, d_val, val.size() * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(d_Kt, d_val, (size_t)nval * sizeof(double), cudaMemcpyDeviceToDevice,
+                           st));
         launch_scale_blocks(kin, d_brow, nnzb, F, d_Kt, st);
         launch_gather(d_src32S, (long long)HS32.src.size(), d_Kt, nullptr, v32S, st);
         launch_gather(d_src32X, (long long)HX32.src.size(), d_Kt, nullptr, v32X, st);
@@ -1673,6 +1844,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         c->L32.dofStart64 = d_dof;
         c->L32.dofStart32 = d_dof32;
     }
+    if (!mark(5)) return XDCG_CUDA_ERROR;   // FP32 level
     // ---- caller blocks: K's diagonal blocks gathered densely and inverted in
     // FP64; for MIXED also L_b^T (K_bb)^-1 L_b in FP32 (the blocks of the
     // block-scaled system's M~^-1)
@@ -1759,6 +1931,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         c->userBlocks = true;
     }
 
+    if (!mark(6)) return XDCG_CUDA_ERROR;   // caller blocks
     int hbad[3];
     CK(cudaMemcpyAsync(hbad, d_bad, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -1812,7 +1985,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     CK(cudaMemsetAsync(c->aux, 0, sizeof(Scalars), st));
     if (cudaMallocHost(&c->h_sc, sizeof(Scalars)) != cudaSuccess) return XDCG_OOM;
     if (cudaMallocHost(&c->h_done, 2 * sizeof(int)) != cudaSuccess) return XDCG_OOM;
-    if (cudaMallocHost(&c->h_rr, 2 * sizeof(double)) != cudaSuccess) return XDCG_OOM;
+    if (cudaMallocHost(&c->h_poll, 2 * sizeof(Scalars)) != cudaSuccess) return XDCG_OOM;
     CK(cudaEventCreate(&c->ev0));
     CK(cudaEventCreate(&c->ev1));
     CK(cudaEventCreateWithFlags(&c->evb[0], cudaEventDisableTiming));
@@ -1867,6 +2040,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     c->info.spmv_alg_bytes_fp64 = spmv_alg(8);
     c->info.spmv_alg_bytes_fp32 = spmv_alg(4);
     c->info.block_entries = c->blkEntries;
+    if (!mark(7)) return XDCG_CUDA_ERROR;   // work vectors, scalar blocks
     return XDCG_OK;
 }
 
@@ -1890,10 +2064,10 @@ xdcg_status xdcg_default_options(xdcg_options *opt) {
     return XDCG_OK;
 }
 
-xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflation *Z,
-                       const xdcg_blocks *blocks, const xdcg_options *opt, void *stream,
-                       int32_t *bad_index) {
-    NvtxRange range("xdcg setup");
+static xdcg_status setup_common(xdcg_ctx **out, const xdcg_ctx *prev, const xdcg_matrix *K,
+                         const xdcg_deflation *Z, const xdcg_blocks *blocks,
+                         const xdcg_options *opt, void *stream, int32_t *bad_index) {
+    NvtxRange range(prev ? "xdcg setup update" : "xdcg setup");
     if (bad_index) *bad_index = -1;
     if (!out) return XDCG_INVALID_ARG;
     *out = nullptr;
@@ -1920,7 +2094,7 @@ xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflatio
     if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return XDCG_CUDA_ERROR; }
     const auto t0 = std::chrono::steady_clock::now();
     int bad = -1;
-    xdcg_status s = setup_impl(c, K, Z, blocks, &bad);
+    xdcg_status s = setup_impl(c, K, Z, blocks, &bad, prev);
     if (bad_index) *bad_index = bad;
     if (s != XDCG_OK) {
         cudaStreamSynchronize(c->st);
@@ -1929,8 +2103,29 @@ xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflatio
     }
     c->info.t_setup_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    c->info.reused_node_factors = c->reusedFactors;
+    c->info.reused_coarse_inverse = c->reusedCoarse;
     *out = c;
     return XDCG_OK;
+}
+
+xdcg_status xdcg_setup(xdcg_ctx **out, const xdcg_matrix *K, const xdcg_deflation *Z,
+                       const xdcg_blocks *blocks, const xdcg_options *opt, void *stream,
+                       int32_t *bad_index) {
+    return setup_common(out, nullptr, K, Z, blocks, opt, stream, bad_index);
+}
+
+xdcg_status xdcg_setup_update(xdcg_ctx **out, const xdcg_ctx *prev, const xdcg_matrix *K,
+                              const xdcg_deflation *Z, const xdcg_blocks *blocks,
+                              const xdcg_options *opt, void *stream, int32_t *bad_index) {
+    if (!prev) {
+        if (bad_index) *bad_index = -1;
+        if (out) *out = nullptr;
+        return XDCG_INVALID_ARG;
+    }
+    // the previous context's device arrays are read on this call's stream
+    if (cudaStreamSynchronize(prev->st) != cudaSuccess) return XDCG_CUDA_ERROR;
+    return setup_common(out, prev, K, Z, blocks, opt, stream, bad_index);
 }
 
 xdcg_status xdcg_solve(xdcg_ctx *c, const double *f, double *u, double tol, xdcg_result *res) {

@@ -273,7 +273,8 @@ constexpr int kRowThreads = 256;
 // extEnd) of one box (most boxes are one unit).  acc[0..M): Z~^T r over its
 // own rows, acc[M..2M): W~^T r over its coupled rows, acc[2M]: ||r||^2;
 // returns (in thread 0) the unit's ||r||^2 after one block reduction.
-template <int M>
+// YV (caller blocks, mode 3): the coupled rows take W~^T of y = M~^-1 r
+template <int M, bool YV>
 __device__ __forceinline__ float restrict_update_unit(const RowBoxDev &B, int unit, float *u,
                                                       const float *r_cur, float *r_next,
                                                       const float *p, const float *q,
@@ -307,12 +308,10 @@ __device__ __forceinline__ float restrict_update_unit(const RowBoxDev &B, int un
         const int r0 = B.extRowPtr[s], R = B.extRowPtr[s + 1] - r0;
         const float *W = B.W + B.wBase[s];
         const int re = B.unitExtEnd[unit];
-        // coupled rows take W~^T of y = M~^-1 r (mode 3) or of r itself
-        const float *rv = (mode == 3) ? yv : r_cur;
 #pragma unroll 4
         for (int r = B.unitExtBegin[unit] + threadIdx.x; r < re; r += blockDim.x) {
             const int d = ld_keep(B.extRowDof + r, keep);
-            const float rn = (mode == 0) ? fmaf(-alpha, q[d], rv[d]) : rv[d];
+            const float rn = YV ? yv[d] : ((mode == 0) ? fmaf(-alpha, q[d], r_cur[d]) : r_cur[d]);
             const int rl = r - r0;
 #pragma unroll
             for (int c = 0; c < M; ++c)
@@ -365,6 +364,7 @@ __device__ __forceinline__ float restrict_update_unit(const RowBoxDev &B, int un
     return acc[2 * M];
 }
 
+template <bool YV>
 __global__ void __launch_bounds__(kRowThreads)
 k_restrict_update(RowBoxDev B, float *u, const float *r_cur, float *r_next, const float *p,
                   const float *q, const float *yv, int mode, double *g, double *zr,
@@ -375,9 +375,9 @@ k_restrict_update(RowBoxDev B, float *u, const float *r_cur, float *r_next, cons
     const float alpha = (mode == 0) ? (float)sc->alpha : 0.0f;
     float rr;
     if (B.menr[B.unitBox[unit]])
-        rr = restrict_update_unit<12>(B, unit, u, r_cur, r_next, p, q, yv, mode, alpha, g, zr);
+        rr = restrict_update_unit<12, YV>(B, unit, u, r_cur, r_next, p, q, yv, mode, alpha, g, zr);
     else
-        rr = restrict_update_unit<6>(B, unit, u, r_cur, r_next, p, q, yv, mode, alpha, g, zr);
+        rr = restrict_update_unit<6, YV>(B, unit, u, r_cur, r_next, p, q, yv, mode, alpha, g, zr);
     if (mode >= 2) return;
     double tot;
     if (grid_sum_t0((double)rr, partials, &sc->ticket[2], tot) && threadIdx.x == 0) {
@@ -395,8 +395,8 @@ k_restrict_update(RowBoxDev B, float *u, const float *r_cur, float *r_next, cons
 void launch_restrict_update(const RowBoxDev &B, float *u, const float *r_cur, float *r_next,
                             const float *p, const float *q, int mode, double *g, double *zr,
                             double *partials, Scalars *sc, cudaStream_t st, const float *y) {
-    launch_pdl(k_restrict_update, B.nUnits, kRowThreads, 0, st, B, u, r_cur, r_next, p, q, y, mode,
-               g, zr, partials, sc);
+    launch_pdl(mode == 3 ? k_restrict_update<true> : k_restrict_update<false>, B.nUnits,
+               kRowThreads, 0, st, B, u, r_cur, r_next, p, q, y, mode, g, zr, partials, sc);
 }
 
 template <int M>

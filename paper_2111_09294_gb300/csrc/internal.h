@@ -319,8 +319,14 @@ void launch_update_plain(T *u, T *r, const T *p, const T *q, long long n, int mo
                          double *partials, Scalars *sc, cudaStream_t st);
 
 
+// pos (optional): node t of the list is written to position pos[t] of a list
+// of total nodes (default: position t of count)
 int launch_block_cholesky(int B, int count, const int *nodes, const double *Dsoa, double *L64,
-                          float *L32, int *bad, cudaStream_t st);
+                          float *L32, int *bad, cudaStream_t st, const int *pos = nullptr,
+                          int total = 0);
+void launch_copy_factors(int count, int ents, const int *src, const int *dst, const double *prev,
+                         int prevTotal, double *L, int total, cudaStream_t st);
+void launch_differ(const double *a, const double *b, long long n, int *differ, cudaStream_t st);
 void launch_xrel(int nNodes, const double *coords, const double *centre, const int *sub,
                  double *x64, float *x32, cudaStream_t st);
 void launch_build_W(const KinDev &K, int nExt, const int *extBox, const int *extNode,

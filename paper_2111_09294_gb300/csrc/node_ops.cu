@@ -153,11 +153,14 @@ template void launch_update<float>(const NodeDev<float> &, float *, float *, con
 
 // ---- set-up: node-block Cholesky (FP64) ------------------------------------
 
+// Node t of the list (count nodes) factored into position pos[t] of a list
+// of total entries (pos == nullptr: t itself, total = count).
 template <int B>
 __global__ void k_block_cholesky(int count, const int *nodes, const double *__restrict__ D,
-                                 double *L64, float *L32, int *bad) {
+                                 double *L64, float *L32, int *bad, const int *pos, int total) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= count) return;
+    const int w = pos ? pos[t] : t;
     double a[B * (B + 1) / 2];
     double dmax = 0.0;
 #pragma unroll
@@ -189,23 +192,66 @@ __global__ void k_block_cholesky(int count, const int *nodes, const double *__re
 #pragma unroll
         for (int j = 0; j <= i; ++j) {
             const double v = (i == j) ? 1.0 / a[tri(i, i)] : a[tri(i, j)];
-            L64[(size_t)tri(i, j) * count + t] = v;
-            if (L32) L32[(size_t)tri(i, j) * count + t] = (float)v;
+            L64[(size_t)tri(i, j) * total + w] = v;
+            if (L32) L32[(size_t)tri(i, j) * total + w] = (float)v;
         }
     }
 }
 
 int launch_block_cholesky(int B, int count, const int *nodes, const double *Dsoa, double *L64,
-                          float *L32, int *bad, cudaStream_t st) {
+                          float *L32, int *bad, cudaStream_t st, const int *pos, int total) {
     if (count == 0) return 0;
+    if (!pos) total = count;
     const int th = 128, grid = cdiv(count, th);
     switch (B) {
-        case 3: k_block_cholesky<3><<<grid, th, 0, st>>>(count, nodes, Dsoa, L64, L32, bad); break;
-        case 6: k_block_cholesky<6><<<grid, th, 0, st>>>(count, nodes, Dsoa, L64, L32, bad); break;
-        case 15: k_block_cholesky<15><<<grid, th, 0, st>>>(count, nodes, Dsoa, L64, L32, bad); break;
+        case 3:
+            k_block_cholesky<3><<<grid, th, 0, st>>>(count, nodes, Dsoa, L64, L32, bad, pos, total);
+            break;
+        case 6:
+            k_block_cholesky<6><<<grid, th, 0, st>>>(count, nodes, Dsoa, L64, L32, bad, pos, total);
+            break;
+        case 15:
+            k_block_cholesky<15><<<grid, th, 0, st>>>(count, nodes, Dsoa, L64, L32, bad, pos, total);
+            break;
         default: return -1;
     }
     return 0;
+}
+
+// Factors carried over from an earlier context: entry e of position dst[i]
+// (list of total entries) = entry e of position src[i] of the earlier list
+// (prevTotal entries); ents = B (B + 1) / 2 entries per node.
+__global__ void k_copy_factors(int count, int ents, const int *src, const int *dst,
+                               const double *prev, int prevTotal, double *L, int total) {
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)count * ents) return;
+    const int i = (int)(idx % count), e = (int)(idx / count);
+    L[(size_t)e * total + dst[i]] = prev[(size_t)e * prevTotal + src[i]];
+}
+
+void launch_copy_factors(int count, int ents, const int *src, const int *dst, const double *prev,
+                         int prevTotal, double *L, int total, cudaStream_t st) {
+    if (count == 0) return;
+    const long long n = (long long)count * ents;
+    k_copy_factors<<<(int)((n + 255) / 256), 256, 0, st>>>(count, ents, src, dst, prev, prevTotal, L,
+                                                          total);
+}
+
+// *differ = 1 if a and b (n doubles) differ anywhere (bitwise)
+__global__ void k_differ(const double *a, const double *b, long long n, int *differ) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        if (__double_as_longlong(a[i]) != __double_as_longlong(b[i])) {
+            *differ = 1;
+            return;
+        }
+}
+
+void launch_differ(const double *a, const double *b, long long n, int *differ, cudaStream_t st) {
+    if (n <= 0) return;
+    const long long g = (n + 255) / 256;
+    k_differ<<<(int)(g < 4LL * device_sm_count() ? g : 4LL * device_sm_count()), 256, 0, st>>>(
+        a, b, n, differ);
 }
 
 __global__ void k_xrel(int n, const double *coords, const double *centre, const int *sub,

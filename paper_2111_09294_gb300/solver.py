@@ -68,14 +68,16 @@ class Solver:
     (whole nodes each; xdcg_blocks), e.g. one per subdomain of a problem
     numbered subdomain by subdomain.  z_cols, z_values: Z by value instead of
     from the geometry (xdcg_deflation's valued form: 6 or 12 columns per box,
-    node I's b_I x z_cols[sub[I]] block row-major, nodes in order).
+    node I's b_I x z_cols[sub[I]] block row-major, nodes in order).  prev: a
+    Solver of the same mesh for the previous crack front, whose unchanged
+    parts are carried over (xdcg_setup_update).
     """
 
     def __init__(self, dof_ptr, row_ptr, col, val_ptr, val, sub_of_node, coords, hsign, centres,
                  precision="fp64", tol=1e-8, max_iter=10000, inner_tol=1e-3, max_outer=30,
                  time_spmv=False, enriched_modes=True, stream=None, jacobi="block",
                  record_history=False, max_batch=0, coarse_fp64=False, wait_s=2.0,
-                 blocks=None, z_cols=None, z_values=None):
+                 blocks=None, z_cols=None, z_values=None, prev=None):
         lib = L.load()
         self._lib = lib
         self.ctx = ctypes.c_void_p()
@@ -118,9 +120,16 @@ class Solver:
             keep.append(bp)
             blk = ctypes.byref(L.Blocks(bp.size - 1, bp.ctypes.data, L.XDCG_HOST))
         bad = ctypes.c_int32(-1)
-        st = lib.xdcg_setup(ctypes.byref(self.ctx), ctypes.byref(m), ctypes.byref(z), blk,
-                            ctypes.byref(opt), ctypes.c_void_p(stream.cuda_stream),
-                            ctypes.byref(bad))
+        if prev is not None:
+            # the next crack front of prev's mesh: unchanged node factors and an
+            # unchanged E^-1 are carried over (xdcg_setup_update)
+            st = lib.xdcg_setup_update(ctypes.byref(self.ctx), prev.ctx, ctypes.byref(m),
+                                       ctypes.byref(z), blk, ctypes.byref(opt),
+                                       ctypes.c_void_p(stream.cuda_stream), ctypes.byref(bad))
+        else:
+            st = lib.xdcg_setup(ctypes.byref(self.ctx), ctypes.byref(m), ctypes.byref(z), blk,
+                                ctypes.byref(opt), ctypes.c_void_p(stream.cuda_stream),
+                                ctypes.byref(bad))
         L.check(st, "xdcg_setup", bad.value)
         info = L.Info()
         L.check(lib.xdcg_get_info(self.ctx, ctypes.byref(info)), "xdcg_get_info")

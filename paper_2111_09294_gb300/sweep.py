@@ -46,3 +46,30 @@ def solve_systems(solvers, loads, tol, outs=None, concurrent=True, raise_on_erro
         return [run(i) for i in range(len(solvers))]
     with cf.ThreadPoolExecutor(len(solvers)) as ex:
         return list(ex.map(run, range(len(solvers))))
+
+
+def transfer_index(dof_prev, kind_prev, dof_next, kind_next):
+    """Dof maps (src, dst) that carry a solution of one crack front's system
+    into the numbering of the next front's system on the same nodes: each
+    node's standard dofs, and its enriched dofs where the node keeps its
+    enrichment; every other dof of the next system starts at 0."""
+    import numpy as np
+    dp, dn = np.asarray(dof_prev, np.int64), np.asarray(dof_next, np.int64)
+    kp, kn = np.asarray(kind_prev), np.asarray(kind_next)
+    if dp.size != dn.size:
+        raise ValueError("the two systems must share their nodes")
+    bp, bn = np.diff(dp), np.diff(dn)
+    width = np.where(kp == kn, np.minimum(bp, bn), 3)
+    src = np.concatenate([dp[:-1][width >= w] + w - 1 for w in range(1, 16)] or [[]])
+    dst = np.concatenate([dn[:-1][width >= w] + w - 1 for w in range(1, 16)] or [[]])
+    return src.astype(np.int64), dst.astype(np.int64)
+
+
+def transfer_guess(u_prev, maps, n_next):
+    """The previous front's solution in the next system's numbering (a warm
+    start, u_-1 of Algorithm 2, for xdcg_solve_x0)."""
+    src, dst = maps
+    out = torch.zeros(n_next, dtype=u_prev.dtype, device=u_prev.device)
+    out[torch.as_tensor(dst, device=u_prev.device)] = u_prev[torch.as_tensor(src,
+                                                                             device=u_prev.device)]
+    return out

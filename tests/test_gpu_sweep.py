@@ -39,3 +39,57 @@ def test_sweep_concurrent_matches_sequential_and_oracle():
         assert err <= 1e-7, (j, err)
     for s in solvers:
         s.close()
+
+
+def test_update_for_next_front_matches_fresh_setup():
+    # the context for the next crack front built from the previous one
+    # (xdcg_setup_update): the node factors the front left unchanged are
+    # carried over, the rest factored; results bit for bit those of a fresh
+    # set-up.  The same system again carries over every factor and E^-1.
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2111_09294_gb300 import Solver
+    P0, P1 = X.make_many(X.SWEEP[:2])
+    f1 = torch.tensor(P1.f, device="cuda:0")
+    for prec in ("fp64", "mixed"):
+        s0 = Solver.from_problem(P0, precision=prec)
+        fresh = Solver.from_problem(P1, precision=prec)
+        upd = Solver.from_problem(P1, precision=prec, prev=s0)
+        assert 0 < upd.info["reused_node_factors"] < P1.n_nodes
+        assert np.array_equal(upd.coarse_matrix(), fresh.coarse_matrix())
+        ua, ia = fresh.solve(f1, tol=1e-8)
+        ub, ib = upd.solve(f1, tol=1e-8)
+        assert torch.equal(ua, ub) and ia["iterations"] == ib["iterations"], prec
+        same = Solver.from_problem(P0, precision=prec, prev=s0)
+        assert same.info["reused_node_factors"] == P0.n_nodes
+        assert same.info["reused_coarse_inverse"] == 1
+        f0 = torch.tensor(P0.f, device="cuda:0")
+        assert torch.equal(same.solve(f0, tol=1e-8)[0], s0.solve(f0, tol=1e-8)[0])
+        for s in (s0, fresh, upd, same):
+            s.close()
+
+
+def test_warm_start_from_previous_front():
+    # the previous front's solution carried into the next system's numbering
+    # (standard dofs, and enriched dofs of nodes that keep their enrichment)
+    # as u_-1 of Algorithm 2: the same answer as a cold start, in no more
+    # iterations
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2111_09294_gb300 import Solver
+    from paper_2111_09294_gb300.sweep import transfer_guess, transfer_index
+    P0, P1 = X.make_many(X.SWEEP[:2])
+    dev = torch.device("cuda:0")
+    s0 = Solver.from_problem(P0)
+    u0, _ = s0.solve(torch.tensor(P0.f, device=dev), tol=1e-10)
+    s1 = Solver.from_problem(P1, prev=s0)
+    f1 = torch.tensor(P1.f, device=dev)
+    cold, ic = s1.solve(f1, tol=1e-10)
+    guess = transfer_guess(u0, transfer_index(P0.dof_ptr, P0.kind, P1.dof_ptr, P1.kind), P1.n)
+    warm, iw = s1.solve(f1, tol=1e-10, x0=guess)
+    assert iw["rel_res_true"] <= 1.05e-10
+    assert float(torch.linalg.norm(warm - cold) / torch.linalg.norm(cold)) <= 1e-7
+    assert iw["iterations"] <= ic["iterations"], (iw["iterations"], ic["iterations"])
+    print(f"\nnext front, tol 1e-10: cold {ic['iterations']} iterations, warm {iw['iterations']}")
+    s0.close()
+    s1.close()
