@@ -286,12 +286,15 @@ def run_ours(args):
     # the solves timed for the value carry no events inside (events between
     # kernels would break their programmatic dependent launches); separate
     # solvers with CUDA events around every SpMV give the SpMV's own time
-    mixed = Solver.from_problem(P, precision="mixed", inner_tol=args.inner_tol)
-    fp64 = Solver.from_problem(P, precision="fp64")
+    # every SpMV pipeline shape timed at set-up on this matrix, the fastest kept
+    at = bool(args.autotune)
+    mixed = Solver.from_problem(P, precision="mixed", inner_tol=args.inner_tol, autotune=at)
+    fp64 = Solver.from_problem(P, precision="fp64", autotune=at)
     mixed_c64 = Solver.from_problem(P, precision="mixed", inner_tol=args.inner_tol,
-                                    coarse_fp64=True)
-    mixed_t = Solver.from_problem(P, precision="mixed", time_spmv=True, inner_tol=args.inner_tol)
-    fp64_t = Solver.from_problem(P, precision="fp64", time_spmv=True)
+                                    coarse_fp64=True, autotune=at)
+    mixed_t = Solver.from_problem(P, precision="mixed", time_spmv=True, inner_tol=args.inner_tol,
+                                  autotune=at)
+    fp64_t = Solver.from_problem(P, precision="fp64", time_spmv=True, autotune=at)
     f = torch.tensor(P.f, device=dev)
     u = torch.empty_like(f)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -674,6 +677,14 @@ def run_ours(args):
                               "note": "E^-1 applied in FP64 inside the FP32 iteration"},
         "rel_res_true_mixed": res_true, "rel_res_true_fp64": inf_fp64[-1]["rel_res_true"],
         "setup_ms": info["t_setup_ms"],
+        "setup_phases_ms": {k: round(v, 1) for k, v in info["t_setup_phase_ms"].items()},
+        "autotune": {"fp32_shape": info["spmv_shape_fp32"], "fp64_shape": fp64.info["spmv_shape_fp64"],
+                     "fp32_shape_us": [round(t, 1) for t in info["spmv_shape_us_fp32"] if t >= 0],
+                     "fp64_shape_us": [round(t, 1) for t in fp64.info["spmv_shape_us_fp64"]
+                                       if t >= 0],
+                     "timed_shape_fp32": mixed_t.info["spmv_shape_fp32"],
+                     "shapes": "FP32 (steps/stage, stages, blocks/SM): (2,3,3) (1,4,4) (2,4,2) "
+                               "(1,6,3) (3,3,2); FP64: (1,3,3) (1,4,2) (2,2,2) (1,2,4)"},
         "spmv_fp32_gbs": achieved, "spmv_fp64_gbs": achieved64,
         "kernel_us_per_iteration": phases,
         "batched_load_cases": batch,
@@ -760,6 +771,9 @@ def main():
                     help="internal: one timed FP64 oracle solve of --workload, printed as JSON "
                          "(run in a child process with a fixed BLAS thread count)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="time every SpMV pipeline shape at set-up and keep the fastest (0: "
+                         "default shape)")
     ap.add_argument("--chain-steps", type=int, default=0,
                     help="with --workload cube64_penny_lognormal: also time the compliance "
                          "over this many crack-front steps (u recomputed, not stored)")

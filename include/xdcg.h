@@ -165,6 +165,11 @@ typedef struct {
                                 XDCG_TIMEOUT after the copies in flight have landed (their own
                                 limit, 0.1 s, is fixed).  0 gives up at the first wait: it
                                 exists to exercise that status, not for use */
+    int32_t autotune;        /* 1: set-up times every compiled pipeline shape of the SpMV (steps
+                                per bulk-copy stage, stages per warp, blocks per SM) on this
+                                matrix and keeps the fastest (info.spmv_shape_*); a few ms.
+                                Default 0: the default shape.  Two contexts with different
+                                shapes may round the fused dot differently */
 } xdcg_options;
 
 typedef struct {
@@ -216,6 +221,12 @@ typedef struct {
                                     blocks; work vectors */
     int32_t reused_node_factors; /* xdcg_setup_update: node-block factors carried over */
     int32_t reused_coarse_inverse; /* xdcg_setup_update: 1 if E^-1 was carried over */
+    int32_t spmv_shape_fp64;     /* SpMV pipeline shape in use (0 = default; autotune) */
+    int32_t spmv_shape_fp32;
+    double spmv_shape_us_fp64[8]; /* autotune: median time of each shape's product, -1 untimed;
+                                    FP64 shapes (steps per stage, stages, blocks per SM):
+                                    (1,3,3) (1,4,2) (2,2,2) (1,2,4) */
+    double spmv_shape_us_fp32[8]; /* FP32 shapes: (2,3,3) (1,4,4) (2,4,2) (1,6,3) (3,3,2) */
 } xdcg_info_t;
 
 /* Fill *opt with the defaults listed above. */

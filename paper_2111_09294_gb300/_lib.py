@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
     _fields_ = [("tol", c_double), ("max_iter", c_int32), ("precision", c_int32),
                 ("inner_tol", c_double), ("max_outer", c_int32), ("time_spmv", c_int32),
                 ("jacobi", c_int32), ("record_history", c_int32), ("max_batch", c_int32),
-                ("coarse_fp64", c_int32), ("wait_s", c_double)]
+                ("coarse_fp64", c_int32), ("wait_s", c_double), ("autotune", c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -72,7 +72,9 @@ class Info(ctypes.Structure):
                 ("nnzb", c_int64), ("spmv_alg_bytes_fp64", c_int64),
                 ("spmv_alg_bytes_fp32", c_int64), ("block_entries", c_int64),
                 ("t_setup_phase_ms", c_double * 8), ("reused_node_factors", c_int32),
-                ("reused_coarse_inverse", c_int32)]
+                ("reused_coarse_inverse", c_int32), ("spmv_shape_fp64", c_int32),
+                ("spmv_shape_fp32", c_int32), ("spmv_shape_us_fp64", c_double * 8),
+                ("spmv_shape_us_fp32", c_double * 8)]
 
     PHASES = ("validate", "host_layout", "upload", "factors_W_E", "E_inverse", "fp32_level",
               "blocks", "work_vectors")
@@ -80,6 +82,8 @@ class Info(ctypes.Structure):
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["t_setup_phase_ms"] = dict(zip(self.PHASES, list(self.t_setup_phase_ms)))
+        d["spmv_shape_us_fp64"] = list(self.spmv_shape_us_fp64)
+        d["spmv_shape_us_fp32"] = list(self.spmv_shape_us_fp32)
         return d
 
 

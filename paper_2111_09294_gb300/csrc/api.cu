@@ -1487,10 +1487,68 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     };
     const unsigned long long waitNs = (unsigned long long)(c->opt.wait_s * 1e9);
     A.waitNs = waitNs;
-    A.grid = spmv_persistent_grid<double>(HS.nSlices + HX.nSlices);
+    A.shape = 0;
+    A.grid = spmv_persistent_grid<double>(HS.nSlices + HX.nSlices, 0);
     if (A.grid < 1) return XDCG_CUDA_ERROR;
     A.warpSlice = partition(HS, HX, A.grid);
     if (!A.warpSlice) return XDCG_OOM;
+    // The autotuner: every compiled pipeline shape of the SpMV (steps per
+    // bulk-copy stage, stages per warp, blocks per SM; each with its own
+    // persistent grid and step-balanced warp ranges) timed on this matrix,
+    // the fastest kept.  Two warm-up launches and five timed ones (CUDA
+    // events, median) per shape, x = 0 (the time does not depend on x).
+    auto autotune = [&](auto &Ad, const SellHost &PS, const SellHost &PX, auto zero, double *usOut,
+                        int32_t *pick) -> xdcg_status {
+        using T = decltype(zero);
+        const int nShapes = spmv_shape_count<T>();
+        T *x = dalloc_tmp<T>(c, n), *y = dalloc_tmp<T>(c, n);
+        double *parts = dalloc_tmp<double>(c, kMaxGrid);
+        Scalars *scT = dalloc_tmp<Scalars>(c, 1);
+        if (!x || !y || !parts || !scT) return XDCG_OOM;
+        CK(cudaMemsetAsync(x, 0, n * sizeof(T), st));
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        double best = 1e300;
+        SpmvDev<T> keep = Ad;
+        for (int sh = 0; sh < nShapes && sh < 8; ++sh) {
+            SpmvDev<T> cand = Ad;
+            cand.shape = sh;
+            cand.grid = spmv_persistent_grid<T>(PS.nSlices + PX.nSlices, sh);
+            usOut[sh] = -1.0;
+            if (cand.grid < 1 || cand.grid > kMaxGrid) continue;
+            cand.warpSlice = sh == Ad.shape ? Ad.warpSlice : partition(PS, PX, cand.grid);
+            if (!cand.warpSlice) return XDCG_OOM;
+            std::vector<float> t;
+            for (int rep = 0; rep < 7; ++rep) {
+                init_scalars(c, scT, -1.0, nullptr, INT_MAX);
+                CK(cudaEventRecord(e0, st));
+                launch_spmv<T>(cand, x, y, nullptr, 0, parts, scT, kFinStore, 0, st);
+                CK(cudaEventRecord(e1, st));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (rep >= 2) t.push_back(ms);
+            }
+            std::sort(t.begin(), t.end());
+            usOut[sh] = 1e3 * t[t.size() / 2];
+            if (usOut[sh] < best) {
+                best = usOut[sh];
+                keep = cand;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        Ad = keep;
+        *pick = keep.shape;
+        return XDCG_OK;
+    };
+    for (int sh = 0; sh < 8; ++sh) c->info.spmv_shape_us_fp64[sh] = c->info.spmv_shape_us_fp32[sh] = -1.0;
+    if (c->opt.autotune) {
+        xdcg_status ts = autotune(A, HS, HX, 0.0, c->info.spmv_shape_us_fp64,
+                                  &c->info.spmv_shape_fp64);
+        if (ts != XDCG_OK) return ts;
+    }
 
     if (!mark(2)) return XDCG_CUDA_ERROR;   // uploads, SpMV values
     // node data and block factors (FP64)
@@ -1733,10 +1791,16 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         launch_gather(d_src32S, (long long)HS32.src.size(), d_Kt, nullptr, v32S, st);
         launch_gather(d_src32X, (long long)HX32.src.size(), d_Kt, nullptr, v32X, st);
         A2.waitNs = waitNs;
-        A2.grid = spmv_persistent_grid<float>(HS32.nSlices + HX32.nSlices);
+        A2.shape = 0;
+        A2.grid = spmv_persistent_grid<float>(HS32.nSlices + HX32.nSlices, 0);
         if (A2.grid < 1) return XDCG_CUDA_ERROR;
         A2.warpSlice = partition(HS32, HX32, A2.grid);
         if (!A2.warpSlice) return XDCG_OOM;
+        if (c->opt.autotune) {
+            xdcg_status ts = autotune(A2, HS32, HX32, 0.0f, c->info.spmv_shape_us_fp32,
+                                      &c->info.spmv_shape_fp32);
+            if (ts != XDCG_OK) return ts;
+        }
         launch_build_Zt(N, d_own, d_dof, d_sub, d_x64, d_hs, d_menr, zv, F, d_zOff, d_Zt, st);
         launch_scale_W(nExt, d_extBox, d_extNode, d_wOff, d_menr, d_dof, F, d_W, d_Wt, st);
         // row-parallel layouts: own rows (Z~) and coupled rows (W~) of each box,
@@ -2061,6 +2125,7 @@ xdcg_status xdcg_default_options(xdcg_options *opt) {
     opt->max_batch = 0;
     opt->coarse_fp64 = 0;
     opt->wait_s = 2.0;
+    opt->autotune = 0;
     return XDCG_OK;
 }
 
@@ -2084,6 +2149,7 @@ static xdcg_status setup_common(xdcg_ctx **out, const xdcg_ctx *prev, const xdcg
         (c->opt.jacobi != XDCG_BLOCK_JACOBI && c->opt.jacobi != XDCG_POINT_JACOBI) ||
         c->opt.max_batch < 0 || c->opt.max_batch > kMaxBatch ||
         (c->opt.coarse_fp64 != 0 && c->opt.coarse_fp64 != 1) ||
+        (c->opt.autotune != 0 && c->opt.autotune != 1) ||
         !(c->opt.wait_s >= 0.0 && c->opt.wait_s <= 60.0) ||
         !(c->opt.inner_tol > 0 && c->opt.inner_tol < 1) ||
         (blocks && (c->opt.jacobi != XDCG_BLOCK_JACOBI || c->opt.max_batch > 0))) {

@@ -49,7 +49,7 @@ template <int MB, bool RES>
 __global__ void __launch_bounds__(kSpmvThreads)
 k_spmm(SpmvDev<float> A, int m, const float *__restrict__ x, float *__restrict__ y,
        const float *__restrict__ b, double *partials, BatchScalars *bs, int fin) {
-    constexpr int C = SpmvCfg<float>::C, NS = SpmvCfg<float>::NS, SB = stage_bytes<float>();
+    constexpr int C = SpmvCfg<float, 0>::C, NS = SpmvCfg<float, 0>::NS, SB = stage_bytes<float, 0>();
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *ring = smem + (size_t)warp * NS * SB;
@@ -239,13 +239,13 @@ template <int MB>
 void launch_spmm(const SpmvDev<float> &A, int m, const float *x, float *y, const float *b,
                  int residual_mode, double *partials, BatchScalars *bs, int fin,
                  cudaStream_t st) {
-    const int smem = spmv_smem_bytes<float>();
+    const int smem = spmv_smem_bytes<float, 0>();
     launch_pdl(residual_mode ? k_spmm<MB, true> : k_spmm<MB, false>, A.grid, kSpmvThreads, smem,
                st, A, m, x, y, b, partials, bs, fin);
 }
 
 bool spmm_prepare() {
-    const int smem = spmv_smem_bytes<float>();
+    const int smem = spmv_smem_bytes<float, 0>();
     return cudaFuncSetAttribute(k_spmm<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 smem) == cudaSuccess &&
            cudaFuncSetAttribute(k_spmm<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -91,6 +91,7 @@ struct BatchScalars {
 template <typename T>
 struct SpmvDev {
     SellDev<T> S, X;
+    int shape;                 // pipeline shape (spmv_cfg.cuh), 0 = default
     int grid;                  // persistent blocks (kSpmvThreads each)
     const int *warpSlice;      // [grid * kSpmvWarps + 1] slice range of each warp
                                // (S slices, then X slices offset by S.nSlices)
@@ -147,8 +148,12 @@ int device_sm_count();
 template <typename T>
 void launch_spmv(const SpmvDev<T> &A, const T *x, T *y, const T *b, int residual_mode,
                  double *partials, Scalars *sc, int fin, int slot, cudaStream_t st);
+// persistent grid of pipeline shape `shape` (< 0 on a CUDA error), and the
+// number of compiled shapes per precision (spmv_cfg.cuh)
 template <typename T>
-int spmv_persistent_grid(int nSlicesTotal);   // < 0 on a CUDA error
+int spmv_persistent_grid(int nSlicesTotal, int shape);
+template <typename T>
+int spmv_shape_count();
 
 template <typename T>
 void launch_update(const NodeDev<T> &N, T *u, T *r, const T *p, const T *q, T *y, int mode,

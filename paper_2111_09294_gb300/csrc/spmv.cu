@@ -31,11 +31,12 @@ namespace xdcg {
 // next: the first 32 slices' extents are read into shared memory at kernel
 // start (one slice per lane), and a slice's row indices are loaded when the
 // slice begins, its x (or b) entries one stage later, for use when it ends.
-template <typename T, bool RES>
-__global__ void __launch_bounds__(kSpmvThreads, SpmvCfg<T>::MINB)
+template <typename T, bool RES, int SHAPE>
+__global__ void __launch_bounds__(kSpmvThreads, SpmvCfg<T, SHAPE>::MINB)
 k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__restrict__ b,
        double *partials, Scalars *sc, int fin, int slot) {
-    constexpr int C = SpmvCfg<T>::C, NS = SpmvCfg<T>::NS, SB = stage_bytes<T>();
+    using Cfg = SpmvCfg<T, SHAPE>;
+    constexpr int C = Cfg::C, NS = Cfg::NS, SB = stage_bytes<T, SHAPE>();
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *ring = smem + (size_t)warp * NS * SB;
@@ -206,7 +207,7 @@ k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__rest
             rl = (isS ? sl : sl - nS) * rpw + (lane % rpw);
             h = lane / rpw;
             valid = rl < (isS ? A.S.nRows : A.X.nRows);
-            if (SpmvCfg<T>::GUARD) len = valid ? (isS ? A.S.len[rl] : A.X.len[rl]) : 0;
+            if (Cfg::GUARD) len = valid ? (isS ? A.S.len[rl] : A.X.len[rl]) : 0;
             own = valid && h == 0;
             // consumed when the slice ends; the row's x (or b) entries are
             // loaded after this stage, once the index has arrived
@@ -218,7 +219,7 @@ k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__rest
         const T *vs = reinterpret_cast<const T *>(ring + st * SB + C * 128);
 #pragma unroll
         for (int t = 0; t < C; ++t) {
-            if (t < na && (!SpmvCfg<T>::GUARD || (s0 + t) * tpr + h < len)) {
+            if (t < na && (!Cfg::GUARD || (s0 + t) * tpr + h < len)) {
                 const T *v = vs + t * 288 + lane;
                 a0 = fma(v[0], xa[t][0], a0);
                 a0 = fma(v[32], xa[t][1], a0);
@@ -262,32 +263,85 @@ k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__rest
     }
 }
 
-template <typename T>
-int spmv_persistent_grid(int nSlicesTotal) {
+// Persistent grid of a shape: its resident blocks per SM times the SMs (at
+// most one warp per slice); < 0 on a CUDA error.
+template <typename T, int SHAPE>
+int persistent_grid_of(int nSlicesTotal) {
     int dev = 0, sms = 0, nb = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return -1;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
-    const int smem = spmv_smem_bytes<T>();
-    if (cudaFuncSetAttribute(k_spmv<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_spmv<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-            cudaSuccess)
+    const int smem = spmv_smem_bytes<T, SHAPE>();
+    if (cudaFuncSetAttribute(k_spmv<T, false, SHAPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_spmv<T, true, SHAPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem) != cudaSuccess)
         return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv<T, false>, kSpmvThreads, smem) !=
-            cudaSuccess || nb < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv<T, false, SHAPE>, kSpmvThreads,
+                                                      smem) != cudaSuccess || nb < 1)
         return -1;
     const int need = (nSlicesTotal + kSpmvWarps - 1) / kSpmvWarps;
     return std::max(1, std::min(nb * sms, need));
 }
-template int spmv_persistent_grid<float>(int);
-template int spmv_persistent_grid<double>(int);
+
+template <typename T, bool RES, int SHAPE>
+void launch_shape(const SpmvDev<T> &A, const T *x, T *y, const T *b, double *partials,
+                  Scalars *sc, int fin, int slot, cudaStream_t st) {
+    launch_pdl(k_spmv<T, RES, SHAPE>, A.grid, kSpmvThreads, spmv_smem_bytes<T, SHAPE>(), st, A, x,
+               y, b, partials, sc, fin, slot);
+}
+
+template <typename T>
+int spmv_shape_count() { return SpmvShapes<T>::count; }
+template int spmv_shape_count<float>();
+template int spmv_shape_count<double>();
+
+template <>
+int spmv_persistent_grid<float>(int nSlicesTotal, int shape) {
+    switch (shape) {
+        case 0: return persistent_grid_of<float, 0>(nSlicesTotal);
+        case 1: return persistent_grid_of<float, 1>(nSlicesTotal);
+        case 2: return persistent_grid_of<float, 2>(nSlicesTotal);
+        case 3: return persistent_grid_of<float, 3>(nSlicesTotal);
+        case 4: return persistent_grid_of<float, 4>(nSlicesTotal);
+    }
+    return -1;
+}
+template <>
+int spmv_persistent_grid<double>(int nSlicesTotal, int shape) {
+    switch (shape) {
+        case 0: return persistent_grid_of<double, 0>(nSlicesTotal);
+        case 1: return persistent_grid_of<double, 1>(nSlicesTotal);
+        case 2: return persistent_grid_of<double, 2>(nSlicesTotal);
+        case 3: return persistent_grid_of<double, 3>(nSlicesTotal);
+    }
+    return -1;
+}
+
+template <typename T, bool RES>
+void launch_spmv_res(const SpmvDev<T> &A, const T *x, T *y, const T *b, double *partials,
+                     Scalars *sc, int fin, int slot, cudaStream_t st) {
+    switch (A.shape) {
+        case 1: launch_shape<T, RES, 1>(A, x, y, b, partials, sc, fin, slot, st); return;
+        case 2: launch_shape<T, RES, 2>(A, x, y, b, partials, sc, fin, slot, st); return;
+        case 3: launch_shape<T, RES, 3>(A, x, y, b, partials, sc, fin, slot, st); return;
+        case 4:
+            if constexpr (SpmvShapes<T>::count > 4) {
+                launch_shape<T, RES, 4>(A, x, y, b, partials, sc, fin, slot, st);
+                return;
+            }
+            break;
+        default: break;
+    }
+    launch_shape<T, RES, 0>(A, x, y, b, partials, sc, fin, slot, st);
+}
 
 template <typename T>
 void launch_spmv(const SpmvDev<T> &A, const T *x, T *y, const T *b, int residual_mode,
                  double *partials, Scalars *sc, int fin, int slot, cudaStream_t st) {
-    const int smem = spmv_smem_bytes<T>();
-    launch_pdl(residual_mode ? k_spmv<T, true> : k_spmv<T, false>, A.grid, kSpmvThreads, smem, st,
-               A, x, y, b, partials, sc, fin, slot);
+    if (residual_mode)
+        launch_spmv_res<T, true>(A, x, y, b, partials, sc, fin, slot, st);
+    else
+        launch_spmv_res<T, false>(A, x, y, b, partials, sc, fin, slot, st);
 }
 
 template void launch_spmv<double>(const SpmvDev<double> &, const double *, double *,

@@ -77,7 +77,7 @@ class Solver:
                  precision="fp64", tol=1e-8, max_iter=10000, inner_tol=1e-3, max_outer=30,
                  time_spmv=False, enriched_modes=True, stream=None, jacobi="block",
                  record_history=False, max_batch=0, coarse_fp64=False, wait_s=2.0,
-                 blocks=None, z_cols=None, z_values=None, prev=None):
+                 blocks=None, z_cols=None, z_values=None, prev=None, autotune=False):
         lib = L.load()
         self._lib = lib
         self.ctx = ctypes.c_void_p()
@@ -110,6 +110,7 @@ class Solver:
         opt.max_batch = int(max_batch)
         opt.coarse_fp64 = int(bool(coarse_fp64))
         opt.wait_s = float(wait_s)
+        opt.autotune = int(bool(autotune))
         self.precision = precision
         if stream is None:
             stream = torch.cuda.current_stream()
