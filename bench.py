@@ -499,8 +499,9 @@ def run_ours(args):
         return out
 
     # a propagation sweep: --sweep systems of the 32^3 inclined-penny sweep,
-    # 8 load cases each, every system a batched mixed solve on its own stream;
-    # concurrent against one after another (outside the value)
+    # 8 load cases each, every system a batched mixed solve: fused (one
+    # launch per kernel over all systems), concurrent (a host thread and a
+    # stream per system) and one after another (outside the value)
     def measure_sweep():
         from paper_2111_09294_gb300 import sweep as S
         Ps = X.make_many(X.SWEEP[:args.sweep])
@@ -508,31 +509,33 @@ def run_ours(args):
         Fs = [torch.tensor(X.load_cases(Pi, 8, seed=100 + i), device=dev)
               for i, Pi in enumerate(Ps)]
         Us = [torch.empty_like(Fi) for Fi in Fs]
-        for _ in range(max(1, args.warmup)):
-            S.solve_systems(ssol, Fs, TOL, outs=Us)
-        tc, ts_, res = [], [], None
-        for _ in range(args.steps):
-            flush.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            res = S.solve_systems(ssol, Fs, TOL, outs=Us)
-            tc.append((time.perf_counter() - t0) * 1e3)
-        for _ in range(args.steps):
-            flush.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            S.solve_systems(ssol, Fs, TOL, outs=Us, concurrent=False)
-            ts_.append((time.perf_counter() - t0) * 1e3)
-        infos = [i for _, inf in res for i in inf]
+        modes = {"fused": {}, "concurrent": {"fused": False},
+                 "one_after_another": {"fused": False, "concurrent": False}}
+        times, res = {}, {}
+        for name, kw in modes.items():
+            for _ in range(max(1, args.warmup)):
+                S.solve_systems(ssol, Fs, TOL, outs=Us, **kw)
+            ts_ = []
+            for _ in range(args.steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                res[name] = S.solve_systems(ssol, Fs, TOL, outs=Us, **kw)
+                ts_.append((time.perf_counter() - t0) * 1e3)
+            times[name] = float(np.mean(ts_))
+        infos = [i for _, inf in res["fused"] for i in inf]
         assert max(i["rel_res_true"] for i in infos) <= TOL
-        ms_c, ms_s = float(np.mean(tc)), float(np.mean(ts_))
         sweep = {"systems": len(Ps), "rhs_per_system": 8,
-                 "n_dofs": [int(Pi.n) for Pi in Ps], "ms": ms_c, "ms_one_after_another": ms_s,
-                 "speedup_concurrent": ms_s / ms_c,
-                 "systems_rhs_per_s": len(Ps) * 8 / ms_c * 1e3,
+                 "n_dofs": [int(Pi.n) for Pi in Ps], "ms": times["fused"],
+                 "ms_concurrent": times["concurrent"],
+                 "ms_one_after_another": times["one_after_another"],
+                 "speedup_fused_vs_one_after_another": times["one_after_another"] / times["fused"],
+                 "speedup_fused_vs_concurrent": times["concurrent"] / times["fused"],
+                 "systems_rhs_per_s": len(Ps) * 8 / times["fused"] * 1e3,
                  "iterations_max": max(i["iterations"] for i in infos),
+                 "iterations_mean": float(np.mean([i["iterations"] for i in infos])),
                  "rel_res_true_max": max(i["rel_res_true"] for i in infos),
-                 "timing": "host wall clock around the calls (each returns after its stream)"}
+                 "timing": "host wall clock around the calls (each returns after its work)"}
         for s_ in ssol:
             s_.close()
         return sweep

@@ -280,16 +280,36 @@ xdcg_status xdcg_solve_x0(xdcg_ctx *ctx, const double *f, double *u, double tol,
  * cases of one crack configuration).  F, U: device arrays of m * n doubles,
  * column j at offset j * n (may not alias).  With MIXED and opt.max_batch >= m
  * the columns run as one batched FP32 iteration: each iteration reads K~, Z~,
- * W~ and E^-1 once for all columns; each column stops once its FP64 true
- * residual meets tol.  A column's FP64 residual replacement happens when its
- * own FP32 residual has dropped far enough (the other columns finish the
- * interrupted iteration); a breakdown in any column replaces every active
- * column.  Otherwise (FP64, or max_batch = 0) the columns are solved one
- * after another.  res: NULL or m results; iterations are counted per
- * column (the shared counter when the column converged).  Returns the worst
- * status over the columns. */
+ * W~ and E^-1 once for all columns.  Each column advances on its own: when
+ * its FP32 recursive residual has dropped by inner_tol (or its p^T K p is not
+ * positive, or it reaches max_iter iterations) it is held while the others
+ * iterate, its FP32 correction is folded into U_j and its FP64 residual
+ * f_j - K U_j replaces the recursive one; it leaves once that residual meets
+ * tol (or is not finite: BREAKDOWN with bad_index = j; or after max_outer
+ * replacements or at max_iter: NO_CONVERGENCE).  A column's result does not
+ * depend on the other columns.  Otherwise (FP64, or max_batch = 0) the
+ * columns are solved one after another.  res: NULL or m results, iterations
+ * counted per column.  Returns the worst status over the columns. */
 xdcg_status xdcg_solve_batch(xdcg_ctx *ctx, const double *F, double *U, int32_t m, double tol,
                              xdcg_result *res);
+
+/* xdcg_solve_batch for several systems at once (the crack fronts of a
+ * propagation sweep, Section 4: each front has its own K, Z and
+ * preconditioner), run as one batched FP32 iteration: every iteration is one
+ * launch per kernel over all systems' blocks, on ctxs[0]'s stream (ordered
+ * after the work already queued on the other contexts' streams, and before
+ * what is queued on them later).  ctxs: n_sys distinct MIXED contexts on one
+ * device, set up with the same max_batch rounding (1..4 or 5..8); F[s], U[s]:
+ * device arrays of m[s] * n_s doubles as for xdcg_solve_batch, 1 <= m[s] <=
+ * that context's max_batch.  tol <= 0 takes each context's opt.tol.  Every
+ * column's result is the same bits as from xdcg_solve_batch on its own
+ * context.  res: NULL or sum(m) results, system by system; status: NULL or
+ * n_sys statuses.  Contexts must not be used by another thread meanwhile.
+ * Returns INVALID_ARG, CUDA_ERROR or TIMEOUT for the call, else the worst
+ * system status. */
+xdcg_status xdcg_solve_systems(xdcg_ctx *const *ctxs, int32_t n_sys, const double *const *F,
+                               double *const *U, const int32_t *m, double tol,
+                               xdcg_result *res, xdcg_status *status);
 
 /* As xdcg_solve with host arrays: copies f to the device, solves, copies u
  * back, all on the context stream; returns after u is on the host. */

@@ -22,7 +22,7 @@ STATUS = {0: "XDCG_OK", 1: "XDCG_INVALID_ARG", 2: "XDCG_NOT_SPD_BLOCK",
 
 # every function the header declares
 EXPORTS = ["xdcg_default_options", "xdcg_setup", "xdcg_setup_update", "xdcg_solve", "xdcg_solve_x0", "xdcg_solve_batch",
-           "xdcg_solve_host", "xdcg_get_info", "xdcg_get_history", "xdcg_spmv", "xdcg_spmv_noalloc",
+           "xdcg_solve_systems", "xdcg_solve_host", "xdcg_get_info", "xdcg_get_history", "xdcg_spmv", "xdcg_spmv_noalloc",
            "xdcg_precond", "xdcg_element_sensitivity", "xdcg_stiffness_gradient",
            "xdcg_coarse_matrix", "xdcg_destroy", "xdcg_status_string"]
 
@@ -109,6 +109,8 @@ def load():
     lib.xdcg_solve_x0.argtypes = [c_void_p, c_void_p, c_void_p, c_double, POINTER(Result)]
     lib.xdcg_solve_batch.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_double, c_void_p]
     lib.xdcg_solve_host.argtypes = [c_void_p, c_void_p, c_void_p, c_double, POINTER(Result)]
+    lib.xdcg_solve_systems.argtypes = [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_double,
+                                       c_void_p, c_void_p]
     lib.xdcg_get_info.argtypes = [c_void_p, POINTER(Info)]
     lib.xdcg_get_history.argtypes = [c_void_p, c_void_p, c_int32, POINTER(c_int32)]
     lib.xdcg_spmv.argtypes = [c_void_p, c_int32, c_void_p, c_void_p, POINTER(c_double)]

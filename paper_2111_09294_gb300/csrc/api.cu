@@ -66,6 +66,7 @@ struct xdcg_ctx {
           *bQ = nullptr, *bG32 = nullptr, *bNU32 = nullptr;
     double *bG = nullptr, *bZR = nullptr, *bNU = nullptr, *bUnitPart = nullptr, *bR64 = nullptr;
     BatchScalars *bs = nullptr, *h_bs = nullptr;
+    Scalars *bSlots = nullptr, *h_slots = nullptr;   // per-column FP64 reductions (device, pinned)
     // kept for xdcg_setup_update: each node's dofs, its (Jacobi-filtered)
     // diagonal block (host) and its position in its factor list
     std::vector<int> hostKind, hostListPos;
@@ -398,8 +399,6 @@ xdcg_status run_pcg(xdcg_ctx *c, Path path, const T *f, T *u, T *r, T *p, T *q, 
 // writes the new one of its own.  Iteration i reads residual buffer
 // (i & 1 ? rB : rA) and writes the other.
 
-constexpr double kMinGroupDrop2 = 1e-2;   // (1/10)^2
-
 __global__ void k_set_trigger(Scalars *sc, int mode, double delta2, double floor2) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         if (mode == 0) {            // re-arm without a convergence test; keep the
@@ -723,191 +722,320 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, boo
     return status;
 }
 
-// ---- batched mixed solve: m right-hand sides of one system --------------------
+// ---- batched mixed solve: m right-hand sides per system, one or several systems ----
+//
+// The start (||f_j||^2, Algorithm 2 and the first directions for every
+// column) is enqueued for every system after one wait.  Then each tick
+// enqueues kTick FP32 iterations (one launch per kernel over all systems
+// when there are several), reads the snapshot of every system's scalars
+// taken at the end of the previous tick (so the device works on this tick
+// meanwhile) and enqueues a replacement of the columns held there: fold of
+// the FP32 correction into U, FP64 residual f_j - K U_j, the test against
+// tol, the transform of the new residual and Algorithm 3 on it.  The held
+// columns of a system wait for that while its other columns and the other
+// systems iterate; a system whose columns have all left drops out.
 
+constexpr int kTick = 2;    // batched iterations enqueued between snapshots
+
+struct BatchRun {
+    xdcg_ctx *c = nullptr;
+    const double *F = nullptr;
+    double *U = nullptr;
+    int m = 0;
+    double tol = 0.0;
+    bool live = false;         // columns left
+    SpmmArgs spmm{};
+    RestrictBArgs rst{};
+    CoarseBArgs crs{};
+    ProlongBArgs pro{};
+};
+
+RestrictBArgs restrict_args(xdcg_ctx *c, int m, int mode) {
+    return RestrictBArgs{c->L32.Rb, m, mode, c->bU32, c->bRA, c->bRB, c->bF32, c->bP, c->bQ,
+                         c->bG, mode == 2 ? nullptr : c->bZR, c->bUnitPart, c->partials,
+                         c->bG32, c->bs};
+}
+CoarseBArgs coarse_args(xdcg_ctx *c, int m, int mode) {
+    return CoarseBArgs{c->Einv32, c->bG32, c->k, m, mode, mode == 0 ? nullptr : c->bZR,
+                       c->bNU, c->partials, c->bNU32, c->bs};
+}
+ProlongBArgs prolong_args(xdcg_ctx *c, int m, int mode) {
+    return ProlongBArgs{c->L32.Rb, m, mode, c->bNU32, c->bRA, c->bRB,
+                        mode == 1 ? c->bU32 : c->bP, c->bs};
+}
+
+// host scalars from the columns' ||f_j||^2 (fresh slots), then the start
 template <int MB>
-xdcg_status batch_iterate(xdcg_ctx *c, int m, int max_it) {
-    cudaStream_t st = c->st;
+xdcg_status batch_start(BatchRun &R, cudaStream_t st) {
+    xdcg_ctx *c = R.c;
     Level32 &L = c->L32;
-    CK(cudaMemcpyAsync(c->h_bs, c->bs, sizeof(BatchScalars), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    int i = c->h_bs->its;
-    const int max_batches = (max_it - i) / kBatch + 2;
-    for (int b = 0; b < max_batches; ++b) {
-        for (int j = 0; j < kBatch; ++j, ++i) {
-            float *rc = (i & 1) ? c->bRB : c->bRA;
-            float *rn = (i & 1) ? c->bRA : c->bRB;
-            launch_spmm<MB>(L.A, m, c->bP, c->bQ, nullptr, 0, c->partials, c->bs, 0, st);
-            launch_restrict_b<MB>(L.Rb, m, c->bU32, rc, rn, c->bP, c->bQ, 0, c->bG, c->bG32,
-                                  c->bZR, c->bUnitPart, c->partials, c->bs, st);
-            launch_coarse_b<MB>(c->Einv32, c->k, m, c->bG32, c->bZR, c->bNU, c->bNU32, 2,
-                                c->partials, c->bs, st);
-            launch_prolong_b<MB>(L.Rb, m, c->bNU32, rn, c->bP, 0, c->bs, st);
-            c->launches += 4;
+    const long long n = c->n;
+    const int m = R.m;
+    BatchScalars &hb = *c->h_bs;
+    hb = BatchScalars{};
+    hb.max_it = c->opt.max_iter;
+    hb.max_outer = c->opt.max_outer;
+    hb.tol = R.tol;
+    hb.delta2 = c->opt.inner_tol * c->opt.inner_tol;
+    int nActive = 0;
+    for (int j = 0; j < m; ++j) {
+        if (c->h_slots[j].done == kFault) return XDCG_TIMEOUT;
+        const double ff = c->h_slots[j].scratch[0];
+        hb.ff[j] = hb.rn2[j] = ff;
+        hb.repl[j] = 1;
+        hb.trig[j] = -1.0;
+        if (!std::isfinite(ff)) {
+            hb.outcome[j] = kColBad;
+            continue;
         }
-        CK(cudaMemcpyAsync(&c->h_done[b & 1], &c->bs->done, sizeof(int), cudaMemcpyDeviceToHost,
-                           st));
-        CK(cudaEventRecord(c->evb[b & 1], st));
-        if (b >= 1) {
-            CK(cudaEventSynchronize(c->evb[(b - 1) & 1]));
-            if (c->h_done[(b - 1) & 1] != kRunning) break;
+        hb.active[j] = ff > 0.0;
+        hb.scale[j] = ff > 0.0 ? 1.0 / std::sqrt(ff) : 0.0;
+        nActive += hb.active[j];
+    }
+    hb.done = kRunning;
+    CK(cudaMemsetAsync(R.U, 0, (size_t)m * n * sizeof(double), st));
+    R.live = nActive > 0;
+    if (!R.live) return XDCG_OK;
+    CK(cudaMemcpyAsync(c->bs, c->h_bs, sizeof(BatchScalars), cudaMemcpyHostToDevice, st));
+    // F~ = s_j L^-1 f_j; u~ = Z~ E^-1 Z~^T F~ (Algorithm 2); r = F~ - K~ u~; the
+    // first directions p = r + Z~ E^-1 (Z~^T r - W~^T r)
+    launch_fwd_scale_b<MB>(c->nNodes, m, L.dofStart64, L.dofStart32, L.F, R.F, n, c->bs, c->bF32,
+                           c->bF32, st);
+    CK(cudaMemsetAsync(c->bU32, 0, (size_t)n * MB * sizeof(float), st));
+    launch_restrict_b<MB>(restrict_args(c, m, 2), st);
+    launch_coarse_b<MB>(coarse_args(c, m, 0), st);
+    launch_prolong_b<MB>(prolong_args(c, m, 1), st);
+    launch_spmm<MB>(SpmmArgs{L.A, m, 1, c->bU32, c->bF32, c->bRA, c->partials, c->bs}, st);
+    launch_restrict_b<MB>(restrict_args(c, m, 1), st);
+    launch_coarse_b<MB>(coarse_args(c, m, 1), st);
+    launch_prolong_b<MB>(prolong_args(c, m, 2), st);
+    launch_batch_arm(c->bs, m, 1, st);
+    c->launches += 10;
+    R.spmm = SpmmArgs{L.A, m, 0, c->bP, nullptr, c->bQ, c->partials, c->bs};
+    R.rst = restrict_args(c, m, 0);
+    R.crs = coarse_args(c, m, 2);
+    R.pro = prolong_args(c, m, 0);
+    return XDCG_OK;
+}
+
+// replacement of the columns in mask M of one system
+template <int MB>
+void batch_replace(BatchRun &R, unsigned M, cudaStream_t st) {
+    xdcg_ctx *c = R.c;
+    Level32 &L = c->L32;
+    const long long n = c->n;
+    const int m = R.m;
+    launch_batch_open(c->bs, c->bSlots, M, st);
+    launch_bwd_accum_b<MB>(c->nNodes, m, L.dofStart64, L.dofStart32, L.F, c->bU32, c->bs, R.U, n,
+                           st);
+    int nr = 0;
+    for (int j = 0; j < m; ++j)
+        if ((M >> j) & 1u) {
+            launch_spmv<double>(c->L64.A, R.U + j * n, c->bR64 + j * n, R.F + j * n, 1,
+                                c->partials, c->bSlots + j, kFinStore, 0, st);
+            ++nr;
+        }
+    launch_batch_judge(c->bs, c->bSlots, m, st);
+    launch_fwd_scale_b<MB>(c->nNodes, m, L.dofStart64, L.dofStart32, L.F, c->bR64, n, c->bs,
+                           c->bRA, c->bRB, st);
+    launch_restrict_b<MB>(restrict_args(c, m, 1), st);
+    launch_coarse_b<MB>(coarse_args(c, m, 3), st);
+    launch_prolong_b<MB>(prolong_args(c, m, 3), st);
+    launch_batch_arm(c->bs, m, 0, st);
+    c->launches += 8 + nr;
+}
+
+// per-column results from the final scalars; the system's status
+xdcg_status batch_results(const BatchRun &R, xdcg_result *res) {
+    const BatchScalars &hb = *R.c->h_bs;
+    bool bad = false, limit = false;
+    for (int j = 0; j < R.m; ++j) {
+        xdcg_result r{};
+        r.bad_index = hb.outcome[j] == kColBad ? j : -1;
+        r.iterations = hb.itsc[j];
+        r.outer_cycles = hb.cycles[j];
+        // the FP32 recursion's residual before the last replacement
+        r.rel_res_recursive = std::sqrt(hb.cycles[j] ? hb.rrRep[j] : hb.rr[j]);
+        r.rel_res_true = hb.outcome[j] == kColBad ? std::nan("")
+                         : hb.ff[j] > 0.0        ? std::sqrt(hb.rn2[j] / hb.ff[j])
+                                                 : 0.0;
+        bad |= hb.outcome[j] == kColBad;
+        limit |= hb.outcome[j] == kColLimit;
+        if (res) res[j] = r;
+    }
+    return bad ? XDCG_BREAKDOWN : limit ? XDCG_NO_CONVERGENCE : XDCG_OK;
+}
+
+// Device tables of the live systems' iteration arguments for launches over
+// several systems: one version per live set (a version is never rewritten
+// while launches that read it may be queued).
+struct SysTables {
+    int nSys = 0, versions = 0, used = 0;
+    size_t vbytes = 0;
+    unsigned char *dev = nullptr, *host = nullptr;   // device / pinned staging
+    cudaStream_t st = nullptr;
+    ~SysTables() {
+        if (dev) cudaFreeAsync(dev, st);
+        if (host) {
+            cudaStreamSynchronize(st);   // copies from the staging may still be queued
+            cudaFreeHost(host);
         }
     }
-    CK(cudaMemcpyAsync(c->h_bs, c->bs, sizeof(BatchScalars), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    CK(cudaGetLastError());
+};
+
+xdcg_status sys_tables_init(SysTables &T, int nSys, cudaStream_t st) {
+    T.st = st;
+    T.nSys = nSys;
+    T.versions = nSys + 1;
+    T.vbytes = (size_t)nSys * (sizeof(SpmmArgs) + sizeof(RestrictBArgs) + sizeof(CoarseBArgs) +
+                               sizeof(ProlongBArgs)) +
+               4 * sizeof(int) * (size_t)(nSys + 1);
+    T.vbytes = (T.vbytes + 255) & ~(size_t)255;
+    CK(cudaMallocAsync(reinterpret_cast<void **>(&T.dev), T.vbytes * T.versions, st));
+    CK(cudaMallocHost(reinterpret_cast<void **>(&T.host), T.vbytes * T.versions));
+    return XDCG_OK;
+}
+
+xdcg_status sys_tables_build(SysTables &T, BatchRun *runs, int nSys, cudaStream_t st,
+                             BatchSysTab *tab) {
+    if (T.used >= T.versions) return XDCG_CUDA_ERROR;
+    const size_t base = T.vbytes * T.used++;
+    unsigned char *h = T.host + base, *d = T.dev + base;
+    int nLive = 0;
+    for (int s = 0; s < nSys; ++s) nLive += runs[s].live;
+    auto *hs = reinterpret_cast<SpmmArgs *>(h);
+    auto *hr = reinterpret_cast<RestrictBArgs *>(hs + nLive);
+    auto *hc = reinterpret_cast<CoarseBArgs *>(hr + nLive);
+    auto *hp = reinterpret_cast<ProlongBArgs *>(hc + nLive);
+    int *ho = reinterpret_cast<int *>(hp + nLive);
+    int *off[4];
+    for (int q = 0; q < 4; ++q) {
+        off[q] = ho + q * (nLive + 1);
+        off[q][0] = 0;
+    }
+    int i = 0;
+    for (int s = 0; s < nSys; ++s) {
+        if (!runs[s].live) continue;
+        const BatchRun &R = runs[s];
+        hs[i] = R.spmm;
+        hr[i] = R.rst;
+        hc[i] = R.crs;
+        hp[i] = R.pro;
+        off[0][i + 1] = off[0][i] + R.spmm.A.grid;
+        off[1][i + 1] = off[1][i] + R.rst.B.nUnits;
+        off[2][i + 1] = off[2][i] + coarse_b_blocks(R.crs.k);
+        off[3][i + 1] = off[3][i] + R.pro.B.nPUnits;
+        ++i;
+    }
+    const size_t used = reinterpret_cast<unsigned char *>(ho + 4 * (nLive + 1)) - h;
+    CK(cudaMemcpyAsync(d, h, used, cudaMemcpyHostToDevice, st));
+    tab->nSys = nLive;
+    tab->spmm = reinterpret_cast<const SpmmArgs *>(d);
+    tab->rst = reinterpret_cast<const RestrictBArgs *>(d + ((unsigned char *)hr - h));
+    tab->crs = reinterpret_cast<const CoarseBArgs *>(d + ((unsigned char *)hc - h));
+    tab->pro = reinterpret_cast<const ProlongBArgs *>(d + ((unsigned char *)hp - h));
+    for (int q = 0; q < 4; ++q) {
+        tab->off[q] = reinterpret_cast<const int *>(d + ((unsigned char *)off[q] - h));
+        tab->blocks[q] = off[q][nLive];
+    }
     return XDCG_OK;
 }
 
 template <int MB>
-xdcg_status solve_batch_mixed(xdcg_ctx *c, const double *F, double *U, int m, double tol,
-                              xdcg_result *res) {
-    cudaStream_t st = c->st;
-    Level32 &L = c->L32;
-    const long long n = c->n;
-    double ff[kMaxBatch] = {0}, rn2[kMaxBatch] = {0};
-    int itsAt[kMaxBatch] = {0};
+xdcg_status solve_batches(BatchRun *runs, int nSys, cudaStream_t st, xdcg_status *status) {
+    xdcg_ctx *c0 = runs[0].c;
     xdcg_status s;
-    for (int j = 0; j < m; ++j) {
-        init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
-        launch_dot<double>(F + j * n, F + j * n, n, c->partials, c->aux, kFinStore, 0, st);
-        c->launches += 1;
-        double v[1];
-        if ((s = read_aux(c, v, 1)) != XDCG_OK) return s;
-        ff[j] = rn2[j] = v[0];
-        if (!std::isfinite(ff[j])) return XDCG_BREAKDOWN;
+    // ||f_j||^2 of every column of every system, one wait
+    for (int q = 0; q < nSys; ++q) {
+        xdcg_ctx *c = runs[q].c;
+        const long long n = c->n;
+        launch_batch_slots(c->bSlots, (1u << runs[q].m) - 1u, st);
+        for (int j = 0; j < runs[q].m; ++j)
+            launch_dot<double>(runs[q].F + j * n, runs[q].F + j * n, n, c->partials,
+                               c->bSlots + j, kFinStore, 0, st);
+        c->launches += 1 + runs[q].m;
+        CK(cudaMemcpyAsync(c->h_slots, c->bSlots, sizeof(Scalars) * runs[q].m,
+                           cudaMemcpyDeviceToHost, st));
     }
-    CK(cudaMemsetAsync(U, 0, (size_t)m * n * sizeof(double), st));
-    BatchScalars &hb = *c->h_bs;
-    hb = BatchScalars{};
-    hb.max_it = c->opt.max_iter;
-    int nActive = 0;
-    for (int j = 0; j < m; ++j) {
-        hb.active[j] = ff[j] > 0.0;
-        hb.repl[j] = 1;
-        hb.scale[j] = ff[j] > 0.0 ? 1.0 / std::sqrt(ff[j]) : 0.0;
-        hb.trig[j] = -1.0;
-        nActive += hb.active[j];
-    }
-    for (int j = 0; j < m; ++j) {
-        res[j] = xdcg_result{};
-        res[j].bad_index = -1;
-    }
-    if (nActive == 0) return XDCG_OK;
-    CK(cudaMemcpyAsync(c->bs, c->h_bs, sizeof(BatchScalars), cudaMemcpyHostToDevice, st));
-    // F~ = s_j L^-1 f_j, then Algorithm 2 and the first directions for every column
-    launch_fwd_scale_b<MB>(c->nNodes, m, L.dofStart64, L.dofStart32, L.F, F, n, c->bs, c->bF32,
-                           st);
-    CK(cudaMemsetAsync(c->bU32, 0, (size_t)n * MB * sizeof(float), st));
-    launch_restrict_b<MB>(L.Rb, m, nullptr, c->bF32, nullptr, nullptr, nullptr, 2, c->bG,
-                          c->bG32, nullptr, c->bUnitPart, c->partials, c->bs, st);
-    launch_coarse_b<MB>(c->Einv32, c->k, m, c->bG32, nullptr, c->bNU, c->bNU32, 0, c->partials,
-                        c->bs, st);
-    launch_prolong_b<MB>(L.Rb, m, c->bNU32, nullptr, c->bU32, 1, c->bs, st);
-    launch_spmm<MB>(L.A, m, c->bU32, c->bRA, c->bF32, 1, c->partials, c->bs, 1, st);
-    launch_restrict_b<MB>(L.Rb, m, nullptr, c->bRA, nullptr, nullptr, nullptr, 1, c->bG,
-                          c->bG32, c->bZR, c->bUnitPart, c->partials, c->bs, st);
-    launch_coarse_b<MB>(c->Einv32, c->k, m, c->bG32, c->bZR, c->bNU, c->bNU32, 1, c->partials,
-                        c->bs, st);
-    launch_prolong_b<MB>(L.Rb, m, c->bNU32, c->bRA, c->bP, 2, c->bs, st);
-    c->launches += 9;
-    CK(cudaMemcpyAsync(c->h_bs, c->bs, sizeof(BatchScalars), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    const double delta2 = c->opt.inner_tol * c->opt.inner_tol;
-    for (int j = 0; j < m; ++j) hb.trig[j] = hb.active[j] ? delta2 * hb.rr[j] : -1.0;
-    CK(cudaMemcpyAsync(c->bs, c->h_bs, sizeof(BatchScalars), cudaMemcpyHostToDevice, st));
-    int passes = 0, cycles[kMaxBatch] = {0};
-    xdcg_status status = XDCG_NO_CONVERGENCE;
-    bool anyBad = false;
-    while (true) {
-        if ((s = batch_iterate<MB>(c, m, c->opt.max_iter)) != XDCG_OK) return s;
-        if (hb.done == kFault) return XDCG_TIMEOUT;
-        const bool last = hb.done == kMaxIter || passes + 1 >= c->opt.max_outer;
-        // which columns are replaced now: those at their trigger or not finite
-        // (all of them at the end, or after a breakdown, which stops the
-        // iteration before its residual update); the others finish the
-        // interrupted iteration and keep going
-        bool anyBroken = false;
-        for (int j = 0; j < m; ++j) anyBroken |= hb.active[j] && hb.broken[j];
-        for (int j = 0; j < m; ++j)
-            hb.repl[j] = hb.active[j] && (last || anyBroken || hb.rr[j] <= hb.trig[j] ||
-                                          !std::isfinite(hb.rr[j]));
-        // fold the FP32 corrections of every active column into U (exact for the
-        // columns that continue too: their recursion now refers to the new U)
-        launch_bwd_accum_b<MB>(c->nNodes, m, L.dofStart64, L.dofStart32, L.F, c->bU32, c->bs, U, n,
-                               st);
-        CK(cudaMemsetAsync(c->bU32, 0, (size_t)n * MB * sizeof(float), st));
-        c->launches += 1;
-        passes++;
-        nActive = 0;
-        for (int j = 0; j < m; ++j) {
-            if (!hb.active[j]) continue;
-            if (!hb.repl[j]) {
-                nActive++;
-                continue;
-            }
-            cycles[j]++;
-            init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
-            launch_spmv<double>(c->L64.A, U + j * n, c->bR64 + j * n, F + j * n, 1, c->partials,
-                                c->aux, kFinStore, 0, st);
-            c->launches += 1;
-            double v[1];
-            if ((s = read_aux(c, v, 1)) != XDCG_OK) return s;
-            rn2[j] = v[0];
-            if (!std::isfinite(rn2[j])) {
-                anyBad = true;
-                hb.active[j] = 0;
-                itsAt[j] = hb.its;
-                res[j].bad_index = j;
-            } else if (rn2[j] <= tol * tol * ff[j]) {
-                hb.active[j] = 0;
-                itsAt[j] = hb.its;
-            } else {
-                nActive++;
-            }
-        }
-        if (nActive == 0) {
-            status = anyBad ? XDCG_BREAKDOWN : XDCG_OK;
+    int nLive = 0;
+    for (int q = 0; q < nSys; ++q) {
+        if ((s = batch_start<MB>(runs[q], st)) != XDCG_OK) return s;
+        nLive += runs[q].live;
+    }
+    const bool multi = nSys > 1;
+    SysTables T;
+    BatchSysTab tab{};
+    if (multi && nLive > 0) {
+        if ((s = sys_tables_init(T, nSys, st)) != XDCG_OK) return s;
+        if ((s = sys_tables_build(T, runs, nSys, st, &tab)) != XDCG_OK) return s;
+    }
+    long long maxTicks = 16;
+    for (int q = 0; q < nSys; ++q) {
+        const xdcg_options &o = runs[q].c->opt;
+        maxTicks = std::max(maxTicks, (long long)kMaxBatch *
+                                          ((long long)o.max_iter / kTick + 2LL * o.max_outer + 2));
+    }
+    xdcg_status status_all = XDCG_OK;
+    bool snap = false;
+    for (long long tick = 0; nLive > 0; ++tick) {
+        if (tick > maxTicks) {
+            status_all = XDCG_NO_CONVERGENCE;
             break;
         }
-        if (last) break;
-        // replace the recursive residuals of the replaced columns by their scaled
-        // true ones (zero for the columns that just left) and re-arm
-        for (int j = 0; j < m; ++j)
-            if (hb.repl[j]) {
-                hb.rrRep[j] = hb.rr[j];
-                hb.trig[j] = -1.0;
+        for (int i = 0; i < kTick; ++i) {
+            if (multi) {
+                launch_iteration_sys<MB>(tab, st);
+                c0->launches += 4;
+            } else {
+                launch_spmm<MB>(runs[0].spmm, st);
+                launch_restrict_b<MB>(runs[0].rst, st);
+                launch_coarse_b<MB>(runs[0].crs, st);
+                launch_prolong_b<MB>(runs[0].pro, st);
+                c0->launches += 4;
             }
-        hb.done = kRunning;
-        CK(cudaMemcpyAsync(c->bs, c->h_bs, sizeof(BatchScalars), cudaMemcpyHostToDevice, st));
-        float *rbuf = (hb.its & 1) ? c->bRB : c->bRA;
-        launch_fwd_scale_b<MB>(c->nNodes, m, L.dofStart64, L.dofStart32, L.F, c->bR64, n, c->bs,
-                               rbuf, st);
-        launch_restrict_b<MB>(L.Rb, m, nullptr, rbuf, nullptr, nullptr, nullptr, 1, c->bG,
-                              c->bG32, c->bZR, c->bUnitPart, c->partials, c->bs, st);
-        launch_coarse_b<MB>(c->Einv32, c->k, m, c->bG32, c->bZR, c->bNU, c->bNU32, 3, c->partials,
-                            c->bs, st);
-        launch_prolong_b<MB>(L.Rb, m, c->bNU32, rbuf, c->bP, 0, c->bs, st);
-        c->launches += 4;
-        CK(cudaMemcpyAsync(c->h_bs, c->bs, sizeof(BatchScalars), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        for (int j = 0; j < m; ++j) {
-            if (!hb.active[j] || !hb.repl[j]) continue;
-            const double sj = hb.scale[j];
-            const double gamma2 = hb.rr[j] / (sj * sj * rn2[j]);
-            const double floor2 = std::min(0.25 * tol * tol * ff[j] * sj * sj * gamma2,
-                                           kMinGroupDrop2 * hb.rr[j]);
-            hb.trig[j] = std::max(delta2 * hb.rr[j], floor2);
         }
-        CK(cudaMemcpyAsync(c->bs, c->h_bs, sizeof(BatchScalars), cudaMemcpyHostToDevice, st));
+        if (snap) {
+            CK(cudaEventSynchronize(c0->evb[(tick - 1) & 1]));
+            bool changed = false;
+            for (int q = 0; q < nSys; ++q) {
+                BatchRun &R = runs[q];
+                if (!R.live) continue;
+                const BatchScalars &hb = *R.c->h_bs;
+                if (hb.done == kFault || hb.fault) {
+                    CK(cudaStreamSynchronize(st));
+                    return XDCG_TIMEOUT;
+                }
+                unsigned M = 0;
+                int nAct = 0;
+                for (int j = 0; j < R.m; ++j)
+                    if (hb.active[j]) {
+                        ++nAct;
+                        if (hb.pend[j]) M |= 1u << j;
+                    }
+                if (nAct == 0) {
+                    R.live = false;
+                    changed = true;
+                    --nLive;
+                } else if (M) {
+                    batch_replace<MB>(R, M, st);
+                }
+            }
+            if (nLive == 0) break;
+            if (changed && multi)
+                if ((s = sys_tables_build(T, runs, nSys, st, &tab)) != XDCG_OK) return s;
+        }
+        for (int q = 0; q < nSys; ++q)
+            if (runs[q].live)
+                CK(cudaMemcpyAsync(runs[q].c->h_bs, runs[q].c->bs, sizeof(BatchScalars),
+                                   cudaMemcpyDeviceToHost, st));
+        CK(cudaEventRecord(c0->evb[tick & 1], st));
+        snap = true;
     }
-    for (int j = 0; j < m; ++j) {
-        res[j].iterations = hb.active[j] ? hb.its : itsAt[j];
-        res[j].outer_cycles = cycles[j];
-        res[j].rel_res_recursive = std::sqrt(hb.rr[j]);
-        res[j].rel_res_true = ff[j] > 0 ? std::sqrt(rn2[j] / ff[j]) : 0.0;
-    }
-    return status;
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    for (int q = 0; q < nSys; ++q) status[q] = status_all;
+    return XDCG_OK;
 }
 
 xdcg_status do_solve(xdcg_ctx *c, const double *f, double *u, double tol, bool guess,
@@ -937,6 +1065,7 @@ void free_ctx(xdcg_ctx *c) {
     for (void *p : c->temps) cudaFree(p);
     if (c->h_sc) cudaFreeHost(c->h_sc);
     if (c->h_bs) cudaFreeHost(c->h_bs);
+    if (c->h_slots) cudaFreeHost(c->h_slots);
     if (c->h_done) cudaFreeHost(c->h_done);
     if (c->h_poll) cudaFreeHost(c->h_poll);
     for (auto e : c->evS) cudaEventDestroy(e);
@@ -2035,10 +2164,14 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         c->bUnitPart = dalloc<double>(c, (size_t)c->L32.Rb.nUnits * MB * 24);
         c->bR64 = dalloc<double>(c, (size_t)n * MB);
         c->bs = dalloc<BatchScalars>(c, 1);
+        c->bSlots = dalloc<Scalars>(c, kMaxBatch);
         if (!c->bF32 || !c->bU32 || !c->bRA || !c->bRB || !c->bP || !c->bQ || !c->bG32 ||
-            !c->bNU32 || !c->bG || !c->bZR || !c->bNU || !c->bUnitPart || !c->bR64 || !c->bs)
+            !c->bNU32 || !c->bG || !c->bZR || !c->bNU || !c->bUnitPart || !c->bR64 || !c->bs ||
+            !c->bSlots)
             return XDCG_OOM;
         if (cudaMallocHost(&c->h_bs, sizeof(BatchScalars)) != cudaSuccess) return XDCG_OOM;
+        if (cudaMallocHost(&c->h_slots, sizeof(Scalars) * kMaxBatch) != cudaSuccess)
+            return XDCG_OOM;
         if (!spmm_prepare()) return XDCG_CUDA_ERROR;
     }
     if (!c->u64 || !c->r64 || !c->p64 || !c->q64 || !c->y64 || !c->f64 || !c->uh64 || !c->g ||
@@ -2209,7 +2342,6 @@ xdcg_status xdcg_solve_batch(xdcg_ctx *c, const double *F, double *U, int32_t m,
     NvtxRange range("xdcg solve_batch");
     if (!c || !F || !U || F == U || m < 1) return XDCG_INVALID_ARG;
     if (tol <= 0) tol = c->opt.tol;
-    xdcg_result local[kMaxBatch];
     if (c->bMB == 0) {
         // no batched run on this context: the columns one after another
         xdcg_status worst = XDCG_OK;
@@ -2223,21 +2355,93 @@ xdcg_status xdcg_solve_batch(xdcg_ctx *c, const double *F, double *U, int32_t m,
         return worst;
     }
     if (m > c->opt.max_batch) return XDCG_INVALID_ARG;
-    const long long l0 = c->launches;
-    CK(cudaEventRecord(c->ev0, c->st));
-    xdcg_status s = c->bMB == 4 ? solve_batch_mixed<4>(c, F, U, m, tol, local)
-                                : solve_batch_mixed<8>(c, F, U, m, tol, local);
-    if (s == XDCG_CUDA_ERROR) return s;
-    CK(cudaEventRecord(c->ev1, c->st));
-    CK(cudaEventSynchronize(c->ev1));
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-    for (int j = 0; j < m; ++j) {
-        local[j].t_solve_ms = ms;
-        local[j].n_launches = c->launches - l0;
-        if (res) res[j] = local[j];
+    xdcg_ctx *one[1] = {c};
+    const double *Fs[1] = {F};
+    double *Us[1] = {U};
+    const int32_t ms[1] = {m};
+    xdcg_status st1 = XDCG_OK;
+    xdcg_status s = xdcg_solve_systems(one, 1, Fs, Us, ms, tol, res, &st1);
+    return s == XDCG_OK ? st1 : s;
+}
+
+xdcg_status xdcg_solve_systems(xdcg_ctx *const *ctxs, int32_t n_sys, const double *const *F,
+                               double *const *U, const int32_t *m, double tol,
+                               xdcg_result *res, xdcg_status *status) {
+    NvtxRange range("xdcg solve_systems");
+    if (!ctxs || n_sys < 1 || !F || !U || !m) return XDCG_INVALID_ARG;
+    std::vector<BatchRun> runs(n_sys);
+    for (int q = 0; q < n_sys; ++q) {
+        xdcg_ctx *c = ctxs[q];
+        if (!c || !c->mixed || c->bMB == 0 || c->bMB != ctxs[0]->bMB ||
+            c->device != ctxs[0]->device)
+            return XDCG_INVALID_ARG;
+        if (!F[q] || !U[q] || (const double *)U[q] == F[q] || m[q] < 1 ||
+            m[q] > c->opt.max_batch)
+            return XDCG_INVALID_ARG;
+        for (int r = 0; r < q; ++r)
+            if (ctxs[r] == c) return XDCG_INVALID_ARG;   // one set of scalars per context
+        runs[q].c = c;
+        runs[q].F = F[q];
+        runs[q].U = U[q];
+        runs[q].m = m[q];
+        runs[q].tol = tol > 0 ? tol : c->opt.tol;
     }
-    return s;
+    xdcg_ctx *c0 = ctxs[0];
+    int prev = -1;
+    CK(cudaGetDevice(&prev));
+    CK(cudaSetDevice(c0->device));
+    cudaStream_t st = c0->st;
+    // every system's work runs on the first context's stream, ordered after
+    // and before the work queued on the others' streams
+    std::vector<cudaEvent_t> evs;
+    auto order = [&](cudaStream_t from, cudaStream_t to) -> xdcg_status {
+        if (from == to) return XDCG_OK;
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        evs.push_back(e);
+        CK(cudaEventRecord(e, from));
+        CK(cudaStreamWaitEvent(to, e, 0));
+        return XDCG_OK;
+    };
+    xdcg_status s = XDCG_OK;
+    for (int q = 1; q < n_sys && s == XDCG_OK; ++q) s = order(ctxs[q]->st, st);
+    std::vector<xdcg_status> sst(n_sys, XDCG_OK);
+    std::vector<long long> l0(n_sys);
+    for (int q = 0; q < n_sys; ++q) l0[q] = ctxs[q]->launches;
+    float ms = 0.f;
+    if (s == XDCG_OK) {
+        CK(cudaEventRecord(c0->ev0, st));
+        s = c0->bMB == 4 ? solve_batches<4>(runs.data(), n_sys, st, sst.data())
+                         : solve_batches<8>(runs.data(), n_sys, st, sst.data());
+        if (s == XDCG_OK) {
+            CK(cudaEventRecord(c0->ev1, st));
+            CK(cudaEventSynchronize(c0->ev1));
+            CK(cudaEventElapsedTime(&ms, c0->ev0, c0->ev1));
+        }
+    }
+    for (int q = 1; q < n_sys; ++q) {
+        xdcg_status s2 = order(st, ctxs[q]->st);
+        if (s == XDCG_OK) s = s2;
+    }
+    for (auto e : evs) cudaEventDestroy(e);
+    cudaSetDevice(prev);
+    if (s != XDCG_OK) return s;
+    xdcg_status worst = XDCG_OK;
+    long long off = 0;
+    for (int q = 0; q < n_sys; ++q) {
+        xdcg_result local[kMaxBatch];
+        xdcg_status sq = batch_results(runs[q], local);
+        if (sst[q] != XDCG_OK) sq = sst[q];
+        for (int j = 0; j < m[q]; ++j) {
+            local[j].t_solve_ms = ms;
+            local[j].n_launches = ctxs[q]->launches - l0[q];
+            if (res) res[off + j] = local[j];
+        }
+        off += m[q];
+        if (status) status[q] = sq;
+        if (sq == XDCG_BREAKDOWN || (sq == XDCG_NO_CONVERGENCE && worst == XDCG_OK)) worst = sq;
+    }
+    return worst;
 }
 
 xdcg_status xdcg_solve_host(xdcg_ctx *c, const double *f_host, double *u_host, double tol,

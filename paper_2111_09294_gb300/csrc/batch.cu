@@ -4,9 +4,21 @@
 // per iteration for all columns, so the bytes per right-hand side fall by up
 // to MB.  Vectors are interleaved by column: entry (dof d, column j) at
 // d * MB + j, so a chunk gathered by the product is one run of 3 * MB floats
-// and a row of the box kernels is one run of MB floats.  Columns that have
-// converged (or are padding) are inactive: their alpha and beta are 0 and
-// their vectors stay as they are.
+// and a row of the box kernels is one run of MB floats.
+//
+// Columns advance independently (BatchScalars): an iteration updates the
+// running columns (active and not held); a held column's residual is copied
+// into the next buffer and its other vectors stay as they are, and a column
+// that has left keeps zero vectors.  A replacement (open, FP64 residuals,
+// judge, transforms, restriction / coarse / prolongation in their
+// replacement modes, arm) touches only the columns it replaces.
+//
+// Every kernel body takes its block index and block count within its own
+// system, so the same body runs as a launch for one system or as one launch
+// over several systems (BatchSysTab): a column's result is the same bits
+// either way.
+#include <climits>
+
 #include "cache.cuh"
 #include "factor.cuh"
 #include "reduce.cuh"
@@ -15,29 +27,55 @@
 
 namespace xdcg {
 
+__device__ __forceinline__ bool col_runs(const BatchScalars *bs, int j, int m) {
+    return j < m && bs->active[j] && !bs->pend[j];
+}
+
+// the block's system in a launch over several systems: the largest s with
+// off[s] <= b
+__device__ __forceinline__ int sys_of(const int *__restrict__ off, int nSys, int b) {
+    int lo = 0, hi = nSys - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
 // ---- per-column scalar updates ----------------------------------------------
 
-// fin 0 (iteration): pq_j, its, alpha_j (0 for inactive columns); a column
-// whose p^T K p is not positive is marked broken and a replacement requested.
+// fin 0 (iteration): pq_j, alpha_j for the running columns (0 for the
+// others); a running column whose p^T K p is not positive is held as broken.
+// The iteration counts (its, its_j) advance when a column still runs;
+// otherwise the system stops until the host's next replacement.
 // fin 1 (start): rr_j.
 __device__ __forceinline__ void batch_finalize(BatchScalars *bs, int m, int fin,
                                                const double *tot) {
     if (fin == 0) {
-        bs->its += 1;
-        bool request = false;
+        bool any = false;
         for (int j = 0; j < m; ++j) {
             bs->pq[j] = tot[j];
-            if (!bs->active[j]) {
+            if (!col_runs(bs, j, m)) {
                 bs->alpha[j] = 0.0;
-            } else if (!(tot[j] > 0.0) || !isfinite(tot[j])) {
+                continue;
+            }
+            bs->itsc[j] += 1;
+            if (!(tot[j] > 0.0) || !isfinite(tot[j])) {
                 bs->alpha[j] = 0.0;
                 bs->broken[j] = 1;
-                request = true;
+                bs->pend[j] = 1;
             } else {
                 bs->alpha[j] = bs->rho[j] / tot[j];
+                any = true;
             }
         }
-        if (request) bs->done = kConverged;
+        if (any)
+            bs->its += 1;
+        else
+            bs->done = kConverged;
     } else {
         for (int j = 0; j < m; ++j) bs->rr[j] = tot[j];
     }
@@ -46,17 +84,21 @@ __device__ __forceinline__ void batch_finalize(BatchScalars *bs, int m, int fin,
 // ---- batched product Y = K~ X (+ x_j^T y_j, or ||y_j||^2 with y = b - K~ x) --
 
 template <int MB, bool RES>
-__global__ void __launch_bounds__(kSpmvThreads)
-k_spmm(SpmvDev<float> A, int m, const float *__restrict__ x, float *__restrict__ y,
-       const float *__restrict__ b, double *partials, BatchScalars *bs, int fin) {
+__device__ __forceinline__ void spmm_body(const SpmmArgs &args, int blk, int nblk,
+                                          unsigned char *smem) {
     constexpr int C = SpmvCfg<float, 0>::C, NS = SpmvCfg<float, 0>::NS, SB = stage_bytes<float, 0>();
-    extern __shared__ __align__(128) unsigned char smem[];
+    const SpmvDev<float> &A = args.A;
+    const int m = args.m, fin = args.fin;
+    const float *__restrict__ x = args.x;
+    const float *__restrict__ b = args.b;
+    float *__restrict__ y = args.y;
+    BatchScalars *bs = args.bs;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *ring = smem + (size_t)warp * NS * SB;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)kSpmvWarps * NS * SB) + warp * NS;
     int *meta = reinterpret_cast<int *>(smem + (size_t)kSpmvWarps * NS * (SB + 8)) + warp * NS * 3;
     const int nS = A.S.nSlices;
-    const int gw = blockIdx.x * kSpmvWarps + warp;
+    const int gw = blk * kSpmvWarps + warp;
     const int sEnd = A.warpSlice[gw + 1];
     if (lane == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(bars + s, 1);
@@ -227,7 +269,8 @@ k_spmm(SpmvDev<float> A, int m, const float *__restrict__ x, float *__restrict__
         __syncwarp();
     }
     double tot[MB];
-    if (grid_sum<float, MB>(part, partials, &bs->ticket[0], tot) && threadIdx.x == 0) {
+    if (grid_sum_of<float, MB>(part, args.partials, &bs->ticket[0], tot, blk, nblk) &&
+        threadIdx.x == 0) {
         if (bs->fault)
             bs->done = kFault;
         else
@@ -235,25 +278,38 @@ k_spmm(SpmvDev<float> A, int m, const float *__restrict__ x, float *__restrict__
     }
 }
 
+template <int MB, bool RES>
+__global__ void __launch_bounds__(kSpmvThreads) k_spmm(SpmmArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    spmm_body<MB, RES>(a, (int)blockIdx.x, (int)gridDim.x, smem);
+}
+
 template <int MB>
-void launch_spmm(const SpmvDev<float> &A, int m, const float *x, float *y, const float *b,
-                 int residual_mode, double *partials, BatchScalars *bs, int fin,
-                 cudaStream_t st) {
+__global__ void __launch_bounds__(kSpmvThreads)
+k_spmm_sys(const SpmmArgs *__restrict__ tab, const int *__restrict__ off, int nSys) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int s = sys_of(off, nSys, (int)blockIdx.x);
+    const int b0 = __ldg(off + s);
+    spmm_body<MB, false>(tab[s], (int)blockIdx.x - b0, __ldg(off + s + 1) - b0, smem);
+}
+
+template <int MB>
+void launch_spmm(const SpmmArgs &a, cudaStream_t st) {
     const int smem = spmv_smem_bytes<float, 0>();
-    launch_pdl(residual_mode ? k_spmm<MB, true> : k_spmm<MB, false>, A.grid, kSpmvThreads, smem,
-               st, A, m, x, y, b, partials, bs, fin);
+    launch_pdl(a.fin ? k_spmm<MB, true> : k_spmm<MB, false>, a.A.grid, kSpmvThreads, smem, st, a);
+}
+
+template <typename K>
+static bool set_smem(K k, int smem) {
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+           cudaSuccess;
 }
 
 bool spmm_prepare() {
     const int smem = spmv_smem_bytes<float, 0>();
-    return cudaFuncSetAttribute(k_spmm<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem) == cudaSuccess &&
-           cudaFuncSetAttribute(k_spmm<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem) == cudaSuccess &&
-           cudaFuncSetAttribute(k_spmm<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem) == cudaSuccess &&
-           cudaFuncSetAttribute(k_spmm<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem) == cudaSuccess;
+    return set_smem(k_spmm<4, false>, smem) && set_smem(k_spmm<4, true>, smem) &&
+           set_smem(k_spmm<8, false>, smem) && set_smem(k_spmm<8, true>, smem) &&
+           set_smem(k_spmm_sys<4>, smem) && set_smem(k_spmm_sys<8>, smem);
 }
 
 // ---- batched restriction + update ---------------------------------------------
@@ -284,17 +340,22 @@ __device__ __forceinline__ float block_sum_by_column(float (&v)[NV]) {
 
 // One unit (own rows, then coupled rows, of one box); thread t handles column
 // j = t % MB of rows t / MB, t / MB + 256 / MB, ...  acc: Z~^T r (M), W~^T r (M),
-// ||r||^2 of its column.
+// ||r||^2 of its column.  Mode 0 updates the running columns (r' = r -
+// alpha_j q, u += alpha_j p) and copies the residual of the others.
 template <int MB, int M>
-__device__ __forceinline__ void restrict_b_unit(const RowBoxDev &B, int unit, int m, float *u,
-                                                const float *r_cur, float *r_next, const float *p,
-                                                const float *q, int mode, const BatchScalars *bs,
-                                                double *G, float *G32, double *ZR,
-                                                double *unitPart, float (&rr)[MB]) {
+__device__ __forceinline__ void restrict_b_unit(const RestrictBArgs &a, int unit,
+                                                const float *r_cur, float *r_next,
+                                                float (&rr)[MB]) {
+    const RowBoxDev &B = a.B;
+    const BatchScalars *bs = a.bs;
+    const int mode = a.mode;
+    float *u = a.u;
+    const float *p = a.p, *q = a.q;
     const int s = B.unitBox[unit];
     const int j = threadIdx.x % MB, row0 = threadIdx.x / MB;
     constexpr int kRowStep = kThreads / MB;
-    const float alpha = (mode == 0 && j < m) ? (float)bs->alpha[j] : 0.0f;
+    const bool run = mode == 0 && col_runs(bs, j, a.m);
+    const float alpha = run ? (float)bs->alpha[j] : 0.0f;
     float acc[2 * M + 1];
 #pragma unroll
     for (int c = 0; c <= 2 * M; ++c) acc[c] = 0.0f;
@@ -308,9 +369,11 @@ __device__ __forceinline__ void restrict_b_unit(const RowBoxDev &B, int unit, in
             const size_t e = (size_t)r * MB + j;
             float rn = r_cur[e];
             if (mode == 0) {
-                rn = fmaf(-alpha, q[e], rn);
+                if (run) {
+                    rn = fmaf(-alpha, q[e], rn);
+                    u[e] = fmaf(alpha, p[e], u[e]);
+                }
                 r_next[e] = rn;
-                u[e] = fmaf(alpha, p[e], u[e]);
             }
             acc[2 * M] = fmaf(rn, rn, acc[2 * M]);
             const int rl = r - r0;
@@ -326,7 +389,7 @@ __device__ __forceinline__ void restrict_b_unit(const RowBoxDev &B, int unit, in
 #pragma unroll 2
         for (int r = B.unitExtBegin[unit] + row0; r < re; r += kRowStep) {
             const size_t e = (size_t)ld_keep(B.extRowDof + r, keep) * MB + j;
-            const float rn = (mode == 0) ? fmaf(-alpha, q[e], r_cur[e]) : r_cur[e];
+            const float rn = run ? fmaf(-alpha, q[e], r_cur[e]) : r_cur[e];
             const int rl = r - r0;
 #pragma unroll
             for (int c = 0; c < M; ++c)
@@ -341,6 +404,8 @@ __device__ __forceinline__ void restrict_b_unit(const RowBoxDev &B, int unit, in
     if (holder && tc == 2 * M) rrs[tj] = tsum;
     const int u0 = B.boxUnit[s], nu = B.boxUnit[s + 1] - u0;
     const int c0 = B.col0[s];
+    double *G = a.G, *ZR = a.ZR, *unitPart = a.unitPart;
+    float *G32 = a.G32;
     __shared__ float red[MB][2 * 12];
     __shared__ bool lastUnit;
     if (nu == 1) {
@@ -383,52 +448,72 @@ __device__ __forceinline__ void restrict_b_unit(const RowBoxDev &B, int unit, in
         for (int jj = 0; jj < MB; ++jj) rr[jj] = rrs[jj];
 }
 
-// mode 0: r' = r - alpha_j q, u += alpha_j p, G from r'; mode 1: G from r;
-// mode 2: G = Z~^T f only, no ||r||^2.  The last block sets rr_j and asks for
-// a replacement once an active column reaches its trigger.
+// mode 0 (iteration): r' = r - alpha_j q, u += alpha_j p for the running
+// columns, G from r'; the last block sets rr_j of the running columns and
+// holds those at their trigger or at the iteration limit.  mode 1: G and
+// rr_j of the columns being replaced from the current residual.  mode 2:
+// G = Z~^T f only.
 template <int MB>
-__global__ void __launch_bounds__(kThreads)
-k_restrict_b(RowBoxDev B, int m, float *u, const float *r_cur, float *r_next, const float *p,
-             const float *q, int mode, double *G, float *G32, double *ZR, double *unitPart,
-             double *partials, BatchScalars *bs) {
+__device__ __forceinline__ void restrict_b_body(const RestrictBArgs &a, int blk, int nblk) {
     pdl_wait();
+    BatchScalars *bs = a.bs;
     if (bs->done != kRunning) return;
-    const int unit = blockIdx.x;
+    const int its = bs->its, m = a.m, mode = a.mode;
+    // iteration: the product advanced its, so buffer (its - 1) & 1 is read
+    const float *r_cur = mode == 2 ? a.f : (((its & 1) != (mode == 0)) ? a.rB : a.rA);
+    float *r_next = mode == 0 ? ((its & 1) ? a.rB : a.rA) : nullptr;
+    const int unit = blk;
     float rr[MB];
 #pragma unroll
     for (int j = 0; j < MB; ++j) rr[j] = 0.0f;
-    if (B.menr[B.unitBox[unit]])
-        restrict_b_unit<MB, 12>(B, unit, m, u, r_cur, r_next, p, q, mode, bs, G, G32, ZR,
-                                unitPart, rr);
+    if (a.B.menr[a.B.unitBox[unit]])
+        restrict_b_unit<MB, 12>(a, unit, r_cur, r_next, rr);
     else
-        restrict_b_unit<MB, 6>(B, unit, m, u, r_cur, r_next, p, q, mode, bs, G, G32, ZR,
-                               unitPart, rr);
+        restrict_b_unit<MB, 6>(a, unit, r_cur, r_next, rr);
     if (mode == 2) return;
     // rr holds the block's totals in thread 0 (zeros elsewhere)
     if (threadIdx.x != 0)
 #pragma unroll
         for (int j = 0; j < MB; ++j) rr[j] = 0.0f;
     double tot[MB];
-    if (grid_sum<float, MB>(rr, partials, &bs->ticket[2], tot) && threadIdx.x == 0) {
-        bool request = false;
-        for (int j = 0; j < m; ++j) {
-            bs->rr[j] = tot[j];
-            if (bs->active[j] && (tot[j] <= bs->trig[j] || !isfinite(tot[j]))) request = true;
+    if (grid_sum_of<float, MB>(rr, a.partials, &bs->ticket[2], tot, blk, nblk) &&
+        threadIdx.x == 0) {
+        if (mode == 1) {
+            for (int j = 0; j < m; ++j)
+                if (bs->repl[j]) bs->rr[j] = tot[j];
+            return;
         }
-        if (request)
-            bs->done = kConverged;
-        else if (bs->its >= bs->max_it)
-            bs->done = kMaxIter;
+        bool any = false;
+        for (int j = 0; j < m; ++j) {
+            if (!col_runs(bs, j, m)) continue;
+            bs->rr[j] = tot[j];
+            if (tot[j] <= bs->trig[j] || !isfinite(tot[j])) bs->pend[j] = 1;
+            if (bs->itsc[j] >= bs->max_it) {
+                bs->pend[j] = 1;
+                bs->last[j] = 1;
+            }
+            any |= !bs->pend[j];
+        }
+        if (!any) bs->done = kConverged;
     }
 }
 
 template <int MB>
-void launch_restrict_b(const RowBoxDev &B, int m, float *u, const float *r_cur, float *r_next,
-                       const float *p, const float *q, int mode, double *G, float *G32,
-                       double *ZR, double *unitPart, double *partials, BatchScalars *bs,
-                       cudaStream_t st) {
-    launch_pdl(k_restrict_b<MB>, B.nUnits, kThreads, 0, st, B, m, u, r_cur, r_next, p, q, mode, G,
-               G32, ZR, unitPart, partials, bs);
+__global__ void __launch_bounds__(kThreads) k_restrict_b(RestrictBArgs a) {
+    restrict_b_body<MB>(a, (int)blockIdx.x, (int)gridDim.x);
+}
+
+template <int MB>
+__global__ void __launch_bounds__(kThreads)
+k_restrict_b_sys(const RestrictBArgs *__restrict__ tab, const int *__restrict__ off, int nSys) {
+    const int s = sys_of(off, nSys, (int)blockIdx.x);
+    const int b0 = __ldg(off + s);
+    restrict_b_body<MB>(tab[s], (int)blockIdx.x - b0, __ldg(off + s + 1) - b0);
+}
+
+template <int MB>
+void launch_restrict_b(const RestrictBArgs &a, cudaStream_t st) {
+    launch_pdl(k_restrict_b<MB>, a.B.nUnits, kThreads, 0, st, a);
 }
 
 // ---- batched coarse solve NU = E^-1 G -----------------------------------------
@@ -436,26 +521,25 @@ void launch_restrict_b(const RowBoxDev &B, int m, float *u, const float *r_cur, 
 constexpr int kCoarseChunkB = 1024;
 constexpr int kCoarsePadB = kCoarseChunkB + 4;   // row pitch of the transposed G chunk
 
-// mode 0: nothing else; mode 1: rho_j = rr_j + nu_j^T zr_j, beta_j = 0; mode 2:
-// the same rho_new, beta_j = rho_new / rho_j; mode 3 (after a replacement): as
-// 2, with beta_j = 0 for a replaced column whose residual the replacement
-// lengthened by more than 2x or that broke down (the other columns finish the
-// iteration the trigger interrupted, as in mode 2).  Inactive columns get
-// beta = 0.  One warp per row of E^-1 (16-byte loads when k is a multiple of
-// 4); G staged in shared memory chunk by chunk, transposed (one padded row
-// per column), so a lane's four consecutive entries of a column are one
-// conflict-free 16-byte load.
+// mode 0: nu only; mode 1 (start, every column): rho_j = rr_j + nu_j^T zr_j,
+// beta_j = 0; mode 2 (iteration, running columns): the same rho_new, beta_j =
+// rho_new / rho_j; mode 3 (replacement, the replaced columns): as 2, with
+// beta_j = 0 for a column that leaves, that broke down or whose residual the
+// replacement lengthened by more than 2x.  One warp per row of E^-1 (16-byte
+// loads when k is a multiple of 4); G staged in shared memory chunk by chunk,
+// transposed (one padded row per column), so a lane's four consecutive
+// entries of a column are one conflict-free 16-byte load.
 template <int MB, int V>
-__global__ void __launch_bounds__(kThreads)
-k_coarse_b(const float *__restrict__ Einv, int k, int m, const float *__restrict__ G32,
-           const double *__restrict__ ZR, double *NU, float *NU32, int mode, double *partials,
-           BatchScalars *bs) {
+__device__ __forceinline__ void coarse_b_body(const CoarseBArgs &a, int blk, int nblk,
+                                              float *gs) {
     pdl_wait();
+    BatchScalars *bs = a.bs;
     if (bs->done != kRunning) return;
-    __shared__ __align__(16) float gs[MB * kCoarsePadB];
+    const int k = a.k, m = a.m, mode = a.mode;
+    const float *__restrict__ G32 = a.G32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * kWarps + warp;
-    const float *row = Einv + (size_t)(i < k ? i : 0) * k;
+    const int i = blk * kWarps + warp;
+    const float *row = a.Einv + (size_t)(i < k ? i : 0) * k;
     const uint64_t keep = l2_keep_policy();
     float acc[MB];
 #pragma unroll
@@ -475,10 +559,10 @@ k_coarse_b(const float *__restrict__ Einv, int k, int m, const float *__restrict
 #pragma unroll
                 for (int j = 0; j < MB; ++j) {
                     const float4 g = *reinterpret_cast<const float4 *>(gs + j * kCoarsePadB + 4 * l4);
-                    float a = fmaf(ev.x, g.x, acc[j]);
-                    a = fmaf(ev.y, g.y, a);
-                    a = fmaf(ev.z, g.z, a);
-                    acc[j] = fmaf(ev.w, g.w, a);
+                    float t = fmaf(ev.x, g.x, acc[j]);
+                    t = fmaf(ev.y, g.y, t);
+                    t = fmaf(ev.z, g.z, t);
+                    acc[j] = fmaf(ev.w, g.w, t);
                 }
             }
         } else {
@@ -497,46 +581,69 @@ k_coarse_b(const float *__restrict__ Einv, int k, int m, const float *__restrict
     if (i < k && lane == 0) {
 #pragma unroll
         for (int j = 0; j < MB; ++j) {
-            NU[(size_t)i * MB + j] = (double)acc[j];
-            NU32[(size_t)i * MB + j] = acc[j];
-            if (mode != 0) part[j] = (double)acc[j] * ZR[(size_t)i * MB + j];
+            a.NU[(size_t)i * MB + j] = (double)acc[j];
+            a.NU32[(size_t)i * MB + j] = acc[j];
+            if (mode != 0) part[j] = (double)acc[j] * a.ZR[(size_t)i * MB + j];
         }
     }
     double tot[MB];
-    if (grid_sum<double, MB>(part, partials, &bs->ticket[3], tot) && threadIdx.x == 0 &&
-        mode != 0) {
+    if (grid_sum_of<double, MB>(part, a.partials, &bs->ticket[3], tot, blk, nblk) &&
+        threadIdx.x == 0 && mode != 0) {
         for (int j = 0; j < m; ++j) {
-            // a column not being replaced finishes its interrupted iteration as in mode 2
-            const bool rep = mode == 1 || (mode == 3 && bs->repl[j]);
+            const bool upd = mode == 2 ? col_runs(bs, j, m) : (mode == 1 || bs->repl[j]);
+            if (!upd) continue;
             const double rho_new = bs->rr[j] + tot[j];
-            if (!bs->active[j]) {
+            if (mode == 1 || !bs->active[j] ||
+                (mode == 3 && (bs->broken[j] || bs->rr[j] > 4.0 * bs->rrRep[j])))
                 bs->beta[j] = 0.0;
-            } else if (mode == 1 || (rep && (bs->broken[j] || bs->rr[j] > 4.0 * bs->rrRep[j]))) {
-                bs->beta[j] = 0.0;
-            } else {
+            else
                 bs->beta[j] = rho_new / bs->rho[j];
-            }
             bs->rho[j] = rho_new;
-            if (rep) bs->broken[j] = 0;
+            if (mode == 3) bs->broken[j] = 0;
         }
     }
 }
 
+template <int MB, int V>
+__global__ void __launch_bounds__(kThreads) k_coarse_b(CoarseBArgs a) {
+    __shared__ __align__(16) float gs[MB * kCoarsePadB];
+    coarse_b_body<MB, V>(a, (int)blockIdx.x, (int)gridDim.x, gs);
+}
+
 template <int MB>
-void launch_coarse_b(const float *Einv, int k, int m, const float *G32, const double *ZR,
-                     double *NU, float *NU32, int mode, double *partials, BatchScalars *bs,
-                     cudaStream_t st) {
+__global__ void __launch_bounds__(kThreads)
+k_coarse_b_sys(const CoarseBArgs *__restrict__ tab, const int *__restrict__ off, int nSys) {
+    __shared__ __align__(16) float gs[MB * kCoarsePadB];
+    const int s = sys_of(off, nSys, (int)blockIdx.x);
+    const int b0 = __ldg(off + s), nb = __ldg(off + s + 1) - b0;
+    const CoarseBArgs &a = tab[s];
+    if ((a.k & 3) == 0)
+        coarse_b_body<MB, 4>(a, (int)blockIdx.x - b0, nb, gs);
+    else
+        coarse_b_body<MB, 1>(a, (int)blockIdx.x - b0, nb, gs);
+}
+
+int coarse_b_blocks(int k) {
     const int grid = (k + kWarps - 1) / kWarps;
-    launch_pdl(k % 4 == 0 ? k_coarse_b<MB, 4> : k_coarse_b<MB, 1>, grid > 0 ? grid : 1, kThreads,
-               0, st, Einv, k, m, G32, ZR, NU, NU32, mode, partials, bs);
+    return grid > 0 ? grid : 1;
+}
+
+template <int MB>
+void launch_coarse_b(const CoarseBArgs &a, cudaStream_t st) {
+    launch_pdl(a.k % 4 == 0 ? k_coarse_b<MB, 4> : k_coarse_b<MB, 1>, coarse_b_blocks(a.k),
+               kThreads, 0, st, a);
 }
 
 // ---- batched prolongation -----------------------------------------------------
 
-// mode 0: p = y + Z~ nu + beta_j p; mode 1: p = Z~ nu; mode 2: p = y + Z~ nu
+// mode 0 (iteration, running columns) and mode 3 (replacement, the replaced
+// columns): p = y + Z~ nu + beta_j p, 0 for a replaced column that leaves;
+// mode 1 (start): p = Z~ nu; mode 2 (start): p = y + Z~ nu.  y is the current
+// residual buffer.
 template <int MB, int M>
 __device__ __forceinline__ void prolong_b_unit(const RowBoxDev &B, int unit, const float *NU32,
-                                               const float *y, float *p, int mode, float beta) {
+                                               const float *y, float *p, int mode, float beta,
+                                               bool leaves) {
     const int s = B.pUnitBox[unit];
     const int j = threadIdx.x % MB, row0 = threadIdx.x / MB;
     constexpr int kRowStep = kThreads / MB;
@@ -555,8 +662,8 @@ __device__ __forceinline__ void prolong_b_unit(const RowBoxDev &B, int unit, con
 #pragma unroll
         for (int c = 0; c < M; ++c) zv = fmaf(ld_keep(Z + (size_t)c * R + rl, keep), nv[c], zv);
         const size_t e = (size_t)r * MB + j;
-        if (mode == 0)
-            p[e] = y[e] + zv + beta * p[e];
+        if (mode == 0 || mode == 3)
+            p[e] = leaves ? 0.0f : y[e] + zv + beta * p[e];
         else if (mode == 1)
             p[e] = zv;
         else
@@ -565,42 +672,172 @@ __device__ __forceinline__ void prolong_b_unit(const RowBoxDev &B, int unit, con
 }
 
 template <int MB>
-__global__ void __launch_bounds__(kThreads)
-k_prolong_b(RowBoxDev B, int m, const float *NU32, const float *y, float *p, int mode,
-            const BatchScalars *bs) {
+__device__ __forceinline__ void prolong_b_body(const ProlongBArgs &a, int blk) {
     pdl_wait();
+    const BatchScalars *bs = a.bs;
     if (bs->done != kRunning) return;
-    const int unit = blockIdx.x;
+    const int unit = blk, mode = a.mode;
     const int j = threadIdx.x % MB;
-    const float beta = (mode == 0 && j < m) ? (float)bs->beta[j] : 0.0f;
-    if (B.menr[B.pUnitBox[unit]])
-        prolong_b_unit<MB, 12>(B, unit, NU32, y, p, mode, beta);
+    bool wr = true, leaves = false;
+    if (mode == 0) {
+        wr = col_runs(bs, j, a.m);
+    } else if (mode == 3) {
+        wr = j < a.m && bs->repl[j];
+        leaves = wr && !bs->active[j];
+    }
+    if (!wr) return;   // no block-wide step follows
+    const float beta = (mode == 0 || mode == 3) && !leaves ? (float)bs->beta[j] : 0.0f;
+    const float *y = (bs->its & 1) ? a.rB : a.rA;
+    if (a.B.menr[a.B.pUnitBox[unit]])
+        prolong_b_unit<MB, 12>(a.B, unit, a.NU32, y, a.p, mode, beta, leaves);
     else
-        prolong_b_unit<MB, 6>(B, unit, NU32, y, p, mode, beta);
+        prolong_b_unit<MB, 6>(a.B, unit, a.NU32, y, a.p, mode, beta, leaves);
 }
 
 template <int MB>
-void launch_prolong_b(const RowBoxDev &B, int m, const float *NU32, const float *y, float *p,
-                      int mode, const BatchScalars *bs, cudaStream_t st) {
-    launch_pdl(k_prolong_b<MB>, B.nPUnits, kThreads, 0, st, B, m, NU32, y, p, mode, bs);
+__global__ void __launch_bounds__(kThreads) k_prolong_b(ProlongBArgs a) {
+    prolong_b_body<MB>(a, (int)blockIdx.x);
+}
+
+template <int MB>
+__global__ void __launch_bounds__(kThreads)
+k_prolong_b_sys(const ProlongBArgs *__restrict__ tab, const int *__restrict__ off, int nSys) {
+    const int s = sys_of(off, nSys, (int)blockIdx.x);
+    prolong_b_body<MB>(tab[s], (int)blockIdx.x - __ldg(off + s));
+}
+
+template <int MB>
+void launch_prolong_b(const ProlongBArgs &a, cudaStream_t st) {
+    launch_pdl(k_prolong_b<MB>, a.B.nPUnits, kThreads, 0, st, a);
+}
+
+// one FP32 iteration of every system of the table: four launches
+template <int MB>
+void launch_iteration_sys(const BatchSysTab &t, cudaStream_t st) {
+    const int smem = spmv_smem_bytes<float, 0>();
+    launch_pdl(k_spmm_sys<MB>, t.blocks[0], kSpmvThreads, smem, st, t.spmm, t.off[0], t.nSys);
+    launch_pdl(k_restrict_b_sys<MB>, t.blocks[1], kThreads, 0, st, t.rst, t.off[1], t.nSys);
+    launch_pdl(k_coarse_b_sys<MB>, t.blocks[2], kThreads, 0, st, t.crs, t.off[2], t.nSys);
+    launch_pdl(k_prolong_b_sys<MB>, t.blocks[3], kThreads, 0, st, t.pro, t.off[3], t.nSys);
+}
+
+// ---- column scalars -------------------------------------------------------------
+
+__device__ __forceinline__ void fresh_slot(Scalars *sc) {
+    Scalars z{};
+    z.tol2ff = -1.0;
+    z.max_it = INT_MAX;
+    *sc = z;
+}
+
+__global__ void k_batch_slots(Scalars *slots, unsigned mask) {
+    const int j = threadIdx.x;
+    if (j < kMaxBatch && ((mask >> j) & 1u)) fresh_slot(slots + j);
+}
+
+// repl_j = column j is in mask, fresh reduction slots for them; the
+// replacement's kernels run (done = kRunning) unless a wait has failed
+__global__ void k_batch_open(BatchScalars *bs, Scalars *slots, unsigned mask) {
+    const int j = threadIdx.x;
+    if (j < kMaxBatch) {
+        const int r = (mask >> j) & 1u;
+        bs->repl[j] = r;
+        if (r) fresh_slot(slots + j);
+    }
+    if (j == 0 && bs->done != kFault) bs->done = kRunning;
+}
+
+// the replaced columns' FP64 residuals ||f_j - K u_j||^2 (slot j, scratch 0):
+// a column leaves converged (<= tol^2 ||f_j||^2), not finite, or at its last
+// cycle (iteration limit or max_outer replacements)
+__global__ void k_batch_judge(BatchScalars *bs, const Scalars *slots, int m) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int j = 0; j < m; ++j) {
+        if (!bs->repl[j]) continue;
+        if (slots[j].done == kFault) {
+            bs->fault = 1;
+            bs->done = kFault;
+        }
+        const double rn2 = slots[j].scratch[0];
+        bs->rn2[j] = rn2;
+        bs->cycles[j] += 1;
+        bs->rrRep[j] = bs->rr[j];
+        if (!isfinite(rn2)) {
+            bs->active[j] = 0;
+            bs->outcome[j] = kColBad;
+        } else if (rn2 <= bs->tol * bs->tol * bs->ff[j]) {
+            bs->active[j] = 0;
+        } else if (bs->last[j] || bs->cycles[j] >= bs->max_outer) {
+            bs->active[j] = 0;
+            bs->outcome[j] = kColLimit;
+        }
+    }
+}
+
+// Triggers of the columns being replaced (first: every column, after the
+// start): the next replacement of column j once its recursive residual has
+// dropped by delta (squared: delta2), or to the floor below which the FP32
+// recursion no longer tracks the true residual (a quarter of the target
+// relative to the last replacement's ratio of recursive to true residual),
+// but at least by kMinGroupDrop2; then release them.
+__global__ void k_batch_arm(BatchScalars *bs, int m, int first) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    bool any = false;
+    for (int j = 0; j < m; ++j) {
+        if (first || bs->repl[j]) {
+            if (!bs->active[j]) {
+                bs->trig[j] = -1.0;
+            } else if (first) {
+                bs->trig[j] = bs->delta2 * bs->rr[j];
+            } else {
+                const double sj = bs->scale[j], rr = bs->rr[j], tol = bs->tol;
+                const double gamma2 = rr / (sj * sj * bs->rn2[j]);
+                const double f1 = 0.25 * tol * tol * bs->ff[j] * sj * sj * gamma2;
+                const double f2 = kMinGroupDrop2 * rr;
+                const double floor2 = f2 < f1 ? f2 : f1;
+                const double t = bs->delta2 * rr;
+                bs->trig[j] = floor2 > t ? floor2 : t;
+            }
+            bs->pend[j] = 0;
+            bs->last[j] = 0;
+            bs->repl[j] = 0;
+        }
+        any |= bs->active[j] && !bs->pend[j];
+    }
+    if (bs->done != kFault) bs->done = any ? kRunning : kConverged;
+}
+
+void launch_batch_slots(Scalars *slots, unsigned mask, cudaStream_t st) {
+    k_batch_slots<<<1, 32, 0, st>>>(slots, mask);
+}
+void launch_batch_open(BatchScalars *bs, Scalars *slots, unsigned mask, cudaStream_t st) {
+    k_batch_open<<<1, 32, 0, st>>>(bs, slots, mask);
+}
+void launch_batch_judge(BatchScalars *bs, const Scalars *slots, int m, cudaStream_t st) {
+    k_batch_judge<<<1, 32, 0, st>>>(bs, slots, m);
+}
+void launch_batch_arm(BatchScalars *bs, int m, int first, cudaStream_t st) {
+    k_batch_arm<<<1, 32, 0, st>>>(bs, m, first);
 }
 
 // ---- FP64 <-> FP32 transforms of several columns --------------------------------
 
-// out[(ot[I] + i) * MB + j] = scale_j (L^-1 r_j)_i for the active columns being
-// replaced (repl_j); r_j = r + j * ldr in the caller's numbering (nat).
-// Inactive columns get 0; active columns not being replaced are left as they
-// are.  One thread per (node, column).
+// out[(ot[I] + i) * MB + j] = scale_j (L^-1 r_j)_i for the columns being
+// replaced (repl_j; every column at the start), 0 for those that leave and
+// for padding columns; r_j = r + j * ldr in the caller's numbering (nat).
+// out is the current residual buffer (outA, or outB when its is odd).  One
+// thread per (node, column).
 template <int MB>
 __global__ void k_fwd_scale_b(int nNodes, int m, const int *nat, const int *ot, FacDev F,
                               const double *r, long long ldr, const BatchScalars *bs,
-                              float *out) {
+                              float *outA, float *outB) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= (long long)nNodes * MB) return;
     const int I = (int)(t / MB), j = (int)(t % MB);
+    if (j < m && !bs->repl[j]) return;
+    float *out = (bs->its & 1) ? outB : outA;
     const int b = nat[I + 1] - nat[I], d0 = nat[I], o0 = ot[I];
     const bool on = j < m && bs->active[j];
-    if (on && !bs->repl[j]) return;
     const double sj = on ? bs->scale[j] : 0.0;
     const int q = F.nodeIdx[I];
     with_node_size(b, [&](auto Bc) {
@@ -614,15 +851,15 @@ __global__ void k_fwd_scale_b(int nNodes, int m, const int *nat, const int *ot, 
     });
 }
 
-// u_j += (L^-T ut_j)_i / scale_j for active columns j < m; one thread per
-// (node, column)
+// u_j += (L^-T ut_j)_i / scale_j, then ut_j = 0, for the columns being
+// replaced; one thread per (node, column)
 template <int MB>
 __global__ void k_bwd_accum_b(int nNodes, int m, const int *nat, const int *in, FacDev F,
-                              const float *ut, const BatchScalars *bs, double *u, long long ldu) {
+                              float *ut, const BatchScalars *bs, double *u, long long ldu) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= (long long)nNodes * MB) return;
     const int I = (int)(t / MB), j = (int)(t % MB);
-    if (j >= m || !bs->active[j]) return;
+    if (j >= m || !bs->repl[j]) return;
     const int b = nat[I + 1] - nat[I], d0 = in[I], o0 = nat[I];
     const double inv = 1.0 / bs->scale[j];
     const int q = F.nodeIdx[I];
@@ -630,7 +867,11 @@ __global__ void k_bwd_accum_b(int nNodes, int m, const int *nat, const int *in, 
         constexpr int B = decltype(Bc)::value;
         double x[B];
 #pragma unroll
-        for (int i = 0; i < B; ++i) x[i] = (double)ut[(size_t)(d0 + i) * MB + j];
+        for (int i = 0; i < B; ++i) {
+            float *e = ut + (size_t)(d0 + i) * MB + j;
+            x[i] = (double)*e;
+            *e = 0.0f;
+        }
         bwd_solve_fixed<B>(F, q, x);
 #pragma unroll
         for (int i = 0; i < B; ++i) u[j * ldu + o0 + i] += inv * x[i];
@@ -639,16 +880,16 @@ __global__ void k_bwd_accum_b(int nNodes, int m, const int *nat, const int *in, 
 
 template <int MB>
 void launch_fwd_scale_b(int nNodes, int m, const int *nat, const int *ot, const FacDev &F,
-                        const double *r, long long ldr, const BatchScalars *bs, float *out,
-                        cudaStream_t st) {
+                        const double *r, long long ldr, const BatchScalars *bs, float *outA,
+                        float *outB, cudaStream_t st) {
     const long long nt = (long long)nNodes * MB;
     k_fwd_scale_b<MB><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(nNodes, m, nat, ot, F, r, ldr,
-                                                                     bs, out);
+                                                                     bs, outA, outB);
 }
 
 template <int MB>
 void launch_bwd_accum_b(int nNodes, int m, const int *nat, const int *in, const FacDev &F,
-                        const float *ut, const BatchScalars *bs, double *u, long long ldu,
+                        float *ut, const BatchScalars *bs, double *u, long long ldu,
                         cudaStream_t st) {
     const long long nt = (long long)nNodes * MB;
     k_bwd_accum_b<MB><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(nNodes, m, nat, in, F, ut, bs,
@@ -656,24 +897,17 @@ void launch_bwd_accum_b(int nNodes, int m, const int *nat, const int *in, const 
 }
 
 #define XDCG_BATCH_INST(MB)                                                                    \
-    template void launch_spmm<MB>(const SpmvDev<float> &, int, const float *, float *,          \
-                                  const float *, int, double *, BatchScalars *, int,           \
-                                  cudaStream_t);                                               \
-    template void launch_restrict_b<MB>(const RowBoxDev &, int, float *, const float *,        \
-                                        float *, const float *, const float *, int, double *,  \
-                                        float *, double *, double *, double *, BatchScalars *, \
-                                        cudaStream_t);                                         \
-    template void launch_coarse_b<MB>(const float *, int, int, const float *, const double *,  \
-                                      double *, float *, int, double *, BatchScalars *,        \
-                                      cudaStream_t);                                           \
-    template void launch_prolong_b<MB>(const RowBoxDev &, int, const float *, const float *,   \
-                                       float *, int, const BatchScalars *, cudaStream_t);      \
+    template void launch_spmm<MB>(const SpmmArgs &, cudaStream_t);                             \
+    template void launch_restrict_b<MB>(const RestrictBArgs &, cudaStream_t);                  \
+    template void launch_coarse_b<MB>(const CoarseBArgs &, cudaStream_t);                      \
+    template void launch_prolong_b<MB>(const ProlongBArgs &, cudaStream_t);                    \
+    template void launch_iteration_sys<MB>(const BatchSysTab &, cudaStream_t);                 \
     template void launch_fwd_scale_b<MB>(int, int, const int *, const int *, const FacDev &,   \
                                          const double *, long long, const BatchScalars *,      \
-                                         float *, cudaStream_t);                               \
+                                         float *, float *, cudaStream_t);                      \
     template void launch_bwd_accum_b<MB>(int, int, const int *, const int *, const FacDev &,   \
-                                         const float *, const BatchScalars *, double *,        \
-                                         long long, cudaStream_t);
+                                         float *, const BatchScalars *, double *, long long,    \
+                                         cudaStream_t);
 XDCG_BATCH_INST(4)
 XDCG_BATCH_INST(8)
 #undef XDCG_BATCH_INST

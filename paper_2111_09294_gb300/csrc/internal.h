@@ -75,16 +75,35 @@ constexpr int kXBucket = 8;     // X rows are grouped by len / kXBucket
 constexpr int kMaxBatch = 8;   // right-hand sides per batched solve
 
 // Scalars of a batched FP32 run; column j of every vector is right-hand side j
-// (vectors interleaved: entry (dof d, column j) at d * MB + j).
+// (vectors interleaved: entry (dof d, column j) at d * MB + j).  Columns
+// advance independently: a column whose recursive residual reaches its
+// trigger, whose p^T K p is not positive or that reaches the iteration limit
+// is held (pend) with its vectors carried unchanged while the others keep
+// iterating, until the host replaces its residual; it leaves (active = 0) at
+// a replacement that finds it converged, not finite or out of cycles.  So a
+// column's arithmetic does not depend on the other columns, on the other
+// systems of a launch over several systems, nor on when its replacement runs.
+enum : int { kColOk = 0, kColBad = 1, kColLimit = 2 };
+constexpr double kMinGroupDrop2 = 1e-2;   // (1/10)^2: least drop per replacement cycle
 struct BatchScalars {
     double rho[kMaxBatch], pq[kMaxBatch], alpha[kMaxBatch], beta[kMaxBatch], rr[kMaxBatch];
-    double trig[kMaxBatch];     // a replacement is requested once rr_j <= trig_j
-    double rrRep[kMaxBatch];    // rr_j before the last replacement (restart test)
+    double trig[kMaxBatch];     // column j is held once rr_j <= trig_j
+    double rrRep[kMaxBatch];    // rr_j before its last replacement (restart test)
     double scale[kMaxBatch];    // per-column scale of the FP64 <-> FP32 transforms
-    int active[kMaxBatch];      // 1 while column j iterates
+    double ff[kMaxBatch];       // ||f_j||^2
+    double rn2[kMaxBatch];      // ||f_j - K u_j||^2 at column j's last replacement
+    double tol, delta2;         // relative tolerance; squared inner drop per cycle
+    int active[kMaxBatch];      // 1 until column j leaves
+    int pend[kMaxBatch];        // held until its replacement
+    int last[kMaxBatch];        // held at the iteration limit: its replacement is its last
     int broken[kMaxBatch];      // p_j^T K p_j <= 0 seen (restart at the replacement)
-    int repl[kMaxBatch];        // column j is replaced (or leaves) at this replacement
-    int its, done, max_it, fault;
+    int repl[kMaxBatch];        // replaced by the replacement now running (all at the start)
+    int itsc[kMaxBatch];        // iterations column j has taken
+    int cycles[kMaxBatch];      // replacements of column j
+    int outcome[kMaxBatch];     // kColOk, kColBad (not finite), kColLimit (no convergence)
+    int its;                    // iterations the system ran: residual buffer its & 1 is current
+    int done;                   // kRunning while a column iterates, else kConverged; kFault
+    int max_it, max_outer, fault, pad;
     unsigned int ticket[4];
 };
 
@@ -353,30 +372,86 @@ void launch_scale_W(int nExt, const int *extBox, const int *extNode, const long 
                     const int *menr, const int *dofStart, const FacDev &F, const double *W,
                     float *Wt, cudaStream_t st);
 
-// batched FP32 iteration (batch.cu); MB = 4 or 8
+// ---- batched FP32 iteration (batch.cu); MB = 4 or 8 ------------------------
+//
+// Arguments of one system's batched kernels.  The residual is double
+// buffered: buffer (bs->its & 1 ? rB : rA) is current, so the kernels pick
+// their buffers from the system's own iteration count and one set of
+// arguments serves every iteration.
+struct SpmmArgs {
+    SpmvDev<float> A;
+    int m, fin;                // fin 0: iteration (p_j^T K p_j); 1: start (||b_j - K x_j||^2)
+    const float *x, *b;
+    float *y;
+    double *partials;
+    BatchScalars *bs;
+};
+struct RestrictBArgs {
+    RowBoxDev B;
+    int m, mode;               // 0 iteration; 1 G from the current residual; 2 G = Z~^T f
+    float *u, *rA, *rB;
+    const float *f;            // mode 2 input
+    const float *p, *q;
+    double *G, *ZR, *unitPart, *partials;
+    float *G32;
+    BatchScalars *bs;
+};
+struct CoarseBArgs {
+    const float *Einv, *G32;
+    int k, m, mode;            // 0 nu only; 1 start; 2 iteration; 3 replacement
+    const double *ZR;
+    double *NU, *partials;
+    float *NU32;
+    BatchScalars *bs;
+};
+struct ProlongBArgs {
+    RowBoxDev B;
+    int m, mode;               // 0 iteration; 1 p = Z~ nu; 2 start; 3 replacement
+    const float *NU32, *rA, *rB;
+    float *p;
+    const BatchScalars *bs;
+};
+// One iteration over several systems: per kernel a device table of the
+// systems' arguments and of their first blocks (system s runs blocks
+// off[s] .. off[s + 1] - 1 of a launch of off[nSys] blocks, as block
+// b - off[s] of its own grid).
+struct BatchSysTab {
+    int nSys;
+    const SpmmArgs *spmm;
+    const RestrictBArgs *rst;
+    const CoarseBArgs *crs;
+    const ProlongBArgs *pro;
+    const int *off[4];         // spmm, restriction, coarse, prolongation
+    int blocks[4];
+};
+
 template <int MB>
-void launch_spmm(const SpmvDev<float> &A, int m, const float *x, float *y, const float *b,
-                 int residual_mode, double *partials, BatchScalars *bs, int fin, cudaStream_t st);
+void launch_spmm(const SpmmArgs &a, cudaStream_t st);
 bool spmm_prepare();
 template <int MB>
-void launch_restrict_b(const RowBoxDev &B, int m, float *u, const float *r_cur, float *r_next,
-                       const float *p, const float *q, int mode, double *G, float *G32,
-                       double *ZR, double *unitPart, double *partials, BatchScalars *bs,
-                       cudaStream_t st);
+void launch_restrict_b(const RestrictBArgs &a, cudaStream_t st);
 template <int MB>
-void launch_coarse_b(const float *Einv, int k, int m, const float *G32, const double *ZR,
-                     double *NU, float *NU32, int mode, double *partials, BatchScalars *bs,
-                     cudaStream_t st);
+void launch_coarse_b(const CoarseBArgs &a, cudaStream_t st);
 template <int MB>
-void launch_prolong_b(const RowBoxDev &B, int m, const float *NU32, const float *y, float *p,
-                      int mode, const BatchScalars *bs, cudaStream_t st);
+void launch_prolong_b(const ProlongBArgs &a, cudaStream_t st);
+template <int MB>
+void launch_iteration_sys(const BatchSysTab &t, cudaStream_t st);
+int coarse_b_blocks(int k);
+// column scalars: fresh FP64 reduction slots for the columns in mask; open a
+// replacement of the columns in mask; judge their FP64 residuals; arm the
+// triggers (first: after the start, every column)
+void launch_batch_slots(Scalars *slots, unsigned mask, cudaStream_t st);
+void launch_batch_open(BatchScalars *bs, Scalars *slots, unsigned mask, cudaStream_t st);
+void launch_batch_judge(BatchScalars *bs, const Scalars *slots, int m, cudaStream_t st);
+void launch_batch_arm(BatchScalars *bs, int m, int first, cudaStream_t st);
+// FP64 <-> FP32 transforms of the columns being replaced (repl_j)
 template <int MB>
 void launch_fwd_scale_b(int nNodes, int m, const int *nat, const int *ot, const FacDev &F,
-                        const double *r, long long ldr, const BatchScalars *bs, float *out,
-                        cudaStream_t st);
+                        const double *r, long long ldr, const BatchScalars *bs, float *outA,
+                        float *outB, cudaStream_t st);
 template <int MB>
 void launch_bwd_accum_b(int nNodes, int m, const int *nat, const int *in, const FacDev &F,
-                        const float *ut, const BatchScalars *bs, double *u, long long ldu,
+                        float *ut, const BatchScalars *bs, double *u, long long ldu,
                         cudaStream_t st);
 
 // element sensitivities -lam_e^T Khat_e u_e (sensitivity.cu)

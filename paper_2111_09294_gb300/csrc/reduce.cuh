@@ -41,20 +41,21 @@ __device__ __forceinline__ void block_sum(A (&v)[NV]) {
     }
 }
 
-// Grid-wide sum.  Returns true in exactly one block (the last to finish),
-// where thread 0 then holds the FP64 totals in tot.
-// partials: NV * gridDim.x doubles.
+// Sum over the blocks blk = 0 .. nblk - 1 of one reduction (the launch's
+// blocks, or one system's share of a launch over several systems).  Returns
+// true in exactly one of them (the last to finish), where thread 0 then holds
+// the FP64 totals in tot.  partials: NV * nblk doubles.
 template <typename A, int NV>
-__device__ __forceinline__ bool grid_sum(A (&v)[NV], double *partials, unsigned int *ticket,
-                                         double (&tot)[NV]) {
+__device__ __forceinline__ bool grid_sum_of(A (&v)[NV], double *partials, unsigned int *ticket,
+                                            double (&tot)[NV], int blk, int nblk) {
     __shared__ bool last;
     block_sum<A, NV>(v);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int i = 0; i < NV; ++i) partials[(size_t)i * gridDim.x + blockIdx.x] = (double)v[i];
+        for (int i = 0; i < NV; ++i) partials[(size_t)i * nblk + blk] = (double)v[i];
         __threadfence();
         unsigned int t = atomicAdd(ticket, 1u);
-        last = (t == gridDim.x - 1);
+        last = (t == (unsigned int)nblk - 1);
     }
     __syncthreads();
     if (!last) return false;
@@ -62,9 +63,9 @@ __device__ __forceinline__ bool grid_sum(A (&v)[NV], double *partials, unsigned 
     double s[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) s[i] = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
 #pragma unroll
-        for (int i = 0; i < NV; ++i) s[i] += __ldcg(partials + (size_t)i * gridDim.x + b);
+        for (int i = 0; i < NV; ++i) s[i] += __ldcg(partials + (size_t)i * nblk + b);
     }
     block_sum<double, NV>(s);
     if (threadIdx.x == 0) {
@@ -73,6 +74,13 @@ __device__ __forceinline__ bool grid_sum(A (&v)[NV], double *partials, unsigned 
         *ticket = 0u;
     }
     return true;
+}
+
+// Grid-wide sum over the launch's blocks (see grid_sum_of).
+template <typename A, int NV>
+__device__ __forceinline__ bool grid_sum(A (&v)[NV], double *partials, unsigned int *ticket,
+                                         double (&tot)[NV]) {
+    return grid_sum_of<A, NV>(v, partials, ticket, tot, (int)blockIdx.x, (int)gridDim.x);
 }
 
 // Grid-wide sum of one value already reduced to thread 0 of each block:

@@ -1,15 +1,17 @@
 """Several systems, each with several load cases, solved together: the
 systems of successive crack-front positions in a propagation sweep.
 
-Every system has its own context on its own CUDA stream (its K, Z, block
-factors and coarse operator differ with the crack front), and its load cases
-run as one batched solve on that context.  The systems' calls are issued
-from one host thread each (the library releases the GIL through ctypes and
-blocks only on its own stream), so their kernels overlap on the GPU: the
-small per-system kernels of the FP32 iteration leave most of the GPU idle
-when a system runs alone.  Results are bit-for-bit those of the same solves
-run one after another (fixed partitions and reduction orders in every
-kernel).
+Every system has its own context (its K, Z, block factors and coarse
+operator differ with the crack front), and its load cases run as one batched
+FP32 iteration.  By default (fused) one call runs all systems' batched
+iterations together: every iteration is one launch per kernel over all
+systems' blocks, on the first context's stream, and the host replaces the
+residuals of the columns that ask for it while the others keep iterating.
+The other modes issue each system's own batched solve from a host thread of
+its own (the systems' kernels then overlap on the GPU as their streams
+allow) or one after another.  Every mode gives the same bits per column
+(fixed partitions and reduction orders in every kernel, and columns that
+advance independently).
 """
 import concurrent.futures as cf
 
@@ -25,18 +27,23 @@ def make_solvers(problems, max_batch=8, precision="mixed", **kw):
                                 stream=torch.cuda.Stream(), **kw) for P in problems]
 
 
-def solve_systems(solvers, loads, tol, outs=None, concurrent=True, raise_on_error=True):
+def solve_systems(solvers, loads, tol, outs=None, concurrent=True, raise_on_error=True,
+                  fused=True):
     """solvers[i].solve_batch(loads[i], tol) for every system i.
 
     loads[i]: (m_i, n_i) contiguous CUDA float64 tensor of system i's load
     cases; outs: optional matching output tensors.  Inputs must be ready on
-    the device (the call synchronises the device first).  concurrent=False
-    runs the systems one after another.  Returns [(U_i, infos_i)]."""
+    the device (the call synchronises the device first).  fused (default,
+    for two or more mixed batched contexts): one xdcg_solve_systems call;
+    otherwise concurrent=True runs each system's solve_batch from a thread of
+    its own and concurrent=False one after another.  Returns [(U_i, infos_i)]."""
     if len(solvers) != len(loads):
         raise ValueError("one load tensor per solver")
     outs = outs if outs is not None else [torch.empty_like(F) for F in loads]
     if torch.cuda.is_available():
         torch.cuda.synchronize()
+    if fused and len(solvers) > 1:
+        return _solve_fused(solvers, loads, tol, outs, raise_on_error)
 
     def run(i):
         return solvers[i].solve_batch(loads[i], tol=tol, out=outs[i],
@@ -46,6 +53,38 @@ def solve_systems(solvers, loads, tol, outs=None, concurrent=True, raise_on_erro
         return [run(i) for i in range(len(solvers))]
     with cf.ThreadPoolExecutor(len(solvers)) as ex:
         return list(ex.map(run, range(len(solvers))))
+
+
+def _solve_fused(solvers, loads, tol, outs, raise_on_error):
+    import ctypes
+
+    from . import _lib as L
+    ns = len(solvers)
+    for S, F, U in zip(solvers, loads, outs):
+        if not (F.is_cuda and F.dtype == torch.float64 and F.is_contiguous() and F.dim() == 2
+                and F.shape[1] == S.n and U.shape == F.shape and U.is_contiguous()):
+            raise ValueError(f"expected contiguous (m, {S.n}) CUDA float64 tensors")
+    ctxs = (ctypes.c_void_p * ns)(*[S.ctx.value for S in solvers])
+    fp = (ctypes.c_void_p * ns)(*[F.data_ptr() for F in loads])
+    up = (ctypes.c_void_p * ns)(*[U.data_ptr() for U in outs])
+    ms = (ctypes.c_int32 * ns)(*[F.shape[0] for F in loads])
+    res = (L.Result * sum(F.shape[0] for F in loads))()
+    st = (ctypes.c_int32 * ns)()
+    lib = solvers[0]._lib
+    s = lib.xdcg_solve_systems(ctypes.cast(ctxs, ctypes.c_void_p), ns,
+                               ctypes.cast(fp, ctypes.c_void_p), ctypes.cast(up, ctypes.c_void_p),
+                               ctypes.cast(ms, ctypes.c_void_p), float(tol),
+                               ctypes.cast(res, ctypes.c_void_p), ctypes.cast(st, ctypes.c_void_p))
+    if raise_on_error:
+        L.check(s, "xdcg_solve_systems")
+    out, k = [], 0
+    for i, F in enumerate(loads):
+        infos = [res[k + j].as_dict() for j in range(F.shape[0])]
+        for d in infos:
+            d["status"] = L.STATUS.get(st[i] if s == 0 else s, s)
+        k += F.shape[0]
+        out.append((outs[i], infos))
+    return out
 
 
 def transfer_index(dof_prev, kind_prev, dof_next, kind_next):

@@ -230,6 +230,24 @@ def test_batched_columns_converge_independently():
     s64.close()
 
 
+def test_batched_column_bits_do_not_depend_on_the_other_columns():
+    # columns advance independently (a column at its replacement trigger is
+    # held while the others iterate), so a column's result is the same bits
+    # whatever the other columns of the batch and whatever its position
+    dev = _cuda()
+    P, K, M, C = problem("cube24_ellipse")
+    F = torch.tensor(X.load_cases(P, 4, seed=9), device=dev)
+    s = _solver(P, precision="mixed", max_batch=4)
+    U, infos = s.solve_batch(F, tol=1e-10)
+    U2, infos2 = s.solve_batch(F[[3, 1]].contiguous(), tol=1e-10)
+    U1, infos1 = s.solve_batch(F[2:3].contiguous(), tol=1e-10)
+    assert torch.equal(U2[0], U[3]) and torch.equal(U2[1], U[1]) and torch.equal(U1[0], U[2])
+    for a, b in ((infos2[0], infos[3]), (infos2[1], infos[1]), (infos1[0], infos[2])):
+        assert a["iterations"] == b["iterations"] and a["outer_cycles"] == b["outer_cycles"]
+        assert a["rel_res_true"] == b["rel_res_true"] <= 1e-10
+    s.close()
+
+
 # ---- dJ/dE: the elements' Young's moduli, through the same adjoint solve
 
 

@@ -1,10 +1,11 @@
 """Systems of a propagation sweep solved together: 32^3 hexes with an
 inclined penny whose radius grows from 0.15 to 0.35 (three of the sixteen
-crack-front positions here, of different sizes), four load cases each, every
-system a batched mixed solve on its own context and stream, the systems'
-calls issued concurrently.  Concurrent and one-after-another runs must agree
-bit for bit, every column must meet its tolerance on the FP64 true residual,
-and one system is checked against the oracle."""
+crack-front positions here, of different sizes), a few load cases each,
+every system a batched mixed solve on its own context.  The fused run (one
+launch per kernel over all systems), the concurrent run (one host thread and
+stream per system) and the one-after-another run must agree bit for bit,
+every column must meet its tolerance on the FP64 true residual, and one
+system is checked against the oracle."""
 import numpy as np
 import pytest
 
@@ -15,28 +16,41 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def test_sweep_concurrent_matches_sequential_and_oracle():
+def test_sweep_fused_concurrent_sequential_agree_and_match_oracle():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     dev = torch.device("cuda:0")
     from paper_2111_09294_gb300 import sweep as S
     Ps = X.make_many([X.SWEEP[0], X.SWEEP[7], X.SWEEP[15]], workers=3)
     assert len({P.n for P in Ps}) == 3        # enriched dof counts differ along the sweep
-    loads = [torch.tensor(X.load_cases(P, 4, seed=11 + i), device=dev) for i, P in enumerate(Ps)]
+    # different column counts per system; system 1 has a zero load case
+    ms = (4, 2, 3)
+    loads = [torch.tensor(X.load_cases(P, m, seed=11 + i), device=dev)
+             for i, (P, m) in enumerate(zip(Ps, ms))]
+    loads[1][1].zero_()
     solvers = S.make_solvers(Ps, max_batch=4)
-    conc = S.solve_systems(solvers, loads, 1e-12)
-    seq = S.solve_systems(solvers, loads, 1e-12, concurrent=False)
-    for (Uc, ic), (Us, iq) in zip(conc, seq):
-        assert torch.equal(Uc, Us)
-        assert [i["iterations"] for i in ic] == [i["iterations"] for i in iq]
-        assert all(i["rel_res_true"] <= 1e-12 for i in ic)
+    fused = S.solve_systems(solvers, loads, 1e-12)
+    conc = S.solve_systems(solvers, loads, 1e-12, fused=False)
+    seq = S.solve_systems(solvers, loads, 1e-12, concurrent=False, fused=False)
+    for (Uf, jf), (Uc, ic), (Us, iq) in zip(fused, conc, seq):
+        assert torch.equal(Uf, Uc) and torch.equal(Uc, Us)
+        its = [i["iterations"] for i in jf]
+        assert its == [i["iterations"] for i in ic] == [i["iterations"] for i in iq]
+        assert [i["outer_cycles"] for i in jf] == [i["outer_cycles"] for i in iq]
+        assert all(i["rel_res_true"] <= 1e-12 for i in jf)
+        assert all(i["status"] == "XDCG_OK" for i in jf)
+    assert torch.all(fused[1][0][1] == 0) and fused[1][1][1]["iterations"] == 0
     P = Ps[2]
     K, M, C = O.setup(P)
     F = loads[2].cpu().numpy()
-    for j in (0, 3):
+    for j in (0, 2):
         ref = O.adef2_pcg(K, F[j], M, C, tol=1e-12)
-        err = np.linalg.norm(conc[2][0][j].cpu().numpy() - ref.u) / np.linalg.norm(ref.u)
+        err = np.linalg.norm(fused[2][0][j].cpu().numpy() - ref.u) / np.linalg.norm(ref.u)
         assert err <= 1e-7, (j, err)
+    # a context passed twice shares one set of scalars: refused
+    from paper_2111_09294_gb300._lib import XdcgError
+    with pytest.raises(XdcgError, match="INVALID_ARG"):
+        S.solve_systems([solvers[0], solvers[0]], [loads[0], loads[0].clone()], 1e-8)
     for s in solvers:
         s.close()
 
