@@ -32,6 +32,7 @@ struct Level64 {
 };
 struct Level32 {          // block-scaled system K~ = L^-1 K L^-T in FP32
     SpmvDev<float> A;
+    SpmvDev<float> Ab;        // the same matrix with the batched product's persistent grid
     RowBoxDev R;
     RowBoxDev Rb;            // the same boxes with the batched kernels' unit tables
     FacDev F;
@@ -750,14 +751,15 @@ struct BatchRun {
     ProlongBArgs pro{};
 };
 
+int g_ld(const xdcg_ctx *c) { return (std::max(c->k, 1) + 3) & ~3; }
 RestrictBArgs restrict_args(xdcg_ctx *c, int m, int mode) {
     return RestrictBArgs{c->L32.Rb, m, mode, c->bU32, c->bRA, c->bRB, c->bF32, c->bP, c->bQ,
                          c->bG, mode == 2 ? nullptr : c->bZR, c->bUnitPart, c->partials,
-                         c->bG32, c->bs};
+                         c->bG32, g_ld(c), c->bs};
 }
 CoarseBArgs coarse_args(xdcg_ctx *c, int m, int mode) {
-    return CoarseBArgs{c->Einv32, c->bG32, c->k, m, mode, mode == 0 ? nullptr : c->bZR,
-                       c->bNU, c->partials, c->bNU32, c->bs};
+    return CoarseBArgs{c->Einv32, c->bG32, c->k, m, mode, g_ld(c), mode == 0 ? nullptr : c->bZR,
+                       c->bNU, c->partials, c->bNU32, c->bs, c->L32.A.waitNs};
 }
 ProlongBArgs prolong_args(xdcg_ctx *c, int m, int mode) {
     return ProlongBArgs{c->L32.Rb, m, mode, c->bNU32, c->bRA, c->bRB,
@@ -805,13 +807,13 @@ xdcg_status batch_start(BatchRun &R, cudaStream_t st) {
     launch_restrict_b<MB>(restrict_args(c, m, 2), st);
     launch_coarse_b<MB>(coarse_args(c, m, 0), st);
     launch_prolong_b<MB>(prolong_args(c, m, 1), st);
-    launch_spmm<MB>(SpmmArgs{L.A, m, 1, c->bU32, c->bF32, c->bRA, c->partials, c->bs}, st);
+    launch_spmm<MB>(SpmmArgs{L.Ab, m, 1, c->bU32, c->bF32, c->bRA, c->partials, c->bs}, st);
     launch_restrict_b<MB>(restrict_args(c, m, 1), st);
     launch_coarse_b<MB>(coarse_args(c, m, 1), st);
     launch_prolong_b<MB>(prolong_args(c, m, 2), st);
     launch_batch_arm(c->bs, m, 1, st);
     c->launches += 10;
-    R.spmm = SpmmArgs{L.A, m, 0, c->bP, nullptr, c->bQ, c->partials, c->bs};
+    R.spmm = SpmmArgs{L.Ab, m, 0, c->bP, nullptr, c->bQ, c->partials, c->bs};
     R.rst = restrict_args(c, m, 0);
     R.crs = coarse_args(c, m, 2);
     R.pro = prolong_args(c, m, 0);
@@ -923,7 +925,7 @@ xdcg_status sys_tables_build(SysTables &T, BatchRun *runs, int nSys, cudaStream_
         hp[i] = R.pro;
         off[0][i + 1] = off[0][i] + R.spmm.A.grid;
         off[1][i + 1] = off[1][i] + R.rst.B.nUnits;
-        off[2][i + 1] = off[2][i] + coarse_b_blocks(R.crs.k);
+        off[2][i + 1] = off[2][i] + coarse_b_blocks(R.crs.k, R.c->bMB);
         off[3][i + 1] = off[3][i] + R.pro.B.nPUnits;
         ++i;
     }
@@ -1930,6 +1932,17 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
                                       &c->info.spmv_shape_fp32);
             if (ts != XDCG_OK) return ts;
         }
+        if (c->opt.max_batch > 0) {
+            // the batched product's own persistent grid (its registers and
+            // stages set its blocks per SM) and step-balanced warp ranges
+            auto &Ab = c->L32.Ab;
+            Ab = A2;
+            Ab.grid = spmm_persistent_grid(c->opt.max_batch <= 4 ? 4 : 8,
+                                           HS32.nSlices + HX32.nSlices);
+            if (Ab.grid < 1) return XDCG_CUDA_ERROR;
+            Ab.warpSlice = partition(HS32, HX32, Ab.grid);
+            if (!Ab.warpSlice) return XDCG_OOM;
+        }
         launch_build_Zt(N, d_own, d_dof, d_sub, d_x64, d_hs, d_menr, zv, F, d_zOff, d_Zt, st);
         launch_scale_W(nExt, d_extBox, d_extNode, d_wOff, d_menr, d_dof, F, d_W, d_Wt, st);
         // row-parallel layouts: own rows (Z~) and coupled rows (W~) of each box,
@@ -2159,7 +2172,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         c->bF32 = dalloc<float>(c, nv); c->bU32 = dalloc<float>(c, nv);
         c->bRA = dalloc<float>(c, nv); c->bRB = dalloc<float>(c, nv);
         c->bP = dalloc<float>(c, nv); c->bQ = dalloc<float>(c, nv);
-        c->bG32 = dalloc<float>(c, kv); c->bNU32 = dalloc<float>(c, kv);
+        c->bG32 = dalloc<float>(c, (size_t)g_ld(c) * MB); c->bNU32 = dalloc<float>(c, kv);
         c->bG = dalloc<double>(c, kv); c->bZR = dalloc<double>(c, kv); c->bNU = dalloc<double>(c, kv);
         c->bUnitPart = dalloc<double>(c, (size_t)c->L32.Rb.nUnits * MB * 24);
         c->bR64 = dalloc<double>(c, (size_t)n * MB);
@@ -2169,6 +2182,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
             !c->bNU32 || !c->bG || !c->bZR || !c->bNU || !c->bUnitPart || !c->bR64 || !c->bs ||
             !c->bSlots)
             return XDCG_OOM;
+        CK(cudaMemsetAsync(c->bG32, 0, (size_t)g_ld(c) * MB * sizeof(float), st));
         if (cudaMallocHost(&c->h_bs, sizeof(BatchScalars)) != cudaSuccess) return XDCG_OOM;
         if (cudaMallocHost(&c->h_slots, sizeof(Scalars) * kMaxBatch) != cudaSuccess)
             return XDCG_OOM;

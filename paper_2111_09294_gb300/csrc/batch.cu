@@ -17,6 +17,7 @@
 // system, so the same body runs as a launch for one system or as one launch
 // over several systems (BatchSysTab): a column's result is the same bits
 // either way.
+#include <algorithm>
 #include <climits>
 
 #include "cache.cuh"
@@ -279,13 +280,13 @@ __device__ __forceinline__ void spmm_body(const SpmmArgs &args, int blk, int nbl
 }
 
 template <int MB, bool RES>
-__global__ void __launch_bounds__(kSpmvThreads) k_spmm(SpmmArgs a) {
+__global__ void __launch_bounds__(kSpmvThreads, 3) k_spmm(SpmmArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     spmm_body<MB, RES>(a, (int)blockIdx.x, (int)gridDim.x, smem);
 }
 
 template <int MB>
-__global__ void __launch_bounds__(kSpmvThreads)
+__global__ void __launch_bounds__(kSpmvThreads, 3)
 k_spmm_sys(const SpmmArgs *__restrict__ tab, const int *__restrict__ off, int nSys) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int s = sys_of(off, nSys, (int)blockIdx.x);
@@ -305,12 +306,20 @@ static bool set_smem(K k, int smem) {
            cudaSuccess;
 }
 
-bool spmm_prepare() {
+int spmm_persistent_grid(int MB, int nSlicesTotal) {
+    if (!spmm_prepare()) return -1;
+    int dev = 0, sms = device_sm_count(), nb = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || sms < 1) return -1;
     const int smem = spmv_smem_bytes<float, 0>();
-    return set_smem(k_spmm<4, false>, smem) && set_smem(k_spmm<4, true>, smem) &&
-           set_smem(k_spmm<8, false>, smem) && set_smem(k_spmm<8, true>, smem) &&
-           set_smem(k_spmm_sys<4>, smem) && set_smem(k_spmm_sys<8>, smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &nb, MB == 4 ? k_spmm<4, false> : k_spmm<8, false>, kSpmvThreads, smem) !=
+            cudaSuccess ||
+        nb < 1)
+        return -1;
+    const int need = (nSlicesTotal + kSpmvWarps - 1) / kSpmvWarps;
+    return std::max(1, std::min(nb * sms, need));
 }
+
 
 // ---- batched restriction + update ---------------------------------------------
 
@@ -415,7 +424,7 @@ __device__ __forceinline__ void restrict_b_unit(const RestrictBArgs &a, int unit
             const int jj = threadIdx.x / M, c = threadIdx.x % M;
             const double zs = red[jj][c], ws = red[jj][M + c];
             G[(size_t)(c0 + c) * MB + jj] = zs - ws;
-            G32[(size_t)(c0 + c) * MB + jj] = (float)(zs - ws);
+            G32[(size_t)jj * a.gld + c0 + c] = (float)(zs - ws);
             if (ZR) ZR[(size_t)(c0 + c) * MB + jj] = zs;
         }
     } else {
@@ -436,7 +445,7 @@ __device__ __forceinline__ void restrict_b_unit(const RestrictBArgs &a, int unit
                     ws += __ldcg(unitPart + ((size_t)v * MB + jj) * 24 + M + c);
                 }
                 G[(size_t)(c0 + c) * MB + jj] = zs - ws;
-                G32[(size_t)(c0 + c) * MB + jj] = (float)(zs - ws);
+                G32[(size_t)jj * a.gld + c0 + c] = (float)(zs - ws);
                 if (ZR) ZR[(size_t)(c0 + c) * MB + jj] = zs;
             }
             if (threadIdx.x == 0) B.boxTicket[s] = 0u;
@@ -518,120 +527,233 @@ void launch_restrict_b(const RestrictBArgs &a, cudaStream_t st) {
 
 // ---- batched coarse solve NU = E^-1 G -----------------------------------------
 
-constexpr int kCoarseChunkB = 1024;
-constexpr int kCoarsePadB = kCoarseChunkB + 4;   // row pitch of the transposed G chunk
+// Sums NV values over the warp's lanes by halving exchanges (fixed tree):
+// afterwards lane L holds in v[0 .. NV / 32) the totals of values
+// (NV / 32) L + i.
+template <int NV>
+__device__ __forceinline__ void lane_reduce_scatter(float (&v)[NV], int lane) {
+    static_assert(NV >= 32 && NV % 32 == 0, "NV: a multiple of 32");
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+        const int o = 16 >> st, half = (NV >> st) >> 1;
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float send = hi ? v[i] : v[i + half];
+            const float keep = hi ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+}
 
-// mode 0: nu only; mode 1 (start, every column): rho_j = rr_j + nu_j^T zr_j,
-// beta_j = 0; mode 2 (iteration, running columns): the same rho_new, beta_j =
-// rho_new / rho_j; mode 3 (replacement, the replaced columns): as 2, with
-// beta_j = 0 for a column that leaves, that broke down or whose residual the
-// replacement lengthened by more than 2x.  One warp per row of E^-1 (16-byte
-// loads when k is a multiple of 4); G staged in shared memory chunk by chunk,
-// transposed (one padded row per column), so a lane's four consecutive
-// entries of a column are one conflict-free 16-byte load.
+// rows of E^-1 per block of the batched coarse solve (RB * MB = 32 partial
+// sums per lane)
+template <int MB>
+__host__ __device__ constexpr int coarse_rows_b() { return 32 / MB; }
+constexpr int kCoarseChunkB = 128;   // columns of G per staged chunk (4 per lane)
+template <int MB>
+constexpr int coarse_smem_b() {
+    return kWarps * 2 * MB * kCoarseChunkB * (int)sizeof(float) +
+           kWarps * 2 * (int)sizeof(uint64_t);
+}
+
+// One chunk's entries of E^-1 for a lane: 4 consecutive columns (one 16-byte
+// load per row, V = 4) or 4 columns 32 apart (V = 1) of each of the RB rows.
+template <int RB, int V>
+__device__ __forceinline__ void coarse_load_e(const float *Eb, int k, int rLast, int lc, int clen,
+                                              int lane, uint64_t keep, float (&e)[RB][4]) {
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+        const float *row = Eb + (size_t)min(r, rLast) * k + lc;
+        if (V == 4) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (4 * lane < clen) v = ld_keep(reinterpret_cast<const float4 *>(row + 4 * lane), keep);
+            e[r][0] = v.x;
+            e[r][1] = v.y;
+            e[r][2] = v.z;
+            e[r][3] = v.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                e[r][q] = lane + 32 * q < clen ? ld_keep(row + lane + 32 * q, keep) : 0.0f;
+        }
+    }
+}
+
+// NU = E^-1 G for the MB columns, then the scalars.  mode 0: nu only; mode 1
+// (start, every column): rho_j = rr_j + nu_j^T zr_j, beta_j = 0; mode 2
+// (iteration, running columns): the same rho_new, beta_j = rho_new / rho_j;
+// mode 3 (replacement, the replaced columns): as 2, with beta_j = 0 for a
+// column that leaves, that broke down or whose residual the replacement
+// lengthened by more than 2x.  A block takes 32 / MB consecutive rows of
+// E^-1 and its warps split the columns into segments (multiples of 4).  Each
+// warp walks its segment in chunks of kCoarseChunkB columns: the chunk's
+// part of G (stored column by column) is staged in shared memory by bulk
+// copies, double-buffered (the next chunk's copy is in flight while this one
+// is used), and the lane's entries of E^-1 are loaded before the wait for
+// the chunk's copy (the first chunk's before the wait for the previous
+// kernel: E^-1 does not depend on it), so a chunk costs one memory round
+// trip.  The partial sums are reduced over the lanes, then over the warps in
+// order.
 template <int MB, int V>
 __device__ __forceinline__ void coarse_b_body(const CoarseBArgs &a, int blk, int nblk,
-                                              float *gs) {
+                                              unsigned char *smem) {
+    constexpr int RB = coarse_rows_b<MB>(), NV = RB * MB, P = NV / 32, CH = kCoarseChunkB;
+    __shared__ float red[kWarps][NV];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *gs = reinterpret_cast<float *>(smem) + (size_t)warp * 2 * MB * CH;   // [2][MB][CH]
+    uint64_t *bar =
+        reinterpret_cast<uint64_t *>(smem + (size_t)kWarps * 2 * MB * CH * sizeof(float)) +
+        2 * warp;
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    const int k = a.k;
+    const int i0 = blk * RB;
+    const int seg = (k + 4 * kWarps - 1) / (4 * kWarps) * 4;
+    const int l0 = warp * seg, l1 = min(k, l0 + seg);
+    const int nch = l1 > l0 ? (l1 - l0 + CH - 1) / CH : 0;
+    const uint64_t keep = l2_keep_policy();
+    const float *Eb = a.Einv + (size_t)i0 * k;
+    const int rLast = k - 1 - i0;
+    float e[RB][4];
+    if (nch > 0) coarse_load_e<RB, V>(Eb, k, rLast, l0, min(CH, l1 - l0), lane, keep, e);
     pdl_wait();
     BatchScalars *bs = a.bs;
     if (bs->done != kRunning) return;
-    const int k = a.k, m = a.m, mode = a.mode;
-    const float *__restrict__ G32 = a.G32;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blk * kWarps + warp;
-    const float *row = a.Einv + (size_t)(i < k ? i : 0) * k;
-    const uint64_t keep = l2_keep_policy();
-    float acc[MB];
+    const int m = a.m, mode = a.mode;
+    const unsigned long long deadline = global_ns() + a.waitNs;
+    auto issue = [&](int c) {   // lane 0: chunk c of G into buffer c & 1
+        const int lc = l0 + c * CH, cpad = (min(CH, l1 - lc) + 3) & ~3;
+        float *dst = gs + (c & 1) * MB * CH;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar + (c & 1), (uint32_t)(MB * cpad * sizeof(float)));
 #pragma unroll
-    for (int j = 0; j < MB; ++j) acc[j] = 0.0f;
-    for (int l0 = 0; l0 < k; l0 += kCoarseChunkB) {
-        const int len = min(kCoarseChunkB, k - l0);
-        __syncthreads();
-        for (int e = threadIdx.x; e < len * MB; e += blockDim.x)
-            gs[(e % MB) * kCoarsePadB + e / MB] = G32[(size_t)l0 * MB + e];
-        __syncthreads();
-        if (i >= k) continue;
-        if (V == 4) {
-            const float4 *r4 = reinterpret_cast<const float4 *>(row + l0);
-#pragma unroll 4
-            for (int l4 = lane; 4 * l4 < len; l4 += 32) {
-                const float4 ev = ld_keep(r4 + l4, keep);
+        for (int j = 0; j < MB; ++j)
+            bulk_g2s(dst + j * CH, a.G32 + (size_t)j * a.gld + lc, (uint32_t)(cpad * sizeof(float)),
+                     bar + (c & 1), keep);
+    };
+    float acc[NV];
 #pragma unroll
-                for (int j = 0; j < MB; ++j) {
-                    const float4 g = *reinterpret_cast<const float4 *>(gs + j * kCoarsePadB + 4 * l4);
-                    float t = fmaf(ev.x, g.x, acc[j]);
-                    t = fmaf(ev.y, g.y, t);
-                    t = fmaf(ev.z, g.z, t);
-                    acc[j] = fmaf(ev.w, g.w, t);
-                }
-            }
-        } else {
-#pragma unroll 4
-            for (int l = lane; l < len; l += 32) {
-                const float ev = ld_keep(row + l0 + l, keep);
-#pragma unroll
-                for (int j = 0; j < MB; ++j) acc[j] = fmaf(ev, gs[j * kCoarsePadB + l], acc[j]);
-            }
-        }
-    }
-    warp_sum<float, MB>(acc);
-    double part[MB];
-#pragma unroll
-    for (int j = 0; j < MB; ++j) part[j] = 0.0;
-    if (i < k && lane == 0) {
+    for (int t = 0; t < NV; ++t) acc[t] = 0.0f;
+    if (lane == 0 && nch > 0) issue(0);
+    int c = 0;
+    bool ok = true;
+    for (; c < nch; ++c) {
+        if (lane == 0 && c + 1 < nch) issue(c + 1);
+        const int lc = l0 + c * CH, clen = min(CH, l1 - lc);
+        if (c > 0) coarse_load_e<RB, V>(Eb, k, rLast, lc, clen, lane, keep, e);
+        ok = __all_sync(0xffffffffu, mbar_wait(bar + (c & 1), (uint32_t)(c >> 1) & 1u, deadline));
+        if (!ok) break;
+        const float *g0 = gs + (c & 1) * MB * CH;
 #pragma unroll
         for (int j = 0; j < MB; ++j) {
-            a.NU[(size_t)i * MB + j] = (double)acc[j];
-            a.NU32[(size_t)i * MB + j] = acc[j];
-            if (mode != 0) part[j] = (double)acc[j] * a.ZR[(size_t)i * MB + j];
+            float g[4];
+            // entries past the chunk are never read (shared memory there may
+            // hold anything, and 0 * NaN is NaN)
+            if (V == 4) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (4 * lane < clen) v = *reinterpret_cast<const float4 *>(g0 + j * CH + 4 * lane);
+                g[0] = v.x;
+                g[1] = v.y;
+                g[2] = v.z;
+                g[3] = v.w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    g[q] = lane + 32 * q < clen ? g0[j * CH + lane + 32 * q] : 0.0f;
+            }
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                float t = fmaf(e[r][0], g[0], acc[r * MB + j]);
+                t = fmaf(e[r][1], g[1], t);
+                t = fmaf(e[r][2], g[2], t);
+                acc[r * MB + j] = fmaf(e[r][3], g[3], t);
+            }
         }
+        __syncwarp();   // the buffer is read before a later copy overwrites it
+    }
+    if (!ok) {
+        // copies in flight (chunks c and c + 1) land before the block leaves
+        const unsigned long long drain = global_ns() + kDrainNs;
+        for (int d = c; d < min(nch, c + 2); ++d) mbar_wait(bar + (d & 1), (uint32_t)(d >> 1) & 1u, drain);
+        __syncwarp();
+        if (lane == 0) atomicExch(&bs->fault, 1);
+    }
+    lane_reduce_scatter<NV>(acc, lane);
+#pragma unroll
+    for (int i = 0; i < P; ++i) red[warp][P * lane + i] = acc[i];
+    __syncthreads();
+    // warp 0 (lane = r * MB + j): nu_i for row i = i0 + r, column j, and its
+    // share of nu_j^T zr_j, summed over the block's rows
+    static_assert(NV == 32, "one lane per (row, column) of the block");
+    double pj = 0.0;
+    if (warp == 0) {
+        float sum = 0.0f;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) sum += red[w][lane];
+        const int r = lane / MB, j = lane % MB, i = i0 + r;
+        if (i < k) {
+            a.NU[(size_t)i * MB + j] = (double)sum;
+            a.NU32[(size_t)i * MB + j] = sum;
+            if (mode != 0) pj = (double)sum * a.ZR[(size_t)i * MB + j];
+        }
+#pragma unroll
+        for (int o = MB; o < 32; o <<= 1) pj += __shfl_xor_sync(0xffffffffu, pj, o);
     }
     double tot[MB];
-    if (grid_sum_of<double, MB>(part, a.partials, &bs->ticket[3], tot, blk, nblk) &&
-        threadIdx.x == 0 && mode != 0) {
-        for (int j = 0; j < m; ++j) {
-            const bool upd = mode == 2 ? col_runs(bs, j, m) : (mode == 1 || bs->repl[j]);
-            if (!upd) continue;
-            const double rho_new = bs->rr[j] + tot[j];
-            if (mode == 1 || !bs->active[j] ||
-                (mode == 3 && (bs->broken[j] || bs->rr[j] > 4.0 * bs->rrRep[j])))
-                bs->beta[j] = 0.0;
-            else
-                bs->beta[j] = rho_new / bs->rho[j];
-            bs->rho[j] = rho_new;
-            if (mode == 3) bs->broken[j] = 0;
+    if (grid_sum_lanes<MB>(pj, a.partials, &bs->ticket[3], tot, blk, nblk) && threadIdx.x == 0) {
+        if (bs->fault) {
+            bs->done = kFault;
+        } else if (mode != 0) {
+            for (int j = 0; j < m; ++j) {
+                const bool upd = mode == 2 ? col_runs(bs, j, m) : (mode == 1 || bs->repl[j]);
+                if (!upd) continue;
+                const double rho_new = bs->rr[j] + tot[j];
+                if (mode == 1 || !bs->active[j] ||
+                    (mode == 3 && (bs->broken[j] || bs->rr[j] > 4.0 * bs->rrRep[j])))
+                    bs->beta[j] = 0.0;
+                else
+                    bs->beta[j] = rho_new / bs->rho[j];
+                bs->rho[j] = rho_new;
+                if (mode == 3) bs->broken[j] = 0;
+            }
         }
     }
 }
 
 template <int MB, int V>
-__global__ void __launch_bounds__(kThreads) k_coarse_b(CoarseBArgs a) {
-    __shared__ __align__(16) float gs[MB * kCoarsePadB];
-    coarse_b_body<MB, V>(a, (int)blockIdx.x, (int)gridDim.x, gs);
+__global__ void __launch_bounds__(kThreads, MB == 8 ? 3 : 2) k_coarse_b(CoarseBArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    coarse_b_body<MB, V>(a, (int)blockIdx.x, (int)gridDim.x, smem);
 }
 
 template <int MB>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, MB == 8 ? 3 : 2)
 k_coarse_b_sys(const CoarseBArgs *__restrict__ tab, const int *__restrict__ off, int nSys) {
-    __shared__ __align__(16) float gs[MB * kCoarsePadB];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int s = sys_of(off, nSys, (int)blockIdx.x);
     const int b0 = __ldg(off + s), nb = __ldg(off + s + 1) - b0;
     const CoarseBArgs &a = tab[s];
     if ((a.k & 3) == 0)
-        coarse_b_body<MB, 4>(a, (int)blockIdx.x - b0, nb, gs);
+        coarse_b_body<MB, 4>(a, (int)blockIdx.x - b0, nb, smem);
     else
-        coarse_b_body<MB, 1>(a, (int)blockIdx.x - b0, nb, gs);
+        coarse_b_body<MB, 1>(a, (int)blockIdx.x - b0, nb, smem);
 }
 
-int coarse_b_blocks(int k) {
-    const int grid = (k + kWarps - 1) / kWarps;
+int coarse_b_blocks(int k, int MB) {
+    const int rb = MB == 4 ? coarse_rows_b<4>() : coarse_rows_b<8>();
+    const int grid = (k + rb - 1) / rb;
     return grid > 0 ? grid : 1;
 }
 
 template <int MB>
 void launch_coarse_b(const CoarseBArgs &a, cudaStream_t st) {
-    launch_pdl(a.k % 4 == 0 ? k_coarse_b<MB, 4> : k_coarse_b<MB, 1>, coarse_b_blocks(a.k),
-               kThreads, 0, st, a);
+    launch_pdl(a.k % 4 == 0 ? k_coarse_b<MB, 4> : k_coarse_b<MB, 1>, coarse_b_blocks(a.k, MB),
+               kThreads, coarse_smem_b<MB>(), st, a);
 }
 
 // ---- batched prolongation -----------------------------------------------------
@@ -717,7 +839,8 @@ void launch_iteration_sys(const BatchSysTab &t, cudaStream_t st) {
     const int smem = spmv_smem_bytes<float, 0>();
     launch_pdl(k_spmm_sys<MB>, t.blocks[0], kSpmvThreads, smem, st, t.spmm, t.off[0], t.nSys);
     launch_pdl(k_restrict_b_sys<MB>, t.blocks[1], kThreads, 0, st, t.rst, t.off[1], t.nSys);
-    launch_pdl(k_coarse_b_sys<MB>, t.blocks[2], kThreads, 0, st, t.crs, t.off[2], t.nSys);
+    launch_pdl(k_coarse_b_sys<MB>, t.blocks[2], kThreads, coarse_smem_b<MB>(), st, t.crs, t.off[2],
+               t.nSys);
     launch_pdl(k_prolong_b_sys<MB>, t.blocks[3], kThreads, 0, st, t.pro, t.off[3], t.nSys);
 }
 
@@ -894,6 +1017,20 @@ void launch_bwd_accum_b(int nNodes, int m, const int *nat, const int *in, const 
     const long long nt = (long long)nNodes * MB;
     k_bwd_accum_b<MB><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(nNodes, m, nat, in, F, ut, bs,
                                                                      u, ldu);
+}
+
+// dynamic shared memory limits of the batched kernels (once per process)
+bool spmm_prepare() {
+    const int smem = spmv_smem_bytes<float, 0>();
+    return set_smem(k_spmm<4, false>, smem) && set_smem(k_spmm<4, true>, smem) &&
+           set_smem(k_spmm<8, false>, smem) && set_smem(k_spmm<8, true>, smem) &&
+           set_smem(k_spmm_sys<4>, smem) && set_smem(k_spmm_sys<8>, smem) &&
+           set_smem(k_coarse_b<4, 4>, coarse_smem_b<4>()) &&
+           set_smem(k_coarse_b<4, 1>, coarse_smem_b<4>()) &&
+           set_smem(k_coarse_b<8, 4>, coarse_smem_b<8>()) &&
+           set_smem(k_coarse_b<8, 1>, coarse_smem_b<8>()) &&
+           set_smem(k_coarse_b_sys<4>, coarse_smem_b<4>()) &&
+           set_smem(k_coarse_b_sys<8>, coarse_smem_b<8>());
 }
 
 #define XDCG_BATCH_INST(MB)                                                                    \

@@ -393,16 +393,19 @@ struct RestrictBArgs {
     const float *f;            // mode 2 input
     const float *p, *q;
     double *G, *ZR, *unitPart, *partials;
-    float *G32;
+    float *G32;                // column j at G32 + j * gld (the coarse solve stages it)
+    int gld;                   // a multiple of 4, >= k
     BatchScalars *bs;
 };
 struct CoarseBArgs {
     const float *Einv, *G32;
     int k, m, mode;            // 0 nu only; 1 start; 2 iteration; 3 replacement
+    int gld;
     const double *ZR;
     double *NU, *partials;
     float *NU32;
     BatchScalars *bs;
+    unsigned long long waitNs; // limit of the bounded waits on the bulk copies of G
 };
 struct ProlongBArgs {
     RowBoxDev B;
@@ -428,6 +431,8 @@ struct BatchSysTab {
 template <int MB>
 void launch_spmm(const SpmmArgs &a, cudaStream_t st);
 bool spmm_prepare();
+// persistent grid of the batched product (resident blocks per SM x SMs); < 0 on error
+int spmm_persistent_grid(int MB, int nSlicesTotal);
 template <int MB>
 void launch_restrict_b(const RestrictBArgs &a, cudaStream_t st);
 template <int MB>
@@ -436,7 +441,7 @@ template <int MB>
 void launch_prolong_b(const ProlongBArgs &a, cudaStream_t st);
 template <int MB>
 void launch_iteration_sys(const BatchSysTab &t, cudaStream_t st);
-int coarse_b_blocks(int k);
+int coarse_b_blocks(int k, int MB);
 // column scalars: fresh FP64 reduction slots for the columns in mask; open a
 // replacement of the columns in mask; judge their FP64 residuals; arm the
 // triggers (first: after the start, every column)

@@ -41,6 +41,60 @@ __device__ __forceinline__ void block_sum(A (&v)[NV]) {
     }
 }
 
+// The last block's share of a grid-wide sum: value i of the nblk blocks'
+// partials (partials[i * nblk + b]) added by one warp, its lanes striding
+// over the blocks with four accumulators each, then across the lanes (a fixed
+// order, and FP64 work spread over the warps: FP64 arithmetic is slow here).
+// Thread 0 gets the totals and resets the ticket.
+template <int NV>
+__device__ __forceinline__ void sum_partials(const double *partials, unsigned int *ticket,
+                                             double (&tot)[NV], int nblk) {
+    __shared__ double fin[NV];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = w; i < NV; i += nw) {
+        const double *p = partials + (size_t)i * nblk;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int b = l;
+        for (; b + 96 < nblk; b += 128) {
+            s0 += __ldcg(p + b);
+            s1 += __ldcg(p + b + 32);
+            s2 += __ldcg(p + b + 64);
+            s3 += __ldcg(p + b + 96);
+        }
+        for (; b < nblk; b += 32) s0 += __ldcg(p + b);
+        double s = (s0 + s1) + (s2 + s3);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (l == 0) fin[i] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) tot[i] = fin[i];
+        *ticket = 0u;
+    }
+}
+
+// Grid-wide sum of NV <= 32 values whose block totals lanes 0 .. NV - 1 of
+// warp 0 already hold (one per lane, in v): as grid_sum_of without the block
+// reduction.  Every thread of the block calls it.
+template <int NV>
+__device__ __forceinline__ bool grid_sum_lanes(double v, double *partials, unsigned int *ticket,
+                                               double (&tot)[NV], int blk, int nblk) {
+    __shared__ bool last;
+    if (threadIdx.x < 32) {
+        if ((int)threadIdx.x < NV) partials[(size_t)threadIdx.x * nblk + blk] = v;
+        __threadfence();
+        __syncwarp();
+        if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == (unsigned int)nblk - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    sum_partials<NV>(partials, ticket, tot, nblk);
+    return true;
+}
+
 // Sum over the blocks blk = 0 .. nblk - 1 of one reduction (the launch's
 // blocks, or one system's share of a launch over several systems).  Returns
 // true in exactly one of them (the last to finish), where thread 0 then holds
@@ -60,19 +114,7 @@ __device__ __forceinline__ bool grid_sum_of(A (&v)[NV], double *partials, unsign
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    double s[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) s[i] = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-#pragma unroll
-        for (int i = 0; i < NV; ++i) s[i] += __ldcg(partials + (size_t)i * nblk + b);
-    }
-    block_sum<double, NV>(s);
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int i = 0; i < NV; ++i) tot[i] = s[i];
-        *ticket = 0u;
-    }
+    sum_partials<NV>(partials, ticket, tot, nblk);
     return true;
 }
 
