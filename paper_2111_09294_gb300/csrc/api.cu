@@ -1988,8 +1988,10 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
             !R.wBase || !Zcm || !Wcm || !d_ownSub || !d_ors || !d_ers)
             return XDCG_OOM;
         // balanced restriction units: each box's own rows followed by its coupled
-        // rows, cut into ceil(total / unitRows) nearly equal pieces; prolongation
-        // units: each box's own rows in pieces of at most pRows
+        // rows, cut into nearly equal pieces of at most unitRows rows (half as
+        // many for a box with 12 columns, whose rows cost about twice as
+        // much); prolongation units: each box's own rows in pieces of at most
+        // pRows
         auto build_units = [&](RowBoxDev &T, int unitRows, int pRows) -> bool {
             std::vector<int> unitBox, uOb, uOe, uEb, uEe, boxUnit(S + 1, 0);
             for (int sb2 = 0; sb2 < S; ++sb2) {
@@ -1997,7 +1999,8 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
                 const long long nOwn = ownRowPtr[sb2 + 1] - ownRowPtr[sb2];
                 const long long nCpl = extRowPtr[sb2 + 1] - extRowPtr[sb2];
                 const long long Tr = nOwn + nCpl;
-                const long long nu = std::max<long long>(1, (Tr + unitRows - 1) / unitRows);
+                const long long ur = menr[sb2] ? std::max(1, unitRows / 2) : unitRows;
+                const long long nu = std::max<long long>(1, (Tr + ur - 1) / ur);
                 for (long long j = 0; j < nu; ++j) {
                     const long long a0 = Tr * j / nu, a1 = Tr * (j + 1) / nu;   // [a0, a1)
                     unitBox.push_back(sb2);
