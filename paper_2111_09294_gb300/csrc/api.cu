@@ -795,6 +795,7 @@ xdcg_status batch_start(BatchRun &R, cudaStream_t st) {
         nActive += hb.active[j];
     }
     hb.done = kRunning;
+    hb.go = 1;
     CK(cudaMemsetAsync(R.U, 0, (size_t)m * n * sizeof(double), st));
     R.live = nActive > 0;
     if (!R.live) return XDCG_OK;
@@ -978,6 +979,32 @@ xdcg_status solve_batches(BatchRun *runs, int nSys, cudaStream_t st, xdcg_status
         maxTicks = std::max(maxTicks, (long long)kMaxBatch *
                                           ((long long)o.max_iter / kTick + 2LL * o.max_outer + 2));
     }
+    // Per system: iterating (its snapshot read each tick), replacing (over
+    // several systems: held, its replacement on its own context's stream
+    // while the others iterate; back when that stream's event has fired) or
+    // done.
+    enum { kSysRun, kSysRepl, kSysDone };
+    std::vector<int> state(nSys), snapOk(nSys, 0);
+    struct Events {
+        std::vector<cudaEvent_t> v;
+        ~Events() {
+            for (auto e : v)
+                if (e) cudaEventDestroy(e);
+        }
+    } evHold, evRepl;
+    if (multi) {
+        evHold.v.assign(nSys, nullptr);
+        evRepl.v.assign(nSys, nullptr);
+        for (int q = 0; q < nSys; ++q) {
+            CK(cudaEventCreateWithFlags(&evHold.v[q], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&evRepl.v[q], cudaEventDisableTiming));
+        }
+    }
+    for (int q = 0; q < nSys; ++q) state[q] = runs[q].live ? kSysRun : kSysDone;
+    auto drain = [&]() {
+        for (int q = 0; q < nSys; ++q) cudaStreamSynchronize(runs[q].c->st);
+        cudaStreamSynchronize(st);
+    };
     xdcg_status status_all = XDCG_OK;
     bool snap = false;
     for (long long tick = 0; nLive > 0; ++tick) {
@@ -985,10 +1012,12 @@ xdcg_status solve_batches(BatchRun *runs, int nSys, cudaStream_t st, xdcg_status
             status_all = XDCG_NO_CONVERGENCE;
             break;
         }
-        for (int i = 0; i < kTick; ++i) {
+        int nRun = 0;
+        for (int q = 0; q < nSys; ++q) nRun += state[q] == kSysRun;
+        for (int i = 0; i < kTick && nRun > 0; ++i) {
             if (multi) {
                 launch_iteration_sys<MB>(tab, st);
-                c0->launches += 4;
+                c0->launches += 5;
             } else {
                 launch_spmm<MB>(runs[0].spmm, st);
                 launch_restrict_b<MB>(runs[0].rst, st);
@@ -997,43 +1026,74 @@ xdcg_status solve_batches(BatchRun *runs, int nSys, cudaStream_t st, xdcg_status
                 c0->launches += 4;
             }
         }
-        if (snap) {
+        if (nRun == 0) {
+            // every live system is replacing: wait for one
+            for (int q = 0; q < nSys; ++q)
+                if (state[q] == kSysRepl) {
+                    CK(cudaEventSynchronize(evRepl.v[q]));
+                    break;
+                }
+        } else if (snap) {
             CK(cudaEventSynchronize(c0->evb[(tick - 1) & 1]));
-            bool changed = false;
-            for (int q = 0; q < nSys; ++q) {
-                BatchRun &R = runs[q];
-                if (!R.live) continue;
-                const BatchScalars &hb = *R.c->h_bs;
-                if (hb.done == kFault || hb.fault) {
-                    CK(cudaStreamSynchronize(st));
-                    return XDCG_TIMEOUT;
-                }
-                unsigned M = 0;
-                int nAct = 0;
-                for (int j = 0; j < R.m; ++j)
-                    if (hb.active[j]) {
-                        ++nAct;
-                        if (hb.pend[j]) M |= 1u << j;
-                    }
-                if (nAct == 0) {
-                    R.live = false;
-                    changed = true;
-                    --nLive;
-                } else if (M) {
-                    batch_replace<MB>(R, M, st);
-                }
-            }
-            if (nLive == 0) break;
-            if (changed && multi)
-                if ((s = sys_tables_build(T, runs, nSys, st, &tab)) != XDCG_OK) return s;
         }
+        bool changed = false;
+        for (int q = 0; q < nSys; ++q) {
+            BatchRun &R = runs[q];
+            if (state[q] == kSysRepl) {
+                const cudaError_t e = cudaEventQuery(evRepl.v[q]);
+                if (e == cudaSuccess) {
+                    state[q] = kSysRun;
+                    snapOk[q] = 0;
+                } else if (e != cudaErrorNotReady) {
+                    return XDCG_CUDA_ERROR;
+                }
+                continue;
+            }
+            if (state[q] != kSysRun || !snapOk[q]) continue;
+            const BatchScalars &hb = *R.c->h_bs;
+            if (hb.done == kFault || hb.fault) {
+                drain();
+                return XDCG_TIMEOUT;
+            }
+            unsigned M = 0;
+            int nAct = 0;
+            for (int j = 0; j < R.m; ++j)
+                if (hb.active[j]) {
+                    ++nAct;
+                    if (hb.pend[j]) M |= 1u << j;
+                }
+            if (nAct == 0) {
+                R.live = false;
+                state[q] = kSysDone;
+                changed = true;
+                --nLive;
+            } else if (M && multi) {
+                cudaStream_t sq = R.c->st;
+                launch_batch_hold(R.c->bs, st);
+                CK(cudaEventRecord(evHold.v[q], st));
+                CK(cudaStreamWaitEvent(sq, evHold.v[q], 0));
+                batch_replace<MB>(R, M, sq);
+                CK(cudaEventRecord(evRepl.v[q], sq));
+                c0->launches += 1;
+                state[q] = kSysRepl;
+                snapOk[q] = 0;
+            } else if (M) {
+                batch_replace<MB>(R, M, st);
+            }
+        }
+        if (nLive == 0) break;
+        if (changed && multi)
+            if ((s = sys_tables_build(T, runs, nSys, st, &tab)) != XDCG_OK) return s;
         for (int q = 0; q < nSys; ++q)
-            if (runs[q].live)
+            if (state[q] == kSysRun) {
                 CK(cudaMemcpyAsync(runs[q].c->h_bs, runs[q].c->bs, sizeof(BatchScalars),
                                    cudaMemcpyDeviceToHost, st));
+                snapOk[q] = 1;
+            }
         CK(cudaEventRecord(c0->evb[tick & 1], st));
         snap = true;
     }
+    if (multi) drain();
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
     for (int q = 0; q < nSys; ++q) status[q] = status_all;

@@ -32,6 +32,13 @@ __device__ __forceinline__ bool col_runs(const BatchScalars *bs, int j, int m) {
     return j < m && bs->active[j] && !bs->pend[j];
 }
 
+// whether a kernel of the system runs: an iteration's kernels also need the
+// gate's go (a launch over several systems skips a system held for its
+// replacement); the start and replacement kernels only need the run state
+__device__ __forceinline__ bool batch_runs(const BatchScalars *bs, bool iteration) {
+    return bs->done == kRunning && (!iteration || bs->go);
+}
+
 // the block's system in a launch over several systems: the largest s with
 // off[s] <= b
 __device__ __forceinline__ int sys_of(const int *__restrict__ off, int nSys, int b) {
@@ -144,12 +151,12 @@ __device__ __forceinline__ void spmm_body(const SpmmArgs &args, int blk, int nbl
     };
     // prologue copies before the wait unless the run has visibly stopped
     // (an L2 read that may be stale; the read after the wait decides)
-    const bool early = __ldcg(&bs->done) == kRunning;
+    const bool early = __ldcg(&bs->done) == kRunning && (fin != 0 || __ldcg(&bs->go));
     if (lane == 0 && early)
         while (more && issued < NS) issue();
     issued = __shfl_sync(0xffffffffu, issued, 0);
     pdl_wait();
-    if (bs->done != kRunning) {
+    if (!batch_runs(bs, fin == 0)) {
         const unsigned long long drain = global_ns() + kDrainNs;
         for (int k = 0; k < issued; ++k) mbar_wait(bars + k % NS, (uint32_t)(k / NS) & 1u, drain);
         __syncwarp();
@@ -466,7 +473,7 @@ template <int MB>
 __device__ __forceinline__ void restrict_b_body(const RestrictBArgs &a, int blk, int nblk) {
     pdl_wait();
     BatchScalars *bs = a.bs;
-    if (bs->done != kRunning) return;
+    if (!batch_runs(bs, a.mode == 0)) return;
     const int its = bs->its, m = a.m, mode = a.mode;
     // iteration: the product advanced its, so buffer (its - 1) & 1 is read
     const float *r_cur = mode == 2 ? a.f : (((its & 1) != (mode == 0)) ? a.rB : a.rA);
@@ -623,7 +630,7 @@ __device__ __forceinline__ void coarse_b_body(const CoarseBArgs &a, int blk, int
     if (nch > 0) coarse_load_e<RB, V>(Eb, k, rLast, l0, min(CH, l1 - l0), lane, keep, e);
     pdl_wait();
     BatchScalars *bs = a.bs;
-    if (bs->done != kRunning) return;
+    if (!batch_runs(bs, a.mode == 2)) return;
     const int m = a.m, mode = a.mode;
     const unsigned long long deadline = global_ns() + a.waitNs;
     auto issue = [&](int c) {   // lane 0: chunk c of G into buffer c & 1
@@ -797,7 +804,7 @@ template <int MB>
 __device__ __forceinline__ void prolong_b_body(const ProlongBArgs &a, int blk) {
     pdl_wait();
     const BatchScalars *bs = a.bs;
-    if (bs->done != kRunning) return;
+    if (!batch_runs(bs, a.mode == 0)) return;
     const int unit = blk, mode = a.mode;
     const int j = threadIdx.x % MB;
     bool wr = true, leaves = false;
@@ -833,9 +840,24 @@ void launch_prolong_b(const ProlongBArgs &a, cudaStream_t st) {
     launch_pdl(k_prolong_b<MB>, a.B.nPUnits, kThreads, 0, st, a);
 }
 
-// one FP32 iteration of every system of the table: four launches
+// Before each iteration over several systems: whether it runs each system
+// (running and not held), read once so that every block of the iteration's
+// four kernels agrees.  A replacement's last kernel releases the hold after
+// its other writes (k_batch_arm), so a gate that sees the release sees them.
+__global__ void k_batch_gate(const SpmmArgs *__restrict__ tab, int nSys) {
+    for (int s = threadIdx.x; s < nSys; s += blockDim.x) {
+        BatchScalars *bs = tab[s].bs;
+        const int held = *reinterpret_cast<volatile const int *>(&bs->hold);
+        __threadfence();
+        const int done = *reinterpret_cast<volatile const int *>(&bs->done);
+        bs->go = done == kRunning && !held;
+    }
+}
+
+// one FP32 iteration of every system of the table: the gate, then four launches
 template <int MB>
 void launch_iteration_sys(const BatchSysTab &t, cudaStream_t st) {
+    k_batch_gate<<<1, 128, 0, st>>>(t.spmm, t.nSys);
     const int smem = spmv_smem_bytes<float, 0>();
     launch_pdl(k_spmm_sys<MB>, t.blocks[0], kSpmvThreads, smem, st, t.spmm, t.off[0], t.nSys);
     launch_pdl(k_restrict_b_sys<MB>, t.blocks[1], kThreads, 0, st, t.rst, t.off[1], t.nSys);
@@ -928,6 +950,12 @@ __global__ void k_batch_arm(BatchScalars *bs, int m, int first) {
         any |= bs->active[j] && !bs->pend[j];
     }
     if (bs->done != kFault) bs->done = any ? kRunning : kConverged;
+    __threadfence();   // every write of the replacement before the release
+    *reinterpret_cast<volatile int *>(&bs->hold) = 0;
+}
+
+__global__ void k_batch_hold(BatchScalars *bs) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) bs->hold = 1;
 }
 
 void launch_batch_slots(Scalars *slots, unsigned mask, cudaStream_t st) {
@@ -942,6 +970,7 @@ void launch_batch_judge(BatchScalars *bs, const Scalars *slots, int m, cudaStrea
 void launch_batch_arm(BatchScalars *bs, int m, int first, cudaStream_t st) {
     k_batch_arm<<<1, 32, 0, st>>>(bs, m, first);
 }
+void launch_batch_hold(BatchScalars *bs, cudaStream_t st) { k_batch_hold<<<1, 32, 0, st>>>(bs); }
 
 // ---- FP64 <-> FP32 transforms of several columns --------------------------------
 

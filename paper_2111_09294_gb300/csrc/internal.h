@@ -103,7 +103,10 @@ struct BatchScalars {
     int outcome[kMaxBatch];     // kColOk, kColBad (not finite), kColLimit (no convergence)
     int its;                    // iterations the system ran: residual buffer its & 1 is current
     int done;                   // kRunning while a column iterates, else kConverged; kFault
-    int max_it, max_outer, fault, pad;
+    int max_it, max_outer, fault;
+    int hold;                   // held for a replacement running on its own stream
+    int go;                     // the iteration in progress runs this system (set by the gate)
+    int pad;
     unsigned int ticket[4];
 };
 
@@ -449,6 +452,7 @@ void launch_batch_slots(Scalars *slots, unsigned mask, cudaStream_t st);
 void launch_batch_open(BatchScalars *bs, Scalars *slots, unsigned mask, cudaStream_t st);
 void launch_batch_judge(BatchScalars *bs, const Scalars *slots, int m, cudaStream_t st);
 void launch_batch_arm(BatchScalars *bs, int m, int first, cudaStream_t st);
+void launch_batch_hold(BatchScalars *bs, cudaStream_t st);
 // FP64 <-> FP32 transforms of the columns being replaced (repl_j)
 template <int MB>
 void launch_fwd_scale_b(int nNodes, int m, const int *nat, const int *ot, const FacDev &F,

@@ -3,15 +3,15 @@ systems of successive crack-front positions in a propagation sweep.
 
 Every system has its own context (its K, Z, block factors and coarse
 operator differ with the crack front), and its load cases run as one batched
-FP32 iteration.  By default (fused) one call runs all systems' batched
-iterations together: every iteration is one launch per kernel over all
-systems' blocks, on the first context's stream, and the host replaces the
-residuals of the columns that ask for it while the others keep iterating.
-The other modes issue each system's own batched solve from a host thread of
-its own (the systems' kernels then overlap on the GPU as their streams
-allow) or one after another.  Every mode gives the same bits per column
-(fixed partitions and reduction orders in every kernel, and columns that
-advance independently).
+FP32 iteration.  By default each system's batched solve is issued from a host
+thread of its own on its own stream, so the systems' kernels overlap on the
+GPU (the library releases the GIL through ctypes and blocks only on its own
+stream).  fused=True runs them as one xdcg_solve_systems call instead: every
+iteration is one launch per kernel over all systems' blocks, and a system
+whose columns wait for their residual replacement is held while the
+replacement runs on its own stream.  Every mode gives the same bits per
+column (fixed partitions and reduction orders in every kernel, and columns
+that advance independently).
 """
 import concurrent.futures as cf
 
@@ -28,15 +28,15 @@ def make_solvers(problems, max_batch=8, precision="mixed", **kw):
 
 
 def solve_systems(solvers, loads, tol, outs=None, concurrent=True, raise_on_error=True,
-                  fused=True):
+                  fused=False):
     """solvers[i].solve_batch(loads[i], tol) for every system i.
 
     loads[i]: (m_i, n_i) contiguous CUDA float64 tensor of system i's load
     cases; outs: optional matching output tensors.  Inputs must be ready on
-    the device (the call synchronises the device first).  fused (default,
-    for two or more mixed batched contexts): one xdcg_solve_systems call;
-    otherwise concurrent=True runs each system's solve_batch from a thread of
-    its own and concurrent=False one after another.  Returns [(U_i, infos_i)]."""
+    the device (the call synchronises the device first).  fused=True (two or
+    more mixed batched contexts): one xdcg_solve_systems call; otherwise
+    concurrent=True runs each system's solve_batch from a thread of its own
+    and concurrent=False one after another.  Returns [(U_i, infos_i)]."""
     if len(solvers) != len(loads):
         raise ValueError("one load tensor per solver")
     outs = outs if outs is not None else [torch.empty_like(F) for F in loads]

@@ -29,9 +29,9 @@ def test_sweep_fused_concurrent_sequential_agree_and_match_oracle():
              for i, (P, m) in enumerate(zip(Ps, ms))]
     loads[1][1].zero_()
     solvers = S.make_solvers(Ps, max_batch=4)
-    fused = S.solve_systems(solvers, loads, 1e-12)
-    conc = S.solve_systems(solvers, loads, 1e-12, fused=False)
-    seq = S.solve_systems(solvers, loads, 1e-12, concurrent=False, fused=False)
+    fused = S.solve_systems(solvers, loads, 1e-12, fused=True)
+    conc = S.solve_systems(solvers, loads, 1e-12)
+    seq = S.solve_systems(solvers, loads, 1e-12, concurrent=False)
     for (Uf, jf), (Uc, ic), (Us, iq) in zip(fused, conc, seq):
         assert torch.equal(Uf, Uc) and torch.equal(Uc, Us)
         its = [i["iterations"] for i in jf]
@@ -50,7 +50,8 @@ def test_sweep_fused_concurrent_sequential_agree_and_match_oracle():
     # a context passed twice shares one set of scalars: refused
     from paper_2111_09294_gb300._lib import XdcgError
     with pytest.raises(XdcgError, match="INVALID_ARG"):
-        S.solve_systems([solvers[0], solvers[0]], [loads[0], loads[0].clone()], 1e-8)
+        S.solve_systems([solvers[0], solvers[0]], [loads[0], loads[0].clone()], 1e-8,
+                        fused=True)
     for s in solvers:
         s.close()
 

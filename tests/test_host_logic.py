@@ -69,14 +69,14 @@ def test_sweep_keeps_system_order_and_overlaps_calls():
     solvers = [_FakeSolver(0.6), _FakeSolver(0.15), _FakeSolver(0.3)]
     loads = [torch.full((2, 3), float(i)) for i in range(3)]
     t0 = time.perf_counter()
-    res = S.solve_systems(solvers, loads, 1e-8, fused=False)
+    res = S.solve_systems(solvers, loads, 1e-8)
     concurrent = time.perf_counter() - t0
     for i, (U, infos) in enumerate(res):
         assert torch.equal(U, 2 * loads[i]) and len(infos) == 2 and infos[0]["tol"] == 1e-8
     # one host thread per system: the calls overlap
     assert len({s.threads[0] for s in solvers}) == 3
     assert concurrent < 0.9           # one after another takes 1.05 s
-    seq = S.solve_systems(solvers, loads, 1e-8, concurrent=False, fused=False)
+    seq = S.solve_systems(solvers, loads, 1e-8, concurrent=False)
     assert all(torch.equal(a[0], b[0]) for a, b in zip(res, seq))
     assert len({s.threads[1] for s in solvers}) == 1
 
@@ -85,10 +85,10 @@ def test_sweep_reports_a_failed_system():
     from paper_2111_09294_gb300 import sweep as S
     solvers = [_FakeSolver(0.0), _FakeSolver(0.0, fail=True)]
     with pytest.raises(RuntimeError, match="solve failed"):
-        S.solve_systems(solvers, [torch.zeros(1, 2), torch.zeros(1, 2)], 1e-8, fused=False)
+        S.solve_systems(solvers, [torch.zeros(1, 2), torch.zeros(1, 2)], 1e-8)
     with pytest.raises(ValueError):
         S.solve_systems(solvers, [torch.zeros(1, 2)], 1e-8)
     # the fused call takes contiguous (m, n) CUDA float64 loads only
     solvers[0].n = solvers[1].n = 2
     with pytest.raises(ValueError):
-        S.solve_systems(solvers, [torch.zeros(1, 2), torch.zeros(1, 2)], 1e-8)
+        S.solve_systems(solvers, [torch.zeros(1, 2), torch.zeros(1, 2)], 1e-8, fused=True)
