@@ -2048,18 +2048,19 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
             !R.wBase || !Zcm || !Wcm || !d_ownSub || !d_ors || !d_ers)
             return XDCG_OOM;
         // balanced restriction units: each box's own rows followed by its coupled
-        // rows, cut into nearly equal pieces of at most unitRows rows (half as
-        // many for a box with 12 columns, whose rows cost about twice as
-        // much); prolongation units: each box's own rows in pieces of at most
+        // rows, cut into nearly equal pieces of at most unitRows rows (with
+        // halve12, half as many for a box with 12 columns, whose rows cost
+        // about twice as much: the batched kernels, whose units are a box
+        // each); prolongation units: each box's own rows in pieces of at most
         // pRows
-        auto build_units = [&](RowBoxDev &T, int unitRows, int pRows) -> bool {
+        auto build_units = [&](RowBoxDev &T, int unitRows, int pRows, bool halve12) -> bool {
             std::vector<int> unitBox, uOb, uOe, uEb, uEe, boxUnit(S + 1, 0);
             for (int sb2 = 0; sb2 < S; ++sb2) {
                 boxUnit[sb2] = (int)unitBox.size();
                 const long long nOwn = ownRowPtr[sb2 + 1] - ownRowPtr[sb2];
                 const long long nCpl = extRowPtr[sb2 + 1] - extRowPtr[sb2];
                 const long long Tr = nOwn + nCpl;
-                const long long ur = menr[sb2] ? std::max(1, unitRows / 2) : unitRows;
+                const long long ur = halve12 && menr[sb2] ? std::max(1, unitRows / 2) : unitRows;
                 const long long nu = std::max<long long>(1, (Tr + ur - 1) / ur);
                 for (long long j = 0; j < nu; ++j) {
                     const long long a0 = Tr * j / nu, a1 = Tr * (j + 1) / nu;   // [a0, a1)
@@ -2093,7 +2094,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
                    T.unitExtEnd && T.boxUnit && T.pUnitBox && T.pUnitBegin && T.pUnitEnd &&
                    T.nPUnits > 0 && T.nUnits <= kMaxGrid;
         };
-        if (!build_units(R, kUnitRows, kProlongRows)) return XDCG_OOM;
+        if (!build_units(R, kUnitRows, kProlongRows, false)) return XDCG_OOM;
         R.unitPart = dalloc<double>(c, 24 * (size_t)R.nUnits);
         R.boxTicket = dalloc<unsigned int>(c, S);
         if (!R.unitPart || !R.boxTicket) return XDCG_OOM;
@@ -2108,7 +2109,7 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
             // the batched kernels give each row MB threads: smaller units keep as
             // many rows in flight per block as the single-column kernels have
             c->L32.Rb = R;
-            if (!build_units(c->L32.Rb, kUnitRowsBatch, kProlongRowsBatch)) return XDCG_OOM;
+            if (!build_units(c->L32.Rb, kUnitRowsBatch, kProlongRowsBatch, true)) return XDCG_OOM;
         }
         c->L32.dofStart64 = d_dof;
         c->L32.dofStart32 = d_dof32;

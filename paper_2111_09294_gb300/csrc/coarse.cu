@@ -146,12 +146,13 @@ void launch_symmetrize(double *E, int k, cudaStream_t st) {
 
 // ---- per-iteration coarse solve -------------------------------------------
 
-// Scalar updates shared by the coarse kernels (modes as for k_coarse); part
-// holds this thread's share of nu^T (Z^T r).
-__device__ __forceinline__ void coarse_scalars(double (&part)[1], int mode, double *partials,
+// Scalar updates shared by the coarse kernels (modes as for k_coarse); blk
+// holds the block's share of nu^T (Z^T r) in thread 0 (the few row sums
+// gathered through shared memory: no FP64 shuffle tree in every warp).
+__device__ __forceinline__ void coarse_scalars(double blk, int mode, double *partials,
                                                Scalars *sc) {
     double tot[1];
-    if (grid_sum<double, 1>(part, partials, &sc->ticket[3], tot) && threadIdx.x == 0) {
+    if (grid_sum_t0(blk, partials, &sc->ticket[3], tot[0]) && threadIdx.x == 0) {
         if (mode == 1) {
             sc->rho = sc->ry + tot[0];
             sc->beta = 0.0;
@@ -220,7 +221,13 @@ k_coarse(const double *__restrict__ Einv, int k, const double *__restrict__ g,
             if (mode != 0) part[0] = s * zr[i];
         }
     }
-    coarse_scalars(part, mode, partials, sc);
+    __shared__ double rowPart[kWarps];
+    if (lane == 0) rowPart[warp] = part[0];
+    __syncthreads();
+    double blk = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kWarps; ++w) blk += rowPart[w];
+    coarse_scalars(blk, mode, partials, sc);
 }
 
 // nu = E^-1 g with E^-1 held in FP32, for the FP32 iteration of the mixed
@@ -271,14 +278,22 @@ k_coarse32(const float *__restrict__ Einv, int k, const float *__restrict__ g32,
     }
     if (lane == 0 && h == 1) upper[warp >> 1] = s;
     __syncthreads();
-    double part[1] = {0.0};
-    if (i < k && lane == 0 && h == 0) {
-        const float v = s + upper[warp >> 1];
-        nu[i] = (double)v;
-        nu32[i] = v;
-        if (mode != 0) part[0] = (double)v * zr[i];
+    __shared__ double rowPart[kWarps / 2];
+    if (lane == 0 && h == 0) {
+        double part = 0.0;
+        if (i < k) {
+            const float v = s + upper[warp >> 1];
+            nu[i] = (double)v;
+            nu32[i] = v;
+            if (mode != 0) part = (double)v * zr[i];
+        }
+        rowPart[warp >> 1] = part;
     }
-    coarse_scalars(part, mode, partials, sc);
+    __syncthreads();
+    double blk = 0.0;
+    if (threadIdx.x == 0)
+        for (int r = 0; r < kWarps / 2; ++r) blk += rowPart[r];
+    coarse_scalars(blk, mode, partials, sc);
 }
 
 void launch_coarse32(const float *Einv, int k, const float *g32, const double *zr, double *nu,
