@@ -725,6 +725,27 @@ def run_profile(args):
     import torch
     import xfem_inputs as X
     from paper_2111_09294_gb300 import Solver
+    if args.profile in ("sweep", "sweep_fused"):
+        # one propagation sweep of --sweep systems, 8 load cases each
+        from paper_2111_09294_gb300 import sweep as S
+        Ps = X.make_many(X.SWEEP[:max(args.sweep, 1)])
+        ssol = S.make_solvers(Ps, max_batch=8)
+        Fs = [torch.tensor(X.load_cases(Pi, 8, seed=100 + i), device="cuda")
+              for i, Pi in enumerate(Ps)]
+        Us = [torch.empty_like(Fi) for Fi in Fs]
+        fused = args.profile == "sweep_fused"
+        for _ in range(max(args.warmup, 1)):
+            S.solve_systems(ssol, Fs, TOL, outs=Us, fused=fused)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        res = S.solve_systems(ssol, Fs, TOL, outs=Us, fused=fused)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        infos = [i for _, inf in res for i in inf]
+        print(json.dumps({"profile": args.profile, "systems": len(Ps),
+                          "iterations_max": max(i["iterations"] for i in infos),
+                          "rel_res_true_max": max(i["rel_res_true"] for i in infos)}))
+        return
     P = X.make(args.workload)
     if args.profile == "batch":
         # the batched solve of args.batch seeded load cases
@@ -785,7 +806,8 @@ def main():
                     help="also report iterations against n at a fixed subdomain size (0: skip)")
     ap.add_argument("--subdomain-blocks", type=int, default=1,
                     help="also time block Jacobi with one block per subdomain (0: skip)")
-    ap.add_argument("--profile", choices=["mixed", "fp64", "batch"], default=None,
+    ap.add_argument("--profile", choices=["mixed", "fp64", "batch", "sweep", "sweep_fused"],
+                    default=None,
                     help="profiler capture: one solve of the given path between "
                          "cudaProfilerStart/Stop after warm-up, nothing else timed")
     args = ap.parse_args()

@@ -212,7 +212,7 @@ struct RowBoxDev {
 constexpr int kUnitRows = 3072;     // own + coupled rows per restriction unit
 constexpr int kProlongRows = 512;
 constexpr int kUnitRowsBatch = 1024;     // the same for the batched kernels (MB threads per row)
-constexpr int kProlongRowsBatch = 256;
+constexpr int kProlongRowsBatch = 64;
 
 void launch_restrict(const BoxDev<double> &B, const double *a, const double *b, int withW,
                      double *g, double *zr, const Scalars *sc, cudaStream_t st);
