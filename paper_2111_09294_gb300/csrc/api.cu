@@ -486,7 +486,14 @@ xdcg_status scaled_iterate(xdcg_ctx *c, float *u, float *rA, float *rB, float *p
                 CK(cudaEventRecord(c->evS[launched], st));
             }
             MARK(launched, 0);
-            launch_spmv<float>(L.A, p, q, nullptr, 0, c->partials, sc, kFinAlpha, 0, st);
+            // without caller blocks the product leaves its blocks' sums of
+            // p^T q for the restriction to add (no ticketed reduction at the
+            // product's end), past the region the restriction's own
+            // reduction uses
+            float2 *pqPart = reinterpret_cast<float2 *>(c->partials + kMaxGrid);
+            launch_spmv<float>(L.A, p, q, nullptr, 0,
+                               c->userBlocks ? c->partials : c->partials + kMaxGrid, sc,
+                               c->userBlocks ? kFinAlpha : kFinDefer, 0, st);
             if (timeSpmv) CK(cudaEventRecord(c->evE[launched], st));
             MARK(launched, 1);
             if (c->userBlocks) {
@@ -498,7 +505,8 @@ xdcg_status scaled_iterate(xdcg_ctx *c, float *u, float *rA, float *rB, float *p
                                        c->partials, sc, st, c->y32);
                 c->launches += 2;
             } else {
-                launch_restrict_update(L.R, u, rc, rn, p, q, 0, c->g, c->zr, c->partials, sc, st);
+                launch_restrict_update_deferred(L.R, u, rc, rn, p, q, c->g, c->zr, c->partials, sc,
+                                                i, pqPart, L.A.grid, st);
             }
             MARK(launched, 2);
             coarse_inner(c, c->zr, 2, sc);

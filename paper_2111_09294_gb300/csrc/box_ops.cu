@@ -364,15 +364,40 @@ __device__ __forceinline__ float restrict_update_unit(const RowBoxDev &B, int un
     return acc[2 * M];
 }
 
+// Deferred form (it >= 0, mode 0 of iteration it of the FP32 iteration): the
+// product left its blocks' sums of p^T q in pqPart instead of reducing them
+// itself; every block adds them (block_read_total), takes alpha = rho / pq,
+// and block 0 records pq, alpha and its = it + 1, or the breakdown (or a
+// failed wait of the product).
 template <bool YV>
 __global__ void __launch_bounds__(kRowThreads)
 k_restrict_update(RowBoxDev B, float *u, const float *r_cur, float *r_next, const float *p,
                   const float *q, const float *yv, int mode, double *g, double *zr,
-                  double *partials, Scalars *sc) {
+                  double *partials, Scalars *sc, int it, const float2 *pqPart, int pqN) {
     pdl_wait();
     if (sc->done != kRunning) return;
     const int unit = blockIdx.x;
-    const float alpha = (mode == 0) ? (float)sc->alpha : 0.0f;
+    float alpha = (mode == 0) ? (float)sc->alpha : 0.0f;
+    if (it >= 0) {
+        const bool fault = sc->fault != 0;
+        const double pq = block_read_total(pqPart, pqN);
+        const double rho = sc->rho;
+        const bool broken = !(pq > 0.0) || !isfinite(pq);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            if (fault) {
+                sc->done = kFault;
+            } else {
+                sc->pq = pq;
+                sc->its = it + 1;
+                if (broken)
+                    sc->done = kBreakdown;
+                else
+                    sc->alpha = rho / pq;
+            }
+        }
+        if (fault || broken) return;
+        alpha = (float)(rho / pq);
+    }
     float rr;
     if (B.menr[B.unitBox[unit]])
         rr = restrict_update_unit<12, YV>(B, unit, u, r_cur, r_next, p, q, yv, mode, alpha, g, zr);
@@ -396,7 +421,16 @@ void launch_restrict_update(const RowBoxDev &B, float *u, const float *r_cur, fl
                             const float *p, const float *q, int mode, double *g, double *zr,
                             double *partials, Scalars *sc, cudaStream_t st, const float *y) {
     launch_pdl(mode == 3 ? k_restrict_update<true> : k_restrict_update<false>, B.nUnits,
-               kRowThreads, 0, st, B, u, r_cur, r_next, p, q, y, mode, g, zr, partials, sc);
+               kRowThreads, 0, st, B, u, r_cur, r_next, p, q, y, mode, g, zr, partials, sc, -1,
+               (const float2 *)nullptr, 0);
+}
+
+void launch_restrict_update_deferred(const RowBoxDev &B, float *u, const float *r_cur,
+                                     float *r_next, const float *p, const float *q, double *g,
+                                     double *zr, double *partials, Scalars *sc, int it,
+                                     const float2 *pqPart, int pqN, cudaStream_t st) {
+    launch_pdl(k_restrict_update<false>, B.nUnits, kRowThreads, 0, st, B, u, r_cur, r_next, p, q,
+               (const float *)nullptr, 0, g, zr, partials, sc, it, pqPart, pqN);
 }
 
 template <int M>

@@ -22,6 +22,7 @@ enum Fin : int {
     kFinAlpha = 0,   // value = p^T q: alpha = rho / pq, its += 1, breakdown test
     kFinRR = 1,      // value = ||r||^2: store rr, converged test against tol2ff
     kFinStore = 2,   // value stored into scratch[slot]
+    kFinDefer = 3,   // each block's sum stored at partials[block]; the next kernel adds them
 };
 
 // Scalars of one CG run, in device memory.  Written only by the last block
@@ -230,6 +231,13 @@ void launch_restrict_update(const RowBoxDev &B, float *u, const float *r_cur, fl
                             const float *y = nullptr);
 void launch_prolong_rows(const RowBoxDev &B, const float *nu32, const float *y, float *p,
                          int mode, Scalars *sc, cudaStream_t st);
+// The FP32 iteration's restriction (mode 0, iteration it) after a product
+// launched with kFinDefer: it adds the product's block sums of p^T q
+// (pqPart, pqN of them) itself and takes alpha from them.
+void launch_restrict_update_deferred(const RowBoxDev &B, float *u, const float *r_cur,
+                                     float *r_next, const float *p, const float *q, double *g,
+                                     double *zr, double *partials, Scalars *sc, int it,
+                                     const float2 *pqPart, int pqN, cudaStream_t st);
 void launch_to_colmajor(int nItems, const int *itemBox, const int *rowStart,
                         const unsigned char *itemB, const long long *srcOff,
                         const int *boxRowPtr, const long long *boxBase, const int *menr,

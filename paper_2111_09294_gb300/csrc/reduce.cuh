@@ -118,6 +118,64 @@ __device__ __forceinline__ bool grid_sum_of(A (&v)[NV], double *partials, unsign
     return true;
 }
 
+// Double-float arithmetic: a value as an unevaluated sum hi + lo of two
+// floats (about 48 significant bits), added with FP32 operations only
+// (Knuth's two-sum, then renormalisation).  Used where many blocks each add
+// the same few hundred partial sums: FP64 runs at about 1/64 of the FP32
+// rate on this part.
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    const float s = a.x + b.x;
+    const float bb = s - a.x;
+    const float e = (a.x - (s - bb)) + (b.x - bb);
+    const float t = (e + a.y) + b.y;
+    const float hi = s + t;
+    return make_float2(hi, t - (hi - s));
+}
+__device__ __forceinline__ float2 df_of(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+
+// The total of n block partials (double-float) a previous kernel stored
+// (kFinDefer and the FP32 iteration's deferred sums): every thread loads its
+// share at once (one round trip), the shares are added in a fixed order
+// within each thread, by a tree over the lanes and over the warps, so every
+// block of the consuming kernel gets the same bits; valid in every thread.
+// Replaces the producer's ticketed last-block reduction (fence, atomic, the
+// last block's tail).
+__device__ __forceinline__ double block_read_total(const float2 *partials, int n) {
+    constexpr int kLoads = 8;
+    __shared__ float2 wsum[32];
+    __shared__ double total;
+    const int t = threadIdx.x, nt = blockDim.x;
+    float2 v[kLoads];
+#pragma unroll
+    for (int q = 0; q < kLoads; ++q) {
+        const int i = t + q * nt;
+        v[q] = i < n ? __ldcg(partials + i) : make_float2(0.f, 0.f);
+    }
+    float2 acc = v[0];
+#pragma unroll
+    for (int q = 1; q < kLoads; ++q) acc = df_add(acc, v[q]);
+    for (int i = t + kLoads * nt; i < n; i += nt) acc = df_add(acc, __ldcg(partials + i));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float2 other;
+        other.x = __shfl_xor_sync(0xffffffffu, acc.x, o);
+        other.y = __shfl_xor_sync(0xffffffffu, acc.y, o);
+        acc = df_add(acc, other);
+    }
+    if ((t & 31) == 0) wsum[t >> 5] = acc;
+    __syncthreads();
+    if (t == 0) {
+        float2 s = wsum[0];
+        for (int w = 1; w < (nt >> 5); ++w) s = df_add(s, wsum[w]);
+        total = (double)s.x + (double)s.y;
+    }
+    __syncthreads();
+    return total;
+}
+
 // Grid-wide sum over the launch's blocks (see grid_sum_of).
 template <typename A, int NV>
 __device__ __forceinline__ bool grid_sum(A (&v)[NV], double *partials, unsigned int *ticket,

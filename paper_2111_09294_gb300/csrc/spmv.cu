@@ -254,6 +254,14 @@ k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__rest
         for (; k < issued; ++k) mbar_wait(bars + k % NS, (uint32_t)(k / NS) & 1u, drain);
         __syncwarp();
     }
+    if (fin == kFinDefer) {
+        // the next kernel adds the blocks' sums (block_read_total); a failed
+        // wait is in sc->fault, which it reads too
+        block_sum<T, 1>(part);
+        if (threadIdx.x == 0)
+            reinterpret_cast<float2 *>(partials)[blockIdx.x] = df_of((double)part[0]);
+        return;
+    }
     double tot[1];
     if (grid_sum<T, 1>(part, partials, &sc->ticket[0], tot) && threadIdx.x == 0) {
         if (sc->fault)
