@@ -299,6 +299,10 @@ def run_ours(args):
     mixed_t = Solver.from_problem(P, precision="mixed", time_spmv=True, inner_tol=args.inner_tol,
                                   autotune=at)
     fp64_t = Solver.from_problem(P, precision="fp64", time_spmv=True, autotune=at)
+    # the same solves with their iterations replayed as recorded CUDA graphs
+    mixed_g = Solver.from_problem(P, precision="mixed", inner_tol=args.inner_tol, autotune=at,
+                                  graph=True)
+    fp64_g = Solver.from_problem(P, precision="fp64", autotune=at, graph=True)
     f = torch.tensor(P.f, device=dev)
     u = torch.empty_like(f)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -330,6 +334,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier(pg)
     ms_c64, inf_c64 = timed(mixed_c64, args.steps, args.warmup, True)
+    torch.cuda.synchronize()
+    barrier(pg)
+    ms_mg, inf_mg = timed(mixed_g, args.steps, args.warmup, True)
+    ms_fg, inf_fg = timed(fp64_g, args.steps, args.warmup, True)
     torch.cuda.synchronize()
     barrier(pg)
     # SpMV kernel time: a timed pass of the same solves with events around each SpMV
@@ -510,38 +518,46 @@ def run_ours(args):
         from paper_2111_09294_gb300 import sweep as S
         Ps = X.make_many(X.SWEEP[:args.sweep])
         ssol = S.make_solvers(Ps, max_batch=8)
+        gsol = S.make_solvers(Ps, max_batch=8, graph=True)
         Fs = [torch.tensor(X.load_cases(Pi, 8, seed=100 + i), device=dev)
               for i, Pi in enumerate(Ps)]
         Us = [torch.empty_like(Fi) for Fi in Fs]
-        modes = {"concurrent": {}, "fused": {"fused": True},
-                 "one_after_another": {"concurrent": False}}
+        modes = {"concurrent": (ssol, {}), "fused": (ssol, {"fused": True}),
+                 "one_after_another": (ssol, {"concurrent": False}),
+                 "concurrent_graph": (gsol, {}), "fused_graph": (gsol, {"fused": True})}
         times, res = {}, {}
-        for name, kw in modes.items():
+        for name, (sol_, kw) in modes.items():
             for _ in range(max(1, args.warmup)):
-                S.solve_systems(ssol, Fs, TOL, outs=Us, **kw)
+                S.solve_systems(sol_, Fs, TOL, outs=Us, **kw)
             ts_ = []
             for _ in range(args.steps):
                 flush.zero_()
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                res[name] = S.solve_systems(ssol, Fs, TOL, outs=Us, **kw)
+                out_ = S.solve_systems(sol_, Fs, TOL, outs=Us, **kw)
                 ts_.append((time.perf_counter() - t0) * 1e3)
+            # the outputs are shared by the modes: keep this mode's
+            res[name] = [(U_.clone(), inf_) for U_, inf_ in out_]
             times[name] = float(np.mean(ts_))
         infos = [i for _, inf in res["concurrent"] for i in inf]
         assert max(i["rel_res_true"] for i in infos) <= TOL
         same = all(torch.equal(a[0], b[0]) for a, b in zip(res["fused"], res["concurrent"]))
+        same_g = all(torch.equal(a[0], b[0]) and torch.equal(a[0], c[0]) for a, b, c in
+                     zip(res["fused_graph"], res["concurrent_graph"], res["concurrent"]))
         sweep = {"systems": len(Ps), "rhs_per_system": 8,
                  "n_dofs": [int(Pi.n) for Pi in Ps], "ms": times["concurrent"],
                  "ms_fused": times["fused"],
                  "ms_one_after_another": times["one_after_another"],
                  "speedup_vs_one_after_another": times["one_after_another"] / times["concurrent"],
                  "fused_same_bits": same,
+                 "ms_concurrent_graph": times["concurrent_graph"],
+                 "ms_fused_graph": times["fused_graph"], "graph_same_bits": same_g,
                  "systems_rhs_per_s": len(Ps) * 8 / times["concurrent"] * 1e3,
                  "iterations_max": max(i["iterations"] for i in infos),
                  "iterations_mean": float(np.mean([i["iterations"] for i in infos])),
                  "rel_res_true_max": max(i["rel_res_true"] for i in infos),
                  "timing": "host wall clock around the calls (each returns after its work)"}
-        for s_ in ssol:
+        for s_ in ssol + gsol:
             s_.close()
         return sweep
 
@@ -639,6 +655,28 @@ def run_ours(args):
                 "solve_warm_ms_total": sum(r["ms_warm"] for r in rows[1:]),
                 "note": "mixed, unit tension, tol 1e-8; totals over fronts 1..15 for the solves"}
 
+    def graph_row():
+        # the value's solves with their iterations replayed as CUDA graphs
+        # (xdcg_options.graph); the bits match when both contexts run the
+        # same SpMV shape (the autotuner may pick another on a close call)
+        same = {}
+        for name, a, b in (("mixed", mixed, mixed_g), ("fp64", fp64, fp64_g)):
+            if a.info["spmv_shape_fp32"] != b.info["spmv_shape_fp32"] or \
+                    a.info["spmv_shape_fp64"] != b.info["spmv_shape_fp64"]:
+                same[name] = None
+                continue
+            ua, _ = a.solve(f, tol=TOL)
+            ub, _ = b.solve(f, tol=TOL)
+            same[name] = bool(torch.equal(ua, ub))
+        return {"mixed_ms": max_over_ranks(pg, float(np.mean(ms_mg)), dev),
+                "fp64_ms": max_over_ranks(pg, float(np.mean(ms_fg)), dev),
+                "mixed_iterations": inf_mg[-1]["iterations"],
+                "fp64_iterations": inf_fg[-1]["iterations"],
+                "graph_launches_per_solve_mixed": inf_mg[-1]["n_graph_launches"],
+                "rel_res_true_mixed": max(i["rel_res_true"] for i in inf_mg),
+                "same_bits_as_stream_launches": same,
+                "note": "8 iterations per graph launch; timed like the value"}
+
     sequence = optional(measure_sequence) if args.sweep > 1 else None
     batch = optional(measure_batch) if args.batch > 0 else None
     fwd_bwd = optional(measure_fwd_bwd)
@@ -683,6 +721,7 @@ def run_ours(args):
                               "outer_cycles": inf_c64[-1]["outer_cycles"],
                               "rel_res_true": max(i["rel_res_true"] for i in inf_c64),
                               "note": "E^-1 applied in FP64 inside the FP32 iteration"},
+        "graph": graph_row(),
         "rel_res_true_mixed": res_true, "rel_res_true_fp64": inf_fp64[-1]["rel_res_true"],
         "setup_ms": info["t_setup_ms"],
         "setup_phases_ms": {k: round(v, 1) for k, v in info["t_setup_phase_ms"].items()},

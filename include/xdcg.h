@@ -170,6 +170,18 @@ typedef struct {
                                 matrix and keeps the fastest (info.spmv_shape_*); a few ms.
                                 Default 0: the default shape.  Two contexts with different
                                 shapes may round the fused dot differently */
+    int32_t graph;           /* 1: the loops of the solves enqueue their iterations as CUDA
+                                graphs: a batch of 8 iterations of xdcg_solve / xdcg_solve_x0
+                                (FP64, and MIXED's FP32 iteration) is recorded by stream capture
+                                once per context (on a private stream of the context, so the
+                                context's own stream may be the legacy default stream) and
+                                replayed with one graph launch per batch; xdcg_solve_batch and
+                                xdcg_solve_systems (the first context's option) record the 2
+                                iterations of each tick, again whenever the set of systems still
+                                iterating changes.  The graphs hold the same launches in the same
+                                order, with the same programmatic ordering between them, so the
+                                results are the same bits.  Ignored with time_spmv (its events
+                                sit between the kernels).  Default 0 */
 } xdcg_options;
 
 typedef struct {
@@ -189,6 +201,8 @@ typedef struct {
                                     MIXED: SpMV, restriction+update, coarse solve, prolongation */
     int32_t n_fp64_iterations;   /* MIXED: iterations of the FP64 finish (included in
                                     iterations), 0 when the FP32 cycles alone met tol */
+    int32_t n_graph_launches;    /* graph launches made by this call (xdcg_options.graph); the
+                                    kernels they ran are counted in n_launches */
 } xdcg_result;
 
 typedef struct {

@@ -46,7 +46,8 @@ class Options(ctypes.Structure):
     _fields_ = [("tol", c_double), ("max_iter", c_int32), ("precision", c_int32),
                 ("inner_tol", c_double), ("max_outer", c_int32), ("time_spmv", c_int32),
                 ("jacobi", c_int32), ("record_history", c_int32), ("max_batch", c_int32),
-                ("coarse_fp64", c_int32), ("wait_s", c_double), ("autotune", c_int32)]
+                ("coarse_fp64", c_int32), ("wait_s", c_double), ("autotune", c_int32),
+                ("graph", c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -55,7 +56,7 @@ class Result(ctypes.Structure):
                 ("t_solve_ms", c_double), ("bad_index", c_int32), ("n_spmv_timed", c_int32),
                 ("t_spmv_ms", c_double), ("n_launches", c_int64),
                 ("n_phase_timed", c_int32), ("t_phase_ms", c_double * 5),
-                ("n_fp64_iterations", c_int32)]
+                ("n_fp64_iterations", c_int32), ("n_graph_launches", c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

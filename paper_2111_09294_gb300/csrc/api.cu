@@ -3,6 +3,7 @@
 // kernels, and the solve drivers for the FP64 and the FP32-inner / FP64-
 // refinement paths.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <climits>
@@ -39,6 +40,16 @@ struct Level32 {          // block-scaled system K~ = L^-1 K L^-T in FP32
     const int *dofStart64;    // [nNodes + 1] node dofs in the FP64 (caller's) numbering
     const int *dofStart32;    // [nNodes + 1] node dofs in the box-major FP32 numbering
     BlkDev<float> J;          // caller blocks: FP32 inverses of the block-scaled blocks
+};
+
+// A batch of iterations recorded once by stream capture and replayed as one
+// graph launch (xdcg_options.graph); key holds the pointers and sizes the
+// batch was recorded with.
+using LoopKey = std::array<const void *, 8>;
+struct LoopGraph {
+    cudaGraphExec_t exec = nullptr;
+    LoopKey key{};
+    long long launches = 0;   // kernels in one replay
 };
 
 }  // namespace
@@ -98,6 +109,12 @@ struct xdcg_ctx {
     std::vector<cudaEvent_t> evS, evE;
     std::vector<cudaEvent_t> evP;      // per-kernel marks of timed iterations (time_spmv = 2)
     long long launches = 0;
+    // opt.graph: the captures are recorded on a private stream (the context's
+    // own may be the legacy default stream, which cannot be captured)
+    cudaStream_t capSt = nullptr;
+    LoopGraph loop32[2];               // FP32 iteration batch, by residual-buffer parity
+    LoopGraph loop64;                  // FP64 iteration batch
+    long long graphLaunches = 0;       // graph launches made (diagnostics)
 };
 
 namespace {
@@ -107,6 +124,39 @@ namespace {
         cudaError_t e_ = (call);                      \
         if (e_ != cudaSuccess) return XDCG_CUDA_ERROR; \
     } while (0)
+
+// opt.graph: (re)record the batch of iterations that enqueue(stream) issues,
+// unless G already holds it for this key.  Recording runs nothing; the graph
+// holds the same launches, with the same programmatic (PDL) ordering between
+// them, as the uncaptured loop, so replaying it gives the same bits.
+template <typename F>
+xdcg_status loop_graph(xdcg_ctx *c, LoopGraph &G, const LoopKey &key, F &&enqueue) {
+    if (G.exec && G.key == key) return XDCG_OK;
+    if (G.exec) {
+        cudaGraphExecDestroy(G.exec);
+        G.exec = nullptr;
+    }
+    if (!c->capSt) CK(cudaStreamCreateWithFlags(&c->capSt, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(c->capSt, cudaStreamCaptureModeThreadLocal));
+    const long long l0 = c->launches;
+    enqueue(c->capSt);
+    G.launches = c->launches - l0;   // counted when replayed, not when recorded
+    c->launches = l0;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->capSt, &g);
+    if (e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        return XDCG_CUDA_ERROR;
+    }
+    const cudaError_t e2 = cudaGraphInstantiate(&G.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) {
+        G.exec = nullptr;
+        return XDCG_CUDA_ERROR;
+    }
+    G.key = key;
+    return XDCG_OK;
+}
 
 // A named range on the profiler timeline (NVTX) for the life of a scope, so
 // that a profiler can select the set-up or one solve; a no-op when no
@@ -281,28 +331,29 @@ xdcg_status phase_collect(xdcg_ctx *c, int n, int P, xdcg_result *res) {
 struct PlainPath {
     xdcg_ctx *c;
     Level64 &L;
+    cudaStream_t st;          // the stream its kernels are enqueued on
     void spmv(const double *x, double *y, const double *b, int res, int fin, Scalars *sc) {
-        launch_spmv<double>(L.A, x, y, b, res, c->partials, sc, fin, 0, c->st);
+        launch_spmv<double>(L.A, x, y, b, res, c->partials, sc, fin, 0, st);
     }
     void update(double *u, double *r, const double *p, const double *q, double *y, int mode,
                 Scalars *sc) {
         if (c->userBlocks) {
             // caller blocks: the update, then y = M^-1 r by the blocks' dense inverses
-            launch_update_plain<double>(u, r, p, q, c->n, mode, c->partials, sc, c->st);
-            launch_block_apply<double>(L.J, r, y, c->partials, sc, c->st);
+            launch_update_plain<double>(u, r, p, q, c->n, mode, c->partials, sc, st);
+            launch_block_apply<double>(L.J, r, y, c->partials, sc, st);
             c->launches++;
         } else {
-            launch_update<double>(L.N, u, r, p, q, y, mode, c->partials, sc, c->st);
+            launch_update<double>(L.N, u, r, p, q, y, mode, c->partials, sc, st);
         }
     }
     void restrict_(const double *a, const double *b, int withW, double *zr, Scalars *sc) {
-        launch_restrict(L.B, a, b, withW, c->g, zr, sc, c->st);
+        launch_restrict(L.B, a, b, withW, c->g, zr, sc, st);
     }
     void coarse(const double *zr, int mode, Scalars *sc) {
-        launch_coarse(c->Einv, c->k, c->g, zr, c->nu, nullptr, mode, c->partials, sc, c->st);
+        launch_coarse(c->Einv, c->k, c->g, zr, c->nu, nullptr, mode, c->partials, sc, st);
     }
     void prolong(const double *y, double *p, int mode, Scalars *sc) {
-        launch_prolong(L.B, c->nu, y, p, mode, sc, c->st);
+        launch_prolong(L.B, c->nu, y, p, mode, sc, st);
     }
 };
 
@@ -336,8 +387,33 @@ xdcg_status run_pcg(xdcg_ctx *c, Path path, const T *f, T *u, T *r, T *p, T *q, 
 
     int launched = 0;
     const int max_batches = max_it / kBatch + 2;
+    // opt.graph: the batch's kernels as one recorded graph (not with the
+    // timing modes, whose events sit between the kernels)
+    const bool useGraph = c->opt.graph && !timeSpmv && !timeKernels;
+    if (useGraph) {
+        const LoopKey key{u, r, p, q, y, sc, c->zr, nullptr};
+        xdcg_status s = loop_graph(c, c->loop64, key, [&](cudaStream_t cs) {
+            Path rec = path;
+            rec.st = cs;
+            for (int i = 0; i < kBatch; ++i) {
+                rec.spmv(p, q, nullptr, 0, kFinAlpha, sc);
+                rec.update(u, r, p, q, y, 0, sc);
+                rec.restrict_(r, y, 1, c->zr, sc);
+                rec.coarse(c->zr, 2, sc);
+                rec.prolong(y, p, 0, sc);
+                c->launches += 5;
+            }
+        });
+        if (s != XDCG_OK) return s;
+    }
     for (int b = 0; b < max_batches; ++b) {
-        for (int i = 0; i < kBatch; ++i) {
+        if (useGraph) {
+            CK(cudaGraphLaunch(c->loop64.exec, st));
+            c->launches += c->loop64.launches;
+            c->graphLaunches++;
+            launched += kBatch;
+        }
+        for (int i = 0; i < kBatch && !useGraph; ++i) {
             if (timeSpmv) {
                 if ((int)c->evS.size() <= launched) {
                     cudaEvent_t e0, e1;
@@ -414,11 +490,11 @@ __global__ void k_set_trigger(Scalars *sc, int mode, double delta2, double floor
 
 // nu = E^-1 g inside the FP32 iteration: the FP32 copy of E^-1 (default) or
 // the FP64 one (opt.coarse_fp64), both writing nu and its FP32 copy nu32
-void coarse_inner(xdcg_ctx *c, const double *zr, int mode, Scalars *sc) {
+void coarse_inner(xdcg_ctx *c, const double *zr, int mode, Scalars *sc, cudaStream_t st) {
     if (c->opt.coarse_fp64)
-        launch_coarse(c->Einv, c->k, c->g, zr, c->nu, c->nu32, mode, c->partials, sc, c->st);
+        launch_coarse(c->Einv, c->k, c->g, zr, c->nu, c->nu32, mode, c->partials, sc, st);
     else
-        launch_coarse32(c->Einv32, c->k, c->g32, zr, c->nu, c->nu32, mode, c->partials, sc, c->st);
+        launch_coarse32(c->Einv32, c->k, c->g32, zr, c->nu, c->nu32, mode, c->partials, sc, st);
 }
 
 // Algorithm 2 and the first direction: u~ = Z~ E^-1 Z~^T f~, r = f~ - K~ u~ (rA),
@@ -428,7 +504,7 @@ void scaled_init(xdcg_ctx *c, const float *f, float *u, float *rA, float *p, Sca
     Level32 &L = c->L32;
     launch_restrict_update(L.R, nullptr, f, nullptr, nullptr, nullptr, 2, c->g, nullptr,
                            c->partials, sc, st);
-    coarse_inner(c, nullptr, 0, sc);
+    coarse_inner(c, nullptr, 0, sc, st);
     launch_prolong_rows(L.R, c->nu32, nullptr, u, 1, sc, st);
     launch_spmv<float>(L.A, u, rA, f, 1, c->partials, sc, kFinRR, 0, st);
     if (c->userBlocks) {
@@ -436,14 +512,14 @@ void scaled_init(xdcg_ctx *c, const float *f, float *u, float *rA, float *p, Sca
         launch_block_apply<float>(L.J, rA, c->y32, c->partials, sc, st);
         launch_restrict_update(L.R, nullptr, rA, nullptr, nullptr, nullptr, 3, c->g, c->zr,
                                c->partials, sc, st, c->y32);
-        coarse_inner(c, c->zr, 1, sc);
+        coarse_inner(c, c->zr, 1, sc, st);
         launch_prolong_rows(L.R, c->nu32, c->y32, p, 2, sc, st);
         c->launches += 8;
         return;
     }
     launch_restrict_update(L.R, nullptr, rA, nullptr, nullptr, nullptr, 1, c->g, c->zr,
                            c->partials, sc, st);
-    coarse_inner(c, c->zr, 1, sc);
+    coarse_inner(c, c->zr, 1, sc, st);
     launch_prolong_rows(L.R, c->nu32, rA, p, 2, sc, st);
     c->launches += 7;
 }
@@ -471,10 +547,61 @@ xdcg_status scaled_iterate(xdcg_ctx *c, float *u, float *rA, float *rB, float *p
     double bestRR = c->h_sc->rr;
     int lastGain = it0;
     *stalled = false;
+    // kernel m (0..3) of iteration it of the FP32 iteration, enqueued on s
+    auto kernel = [&](int m, int it, cudaStream_t s) {
+        float *rc = (it & 1) ? rB : rA;
+        float *rn = (it & 1) ? rA : rB;
+        // without caller blocks the product leaves its blocks' sums of
+        // p^T q for the restriction to add (no ticketed reduction at the
+        // product's end), past the region the restriction's own
+        // reduction uses
+        float2 *pqPart = reinterpret_cast<float2 *>(c->partials + kMaxGrid);
+        if (m == 0) {
+            launch_spmv<float>(L.A, p, q, nullptr, 0,
+                               c->userBlocks ? c->partials : c->partials + kMaxGrid, sc,
+                               c->userBlocks ? kFinAlpha : kFinDefer, 0, s);
+        } else if (m == 1) {
+            if (c->userBlocks) {
+                // residual in place (no neighbour reads before the apply), y
+                // = M~^-1 r by the caller blocks, then the restriction
+                launch_update_plain<float>(u, rA, p, q, c->n, 0, c->partials, sc, s);
+                launch_block_apply<float>(L.J, rA, c->y32, c->partials, sc, s);
+                launch_restrict_update(L.R, nullptr, rA, nullptr, nullptr, nullptr, 3, c->g, c->zr,
+                                       c->partials, sc, s, c->y32);
+                c->launches += 2;
+            } else {
+                launch_restrict_update_deferred(L.R, u, rc, rn, p, q, c->g, c->zr, c->partials, sc,
+                                                pqPart, L.A.grid, s);
+            }
+        } else if (m == 2) {
+            coarse_inner(c, c->zr, 2, sc, s);
+        } else {
+            launch_prolong_rows(L.R, c->nu32, c->userBlocks ? c->y32 : rn, p, 0, sc, s);
+            c->launches += 4;
+        }
+    };
+    // opt.graph: a batch's kernels as one recorded graph per residual-buffer
+    // parity of its first iteration (kBatch is even), not with the timing
+    // modes, whose events sit between the kernels
+    const bool useGraph = c->opt.graph && !timeSpmv && !timeKernels;
+    LoopGraph &G = c->loop32[it0 & 1];
+    if (useGraph) {
+        const LoopKey key{u, rA, rB, p, q, sc, c->zr, c->userBlocks ? c->y32 : nullptr};
+        xdcg_status s = loop_graph(c, G, key, [&](cudaStream_t cs) {
+            for (int j = 0; j < kBatch; ++j)
+                for (int m = 0; m < 4; ++m) kernel(m, it0 + j, cs);
+        });
+        if (s != XDCG_OK) return s;
+    }
     for (int b = 0; b < max_batches; ++b) {
-        for (int j = 0; j < kBatch; ++j, ++i, ++launched) {
-            float *rc = (i & 1) ? rB : rA;
-            float *rn = (i & 1) ? rA : rB;
+        if (useGraph) {
+            CK(cudaGraphLaunch(G.exec, st));
+            c->launches += G.launches;
+            c->graphLaunches++;
+            i += kBatch;
+            launched += kBatch;
+        }
+        for (int j = 0; j < kBatch && !useGraph; ++j, ++i, ++launched) {
             if (timeSpmv) {
                 if ((int)c->evS.size() <= launched) {
                     cudaEvent_t e0, e1;
@@ -486,34 +613,15 @@ xdcg_status scaled_iterate(xdcg_ctx *c, float *u, float *rA, float *rB, float *p
                 CK(cudaEventRecord(c->evS[launched], st));
             }
             MARK(launched, 0);
-            // without caller blocks the product leaves its blocks' sums of
-            // p^T q for the restriction to add (no ticketed reduction at the
-            // product's end), past the region the restriction's own
-            // reduction uses
-            float2 *pqPart = reinterpret_cast<float2 *>(c->partials + kMaxGrid);
-            launch_spmv<float>(L.A, p, q, nullptr, 0,
-                               c->userBlocks ? c->partials : c->partials + kMaxGrid, sc,
-                               c->userBlocks ? kFinAlpha : kFinDefer, 0, st);
+            kernel(0, i, st);
             if (timeSpmv) CK(cudaEventRecord(c->evE[launched], st));
             MARK(launched, 1);
-            if (c->userBlocks) {
-                // residual in place (no neighbour reads before the apply), y
-                // = M~^-1 r by the caller blocks, then the restriction
-                launch_update_plain<float>(u, rA, p, q, c->n, 0, c->partials, sc, st);
-                launch_block_apply<float>(L.J, rA, c->y32, c->partials, sc, st);
-                launch_restrict_update(L.R, nullptr, rA, nullptr, nullptr, nullptr, 3, c->g, c->zr,
-                                       c->partials, sc, st, c->y32);
-                c->launches += 2;
-            } else {
-                launch_restrict_update_deferred(L.R, u, rc, rn, p, q, c->g, c->zr, c->partials, sc,
-                                                i, pqPart, L.A.grid, st);
-            }
+            kernel(1, i, st);
             MARK(launched, 2);
-            coarse_inner(c, c->zr, 2, sc);
+            kernel(2, i, st);
             MARK(launched, 3);
-            launch_prolong_rows(L.R, c->nu32, c->userBlocks ? c->y32 : rn, p, 0, sc, st);
+            kernel(3, i, st);
             MARK(launched, 4);
-            c->launches += 4;
         }
         // one copy per poll: the stop flag and ||r||^2 for the stall test
         CK(cudaMemcpyAsync(&c->h_poll[b & 1], sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
@@ -574,7 +682,7 @@ xdcg_status solve_fp64(xdcg_ctx *c, const double *f, double *u, double tol, bool
                  c->hist ? c->opt.max_iter + 1 : 0);
     c->launches += 1;
     int its = 0, done = 0;
-    xdcg_status s = run_pcg<double>(c, PlainPath{c, c->L64}, f, u, c->r64, c->p64, c->q64,
+    xdcg_status s = run_pcg<double>(c, PlainPath{c, c->L64, c->st}, f, u, c->r64, c->p64, c->q64,
                                     c->y64, c->sc, c->opt.max_iter, guess, &its, &done, res);
     if (s != XDCG_OK) return s;
     const double rr = c->h_sc->rr;
@@ -694,7 +802,7 @@ xdcg_status solve_mixed(xdcg_ctx *c, const double *f, double *u, double tol, boo
             launch_restrict_update(L.R, nullptr, rbuf, nullptr, nullptr, nullptr, 1, c->g, c->zr,
                                    c->partials, c->sc32, st);
         }
-        coarse_inner(c, c->zr, done == kBreakdown ? 1 : 3, c->sc32);
+        coarse_inner(c, c->zr, done == kBreakdown ? 1 : 3, c->sc32, st);
         launch_prolong_rows(L.R, c->nu32, c->userBlocks ? c->y32 : rbuf, c->p32,
                             done == kBreakdown ? 2 : 0, c->sc32, st);
         c->launches += 5;
@@ -1013,6 +1121,30 @@ xdcg_status solve_batches(BatchRun *runs, int nSys, cudaStream_t st, xdcg_status
         for (int q = 0; q < nSys; ++q) cudaStreamSynchronize(runs[q].c->st);
         cudaStreamSynchronize(st);
     };
+    // a tick's iterations, enqueued on s
+    auto enqueueTick = [&](cudaStream_t s) {
+        for (int i = 0; i < kTick; ++i) {
+            if (multi) {
+                launch_iteration_sys<MB>(tab, s);
+                c0->launches += 5;
+            } else {
+                launch_spmm<MB>(runs[0].spmm, s);
+                launch_restrict_b<MB>(runs[0].rst, s);
+                launch_coarse_b<MB>(runs[0].crs, s);
+                launch_prolong_b<MB>(runs[0].pro, s);
+                c0->launches += 4;
+            }
+        }
+    };
+    // opt.graph (of the first context): the tick as one recorded graph,
+    // recorded again whenever the set of live systems (the table) changes
+    struct TickGraph {
+        LoopGraph g;
+        ~TickGraph() {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+        }
+    } tickG;
+    const bool useGraph = c0->opt.graph != 0;
     xdcg_status status_all = XDCG_OK;
     bool snap = false;
     for (long long tick = 0; nLive > 0; ++tick) {
@@ -1022,17 +1154,19 @@ xdcg_status solve_batches(BatchRun *runs, int nSys, cudaStream_t st, xdcg_status
         }
         int nRun = 0;
         for (int q = 0; q < nSys; ++q) nRun += state[q] == kSysRun;
-        for (int i = 0; i < kTick && nRun > 0; ++i) {
-            if (multi) {
-                launch_iteration_sys<MB>(tab, st);
-                c0->launches += 5;
-            } else {
-                launch_spmm<MB>(runs[0].spmm, st);
-                launch_restrict_b<MB>(runs[0].rst, st);
-                launch_coarse_b<MB>(runs[0].crs, st);
-                launch_prolong_b<MB>(runs[0].pro, st);
-                c0->launches += 4;
+        if (nRun > 0 && useGraph) {
+            const LoopKey key{tab.spmm, tab.rst, tab.crs, tab.pro,
+                              reinterpret_cast<const void *>((intptr_t)tab.nSys), runs[0].c,
+                              reinterpret_cast<const void *>((intptr_t)runs[0].m), nullptr};
+            if ((s = loop_graph(c0, tickG.g, key, enqueueTick)) != XDCG_OK) {
+                if (multi) drain();
+                return s;
             }
+            CK(cudaGraphLaunch(tickG.g.exec, st));
+            c0->launches += tickG.g.launches;
+            c0->graphLaunches++;
+        } else if (nRun > 0) {
+            enqueueTick(st);
         }
         if (nRun == 0) {
             // every live system is replacing: wait for one
@@ -1114,7 +1248,7 @@ xdcg_status do_solve(xdcg_ctx *c, const double *f, double *u, double tol, bool g
     xdcg_result res{};
     res.bad_index = -1;
     if (tol <= 0) tol = c->opt.tol;
-    const long long l0 = c->launches;
+    const long long l0 = c->launches, g0 = c->graphLaunches;
     CK(cudaEventRecord(c->ev0, c->st));
     xdcg_status s = (c->opt.precision == XDCG_MIXED) ? solve_mixed(c, f, u, tol, guess, &res)
                                                     : solve_fp64(c, f, u, tol, guess, &res);
@@ -1125,6 +1259,7 @@ xdcg_status do_solve(xdcg_ctx *c, const double *f, double *u, double tol, bool g
     CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     res.t_solve_ms = ms;
     res.n_launches = c->launches - l0;
+    res.n_graph_launches = (int32_t)(c->graphLaunches - g0);
     if (out) *out = res;
     return s;
 }
@@ -1145,8 +1280,13 @@ void free_ctx(xdcg_ctx *c) {
     if (c->ev1) cudaEventDestroy(c->ev1);
     for (auto e : c->evb)
         if (e) cudaEventDestroy(e);
+    for (auto &g : c->loop32)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (c->loop64.exec) cudaGraphExecDestroy(c->loop64.exec);
+    if (c->capSt) cudaStreamDestroy(c->capSt);
     delete c;
 }
+
 
 // ---- set-up -----------------------------------------------------------------
 
@@ -2345,6 +2485,7 @@ xdcg_status xdcg_default_options(xdcg_options *opt) {
     opt->coarse_fp64 = 0;
     opt->wait_s = 2.0;
     opt->autotune = 0;
+    opt->graph = 0;
     return XDCG_OK;
 }
 
@@ -2369,6 +2510,7 @@ static xdcg_status setup_common(xdcg_ctx **out, const xdcg_ctx *prev, const xdcg
         c->opt.max_batch < 0 || c->opt.max_batch > kMaxBatch ||
         (c->opt.coarse_fp64 != 0 && c->opt.coarse_fp64 != 1) ||
         (c->opt.autotune != 0 && c->opt.autotune != 1) ||
+        (c->opt.graph != 0 && c->opt.graph != 1) ||
         !(c->opt.wait_s >= 0.0 && c->opt.wait_s <= 60.0) ||
         !(c->opt.inner_tol > 0 && c->opt.inner_tol < 1) ||
         (blocks && (c->opt.jacobi != XDCG_BLOCK_JACOBI || c->opt.max_batch > 0))) {
@@ -2494,6 +2636,7 @@ xdcg_status xdcg_solve_systems(xdcg_ctx *const *ctxs, int32_t n_sys, const doubl
     std::vector<xdcg_status> sst(n_sys, XDCG_OK);
     std::vector<long long> l0(n_sys);
     for (int q = 0; q < n_sys; ++q) l0[q] = ctxs[q]->launches;
+    const long long g0 = c0->graphLaunches;
     float ms = 0.f;
     if (s == XDCG_OK) {
         CK(cudaEventRecord(c0->ev0, st));
@@ -2521,6 +2664,7 @@ xdcg_status xdcg_solve_systems(xdcg_ctx *const *ctxs, int32_t n_sys, const doubl
         for (int j = 0; j < m[q]; ++j) {
             local[j].t_solve_ms = ms;
             local[j].n_launches = ctxs[q]->launches - l0[q];
+            local[j].n_graph_launches = (int32_t)(c0->graphLaunches - g0);   // shared by all
             if (res) res[off + j] = local[j];
         }
         off += m[q];
@@ -2705,7 +2849,7 @@ xdcg_status xdcg_precond(xdcg_ctx *c, const double *r, double *z) {
     cudaStream_t st = c->st;
     init_scalars(c, c->aux, -1.0, nullptr, INT_MAX);
     CK(cudaMemcpyAsync(c->r64, r, c->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    PlainPath{c, c->L64}.update(nullptr, c->r64, nullptr, nullptr, c->y64, 1, c->aux);
+    PlainPath{c, c->L64, c->st}.update(nullptr, c->r64, nullptr, nullptr, c->y64, 1, c->aux);
     launch_restrict(c->L64.B, c->r64, c->y64, 1, c->g, c->zr, c->aux, st);
     launch_coarse(c->Einv, c->k, c->g, c->zr, c->nu, nullptr, 0, c->partials, c->aux, st);
     launch_prolong(c->L64.B, c->nu, c->y64, z, 2, c->aux, st);

@@ -364,21 +364,23 @@ __device__ __forceinline__ float restrict_update_unit(const RowBoxDev &B, int un
     return acc[2 * M];
 }
 
-// Deferred form (it >= 0, mode 0 of iteration it of the FP32 iteration): the
+// Deferred form (deferred != 0, mode 0 of an iteration of the FP32 iteration): the
 // product left its blocks' sums of p^T q in pqPart instead of reducing them
 // itself; every block adds them (block_read_total), takes alpha = rho / pq,
-// and block 0 records pq, alpha and its = it + 1, or the breakdown (or a
-// failed wait of the product).
+// and block 0 records pq, alpha and counts the iteration (its += 1: the
+// launch's arguments do not depend on the iteration, so a captured batch of
+// iterations can be replayed), or the breakdown (or a failed wait of the
+// product).
 template <bool YV>
 __global__ void __launch_bounds__(kRowThreads)
 k_restrict_update(RowBoxDev B, float *u, const float *r_cur, float *r_next, const float *p,
                   const float *q, const float *yv, int mode, double *g, double *zr,
-                  double *partials, Scalars *sc, int it, const float2 *pqPart, int pqN) {
+                  double *partials, Scalars *sc, int deferred, const float2 *pqPart, int pqN) {
     pdl_wait();
     if (sc->done != kRunning) return;
     const int unit = blockIdx.x;
     float alpha = (mode == 0) ? (float)sc->alpha : 0.0f;
-    if (it >= 0) {
+    if (deferred) {
         const bool fault = sc->fault != 0;
         const double pq = block_read_total(pqPart, pqN);
         const double rho = sc->rho;
@@ -388,7 +390,7 @@ k_restrict_update(RowBoxDev B, float *u, const float *r_cur, float *r_next, cons
                 sc->done = kFault;
             } else {
                 sc->pq = pq;
-                sc->its = it + 1;
+                sc->its += 1;
                 if (broken)
                     sc->done = kBreakdown;
                 else
@@ -421,16 +423,16 @@ void launch_restrict_update(const RowBoxDev &B, float *u, const float *r_cur, fl
                             const float *p, const float *q, int mode, double *g, double *zr,
                             double *partials, Scalars *sc, cudaStream_t st, const float *y) {
     launch_pdl(mode == 3 ? k_restrict_update<true> : k_restrict_update<false>, B.nUnits,
-               kRowThreads, 0, st, B, u, r_cur, r_next, p, q, y, mode, g, zr, partials, sc, -1,
+               kRowThreads, 0, st, B, u, r_cur, r_next, p, q, y, mode, g, zr, partials, sc, 0,
                (const float2 *)nullptr, 0);
 }
 
 void launch_restrict_update_deferred(const RowBoxDev &B, float *u, const float *r_cur,
                                      float *r_next, const float *p, const float *q, double *g,
-                                     double *zr, double *partials, Scalars *sc, int it,
+                                     double *zr, double *partials, Scalars *sc,
                                      const float2 *pqPart, int pqN, cudaStream_t st) {
     launch_pdl(k_restrict_update<false>, B.nUnits, kRowThreads, 0, st, B, u, r_cur, r_next, p, q,
-               (const float *)nullptr, 0, g, zr, partials, sc, it, pqPart, pqN);
+               (const float *)nullptr, 0, g, zr, partials, sc, 1, pqPart, pqN);
 }
 
 template <int M>

@@ -231,12 +231,12 @@ void launch_restrict_update(const RowBoxDev &B, float *u, const float *r_cur, fl
                             const float *y = nullptr);
 void launch_prolong_rows(const RowBoxDev &B, const float *nu32, const float *y, float *p,
                          int mode, Scalars *sc, cudaStream_t st);
-// The FP32 iteration's restriction (mode 0, iteration it) after a product
-// launched with kFinDefer: it adds the product's block sums of p^T q
-// (pqPart, pqN of them) itself and takes alpha from them.
+// The FP32 iteration's restriction (mode 0) after a product launched with
+// kFinDefer: it adds the product's block sums of p^T q (pqPart, pqN of them)
+// itself, takes alpha from them and counts the iteration in sc->its.
 void launch_restrict_update_deferred(const RowBoxDev &B, float *u, const float *r_cur,
                                      float *r_next, const float *p, const float *q, double *g,
-                                     double *zr, double *partials, Scalars *sc, int it,
+                                     double *zr, double *partials, Scalars *sc,
                                      const float2 *pqPart, int pqN, cudaStream_t st);
 void launch_to_colmajor(int nItems, const int *itemBox, const int *rowStart,
                         const unsigned char *itemB, const long long *srcOff,

@@ -70,14 +70,16 @@ class Solver:
     from the geometry (xdcg_deflation's valued form: 6 or 12 columns per box,
     node I's b_I x z_cols[sub[I]] block row-major, nodes in order).  prev: a
     Solver of the same mesh for the previous crack front, whose unchanged
-    parts are carried over (xdcg_setup_update).
+    parts are carried over (xdcg_setup_update).  graph: enqueue the solves'
+    iterations as recorded CUDA graphs (xdcg_options.graph; same bits).
     """
 
     def __init__(self, dof_ptr, row_ptr, col, val_ptr, val, sub_of_node, coords, hsign, centres,
                  precision="fp64", tol=1e-8, max_iter=10000, inner_tol=1e-3, max_outer=30,
                  time_spmv=False, enriched_modes=True, stream=None, jacobi="block",
                  record_history=False, max_batch=0, coarse_fp64=False, wait_s=2.0,
-                 blocks=None, z_cols=None, z_values=None, prev=None, autotune=False):
+                 blocks=None, z_cols=None, z_values=None, prev=None, autotune=False,
+                 graph=False):
         lib = L.load()
         self._lib = lib
         self.ctx = ctypes.c_void_p()
@@ -111,6 +113,7 @@ class Solver:
         opt.coarse_fp64 = int(bool(coarse_fp64))
         opt.wait_s = float(wait_s)
         opt.autotune = int(bool(autotune))
+        opt.graph = int(bool(graph))
         self.precision = precision
         if stream is None:
             stream = torch.cuda.current_stream()
