@@ -60,20 +60,28 @@ def kernel_source_sha(files):
 SPMV_SOURCES = ("spmv.cu", "spmv_cfg.cuh", "tma.cuh", "pdl.cuh", "cache.cuh")
 
 
-def profiled_traffic(kernel_files, summary):
+def profiled_traffic(kernel_files, summary, shape):
     """Per-launch DRAM bytes of the FP32 SpMV from the committed ncu summary,
-    or None when the kernel's sources changed since the capture."""
+    or None when the kernel's sources changed since the capture or the
+    capture is of another pipeline shape than the one timed."""
     path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]{12})", txt)
-    if not m or not h:
+    k = re.search(r"kernel_shape:\s*([0-9]+)", txt)
+    if not m or not h or not k:
         return None
-    if kernel_source_sha(kernel_files) != h.group(1):
+    if kernel_source_sha(kernel_files) != h.group(1) or int(k.group(1)) != shape:
         return None
     return float(m.group(1))
+
+
+def spmv_kernel_name(shape):
+    """The FP32 SpMV kernel a pipeline shape runs (shapes 5-7: the lean kernel)."""
+    return (f"k_spmv_lean<false, {shape}>" if shape >= 5 else
+            f"k_spmv<float, false, {shape}>") + " (inner FP32 SpMV)"
 
 
 class ClockSampler:
@@ -693,7 +701,8 @@ def run_ours(args):
     spmv64_ms = sum(i["t_spmv_ms"] for i in inf_fp64_t) / max(n64, 1)
     achieved64 = info["spmv_alg_bytes_fp64"] / (spmv64_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    traffic = profiled_traffic(SPMV_SOURCES, f"spmv_fp32_{args.workload}.md")
+    timed_shape = mixed_t.info["spmv_shape_fp32"]
+    traffic = profiled_traffic(SPMV_SOURCES, f"spmv_fp32_{args.workload}.md", timed_shape)
     its_fp64 = inf_fp64[-1]["iterations"]
     fp64_tf = optional(lambda: fp64_peak_tflops(dev))
     cpu, oracle_all, one = None, None, None
@@ -731,7 +740,8 @@ def run_ours(args):
                                        if t >= 0],
                      "timed_shape_fp32": mixed_t.info["spmv_shape_fp32"],
                      "shapes": "FP32 (steps/stage, stages, blocks/SM): (2,3,3) (1,4,4) (2,4,2) "
-                               "(1,6,3) (3,3,2); FP64: (1,3,3) (1,4,2) (2,2,2) (1,2,4)"},
+                               "(1,6,3) (3,3,2), lean kernel (2,3,3) (1,6,3) (2,2,4); "
+                               "FP64: (1,3,3) (1,4,2) (2,2,2) (1,2,4)"},
         "spmv_fp32_gbs": achieved, "spmv_fp64_gbs": achieved64,
         "kernel_us_per_iteration": phases,
         "batched_load_cases": batch,
@@ -740,7 +750,7 @@ def run_ours(args):
         "propagation_sequence": sequence,
         "subdomain_blocks": blocks_row,
         "iterations_vs_n": trend,
-        "roofline": {"bound": "hbm", "kernel": "k_spmv<float> (inner FP32 SpMV)",
+        "roofline": {"bound": "hbm", "kernel": spmv_kernel_name(timed_shape),
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind,
                      "traffic": traffic, "algorithmic_bytes": info["spmv_alg_bytes_fp32"],

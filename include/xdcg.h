@@ -168,8 +168,8 @@ typedef struct {
     int32_t autotune;        /* 1: set-up times every compiled pipeline shape of the SpMV (steps
                                 per bulk-copy stage, stages per warp, blocks per SM) on this
                                 matrix and keeps the fastest (info.spmv_shape_*); a few ms.
-                                Default 0: the default shape.  Two contexts with different
-                                shapes may round the fused dot differently */
+                                Default 0: the default shape (FP32 5, FP64 0).  Two contexts
+                                with different shapes may round the fused dot differently */
     int32_t graph;           /* 1: the loops of the solves enqueue their iterations as CUDA
                                 graphs: a batch of 8 iterations of xdcg_solve / xdcg_solve_x0
                                 (FP64, and MIXED's FP32 iteration) is recorded by stream capture
@@ -182,6 +182,11 @@ typedef struct {
                                 order, with the same programmatic ordering between them, so the
                                 results are the same bits.  Ignored with time_spmv (its events
                                 sit between the kernels).  Default 0 */
+    int32_t spmv_shape_fp32; /* >= 0: the FP32 SpMV runs this pipeline shape (xdcg_info_t lists
+                                them), whatever autotune found; -1 (default): the default
+                                shape (5), or the autotuner's pick.  XDCG_INVALID_ARG beyond
+                                the last shape */
+    int32_t spmv_shape_fp64; /* the same for the FP64 SpMV (default shape 0) */
 } xdcg_options;
 
 typedef struct {
@@ -235,12 +240,17 @@ typedef struct {
                                     blocks; work vectors */
     int32_t reused_node_factors; /* xdcg_setup_update: node-block factors carried over */
     int32_t reused_coarse_inverse; /* xdcg_setup_update: 1 if E^-1 was carried over */
-    int32_t spmv_shape_fp64;     /* SpMV pipeline shape in use (0 = default; autotune) */
+    int32_t spmv_shape_fp64;     /* SpMV pipeline shape in use (default FP64 0, FP32 5; the
+                                    FP32 one for MIXED contexts) */
     int32_t spmv_shape_fp32;
     double spmv_shape_us_fp64[8]; /* autotune: median time of each shape's product, -1 untimed;
                                     FP64 shapes (steps per stage, stages, blocks per SM):
                                     (1,3,3) (1,4,2) (2,2,2) (1,2,4) */
-    double spmv_shape_us_fp32[8]; /* FP32 shapes: (2,3,3) (1,4,4) (2,4,2) (1,6,3) (3,3,2) */
+    double spmv_shape_us_fp32[8]; /* FP32 shapes: (2,3,3) (1,4,4) (2,4,2) (1,6,3) (3,3,2), and
+                                    the lean kernel's (2,3,3) (1,6,3) (2,2,4): stages that run
+                                    across slice boundaries, the copy schedule walked by every
+                                    lane, no per-stage record; the same products and, at the
+                                    same grid, the same dot */
 } xdcg_info_t;
 
 /* Fill *opt with the defaults listed above. */

@@ -47,7 +47,7 @@ class Options(ctypes.Structure):
                 ("inner_tol", c_double), ("max_outer", c_int32), ("time_spmv", c_int32),
                 ("jacobi", c_int32), ("record_history", c_int32), ("max_batch", c_int32),
                 ("coarse_fp64", c_int32), ("wait_s", c_double), ("autotune", c_int32),
-                ("graph", c_int32)]
+                ("graph", c_int32), ("spmv_shape_fp32", c_int32), ("spmv_shape_fp64", c_int32)]
 
 
 class Result(ctypes.Structure):

@@ -1826,11 +1826,12 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
     };
     const unsigned long long waitNs = (unsigned long long)(c->opt.wait_s * 1e9);
     A.waitNs = waitNs;
-    A.shape = 0;
-    A.grid = spmv_persistent_grid<double>(HS.nSlices + HX.nSlices, 0);
+    A.shape = kSpmvDefaultShapeF64;
+    A.grid = spmv_persistent_grid<double>(HS.nSlices + HX.nSlices, A.shape);
     if (A.grid < 1) return XDCG_CUDA_ERROR;
     A.warpSlice = partition(HS, HX, A.grid);
     if (!A.warpSlice) return XDCG_OOM;
+    c->info.spmv_shape_fp64 = A.shape;   // until autotuned or pinned below
     // The autotuner: every compiled pipeline shape of the SpMV (steps per
     // bulk-copy stage, stages per warp, blocks per SM; each with its own
     // persistent grid and step-balanced warp ranges) timed on this matrix,
@@ -1882,10 +1883,30 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         *pick = keep.shape;
         return XDCG_OK;
     };
+    // a shape pinned by the caller (options.spmv_shape_fp32 / _fp64 >= 0)
+    // replaces the default or the autotuner's pick
+    auto pin = [&](auto &Ad, const SellHost &PS, const SellHost &PX, auto zero, int sh,
+                   int32_t *pick) -> xdcg_status {
+        using T = decltype(zero);
+        if (sh < 0 || sh == Ad.shape) return XDCG_OK;
+        SpmvDev<T> cand = Ad;
+        cand.shape = sh;
+        cand.grid = spmv_persistent_grid<T>(PS.nSlices + PX.nSlices, sh);
+        if (cand.grid < 1 || cand.grid > kMaxGrid) return XDCG_CUDA_ERROR;
+        cand.warpSlice = partition(PS, PX, cand.grid);
+        if (!cand.warpSlice) return XDCG_OOM;
+        Ad = cand;
+        *pick = sh;
+        return XDCG_OK;
+    };
     for (int sh = 0; sh < 8; ++sh) c->info.spmv_shape_us_fp64[sh] = c->info.spmv_shape_us_fp32[sh] = -1.0;
     if (c->opt.autotune) {
         xdcg_status ts = autotune(A, HS, HX, 0.0, c->info.spmv_shape_us_fp64,
                                   &c->info.spmv_shape_fp64);
+        if (ts != XDCG_OK) return ts;
+    }
+    {
+        xdcg_status ts = pin(A, HS, HX, 0.0, c->opt.spmv_shape_fp64, &c->info.spmv_shape_fp64);
         if (ts != XDCG_OK) return ts;
     }
 
@@ -2130,14 +2151,20 @@ xdcg_status setup_impl(xdcg_ctx *c, const xdcg_matrix *K, const xdcg_deflation *
         launch_gather(d_src32S, (long long)HS32.src.size(), d_Kt, nullptr, v32S, st);
         launch_gather(d_src32X, (long long)HX32.src.size(), d_Kt, nullptr, v32X, st);
         A2.waitNs = waitNs;
-        A2.shape = 0;
-        A2.grid = spmv_persistent_grid<float>(HS32.nSlices + HX32.nSlices, 0);
+        A2.shape = kSpmvDefaultShapeF32;
+        A2.grid = spmv_persistent_grid<float>(HS32.nSlices + HX32.nSlices, A2.shape);
         if (A2.grid < 1) return XDCG_CUDA_ERROR;
         A2.warpSlice = partition(HS32, HX32, A2.grid);
         if (!A2.warpSlice) return XDCG_OOM;
+        c->info.spmv_shape_fp32 = A2.shape;   // until autotuned or pinned below
         if (c->opt.autotune) {
             xdcg_status ts = autotune(A2, HS32, HX32, 0.0f, c->info.spmv_shape_us_fp32,
                                       &c->info.spmv_shape_fp32);
+            if (ts != XDCG_OK) return ts;
+        }
+        {
+            xdcg_status ts = pin(A2, HS32, HX32, 0.0f, c->opt.spmv_shape_fp32,
+                                 &c->info.spmv_shape_fp32);
             if (ts != XDCG_OK) return ts;
         }
         if (c->opt.max_batch > 0) {
@@ -2486,6 +2513,8 @@ xdcg_status xdcg_default_options(xdcg_options *opt) {
     opt->wait_s = 2.0;
     opt->autotune = 0;
     opt->graph = 0;
+    opt->spmv_shape_fp32 = -1;
+    opt->spmv_shape_fp64 = -1;
     return XDCG_OK;
 }
 
@@ -2511,6 +2540,8 @@ static xdcg_status setup_common(xdcg_ctx **out, const xdcg_ctx *prev, const xdcg
         (c->opt.coarse_fp64 != 0 && c->opt.coarse_fp64 != 1) ||
         (c->opt.autotune != 0 && c->opt.autotune != 1) ||
         (c->opt.graph != 0 && c->opt.graph != 1) ||
+        c->opt.spmv_shape_fp32 < -1 || c->opt.spmv_shape_fp32 >= spmv_shape_count<float>() ||
+        c->opt.spmv_shape_fp64 < -1 || c->opt.spmv_shape_fp64 >= spmv_shape_count<double>() ||
         !(c->opt.wait_s >= 0.0 && c->opt.wait_s <= 60.0) ||
         !(c->opt.inner_tol > 0 && c->opt.inner_tol < 1) ||
         (blocks && (c->opt.jacobi != XDCG_BLOCK_JACOBI || c->opt.max_batch > 0))) {

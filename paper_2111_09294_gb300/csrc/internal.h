@@ -69,6 +69,11 @@ struct SellDev {
 // by length, 16 threads per row).
 constexpr int kTprS = 2;
 constexpr int kTprX = 16;
+// the SpMV pipeline shape a context runs unless autotuned or pinned
+// (spmv_cfg.cuh): FP32 the lean kernel's 2 steps x 3 stages x 3 blocks per
+// SM (measured fastest on the 48^3 two-crack system), FP64 1 x 3 x 3
+constexpr int kSpmvDefaultShapeF32 = 5;
+constexpr int kSpmvDefaultShapeF64 = 0;
 constexpr int kXBucket = 8;     // X rows are grouped by len / kXBucket
 
 // ---- batched FP32 iteration (several right-hand sides of one system) ------
@@ -114,7 +119,7 @@ struct BatchScalars {
 template <typename T>
 struct SpmvDev {
     SellDev<T> S, X;
-    int shape;                 // pipeline shape (spmv_cfg.cuh), 0 = default
+    int shape;                 // pipeline shape (spmv_cfg.cuh)
     int grid;                  // persistent blocks (kSpmvThreads each)
     const int *warpSlice;      // [grid * kSpmvWarps + 1] slice range of each warp
                                // (S slices, then X slices offset by S.nSlices)

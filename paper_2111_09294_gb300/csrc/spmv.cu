@@ -271,6 +271,278 @@ k_spmv(SpmvDev<T> A, const T *__restrict__ x, T *__restrict__ y, const T *__rest
     }
 }
 
+// The warp's copy schedule: its S slices, then its X slices, each part one
+// contiguous run of steps (a step = 32 slots: 32 column indices and 9 planes
+// of 32 values), cut into stages of at most C steps that may run across
+// slice boundaries but not across the two parts (separate arrays).  Every
+// lane walks the same schedule (uniform values), so no per-stage record is
+// kept: the producer's walk runs NS stages ahead of the consumer's.
+struct LeanWalk {
+    long long pos, end, xPos, xEnd;
+    int isS;
+    __device__ __forceinline__ bool next(int C, int &sS, long long &p, int &n) {
+        if (pos == end) {
+            if (!isS || xPos == xEnd) return false;
+            isS = 0;
+            pos = xPos;
+            end = xEnd;
+        }
+        sS = isS;
+        p = pos;
+        n = (int)min((long long)C, end - pos);
+        pos += n;
+        return true;
+    }
+};
+
+// Same product as k_spmv (same layout, same per-row order of the 3x3 block
+// terms and of the row reduction, same dot order), with less bookkeeping per
+// step: the ring slot and its parity advance by increments, the row switch is
+// a count of the steps left in the current slice, and the x gathers of the
+// next stage go to the register set the current stage does not use (the
+// stage loop is unrolled by two).
+template <bool RES, int SHAPE>
+__global__ void __launch_bounds__(kSpmvThreads, SpmvCfg<float, SHAPE>::MINB)
+k_spmv_lean(SpmvDev<float> A, const float *__restrict__ x, float *__restrict__ y,
+            const float *__restrict__ b, double *partials, Scalars *sc, int fin, int slot) {
+    using Cfg = SpmvCfg<float, SHAPE>;
+    constexpr int C = Cfg::C, NS = Cfg::NS, SB = stage_bytes<float, SHAPE>();
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *ring = smem + (size_t)warp * NS * SB;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)kSpmvWarps * NS * SB) + warp * NS;
+    const int nS = A.S.nSlices;
+    const int gw = blockIdx.x * kSpmvWarps + warp;
+    const int sFirst = A.warpSlice[gw], sEnd = A.warpSlice[gw + 1];
+    // step counts of the warp's first 32 slices (set-up data)
+    __shared__ int tSteps[kSpmvWarps][32];
+    if (sFirst + lane < sEnd) {
+        const int g = sFirst + lane;
+        const SellDev<float> &P = g < nS ? A.S : A.X;
+        const int sl = g < nS ? g : g - nS;
+        tSteps[warp][lane] = (int)((P.slicePtr[sl + 1] - P.slicePtr[sl]) >> 5);
+    }
+    if (lane == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(bars + s, 1);
+        mbar_init_fence();
+    }
+    // the two parts' step runs: S slices [sFirst, sA), X slices [xa0, xa1)
+    const int sA = min(sEnd, nS);
+    const int xa0 = max(sFirst, nS) - nS, xa1 = sEnd - nS;
+    LeanWalk init;
+    init.xPos = xa0 < xa1 ? (A.X.slicePtr[xa0] >> 5) : 0;
+    init.xEnd = xa0 < xa1 ? (A.X.slicePtr[xa1] >> 5) : 0;
+    if (sFirst < sA) {
+        init.isS = 1;
+        init.pos = A.S.slicePtr[sFirst] >> 5;
+        init.end = A.S.slicePtr[sA] >> 5;
+    } else {
+        init.isS = 0;
+        init.pos = init.xPos;
+        init.end = init.xEnd;
+    }
+    __syncwarp();
+    const uint64_t stream = l2_stream_policy();
+    const unsigned long long deadline = global_ns() + A.waitNs;
+
+    // producer: every lane walks the schedule, lane 0 issues the copies
+    LeanWalk pw = init;
+    int issued = 0, pslot = 0;
+    bool pmore = true;
+    auto issue = [&]() {
+        int sS, n;
+        long long p;
+        if (!pw.next(C, sS, p, n)) {
+            pmore = false;
+            return;
+        }
+        if (lane == 0) {
+            const SellDev<float> &P = sS ? A.S : A.X;
+            unsigned char *dst = ring + pslot * SB;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bars + pslot, (uint32_t)n * 1280u);
+            bulk_g2s(dst, P.col + 32 * p, (uint32_t)n * 128u, bars + pslot, stream);
+            bulk_g2s(dst + C * 128, P.val + 288 * p, (uint32_t)n * 1152u, bars + pslot, stream);
+        }
+        ++issued;
+        pslot = pslot + 1 == NS ? 0 : pslot + 1;
+    };
+    // the first stages stream set-up data only: issue them before waiting
+    // for the kernel that produced x, unless the run has visibly stopped
+    // already (lane 0's early read decides for the warp; the flag read after
+    // the wait decides for the launch)
+    const bool early = __shfl_sync(0xffffffffu, __ldcg(&sc->done) == kRunning ? 1 : 0, 0) != 0;
+    if (early)
+        while (pmore && issued < NS) issue();
+    pdl_wait();
+    if (sc->done != kRunning) {
+        const unsigned long long drain = global_ns() + kDrainNs;
+        for (int k = 0; k < issued; ++k) mbar_wait(bars + k % NS, (uint32_t)(k / NS) & 1u, drain);
+        __syncwarp();
+        return;
+    }
+    if (!early)
+        while (pmore && issued < NS) issue();
+
+    // consumer
+    float part[1] = {0.0f};
+    int sl = sFirst - 1, remS = 0, rpw = 16, h = 0;
+    bool own = false, pend = false;
+    long long r3 = 0;
+    float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+    const float *ev = RES ? b : x;
+    auto fetch_row_entries = [&]() {
+        pend = false;
+        if (own) {
+            e0 = ev[r3];
+            e1 = ev[r3 + 1];
+            e2 = ev[r3 + 2];
+        }
+    };
+    auto finish = [&]() {
+        for (int o = rpw; o < 32; o <<= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        }
+        if (pend) fetch_row_entries();
+        if (own) {
+            if (RES) {
+                a0 = e0 - a0;
+                a1 = e1 - a1;
+                a2 = e2 - a2;
+                part[0] += a0 * a0 + a1 * a1 + a2 * a2;
+            } else {
+                part[0] += e0 * a0 + e1 * a1 + e2 * a2;
+            }
+            y[r3] = a0;
+            y[r3 + 1] = a1;
+            y[r3 + 2] = a2;
+        }
+    };
+    // the next slice of the warp: its rows (one per rpw lanes), its steps
+    auto next_slice = [&]() {
+        if (sl >= sFirst) finish();
+        ++sl;
+        const bool isS = sl < nS;
+        const int tpr = isS ? kTprS : kTprX;
+        rpw = 32 / tpr;
+        const int rl = (isS ? sl : sl - nS) * rpw + (lane % rpw);
+        h = lane / rpw;
+        own = rl < (isS ? A.S.nRows : A.X.nRows) && h == 0;
+        r3 = own ? 3 * (long long)(isS ? A.S.row[rl] : A.X.row[rl]) : 0;
+        pend = true;
+        a0 = a1 = a2 = 0.0f;
+        if (sl - sFirst < 32) {
+            remS = tSteps[warp][sl - sFirst];
+        } else {
+            const SellDev<float> &P = isS ? A.S : A.X;
+            const int ls = isS ? sl : sl - nS;
+            remS = (int)((P.slicePtr[ls + 1] - P.slicePtr[ls]) >> 5);
+        }
+    };
+    auto gather = [&](int st, int n, float (&xv)[C][3]) {
+        const int *cs = reinterpret_cast<const int *>(ring + st * SB);
+#pragma unroll
+        for (int t = 0; t < C; ++t) {
+            if (t < n) {
+                const int c = cs[t * 32 + lane];
+                xv[t][0] = __ldg(x + 3 * c);
+                xv[t][1] = __ldg(x + 3 * c + 1);
+                xv[t][2] = __ldg(x + 3 * c + 2);
+            }
+        }
+    };
+    LeanWalk cw = init;
+    int curS = 1, curN = 0, nxtS = 1, nxtN = 0, cslot = 0, consumed = 0;
+    long long curP = 0, nxtP = 0;
+    uint32_t cpar = 0u;
+    bool ok = true, have = cw.next(C, curS, curP, curN);
+    float xa[C][3], xb[C][3];
+    if (have) {
+        ok = __all_sync(0xffffffffu, mbar_wait(bars, 0u, deadline));
+        if (ok) gather(0, curN, xa);
+    }
+    // one stage: land and gather the next first, then the FMAs of this one
+    // (switching rows where a slice ends), then refill this stage's slot
+    auto stage = [&](float (&xc)[C][3], float (&xn)[C][3]) -> bool {
+        if (!ok || !have) return false;
+        const bool haveN = cw.next(C, nxtS, nxtP, nxtN);
+        const int nslot = cslot + 1 == NS ? 0 : cslot + 1;
+        const uint32_t npar = nslot == 0 ? cpar ^ 1u : cpar;
+        if (haveN) {
+            ok = __all_sync(0xffffffffu, mbar_wait(bars + nslot, npar, deadline));
+            if (!ok) return false;
+            gather(nslot, nxtN, xn);
+        }
+        const float *vs = reinterpret_cast<const float *>(ring + cslot * SB + C * 128);
+#pragma unroll
+        for (int t = 0; t < C; ++t) {
+            if (t < curN) {
+                if (remS == 0) next_slice();
+                --remS;
+                const float *v = vs + t * 288 + lane;
+                a0 = fmaf(v[0], xc[t][0], a0);
+                a0 = fmaf(v[32], xc[t][1], a0);
+                a0 = fmaf(v[64], xc[t][2], a0);
+                a1 = fmaf(v[96], xc[t][0], a1);
+                a1 = fmaf(v[128], xc[t][1], a1);
+                a1 = fmaf(v[160], xc[t][2], a1);
+                a2 = fmaf(v[192], xc[t][0], a2);
+                a2 = fmaf(v[224], xc[t][1], a2);
+                a2 = fmaf(v[256], xc[t][2], a2);
+            }
+        }
+        __syncwarp();
+        if (pmore) issue();
+        if (pend) fetch_row_entries();
+        ++consumed;
+        cslot = nslot;
+        cpar = npar;
+        curS = nxtS;
+        curP = nxtP;
+        curN = nxtN;
+        have = haveN;
+        return true;
+    };
+    while (stage(xa, xb) && stage(xb, xa)) {
+    }
+    if (ok) {
+        if (sl >= sFirst) finish();
+    } else {
+        // a copy did not land in time: flag it, give the copies still in
+        // flight a bounded chance to land, and leave the shared memory
+        if (lane == 0) atomicExch(&sc->fault, 1);
+        const unsigned long long drain = global_ns() + kDrainNs;
+        for (int k = consumed; k < issued; ++k)
+            mbar_wait(bars + k % NS, (uint32_t)(k / NS) & 1u, drain);
+        __syncwarp();
+    }
+    if (fin == kFinDefer) {
+        block_sum<float, 1>(part);
+        if (threadIdx.x == 0)
+            reinterpret_cast<float2 *>(partials)[blockIdx.x] = df_of((double)part[0]);
+        return;
+    }
+    double tot[1];
+    if (grid_sum<float, 1>(part, partials, &sc->ticket[0], tot) && threadIdx.x == 0) {
+        if (sc->fault)
+            sc->done = kFault;
+        else
+            finalize(sc, fin, slot, tot[0]);
+    }
+}
+
+// the kernel of a shape: k_spmv_lean for the LEAN shapes, else k_spmv
+template <typename T, bool RES, int SHAPE>
+constexpr auto spmv_kernel() {
+    if constexpr (SpmvCfg<T, SHAPE>::LEAN)
+        return k_spmv_lean<RES, SHAPE>;
+    else
+        return k_spmv<T, RES, SHAPE>;
+}
+
 // Persistent grid of a shape: its resident blocks per SM times the SMs (at
 // most one warp per slice); < 0 on a CUDA error.
 template <typename T, int SHAPE>
@@ -279,13 +551,14 @@ int persistent_grid_of(int nSlicesTotal) {
     if (cudaGetDevice(&dev) != cudaSuccess) return -1;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
     const int smem = spmv_smem_bytes<T, SHAPE>();
-    if (cudaFuncSetAttribute(k_spmv<T, false, SHAPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem) != cudaSuccess ||
-        cudaFuncSetAttribute(k_spmv<T, true, SHAPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(spmv_kernel<T, false, SHAPE>(),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaFuncSetAttribute(spmv_kernel<T, true, SHAPE>(),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv<T, false, SHAPE>, kSpmvThreads,
-                                                      smem) != cudaSuccess || nb < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmv_kernel<T, false, SHAPE>(),
+                                                      kSpmvThreads, smem) != cudaSuccess ||
+        nb < 1)
         return -1;
     const int need = (nSlicesTotal + kSpmvWarps - 1) / kSpmvWarps;
     return std::max(1, std::min(nb * sms, need));
@@ -294,8 +567,8 @@ int persistent_grid_of(int nSlicesTotal) {
 template <typename T, bool RES, int SHAPE>
 void launch_shape(const SpmvDev<T> &A, const T *x, T *y, const T *b, double *partials,
                   Scalars *sc, int fin, int slot, cudaStream_t st) {
-    launch_pdl(k_spmv<T, RES, SHAPE>, A.grid, kSpmvThreads, spmv_smem_bytes<T, SHAPE>(), st, A, x,
-               y, b, partials, sc, fin, slot);
+    launch_pdl(spmv_kernel<T, RES, SHAPE>(), A.grid, kSpmvThreads, spmv_smem_bytes<T, SHAPE>(), st,
+               A, x, y, b, partials, sc, fin, slot);
 }
 
 template <typename T>
@@ -311,6 +584,9 @@ int spmv_persistent_grid<float>(int nSlicesTotal, int shape) {
         case 2: return persistent_grid_of<float, 2>(nSlicesTotal);
         case 3: return persistent_grid_of<float, 3>(nSlicesTotal);
         case 4: return persistent_grid_of<float, 4>(nSlicesTotal);
+        case 5: return persistent_grid_of<float, 5>(nSlicesTotal);
+        case 6: return persistent_grid_of<float, 6>(nSlicesTotal);
+        case 7: return persistent_grid_of<float, 7>(nSlicesTotal);
     }
     return -1;
 }
@@ -333,9 +609,16 @@ void launch_spmv_res(const SpmvDev<T> &A, const T *x, T *y, const T *b, double *
         case 2: launch_shape<T, RES, 2>(A, x, y, b, partials, sc, fin, slot, st); return;
         case 3: launch_shape<T, RES, 3>(A, x, y, b, partials, sc, fin, slot, st); return;
         case 4:
-            if constexpr (SpmvShapes<T>::count > 4) {
-                launch_shape<T, RES, 4>(A, x, y, b, partials, sc, fin, slot, st);
-                return;
+        case 5:
+        case 6:
+        case 7:
+            if constexpr (SpmvShapes<T>::count > 7) {
+                switch (A.shape) {
+                    case 4: launch_shape<T, RES, 4>(A, x, y, b, partials, sc, fin, slot, st); return;
+                    case 5: launch_shape<T, RES, 5>(A, x, y, b, partials, sc, fin, slot, st); return;
+                    case 6: launch_shape<T, RES, 6>(A, x, y, b, partials, sc, fin, slot, st); return;
+                    default: launch_shape<T, RES, 7>(A, x, y, b, partials, sc, fin, slot, st); return;
+                }
             }
             break;
         default: break;

@@ -72,6 +72,8 @@ class Solver:
     Solver of the same mesh for the previous crack front, whose unchanged
     parts are carried over (xdcg_setup_update).  graph: enqueue the solves'
     iterations as recorded CUDA graphs (xdcg_options.graph; same bits).
+    spmv_shape: None, or (fp32_shape, fp64_shape) pinning the SpMV pipeline
+    shapes (-1 keeps the default or the autotuner's pick).
     """
 
     def __init__(self, dof_ptr, row_ptr, col, val_ptr, val, sub_of_node, coords, hsign, centres,
@@ -79,7 +81,7 @@ class Solver:
                  time_spmv=False, enriched_modes=True, stream=None, jacobi="block",
                  record_history=False, max_batch=0, coarse_fp64=False, wait_s=2.0,
                  blocks=None, z_cols=None, z_values=None, prev=None, autotune=False,
-                 graph=False):
+                 graph=False, spmv_shape=None):
         lib = L.load()
         self._lib = lib
         self.ctx = ctypes.c_void_p()
@@ -114,6 +116,8 @@ class Solver:
         opt.wait_s = float(wait_s)
         opt.autotune = int(bool(autotune))
         opt.graph = int(bool(graph))
+        if spmv_shape is not None:
+            opt.spmv_shape_fp32, opt.spmv_shape_fp64 = (int(v) for v in spmv_shape)
         self.precision = precision
         if stream is None:
             stream = torch.cuda.current_stream()
