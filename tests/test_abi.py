@@ -57,3 +57,38 @@ def test_setup_rejects_null_arguments(lib):
     assert lib.xdcg_setup(None, None, None, None, None, None, ctypes.byref(bad)) == 1
     assert bad.value == -1
     assert lib.xdcg_setup(ctypes.byref(ctx), None, None, None, None, None, None) == 1
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    # every struct the binding passes across the ABI has the header's size and
+    # field offsets: a small C program compiled against include/xdcg.h prints
+    # them (gcc; no GPU, no CUDA)
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_2111_09294_gb300 import _lib
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    structs = {"xdcg_options": _lib.Options, "xdcg_result": _lib.Result,
+               "xdcg_info_t": _lib.Info, "xdcg_matrix": _lib.Matrix,
+               "xdcg_deflation": _lib.Deflation, "xdcg_blocks": _lib.Blocks}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "xdcg.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'    printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for line in out.splitlines():
+        cname, key, val = line.split()
+        got[(cname, key)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)

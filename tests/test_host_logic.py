@@ -92,3 +92,23 @@ def test_sweep_reports_a_failed_system():
     solvers[0].n = solvers[1].n = 2
     with pytest.raises(ValueError):
         S.solve_systems(solvers, [torch.zeros(1, 2), torch.zeros(1, 2)], 1e-8, fused=True)
+
+
+def test_profiled_traffic_is_reported_only_for_the_captured_kernel(tmp_path):
+    # the bench line's roofline traffic comes from a committed ncu summary,
+    # and only while the kernel's sources hash to the recorded value and the
+    # timed product runs the captured pipeline shape
+    import bench
+    sha = bench.kernel_source_sha(bench.SPMV_SOURCES)
+    p = tmp_path / "summary.md"
+    p.write_text(f"traffic_bytes_per_launch: 181941248\nkernel_source_sha256: {sha}\n"
+                 "kernel_shape: 5\n")
+    assert bench.profiled_traffic(bench.SPMV_SOURCES, str(p), 5) == 181941248.0
+    assert bench.profiled_traffic(bench.SPMV_SOURCES, str(p), 0) is None
+    p.write_text("traffic_bytes_per_launch: 181941248\nkernel_source_sha256: 000000000000\n"
+                 "kernel_shape: 5\n")
+    assert bench.profiled_traffic(bench.SPMV_SOURCES, str(p), 5) is None
+    p.write_text(f"traffic_bytes_per_launch: 181941248\nkernel_source_sha256: {sha}\n")
+    assert bench.profiled_traffic(bench.SPMV_SOURCES, str(p), 5) is None
+    assert bench.spmv_kernel_name(5).startswith("k_spmv_lean<false, 5>")
+    assert bench.spmv_kernel_name(0).startswith("k_spmv<float, false, 0>")
