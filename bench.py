@@ -685,6 +685,18 @@ def run_ours(args):
                 "same_bits_as_stream_launches": same,
                 "note": "8 iterations per graph launch; timed like the value"}
 
+    def iteration_gbs():
+        # effective bandwidth of whole iterations: one iteration's algorithmic
+        # bytes times the iterations, over the solve time (which also holds the
+        # start and, for the mixed path, the FP64 residual evaluations)
+        its_m = inf_mixed[-1]["iterations"]
+        gm = info["iter_bytes_fp32"] * its_m / (t_mixed * 1e-3) / 1e9
+        gf = fp64.info["iter_bytes_fp64"] * its_fp64 / (t_fp64 * 1e-3) / 1e9
+        pk = peaks()[0]
+        return {"mixed": gm, "mixed_frac": gm / pk, "fp64": gf, "fp64_frac": gf / pk,
+                "iter_bytes_fp32": info["iter_bytes_fp32"],
+                "iter_bytes_fp64": fp64.info["iter_bytes_fp64"], "unit": "GB/s"}
+
     sequence = optional(measure_sequence) if args.sweep > 1 else None
     batch = optional(measure_batch) if args.batch > 0 else None
     fwd_bwd = optional(measure_fwd_bwd)
@@ -730,7 +742,8 @@ def run_ours(args):
                               "outer_cycles": inf_c64[-1]["outer_cycles"],
                               "rel_res_true": max(i["rel_res_true"] for i in inf_c64),
                               "note": "E^-1 applied in FP64 inside the FP32 iteration"},
-        "graph": graph_row(),
+        "graph": optional(graph_row),
+        "iteration_gbs": optional(iteration_gbs),
         "rel_res_true_mixed": res_true, "rel_res_true_fp64": inf_fp64[-1]["rel_res_true"],
         "setup_ms": info["t_setup_ms"],
         "setup_phases_ms": {k: round(v, 1) for k, v in info["t_setup_phase_ms"].items()},
